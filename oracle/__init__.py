@@ -1,0 +1,19 @@
+"""FP64 CPU oracle for the Simplex-GP lattice MVM and CG (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and
+reference legs import this package.  It shares no code with the CUDA library.
+"""
+
+from .oracle import (  # noqa: F401
+    OracleLattice,
+    MATERN32_COVERAGE,
+    RBF_BINOMIAL,
+    RBF_COVERAGE,
+    build_oracle,
+    dense_rbf,
+    elevate,
+    simplex,
+    fourier_coverage,
+    spatial_coverage,
+    stencil,
+)

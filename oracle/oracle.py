@@ -1,0 +1,244 @@
+"""ctypes wrapper of the FP64 C++ oracle (``sgp_oracle.cpp``).
+
+Test infrastructure: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline / reference legs use it.  Each wrapper states the paper passage its C++
+function follows; the C++ file header lists the readings and the pins.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sgp_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RBF_BINOMIAL, RBF_COVERAGE, MATERN32_COVERAGE = 0, 1, 2
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_float_p = ctypes.POINTER(ctypes.c_float)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with g++ (-O2, no FMA contraction, no fast-math)."""
+    with _lock:
+        stale = not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + ".%d.tmp" % os.getpid()
+            cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                   "-fPIC", "-shared", "-o", tmp, _SRC]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        lib = ctypes.CDLL(_LIB)
+        lib.orc_stencil.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _c_double_p,
+                                    _c_double_p, _c_double_p]
+        lib.orc_stencil.restype = ctypes.c_int
+        lib.orc_spatial_coverage.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_spatial_coverage.restype = ctypes.c_double
+        lib.orc_fourier_coverage.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_fourier_coverage.restype = ctypes.c_double
+        lib.orc_build.argtypes = [_c_float_p, _c_float_p, ctypes.c_int64, ctypes.c_int,
+                                  ctypes.c_int, _c_double_p, _c_double_p, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_void_p)]
+        lib.orc_build.restype = ctypes.c_int
+        lib.orc_m.argtypes = [ctypes.c_void_p]
+        lib.orc_m.restype = ctypes.c_int64
+        lib.orc_export.argtypes = [ctypes.c_void_p, _c_double_p, _c_int_p, _c_int_p,
+                                   _c_double_p, _c_int_p, _c_int_p]
+        lib.orc_export.restype = None
+        lib.orc_find.argtypes = [ctypes.c_void_p, _c_int_p]
+        lib.orc_find.restype = ctypes.c_int
+        lib.orc_splat.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p]
+        lib.orc_splat.restype = None
+        lib.orc_blur.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, ctypes.c_int]
+        lib.orc_blur.restype = None
+        lib.orc_slice.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p]
+        lib.orc_slice.restype = None
+        lib.orc_mvm.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_double, _c_double_p]
+        lib.orc_mvm.restype = ctypes.c_int
+        lib.orc_cg.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               _c_double_p, _c_int_p, _c_double_p]
+        lib.orc_cg.restype = ctypes.c_int
+        lib.orc_dense_rbf.argtypes = [_c_float_p, _c_float_p, ctypes.c_int64, ctypes.c_int,
+                                      _c_double_p, ctypes.c_int, _c_double_p]
+        lib.orc_dense_rbf.restype = None
+        lib.orc_simplex.argtypes = [_c_double_p, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p,
+                                    _c_int_p]
+        lib.orc_simplex.restype = None
+        lib.orc_elevate.argtypes = [_c_double_p, ctypes.c_int, ctypes.c_double, _c_double_p]
+        lib.orc_elevate.restype = None
+        lib.orc_free.argtypes = [ctypes.c_void_p]
+        lib.orc_free.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def stencil(kind: int = RBF_BINOMIAL, r: int = 1, spacing: float = 0.0):
+    """(s, c, g): spacing, the paper's taps c_t = k(t s) (Sec. 4.1, Eq. balance_coverage)
+    and the symmetric-blur taps g_t of the half kernel, t = 0..r."""
+    lib = _load()
+    s = ctypes.c_double()
+    coef = np.zeros(r + 1, np.float64)
+    half = np.zeros(r + 1, np.float64)
+    rc = lib.orc_stencil(kind, r, spacing, ctypes.byref(s), _p(coef, ctypes.c_double),
+                         _p(half, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("orc_stencil: invalid arguments")
+    return s.value, coef, half
+
+
+def simplex(y):
+    """Enclosing simplex of one elevated point y (Sec. 3.2 "Splat"): dict of rem0,
+    rank, w ([D]) and keys ([D][D], vertex k in row k)."""
+    y = np.ascontiguousarray(y, np.float64)
+    D = y.shape[0]
+    rem0 = np.zeros(D, np.int32)
+    rank = np.zeros(D, np.int32)
+    w = np.zeros(D, np.float64)
+    keys = np.zeros((D, D), np.int32)
+    _load().orc_simplex(_p(y, ctypes.c_double), D - 1, _p(rem0, ctypes.c_int),
+                        _p(rank, ctypes.c_int), _p(w, ctypes.c_double), _p(keys, ctypes.c_int))
+    return dict(rem0=rem0, rank=rank, w=w, keys=keys)
+
+
+def elevate(z, s: float) -> np.ndarray:
+    """Elevation of one normalised point z into H_d for spacing s (Sec. 3.2 "Splat")."""
+    z = np.ascontiguousarray(z, np.float64)
+    y = np.zeros(z.shape[0] + 1, np.float64)
+    _load().orc_elevate(_p(z, ctypes.c_double), z.shape[0], s, _p(y, ctypes.c_double))
+    return y
+
+
+def spatial_coverage(kind: int, a: float) -> float:
+    return _load().orc_spatial_coverage(kind, a)
+
+
+def fourier_coverage(kind: int, w: float) -> float:
+    return _load().orc_fourier_coverage(kind, w)
+
+
+def dense_rbf(X: np.ndarray, ls: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """Exact RBF kernel MVM (Sec. 3.1), O(n^2): for the approximation report only."""
+    X = np.ascontiguousarray(X, np.float32)
+    ls = np.ascontiguousarray(ls, np.float32)
+    V2 = np.ascontiguousarray(V.reshape(V.shape[0], -1), np.float64)
+    out = np.zeros_like(V2)
+    _load().orc_dense_rbf(_p(X, ctypes.c_float), _p(ls, ctypes.c_float), X.shape[0],
+                          X.shape[1], _p(V2, ctypes.c_double), V2.shape[1],
+                          _p(out, ctypes.c_double))
+    return out.reshape(V.shape)
+
+
+class OracleLattice:
+    """Permutohedral lattice of n points (Sec. 3.2) built by the FP64 oracle."""
+
+    def __init__(self, X, ls, kind: int = RBF_BINOMIAL, r: int = 1, spacing: float = 0.0):
+        lib = _load()
+        self.X = np.ascontiguousarray(X, np.float32)
+        self.ls = np.ascontiguousarray(np.broadcast_to(np.asarray(ls, np.float32),
+                                                       (self.X.shape[1],)))
+        self.n, self.d = self.X.shape
+        self.D = self.d + 1
+        self.r = r
+        self.s, self.coef, self.half = stencil(kind, r, spacing)
+        h = ctypes.c_void_p()
+        rc = lib.orc_build(_p(self.X, ctypes.c_float), _p(self.ls, ctypes.c_float), self.n,
+                           self.d, r, _p(self.coef, ctypes.c_double),
+                           _p(self.half, ctypes.c_double), self.s, ctypes.byref(h))
+        if rc != 0:
+            raise ValueError("orc_build: invalid arguments")
+        self._h = h
+        self.m = lib.orc_m(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_free(h)
+            self._h = None
+
+    def export(self):
+        """Dict of y, rem0, rank, w, idx ([n][D]) and keys ([m][D])."""
+        n, D, m = self.n, self.D, self.m
+        y = np.zeros((n, D), np.float64)
+        rem0 = np.zeros((n, D), np.int32)
+        rank = np.zeros((n, D), np.int32)
+        w = np.zeros((n, D), np.float64)
+        idx = np.zeros((n, D), np.int32)
+        keys = np.zeros((m, D), np.int32)
+        _lib.orc_export(self._h, _p(y, ctypes.c_double), _p(rem0, ctypes.c_int),
+                        _p(rank, ctypes.c_int), _p(w, ctypes.c_double), _p(idx, ctypes.c_int),
+                        _p(keys, ctypes.c_int))
+        return dict(y=y, rem0=rem0, rank=rank, w=w, idx=idx, keys=keys)
+
+    def find(self, key) -> int:
+        key = np.ascontiguousarray(key, np.int32)
+        assert key.shape == (self.D,)
+        return _lib.orc_find(self._h, _p(key, ctypes.c_int))
+
+    @staticmethod
+    def _as2d(V):
+        V = np.asarray(V, np.float64)
+        return np.ascontiguousarray(V.reshape(V.shape[0], -1)), V.shape
+
+    def splat(self, V):
+        V2, _ = self._as2d(V)
+        lat = np.zeros((self.m, V2.shape[1]), np.float64)
+        _lib.orc_splat(self._h, _p(V2, ctypes.c_double), V2.shape[1], _p(lat, ctypes.c_double))
+        return lat
+
+    def blur(self, lat, transpose: bool = False):
+        lat = np.array(lat, np.float64, copy=True, order="C").reshape(self.m, -1)
+        _lib.orc_blur(self._h, _p(lat, ctypes.c_double), lat.shape[1], int(transpose))
+        return lat
+
+    def slice(self, lat):
+        lat = np.ascontiguousarray(lat, np.float64).reshape(self.m, -1)
+        out = np.zeros((self.n, lat.shape[1]), np.float64)
+        _lib.orc_slice(self._h, _p(lat, ctypes.c_double), lat.shape[1], _p(out, ctypes.c_double))
+        return out
+
+    def mvm(self, V, mode: int = 0, alpha: float = 1.0, beta: float = 0.0):
+        """alpha K~ V + beta V; mode 0 sequential blur, 1 its transpose, 2 symmetric."""
+        V2, shape = self._as2d(V)
+        out = np.zeros_like(V2)
+        rc = _lib.orc_mvm(self._h, _p(V2, ctypes.c_double), V2.shape[1], mode, alpha, beta,
+                          _p(out, ctypes.c_double))
+        if rc != 0:
+            raise ValueError("orc_mvm: invalid arguments")
+        return out.reshape(shape)
+
+    def cg(self, B, noise: float, tol: float = 1e-3, max_iter: int = 500,
+           outputscale: float = 1.0, mode: int = 0):
+        """CG on (outputscale K~ + noise I) X = B; returns X, iterations, rel. residuals."""
+        B2, shape = self._as2d(B)
+        k = B2.shape[1]
+        X = np.zeros_like(B2)
+        iters = np.zeros(k, np.int32)
+        rel = np.zeros(k, np.float64)
+        rc = _lib.orc_cg(self._h, _p(B2, ctypes.c_double), k, outputscale, noise, tol,
+                         max_iter, mode, _p(X, ctypes.c_double), _p(iters, ctypes.c_int),
+                         _p(rel, ctypes.c_double))
+        if rc != 0:
+            raise ValueError("orc_cg: invalid arguments")
+        return X.reshape(shape), iters, rel

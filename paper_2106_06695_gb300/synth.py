@@ -1,0 +1,75 @@
+"""Seeded synthetic inputs shaped like the paper's regression workloads.
+
+The paper's UCI datasets (Houseelectric n=2,049,280 d=11, Keggdirected d=20, Protein,
+Elevators, Precipitation; Sec. 5, Table n_lattice) are not available, so these
+generators stand in for them.  This module holds no arithmetic of the method: it only
+draws inputs, and both the CUDA path and the oracle consume exactly the arrays it
+returns (float32, C order).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def uniform_points(n: int, d: int, seed: int) -> np.ndarray:
+    """X ~ Uniform[0, 1]^d (the small single-MVM workload: n=4096, d=3)."""
+    rng = np.random.default_rng(seed)
+    return rng.random((n, d)).astype(np.float32)
+
+
+def gaussian_values(n: int, k: int, seed: int) -> np.ndarray:
+    """Right-hand sides V ~ N(0, 1), shape [n][k]."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.standard_normal((n, k)).astype(np.float32)
+
+
+def gmm_points(n: int, d: int, seed: int, components: int = 16) -> np.ndarray:
+    """Standardised Gaussian mixture: means ~ N(0, I), diagonal scales ~ U[0.2, 1],
+    equal weights, then each dimension shifted/scaled to zero mean and unit variance."""
+    rng = np.random.default_rng(seed)
+    means = rng.standard_normal((components, d))
+    scales = rng.uniform(0.2, 1.0, (components, d))
+    comp = rng.integers(0, components, n)
+    X = means[comp] + scales[comp] * rng.standard_normal((n, d))
+    X = (X - X.mean(0)) / X.std(0)
+    return X.astype(np.float32)
+
+
+def regression_targets(X: np.ndarray, seed: int, noise_std: float = 0.1) -> np.ndarray:
+    """y = sum_j sin(2 x_j) + N(0, noise_std^2)."""
+    rng = np.random.default_rng(seed + 104729)
+    y = np.sin(2.0 * X.astype(np.float64)).sum(1) + noise_std * rng.standard_normal(X.shape[0])
+    return y.astype(np.float32)
+
+
+def rademacher(n: int, k: int, seed: int) -> np.ndarray:
+    """Probe vectors with independent +-1 entries, shape [n][k]."""
+    rng = np.random.default_rng(seed + 1299709)
+    return (2.0 * rng.integers(0, 2, (n, k)) - 1.0).astype(np.float32)
+
+
+def solve_rhs(X: np.ndarray, seed: int, probes: int = 8) -> np.ndarray:
+    """B = [y, probes Rademacher columns] for a posterior-mean-and-variance solve."""
+    y = regression_targets(X, seed)
+    return np.ascontiguousarray(
+        np.concatenate([y[:, None], rademacher(X.shape[0], probes, seed)], 1), np.float32)
+
+
+def correlated_points(n: int, d: int, seed: int):
+    """X ~ N(0, Q diag(lam) Q^T) with Q Haar-orthogonal and lam log-uniform[0.3, 3];
+    ARD lengthscales log-uniform[0.5, 2].  Returns (X, lengthscales)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((d, d))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    lam = np.exp(rng.uniform(np.log(0.3), np.log(3.0), d))
+    X = (rng.standard_normal((n, d)) * np.sqrt(lam)[None, :]) @ Q.T
+    ls = np.exp(rng.uniform(np.log(0.5), np.log(2.0), d))
+    return X.astype(np.float32), ls.astype(np.float32)
+
+
+def subsample(n: int, count: int, seed: int) -> np.ndarray:
+    """Sorted, distinct row indices drawn by seed (for sampled parity checks)."""
+    rng = np.random.default_rng(seed + 15485863)
+    return np.sort(rng.choice(n, size=min(count, n), replace=False)).astype(np.int64)
