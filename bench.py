@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Throughput of the Simplex-GP hot path on one GB300 (or N independent replicas).
+
+One step = the whole path over one batch of synthetic input:
+  build the permutohedral lattice of X (elevate, enclosing simplex, barycentric
+  weights, hash insert, vertex numbering, neighbour table, splat lists; Sec. 3.2), then
+  solve (K~ + noise I) X = V for all k right-hand sides with batched CG (Sec. 2), each
+  iteration one lattice MVM (splat, 2(d+1) blur passes of the symmetric operator, slice).
+Metric: lattice MVM Mpoint/s = n * (MVMs in the step) / step time, whole job.
+
+Workload (default): n = 2,000,000 points, d = 11, standardised 16-component Gaussian
+mixture (the shape of Houseelectric, n=2,049,280 d=11, Sec. 5 Table n_lattice), unit ARD
+lengthscales, binomial stencil r = 1, k = 16 right-hand sides ~ N(0, 1), noise 0.01,
+CG tolerance 1e-3, at most 500 iterations.
+
+`--impl reference` times the FP64 CPU oracle (the reference for this path) on a bounded
+sample of the same workload, on this host's cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "lattice MVM Mpoint/s at n=2M,d=11 (%HBM peak)"
+UNIT = "Mpoint/s"
+WORKLOAD = dict(n=2_000_000, d=11, k=16, seed=4, lengthscale=1.0, noise=0.01, tol=1e-3,
+                max_iter=500, kernel="rbf_binomial", order=1, blur="symmetric")
+CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg
+REF_SAMPLE = dict(n=50_000, iters=2)    # oracle sample per step for --impl reference
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default 2,000,000)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (replicas only: the only collectives are the timing barrier/max)
+# ---------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def aggregate(elapsed_ms: float, units: float, world: int):
+    """Max of the elapsed time over ranks and sum of the work units over ranks."""
+    if world == 1:
+        return elapsed_ms, units
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def blur_traffic_per_launch(m: int, k: int):
+    """DRAM bytes per blur launch from the committed ncu summary, scaled to this m, if the
+    kernel source has not changed since it was captured; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))["blur_pass"]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu"), "rb").read()
+    if hashlib.sha1(src).hexdigest() != rec.get("mvm_cu_sha1") or rec.get("k") != k:
+        return None
+    return float(rec["bytes_per_vertex"]) * m
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2106_06695_gb300 import _lib, build_lib, synth
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the lattice library has no CPU path)")
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    build_lib.build()
+    lib = _lib.load()
+    W = dict(WORKLOAD, n=args.n)
+    n, d, k = W["n"], W["d"], W["k"]
+    Xh = torch.from_numpy(synth.gmm_points(n, d, W["seed"])).pin_memory()
+    Vh = torch.from_numpy(synth.gaussian_values(n, k, W["seed"])).pin_memory()
+    lsh = torch.full((d,), W["lengthscale"], dtype=torch.float32).pin_memory()
+    dev = torch.device("cuda", local)
+    Xd, Vd, lsd = Xh.to(dev), Vh.to(dev), lsh.to(dev)
+    out = torch.empty_like(Vd)
+    prof = {"ms": 0.0, "passes": 0, "m": 0, "iters": [], "build_ms": []}
+
+    def step(Xdev, Vdev, ls_dev, profile=False):
+        t0 = time.perf_counter()
+        lat = Lattice(Xdev, ls_dev, order=W["order"], kernel=W["kernel"])
+        prof["build_ms"].append(1e3 * (time.perf_counter() - t0))
+        if profile:
+            _lib.check(lib.sgp_profile_blur(lat._h, 1))
+        _, iters, rel = lat.cg(Vdev, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
+                               blur=W["blur"], out=out)
+        if profile:
+            import ctypes
+
+            ms, passes = ctypes.c_double(), ctypes.c_int64()
+            _lib.check(lib.sgp_profile_read(lat._h, ctypes.byref(ms), ctypes.byref(passes)))
+            prof["ms"] += ms.value
+            prof["passes"] += passes.value
+        prof["m"] = lat.m
+        prof["iters"].append(int(iters.max()))
+        lat.close()
+        return int(iters.max()), rel
+
+    for _ in range(args.warmup):
+        step(Xd, Vd, lsd)
+    prof.update(ms=0.0, passes=0, iters=[], build_ms=[])
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = lib.sgp_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mvms = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            it, rel = step(Xd, Vd, lsd, profile=True)
+            mvms += it
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = lib.sgp_kernel_launches() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    max_ms, units = aggregate(elapsed_ms, float(n) * mvms, world)
+    value = units / (max_ms / 1e3) / 1e6
+    m = prof["m"]
+
+    # roofline of the dominant kernel (a blur pass), from the live samples
+    peak, peak_kind = measured_peak_gbs()
+    bytes_per_pass = m * (8 * k + 8 * W["order"])  # read + write one fp32 row, 2r ids
+    avg_pass_ms = prof["ms"] / max(prof["passes"], 1)
+    achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9 if prof["passes"] else None
+    traffic = blur_traffic_per_launch(m, k)
+    roofline = {"kernel": "k_blur<4> (one lattice direction)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": bytes_per_pass,
+                "avg_launch_ms": avg_pass_ms, "sampled_launches": prof["passes"]}
+
+    # MVM alone (same lattice, same stream) for context
+    lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"])
+    for _ in range(3):
+        lat.mvm(Vd, blur=W["blur"], out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        lat.mvm(Vd, blur=W["blur"], out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    mvm_ms = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        lat.mvm(Vd, blur="sequential", out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    mvm_seq_ms = e0.elapsed_time(e1) / reps
+    lat.close()
+
+    e2e = None
+    if not args.no_e2e:
+        Xs_host = torch.empty(n, k, dtype=torch.float32).pin_memory()
+        e2e_mvms = 0
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Xdev = Xh.to(dev, non_blocking=True)
+            Vdev = Vh.to(dev, non_blocking=True)
+            ls_dev = lsh.to(dev, non_blocking=True)
+            it, _ = step(Xdev, Vdev, ls_dev)
+            Xs_host.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_mvms += it
+        barrier(world)
+        e2e_ms, e2e_units = aggregate(1e3 * (time.perf_counter() - t0), float(n) * e2e_mvms, world)
+        e2e = {"value": e2e_units / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * 4 + Vh.numel() * 4 + lsh.numel() * 4),
+               "d2h_bytes_per_step": int(n * k * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(W)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: standardised 16-component Gaussian mixture (seeded), "
+                    "V ~ N(0,1); stands in for the paper's UCI datasets",
+            "config": {"workload": "GP solve n=%d d=%d k=%d: lattice build + batched CG "
+                                   "(tol %g, max %d) on the symmetric lattice operator"
+                                   % (n, d, k, W["tol"], W["max_iter"]),
+                       "n": n, "d": d, "k": k, "m": m, "m_over_L": m / (n * (d + 1)),
+                       "kernel": "%s r=%d" % (W["kernel"], W["order"]), "noise": W["noise"],
+                       "cg_iters_per_step": prof["iters"],
+                       "build_ms_median": float(np.median(prof["build_ms"])),
+                       "mvm_symmetric_ms": mvm_ms, "mvm_sequential_ms": mvm_seq_ms,
+                       "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
+                       "l2": "no flush: every step's working set (X 88 MB, V 128 MB, "
+                             "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def oracle_sample(W, n_sample, iters):
+    """Oracle build + `iters` CG iterations on a seeded n_sample-row subsample; returns
+    (seconds, point-MVMs done)."""
+    from oracle import OracleLattice
+    from paper_2106_06695_gb300 import synth
+
+    X = synth.gmm_points(W["n"], W["d"], W["seed"])
+    V = synth.gaussian_values(W["n"], W["k"], W["seed"])
+    rows = synth.subsample(W["n"], n_sample, W["seed"])
+    Xs, Vs = X[rows], V[rows].astype(np.float64)
+    t0 = time.perf_counter()
+    L = OracleLattice(Xs, np.full(W["d"], W["lengthscale"], np.float32), r=W["order"])
+    _, it, _ = L.cg(Vs, W["noise"], tol=0.0, max_iter=iters, mode=2)
+    return time.perf_counter() - t0, float(n_sample) * int(it.max())
+
+
+def cpu_baseline(W):
+    secs, units = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"])
+    return {"value": units / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, single thread: lattice build + %d CG iterations (symmetric "
+                      "operator, k=%d) on a seeded %d-row subsample of the workload; %.1f s"
+                      % (CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"], secs)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    W = dict(WORKLOAD, n=args.n)
+    for _ in range(args.warmup):
+        oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"])
+    secs, units = 0.0, 0.0
+    for _ in range(args.steps):
+        s, u = oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"])
+        secs += s
+        units += u
+    value = units / secs / 1e6
+    sample = ("FP64 oracle, single thread, per step: lattice build + %d CG iterations "
+              "(symmetric operator, k=%d) on a seeded %d-row subsample of the workload"
+              % (REF_SAMPLE["iters"], W["k"], REF_SAMPLE["n"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "GP solve n=%d d=%d k=%d (oracle sample of %d rows)"
+                                   % (W["n"], W["d"], W["k"], REF_SAMPLE["n"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/* sgp.h -- C-ABI of the GB300 (sm_103a) Simplex-GP lattice library.
+ *
+ * The library computes the permutohedral-lattice approximation of a stationary-kernel
+ * matrix-vector product,  K V ~= W B W^T V  (Sec. 3.2 and Eq. ski_to_bf: splat W^T,
+ * blur B, slice W), and solves (outputscale K~ + noise I) X = B with batched conjugate
+ * gradients that touch K~ only through these products (Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major fp32: X is [n][d], V/out/B/X-solutions are [n][k].
+ *   - Pointers marked "device" are CUDA device pointers on the current device (for
+ *     example torch.Tensor.data_ptr() of a contiguous CUDA tensor); pointers marked
+ *     "host" are ordinary host memory.  The caller owns every buffer it passes in.
+ *   - The library owns the lattice handle and the device arrays inside it; it allocates
+ *     them with stream-ordered cudaMallocAsync on the handle's stream and frees them in
+ *     sgp_lattice_free().
+ *   - Work is enqueued on the handle's stream (opts->stream at build time, or the one set
+ *     with sgp_set_stream).  sgp_mvm / sgp_mvm_ex never synchronise; sgp_lattice_build
+ *     synchronises once (to read the vertex count and the device error word);
+ *     sgp_cg_solve synchronises every opts->check_every iterations to read the
+ *     per-column convergence flags, and once at the end.
+ *   - No C++ exception crosses this boundary.  Every call returns an sgp_status; on a
+ *     failure sgp_last_error() returns a thread-local message, the outputs are
+ *     unspecified and an existing handle stays valid.
+ *   - There is no CPU fallback: without a CUDA device every call fails with SGP_ERR_CUDA.
+ */
+#ifndef SGP_H_
+#define SGP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGP_VERSION 1
+
+typedef struct sgp_lattice sgp_lattice; /* opaque; created by sgp_lattice_build */
+
+typedef enum {
+  SGP_OK = 0,
+  SGP_ERR_INVALID_ARG = 1, /* a size, pointer or option is out of range            */
+  SGP_ERR_OOM = 2,         /* a device allocation failed                            */
+  SGP_ERR_RANGE = 3,       /* a lattice coordinate does not fit in int16            */
+  SGP_ERR_HASH_FULL = 4,   /* the vertex hash table ran out of probes               */
+  SGP_ERR_NONFINITE = 5,   /* X holds NaN/Inf, or a lengthscale is <= 0 / not finite */
+  SGP_ERR_CUDA = 6,        /* a CUDA runtime call failed (message has the CUDA error) */
+} sgp_status;
+
+/* Stationary kernel and its stencil (Sec. 4.1).  Stencil taps are kernel values at the
+ * lattice points, c_t = k(t s), t = -r..r, with spacing s in lengthscale units:
+ *   SGP_KERNEL_RBF_BINOMIAL      RBF, s = sqrt(2 ln 2) so that r = 1 gives the binomial
+ *                                stencil [.5, 1, .5] of Sec. 3.2 "Blur" (the default);
+ *   SGP_KERNEL_RBF_COVERAGE      RBF, s balancing spatial and Fourier coverage
+ *                                (Eq. balance_coverage) by numerical integration;
+ *   SGP_KERNEL_MATERN32_COVERAGE Matern-3/2, s from Eq. balance_coverage. */
+enum {
+  SGP_KERNEL_RBF_BINOMIAL = 0,
+  SGP_KERNEL_RBF_COVERAGE = 1,
+  SGP_KERNEL_MATERN32_COVERAGE = 2,
+};
+
+/* Blur operator B.
+ *   SGP_BLUR_SEQUENTIAL  the paper's blur (Sec. 3.2 "Blur"): the 1-D stencil c along
+ *                        lattice directions j = 0, 1, ..., d in turn, vertex set fixed.
+ *   SGP_BLUR_TRANSPOSE   the exact adjoint of the above: directions d, ..., 0.
+ *   SGP_BLUR_SYMMETRIC   M^T M, with M the sequential blur built from the taps g of the
+ *                        half kernel (the kernel whose self-convolution is proportional
+ *                        to k), g normalised so that sum_t g_t^2 = 1: passes 0..d then
+ *                        d..0.  Symmetric positive semi-definite, as K_UU of Eq. k_ski
+ *                        is; the per-direction blurs of a truncated lattice do not
+ *                        commute, so the sequential operator is not symmetric. */
+enum {
+  SGP_BLUR_SEQUENTIAL = 0,
+  SGP_BLUR_TRANSPOSE = 1,
+  SGP_BLUR_SYMMETRIC = 2,
+};
+
+/* Storage type of the lattice values during an MVM.  Arithmetic is fp32 in both. */
+enum {
+  SGP_VALUES_F32 = 0,
+  SGP_VALUES_BF16 = 1,
+};
+
+typedef struct {
+  int order_r;        /* stencil order r, 1..4 (taps -r..r); default 1                  */
+  int kernel;         /* SGP_KERNEL_*; default SGP_KERNEL_RBF_BINOMIAL                  */
+  double spacing_s;   /* > 0 overrides the kernel rule's spacing s; default 0 (rule)    */
+  float outputscale;  /* multiplies K~ in sgp_mvm and in the CG system; default 1       */
+  int value_dtype;    /* SGP_VALUES_*; default SGP_VALUES_F32                           */
+  int check_every;    /* CG iterations between host reads of the flags; default 8       */
+  void* stream;       /* cudaStream_t for all work on this handle; NULL = default stream */
+} sgp_opts;
+
+/* Fill *opts with the defaults listed above. */
+void sgp_opts_init(sgp_opts* opts);
+
+/* Build the lattice of n points (Sec. 3.2 "Splat"): scale each point by the
+ * lengthscales, elevate it into H_d, find its enclosing simplex by rounding and ranking,
+ * compute its d+1 barycentric weights, insert the simplex vertices into a device hash
+ * table, number the distinct vertices, and precompute the per-direction neighbour table
+ * used by the blur and the vertex-to-point lists used by the splat.
+ *   X            device, [n][d] fp32, finite.
+ *   lengthscales device, [d] fp32, each > 0 and finite (ARD lengthscales).
+ *   n >= 1; 1 <= d <= 127.  opts may be NULL (defaults).
+ *   *out         receives the new handle; release it with sgp_lattice_free.
+ * Errors: SGP_ERR_INVALID_ARG (sizes/options), SGP_ERR_NONFINITE, SGP_ERR_RANGE (a
+ * vertex coordinate beyond int16: lengthscales far smaller than the data's spread),
+ * SGP_ERR_HASH_FULL, SGP_ERR_OOM, SGP_ERR_CUDA.  On error *out is set to NULL. */
+sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t n, int d,
+                             const sgp_opts* opts, sgp_lattice** out);
+
+/* Number of lattice vertices m (m <= n (d+1), Sec. 5.2 Table n_lattice) and the device
+ * bytes the handle holds.  Either output may be NULL. */
+sgp_status sgp_lattice_info(const sgp_lattice* h, int64_t* m, size_t* device_bytes);
+
+/* Stencil actually used (Sec. 4.1): the spacing s, the paper's taps c[0..r] and the
+ * symmetric-blur taps g[0..r] (host arrays of order_r + 1 doubles).  Any may be NULL. */
+sgp_status sgp_lattice_stencil(const sgp_lattice* h, int* order_r, double* spacing_s,
+                               double* coef, double* half_coef);
+
+/* Copy the lattice structure to host memory (for inspection and tests; synchronises):
+ *   keys  host [m][d+1] int16: integer coordinates of vertex id v (Eq. canon_simplex
+ *         lattice points, coordinate sum 0);
+ *   idx   host [n][d+1] int32: vertex id of vertex k of point i (point i in the caller's
+ *         order; vertex k has all coordinates congruent to k mod d+1);
+ *   w     host [n][d+1] fp32: barycentric weight of vertex k of point i.
+ * Any pointer may be NULL.  Vertex ids are the library's own numbering. */
+sgp_status sgp_lattice_export(const sgp_lattice* h, int16_t* keys, int32_t* idx, float* w);
+
+/* Set the stream used by subsequent calls on this handle (cudaStream_t; NULL = default). */
+sgp_status sgp_set_stream(sgp_lattice* h, void* stream);
+
+/* out = outputscale * W B W^T V with the sequential blur (Sec. 3.2, Eq. ski_to_bf).
+ *   V    device [n][k] fp32;  out device [n][k] fp32 (must not alias V);  1 <= k <= 256.
+ * Stream-ordered, no synchronisation, may be captured in a CUDA graph. */
+sgp_status sgp_mvm(sgp_lattice* h, const float* V, int k, float* out);
+
+/* out = alpha * W B W^T V + beta * V for the blur selected by `blur` (SGP_BLUR_*).
+ * Same layout and rules as sgp_mvm; outputscale is not applied (alpha replaces it). */
+sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alpha,
+                      float beta, float* out);
+
+/* Batched conjugate gradients (Sec. 2; App. A: at most max_iter = 500 iterations) on
+ *   (outputscale * W B W^T + noise_var I) X = B,   B = SGP_BLUR_SYMMETRIC,
+ * every column independent: column c stops when ||r_c|| / ||b_c|| <= tol (recurrence
+ * residual), after max_iter iterations, or when <p_c, A p_c> <= 0.  Vector updates are
+ * fp32; dot products and norms are accumulated in fp64.
+ *   B      device [n][k] fp32;  X device [n][k] fp32 (solution; must not alias B).
+ *   iters  host [k] int (iterations per column) or NULL;
+ *   rel_res host [k] double (final recurrence residual ratio per column) or NULL.
+ * Non-convergence is not an error: it shows in iters / rel_res.  noise_var >= 0,
+ * tol >= 0, max_iter >= 0, 1 <= k <= 256. */
+sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, float tol,
+                        int max_iter, float* X, int* iters, double* rel_res);
+
+/* As sgp_cg_solve with the blur operator chosen by `blur` (SGP_BLUR_*).  CG assumes a
+ * symmetric positive-definite matrix; only SGP_BLUR_SYMMETRIC guarantees one. */
+sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
+                           float tol, int max_iter, float* X, int* iters, double* rel_res);
+
+/* Blur timing for measurement tools.  While enabled, every CG solve on this handle
+ * brackets the blur passes of one MVM with CUDA events recorded on the solve's stream (as
+ * nodes of its graph) and, at each flag check, adds the elapsed time of the last replay
+ * to a running total.  Enabling (or disabling) resets the totals. */
+sgp_status sgp_profile_blur(sgp_lattice* h, int enable);
+
+/* Totals collected since sgp_profile_blur: milliseconds spent in the sampled blur passes
+ * and the number of passes those samples cover.  Either output may be NULL. */
+sgp_status sgp_profile_read(const sgp_lattice* h, double* blur_ms, int64_t* blur_passes);
+
+/* Number of kernels this library has enqueued in this process (a replayed CUDA graph
+ * counts each of its kernels), for launch accounting in benchmarks. */
+int64_t sgp_kernel_launches(void);
+
+/* Release the handle and every device array it owns (stream-ordered on its stream). */
+void sgp_lattice_free(sgp_lattice* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sgp_last_error(void);
+
+/* SGP_VERSION of the loaded library. */
+int sgp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGP_H_ */

@@ -1,0 +1,87 @@
+"""ctypes loader for libsgp.so, the sm_103a lattice library (C-ABI in include/sgp.h).
+
+This module only declares the C signatures.  It never substitutes another
+implementation: if the library is missing, loading fails with an error.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsgp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sgp.h")
+
+SGP_OK = 0
+STATUS_NAMES = {0: "SGP_OK", 1: "SGP_ERR_INVALID_ARG", 2: "SGP_ERR_OOM", 3: "SGP_ERR_RANGE",
+                4: "SGP_ERR_HASH_FULL", 5: "SGP_ERR_NONFINITE", 6: "SGP_ERR_CUDA"}
+
+KERNELS = {"rbf_binomial": 0, "rbf_coverage": 1, "matern32_coverage": 2}
+BLURS = {"sequential": 0, "transpose": 1, "symmetric": 2}
+VALUE_DTYPES = {"f32": 0, "bf16": 1}
+
+
+class sgp_opts(ctypes.Structure):
+    _fields_ = [("order_r", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("spacing_s", ctypes.c_double), ("outputscale", ctypes.c_float),
+                ("value_dtype", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class SGPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+_lib = None
+
+
+def declared_functions() -> list:
+    """Names of the functions include/sgp.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgp_[a-z_0-9]+)\s*\(", text)))
+
+
+def load():
+    """Load libsgp.so (built by paper_2106_06695_gb300.build_lib) and declare signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsgp.so is not built; run paper_2106_06695_gb300.build_lib.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I, I64, F, Dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+    sigs = {
+        "sgp_opts_init": (None, [ctypes.POINTER(sgp_opts)]),
+        "sgp_lattice_build": (I, [P, P, I64, I, ctypes.POINTER(sgp_opts), ctypes.POINTER(P)]),
+        "sgp_lattice_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]),
+        "sgp_lattice_stencil": (I, [P, ctypes.POINTER(I), ctypes.POINTER(Dbl), P, P]),
+        "sgp_lattice_export": (I, [P, P, P, P]),
+        "sgp_set_stream": (I, [P, P]),
+        "sgp_mvm": (I, [P, P, I, P]),
+        "sgp_mvm_ex": (I, [P, P, I, I, F, F, P]),
+        "sgp_cg_solve": (I, [P, P, I, F, F, I, P, P, P]),
+        "sgp_cg_solve_ex": (I, [P, P, I, I, F, F, I, P, P, P]),
+        "sgp_lattice_free": (None, [P]),
+        "sgp_profile_blur": (I, [P, I]),
+        "sgp_profile_read": (I, [P, ctypes.POINTER(Dbl), ctypes.POINTER(I64)]),
+        "sgp_kernel_launches": (I64, []),
+        "sgp_last_error": (ctypes.c_char_p, []),
+        "sgp_version": (I, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != SGP_OK:
+        raise SGPError(status, load().sgp_last_error().decode(errors="replace"))

@@ -1,0 +1,259 @@
+// C-ABI entry points of the lattice library (declared in include/sgp.h): argument
+// validation, handle lifetime and error reporting around the build, MVM and CG paths.
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sgp_internal.cuh"
+
+namespace sgp {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+bool have_device() {
+  int count = 0;
+  return cudaGetDeviceCount(&count) == cudaSuccess && count > 0;
+}
+
+void free_lattice(Lattice* L) {
+  if (!L) return;
+  cudaStream_t st = L->stream;
+  void* arrays[] = {L->perm, L->idx, L->w, L->row_ptr, L->items, L->nbr, L->keys, L->err,
+                    L->lat[0], L->lat[1]};
+  for (void* p : arrays)
+    if (p) cudaFreeAsync(p, st);
+  for (cudaEvent_t ev : L->prof_ev)
+    if (ev) cudaEventDestroy(ev);
+  delete L;
+}
+
+sgp_status check_handle(const sgp_lattice* h) {
+  if (!h) {
+    set_error("null lattice handle");
+    return SGP_ERR_INVALID_ARG;
+  }
+  return SGP_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void note_launches(int64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+sgp_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    set_error(std::string(what) + ": out of device memory");
+    return SGP_ERR_OOM;
+  }
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return SGP_ERR_CUDA;
+}
+
+}  // namespace sgp
+
+using namespace sgp;
+
+extern "C" {
+
+void sgp_opts_init(sgp_opts* o) {
+  if (!o) return;
+  o->order_r = 1;
+  o->kernel = SGP_KERNEL_RBF_BINOMIAL;
+  o->spacing_s = 0.0;
+  o->outputscale = 1.0f;
+  o->value_dtype = SGP_VALUES_F32;
+  o->check_every = 8;
+  o->stream = nullptr;
+}
+
+sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t n, int d,
+                             const sgp_opts* opts, sgp_lattice** out) {
+  if (!out) {
+    set_error("sgp_lattice_build: out is null");
+    return SGP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sgp_opts o;
+  sgp_opts_init(&o);
+  if (opts) o = *opts;
+  if (!X || !lengthscales || n < 1 || d < 1 || d + 1 > kMaxD) {
+    set_error("sgp_lattice_build: need X, lengthscales, n >= 1 and 1 <= d <= 127");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (n * (int64_t)(d + 1) > (int64_t)0x7fffffff) {
+    set_error("sgp_lattice_build: n * (d + 1) must stay below 2^31");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (o.value_dtype != SGP_VALUES_F32 && o.value_dtype != SGP_VALUES_BF16) {
+    set_error("sgp_lattice_build: unknown value_dtype");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (!have_device()) {
+    set_error("sgp_lattice_build: no CUDA device (this library has no CPU path)");
+    return SGP_ERR_CUDA;
+  }
+  Lattice* L = new Lattice();
+  L->n = n;
+  L->d = d;
+  L->D = d + 1;
+  L->r = o.order_r;
+  L->kernel = o.kernel;
+  L->outputscale = o.outputscale;
+  L->value_dtype = o.value_dtype;
+  L->check_every = o.check_every > 0 ? o.check_every : 8;
+  L->stream = (cudaStream_t)o.stream;
+  if (!make_stencil(o.kernel, o.order_r, o.spacing_s, &L->s, L->coef, L->half)) {
+    delete L;
+    set_error("sgp_lattice_build: kernel must be an SGP_KERNEL_* value and 1 <= order_r <= 4");
+    return SGP_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaMallocAsync((void**)&L->err, sizeof(unsigned), L->stream);
+  if (e != cudaSuccess) {
+    delete L;
+    return cuda_status(e, "sgp_lattice_build: allocating the error word");
+  }
+  sgp_status s = build_lattice(L, X, lengthscales);
+  if (s != SGP_OK) {
+    free_lattice(L);
+    return s;
+  }
+  *out = L;
+  return SGP_OK;
+}
+
+sgp_status sgp_lattice_info(const sgp_lattice* h, int64_t* m, size_t* device_bytes) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (m) *m = h->m;
+  if (device_bytes) *device_bytes = h->bytes;
+  return SGP_OK;
+}
+
+sgp_status sgp_lattice_stencil(const sgp_lattice* h, int* order_r, double* spacing_s,
+                               double* coef, double* half_coef) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (order_r) *order_r = h->r;
+  if (spacing_s) *spacing_s = h->s;
+  for (int t = 0; t <= h->r; ++t) {
+    if (coef) coef[t] = h->coef[t];
+    if (half_coef) half_coef[t] = h->half[t];
+  }
+  return SGP_OK;
+}
+
+sgp_status sgp_lattice_export(const sgp_lattice* h, int16_t* keys, int32_t* idx, float* w) {
+  if (sgp_status s = check_handle(h)) return s;
+  const int64_t n = h->n, D = h->D, nD = n * D;
+  cudaStream_t st = h->stream;
+  if (keys) {
+    cudaError_t e = cudaMemcpyAsync(keys, h->keys, h->m * D * sizeof(int16_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e, "sgp_lattice_export: keys");
+  }
+  if (idx || w) {
+    std::vector<int32_t> perm(n), hidx(nD);
+    std::vector<float> hw(nD);
+    cudaError_t e = cudaMemcpyAsync(perm.data(), h->perm, n * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hidx.data(), h->idx, nD * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hw.data(), h->w, nD * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "sgp_lattice_export: idx/w");
+    for (int64_t p = 0; p < n; ++p) {
+      const int64_t i = perm[p];
+      for (int64_t c = 0; c < D; ++c) {
+        if (idx) idx[i * D + c] = hidx[p * D + c];
+        if (w) w[i * D + c] = hw[p * D + c];
+      }
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "sgp_lattice_export");
+  return SGP_OK;
+}
+
+sgp_status sgp_set_stream(sgp_lattice* h, void* stream) {
+  if (sgp_status s = check_handle(h)) return s;
+  h->stream = (cudaStream_t)stream;
+  return SGP_OK;
+}
+
+static sgp_status check_mvm_args(const sgp_lattice* h, const float* V, int k, int blur,
+                                 const float* out, const char* who) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (!V || !out || k < 1 || k > kMaxK || blur < SGP_BLUR_SEQUENTIAL || blur > SGP_BLUR_SYMMETRIC) {
+    set_error(std::string(who) + ": need V, out, 1 <= k <= 256 and an SGP_BLUR_* operator");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (V == out) {
+    set_error(std::string(who) + ": out must not alias the input");
+    return SGP_ERR_INVALID_ARG;
+  }
+  return SGP_OK;
+}
+
+sgp_status sgp_mvm(sgp_lattice* h, const float* V, int k, float* out) {
+  if (sgp_status s = check_mvm_args(h, V, k, SGP_BLUR_SEQUENTIAL, out, "sgp_mvm")) return s;
+  return run_mvm(h, V, k, SGP_BLUR_SEQUENTIAL, h->outputscale, 0.f, out);
+}
+
+sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alpha, float beta,
+                      float* out) {
+  if (sgp_status s = check_mvm_args(h, V, k, blur, out, "sgp_mvm_ex")) return s;
+  return run_mvm(h, V, k, blur, alpha, beta, out);
+}
+
+sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
+                           float tol, int max_iter, float* X, int* iters, double* rel_res) {
+  if (sgp_status s = check_mvm_args(h, B, k, blur, X, "sgp_cg_solve")) return s;
+  if (!(noise_var >= 0.f) || !(tol >= 0.f) || max_iter < 0) {
+    set_error("sgp_cg_solve: need noise_var >= 0, tol >= 0 and max_iter >= 0");
+    return SGP_ERR_INVALID_ARG;
+  }
+  return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res);
+}
+
+sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, float tol,
+                        int max_iter, float* X, int* iters, double* rel_res) {
+  return sgp_cg_solve_ex(h, B, k, SGP_BLUR_SYMMETRIC, noise_var, tol, max_iter, X, iters,
+                         rel_res);
+}
+
+void sgp_lattice_free(sgp_lattice* h) { free_lattice(h); }
+
+sgp_status sgp_profile_blur(sgp_lattice* h, int enable) {
+  if (sgp_status s = check_handle(h)) return s;
+  for (int i = 0; i < 2 && enable; ++i) {
+    if (!h->prof_ev[i]) {
+      cudaError_t e = cudaEventCreate(&h->prof_ev[i]);
+      if (e != cudaSuccess) return cuda_status(e, "sgp_profile_blur");
+    }
+  }
+  h->profile = enable ? 1 : 0;
+  h->prof_ms = 0.0;
+  h->prof_passes = 0;
+  return SGP_OK;
+}
+
+sgp_status sgp_profile_read(const sgp_lattice* h, double* blur_ms, int64_t* blur_passes) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (blur_ms) *blur_ms = h->prof_ms;
+  if (blur_passes) *blur_passes = h->prof_passes;
+  return SGP_OK;
+}
+
+int64_t sgp_kernel_launches(void) { return launches_so_far(); }
+
+const char* sgp_last_error(void) { return g_last_error.c_str(); }
+
+int sgp_version(void) { return SGP_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,574 @@
+// Lattice construction on the GPU (Sec. 3.2 "Splat"; Eq. canon_simplex).
+//
+//  1. k_elevate      one thread per point: z = x / l, y = E z in H_d (triangular basis),
+//                    nearest remainder-0 point, rank of residuals, sum fix, barycentric
+//                    weights.  Every floating-point step is a single IEEE-rounded FP64
+//                    operation (explicit _rn intrinsics, file built with -fmad=false) so
+//                    the integer results are identical to any other correct FP64
+//                    evaluation of the same expression order.
+//  2. locality order points sorted by their enclosing remainder-0 cell (lexicographic
+//                    over the leading coordinates, stable), so that neighbouring work
+//                    touches neighbouring vertices.
+//  3. k_insert       one thread per (point, vertex): lock-free open addressing in a
+//                    power-of-two table of 64-bit slots (31-bit hash tag | owner entry);
+//                    the full key of a slot is recomputed from its owner entry, and
+//                    atomicMin keeps the earliest entry as owner.
+//  4. numbering      vertex ids = first occurrence in locality order (owner flags +
+//                    exclusive scan).
+//  5. k_neighbours   per vertex and direction j: ids of v +- t u_j, u_j = (d+1) e_j - 1.
+//  6. splat lists    (vertex, entry) pairs sorted stably by vertex id (radix sort) give
+//                    each vertex the list of (point, weight) it gathers.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sgp_internal.cuh"
+
+namespace sgp {
+namespace {
+
+constexpr uint64_t kEmpty = ~0ull;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+template <int MAXD>
+__device__ __forceinline__ uint64_t hash_key(const int* key, int D) {
+  uint64_t h = 0x243f6a8885a308d3ull;
+  for (int c = 0; c < D; ++c) h = (h ^ (uint64_t)(uint16_t)key[c]) * 0x100000001b3ull;
+  return mix64(h);
+}
+
+// Coordinate c of vertex k of the simplex (rem0, rank): rem0 + k, minus d+1 where the
+// coordinate's rank exceeds d - k (the canonical vertex s_k, coordinates permuted).
+__device__ __forceinline__ int vertex_coord(const int16_t* rem0, const uint8_t* rank, int d,
+                                            int k, int c) {
+  return (int)rem0[c] + k - ((int)rank[c] > d - k ? d + 1 : 0);
+}
+
+// Does the vertex of entry `e` (locality-ordered point e / D, vertex e % D) equal key?
+template <int MAXD>
+__device__ __forceinline__ bool entry_has_key(uint32_t e, const int* key, int d,
+                                              const int32_t* perm, const int16_t* rem0,
+                                              const uint8_t* rank) {
+  const int D = d + 1;
+  const int64_t i = perm[e / D];
+  const int k = (int)(e % D);
+  const int16_t* r0 = rem0 + i * D;
+  const uint8_t* rk = rank + i * D;
+  for (int c = 0; c < D; ++c)
+    if (vertex_coord(r0, rk, d, k, c) != key[c]) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// 1. Elevation, enclosing simplex, barycentric weights.
+// ---------------------------------------------------------------------------------
+template <int MAXD>
+__global__ void __launch_bounds__(128) k_elevate(const float* __restrict__ X,
+                                                 const float* __restrict__ ls,
+                                                 const double* __restrict__ f, int64_t n,
+                                                 int d, int16_t* __restrict__ rem0_out,
+                                                 uint8_t* __restrict__ rank_out,
+                                                 float* __restrict__ w_out,
+                                                 int* __restrict__ qmin, int* __restrict__ qmax,
+                                                 unsigned* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int D = d + 1;
+  const double Dd = (double)D;
+  double y[MAXD];
+  int rem0[MAXD];
+  int rank[MAXD];
+  double b[MAXD + 1];
+  bool bad = false;
+  // y = E z, E's column j is (1, .., 1, -(j+1), 0, ..) / sqrt((j+1)(j+2)) times the scale;
+  // f[j] already holds scale / sqrt((j+1)(j+2)).
+  double sm = 0.0;
+  for (int c = d; c >= 1; --c) {
+    const float xv = X[i * d + (c - 1)];
+    const float lv = ls[c - 1];
+    if (!isfinite(xv) || !isfinite(lv) || !(lv > 0.f)) bad = true;
+    const double z = __ddiv_rn((double)xv, (double)lv);
+    const double cf = __dmul_rn(z, f[c - 1]);
+    y[c] = __dsub_rn(sm, __dmul_rn((double)c, cf));
+    sm = __dadd_rn(sm, cf);
+  }
+  y[0] = sm;
+  if (bad) {
+    atomicOr(err, ERRBIT_NONFINITE);
+    for (int c = 0; c < D; ++c) y[c] = 0.0;
+  }
+  // nearest remainder-0 point coordinate by coordinate (ties go down)
+  int sum = 0;
+  bool range = false;
+  for (int c = 0; c < D; ++c) {
+    const double q = __ddiv_rn(y[c], Dd);
+    const double lo = floor(q);
+    const double down = __dmul_rn(lo, Dd);
+    const double up = __dadd_rn(down, Dd);
+    const double r0 = (__dsub_rn(up, y[c]) < __dsub_rn(y[c], down)) ? up : down;
+    if (!(fabs(r0) <= 32000.0)) {
+      range = true;
+      rem0[c] = 0;
+    } else {
+      rem0[c] = (int)r0;
+    }
+    sum += rem0[c];
+  }
+  if (range) {  // keep the rest of the computation in bounds; the build reports the error
+    sum = 0;
+    for (int c = 0; c < D; ++c) {
+      y[c] = 0.0;
+      rem0[c] = 0;
+    }
+  }
+  // rank: strictly larger residuals, plus equal residuals at a lower index
+  for (int c = 0; c < D; ++c) {
+    const double dc = __dsub_rn(y[c], (double)rem0[c]);
+    int rk = 0;
+    for (int c2 = 0; c2 < D; ++c2) {
+      const double d2 = __dsub_rn(y[c2], (double)rem0[c2]);
+      rk += (d2 > dc || (d2 == dc && c2 < c)) ? 1 : 0;
+    }
+    rank[c] = rk;
+  }
+  // move rem0 onto H_d (coordinate sum 0)
+  const int h = sum / D;
+  for (int c = 0; c < D; ++c) {
+    rank[c] += h;
+    if (rank[c] < 0) {
+      rank[c] += D;
+      rem0[c] += D;
+    } else if (rank[c] > d) {
+      rank[c] -= D;
+      rem0[c] -= D;
+    }
+    rank[c] = min(max(rank[c], 0), d);  // already true when sum(y) = 0; guards the indexing
+  }
+  for (int c = 0; c <= D; ++c) b[c] = 0.0;
+  for (int c = 0; c < D; ++c) {
+    const double v = __ddiv_rn(__dsub_rn(y[c], (double)rem0[c]), Dd);
+    b[d - rank[c]] = __dadd_rn(b[d - rank[c]], v);
+    b[D - rank[c]] = __dsub_rn(b[D - rank[c]], v);
+  }
+  b[0] = __dadd_rn(b[0], __dadd_rn(1.0, b[D]));
+  if (range) atomicOr(err, ERRBIT_RANGE);
+  for (int c = 0; c < D; ++c) {
+    rem0_out[i * D + c] = (int16_t)rem0[c];
+    rank_out[i * D + c] = (uint8_t)rank[c];
+    w_out[i * D + c] = __double2float_rn(b[c]);
+  }
+  const unsigned active = __activemask();
+  const int lane = threadIdx.x & 31;
+  const bool leader = lane == __ffs(active) - 1;
+  for (int c = 0; c < d; ++c) {
+    const int q = rem0[c] / D;  // rem0 is a multiple of D: exact
+    const int qlo = __reduce_min_sync(active, q);
+    const int qhi = __reduce_max_sync(active, q);
+    if (leader) {
+      atomicMin(&qmin[c], qlo);
+      atomicMax(&qmax[c], qhi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// 2. Locality key: the remainder-0 cell's leading coordinates packed MSB-first.
+// ---------------------------------------------------------------------------------
+struct CellPack {
+  int ncoord;
+  int shift[kMaxD];
+  int qmin[kMaxD];
+};
+
+__global__ void k_point_key(const int16_t* __restrict__ rem0, int64_t n, int D, CellPack pk,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = 0;
+  for (int c = 0; c < pk.ncoord; ++c)
+    k |= (uint32_t)((int)rem0[i * D + c] / D - pk.qmin[c]) << pk.shift[c];
+  key[i] = k;
+  val[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------------
+// 3. Hash insert.
+// ---------------------------------------------------------------------------------
+template <int MAXD>
+__global__ void __launch_bounds__(256) k_insert(const int32_t* __restrict__ perm,
+                                                const int16_t* __restrict__ rem0,
+                                                const uint8_t* __restrict__ rank, int64_t nD,
+                                                int d, unsigned long long* __restrict__ table,
+                                                uint64_t mask, int32_t* __restrict__ entry_slot,
+                                                unsigned* __restrict__ err) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nD) return;
+  const int D = d + 1;
+  const int64_t i = perm[e / D];
+  const int k = (int)(e % D);
+  int key[MAXD];
+  for (int c = 0; c < D; ++c) key[c] = vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
+  const uint64_t h = hash_key<MAXD>(key, D);
+  const uint32_t tag = (uint32_t)(h >> 33);
+  const unsigned long long mine = ((unsigned long long)tag << 32) | (uint32_t)e;
+  uint64_t slot = h & mask;
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    const unsigned long long prev = atomicCAS(&table[slot], kEmpty, mine);
+    if (prev == kEmpty) {
+      entry_slot[e] = (int32_t)slot;
+      return;
+    }
+    if ((uint32_t)(prev >> 32) == tag &&
+        entry_has_key<MAXD>((uint32_t)prev, key, d, perm, rem0, rank)) {
+      atomicMin(&table[slot], mine);
+      entry_slot[e] = (int32_t)slot;
+      return;
+    }
+    slot = (slot + 1) & mask;
+  }
+  atomicOr(err, ERRBIT_HASH_FULL);
+  entry_slot[e] = -1;
+}
+
+// ---------------------------------------------------------------------------------
+// 4. Numbering: owner flags, then ids by scan, then slot -> id and vertex keys.
+// ---------------------------------------------------------------------------------
+__global__ void k_owner_flags(const int32_t* __restrict__ entry_slot,
+                              const unsigned long long* __restrict__ table, int64_t nD,
+                              uint32_t* __restrict__ flags) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nD) return;
+  const int32_t s = entry_slot[e];
+  flags[e] = (s >= 0 && (uint32_t)table[s] == (uint32_t)e) ? 1u : 0u;
+}
+
+__global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
+                             const int32_t* __restrict__ entry_slot,
+                             const unsigned long long* __restrict__ table,
+                             const int32_t* __restrict__ perm, const int16_t* __restrict__ rem0,
+                             const uint8_t* __restrict__ rank, int64_t nD, int d,
+                             int32_t* __restrict__ slot_id, int16_t* __restrict__ keys) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nD) return;
+  const int32_t s = entry_slot[e];
+  if (s < 0 || (uint32_t)table[s] != (uint32_t)e) return;
+  const int D = d + 1;
+  const uint32_t id = scanned[e];
+  slot_id[s] = (int32_t)id;
+  const int64_t i = perm[e / D];
+  const int k = (int)(e % D);
+  for (int c = 0; c < D; ++c)
+    keys[(int64_t)id * D + c] = (int16_t)vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
+}
+
+__global__ void k_entry_ids(const int32_t* __restrict__ entry_slot,
+                            const int32_t* __restrict__ slot_id,
+                            const int32_t* __restrict__ perm, const float* __restrict__ w_user,
+                            int64_t nD, int D, int32_t* __restrict__ idx,
+                            float* __restrict__ w) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nD) return;
+  const int32_t s = entry_slot[e];
+  idx[e] = s >= 0 ? slot_id[s] : 0;
+  w[e] = w_user[(int64_t)perm[e / D] * D + (e % D)];
+}
+
+// ---------------------------------------------------------------------------------
+// 5. Neighbour table.
+// ---------------------------------------------------------------------------------
+template <int MAXD>
+__global__ void __launch_bounds__(256) k_neighbours(
+    const int16_t* __restrict__ keys, int64_t m, int d, int r,
+    const unsigned long long* __restrict__ table, uint64_t mask,
+    const int32_t* __restrict__ slot_id, const int32_t* __restrict__ perm,
+    const int16_t* __restrict__ rem0, const uint8_t* __restrict__ rank,
+    int32_t* __restrict__ nbr) {
+  const int64_t t_id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int D = d + 1;
+  if (t_id >= m * D) return;
+  const int64_t v = t_id % m;
+  const int j = (int)(t_id / m);
+  int key[MAXD];
+  for (int t = 1; t <= r; ++t) {
+    for (int sg = 0; sg < 2; ++sg) {
+      const int step = sg ? t : -t;
+      bool in_range = true;
+      for (int c = 0; c < D; ++c) {
+        key[c] = (int)keys[v * D + c] + step * ((c == j ? D : 0) - 1);
+        in_range = in_range && key[c] >= -32768 && key[c] <= 32767;
+      }
+      int32_t found = -1;
+      if (in_range) {
+        const uint64_t h = hash_key<MAXD>(key, D);
+        const uint32_t tag = (uint32_t)(h >> 33);
+        uint64_t slot = h & mask;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+          const unsigned long long cur = table[slot];
+          if (cur == kEmpty) break;
+          if ((uint32_t)(cur >> 32) == tag &&
+              entry_has_key<MAXD>((uint32_t)cur, key, d, perm, rem0, rank)) {
+            found = slot_id[slot];
+            break;
+          }
+          slot = (slot + 1) & mask;
+        }
+      }
+      nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = found;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// 6. Splat lists.
+// ---------------------------------------------------------------------------------
+__global__ void k_splat_items(const uint32_t* __restrict__ sorted_entries,
+                              const int32_t* __restrict__ perm, const float* __restrict__ w,
+                              int64_t nD, int D, int2* __restrict__ items) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nD) return;
+  const uint32_t e = sorted_entries[p];
+  items[p] = make_int2(perm[e / D], __float_as_int(w[e]));
+}
+
+__global__ void k_iota(uint32_t* __restrict__ out, int64_t count) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < count) out[p] = (uint32_t)p;
+}
+
+__global__ void k_row_ptr(const uint32_t* __restrict__ sorted_ids, int64_t nD, int64_t m,
+                          int32_t* __restrict__ row_ptr) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > nD) return;
+  if (p == nD) {
+    row_ptr[m] = (int32_t)nD;
+    return;
+  }
+  const uint32_t v = sorted_ids[p];
+  if (p == 0 || sorted_ids[p - 1] != v) row_ptr[v] = (int32_t)p;
+}
+
+// ---------------------------------------------------------------------------------
+// Host orchestration.
+// ---------------------------------------------------------------------------------
+template <class T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
+  return cudaMallocAsync((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
+}
+
+struct Temps {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  ~Temps() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <class T>
+  cudaError_t get(T** p, size_t count) {
+    cudaError_t e = dalloc(p, count, st);
+    if (e == cudaSuccess) ptrs.push_back((void*)*p);
+    return e;
+  }
+};
+
+int bits_for(uint64_t v) {  // bits needed to hold values 0..v
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+#define SGP_DISPATCH_D(D, KERNEL, GRID, BLOCK, ST, ...)                            \
+  do {                                                                              \
+    if ((D) <= 8) KERNEL<8><<<(GRID), (BLOCK), 0, (ST)>>>(__VA_ARGS__);             \
+    else if ((D) <= 16) KERNEL<16><<<(GRID), (BLOCK), 0, (ST)>>>(__VA_ARGS__);      \
+    else if ((D) <= 32) KERNEL<32><<<(GRID), (BLOCK), 0, (ST)>>>(__VA_ARGS__);      \
+    else if ((D) <= 64) KERNEL<64><<<(GRID), (BLOCK), 0, (ST)>>>(__VA_ARGS__);      \
+    else KERNEL<128><<<(GRID), (BLOCK), 0, (ST)>>>(__VA_ARGS__);                    \
+    note_launches(1);                                                               \
+  } while (0)
+
+#define SGP_CHECK(expr, what)                                  \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return cuda_status(e_, what);       \
+  } while (0)
+
+}  // namespace
+
+sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
+  cudaStream_t st = L->stream;
+  const int64_t n = L->n;
+  const int d = L->d, D = L->D, r = L->r;
+  const int64_t nD = n * D;
+  Temps tmp{st, {}};
+
+  // per-dimension factors of the elevation: scale / sqrt((j+1)(j+2)), scale = sqrt(d(d+1))/s
+  const double scale = std::sqrt((double)(d * (d + 1))) / L->s;
+  std::vector<double> hf(d);
+  for (int j = 0; j < d; ++j) hf[j] = scale / std::sqrt((double)((j + 1) * (j + 2)));
+  double* f = nullptr;
+  SGP_CHECK(tmp.get(&f, d), "alloc f");
+  SGP_CHECK(cudaMemcpyAsync(f, hf.data(), d * sizeof(double), cudaMemcpyHostToDevice, st),
+            "copy f");
+
+  int16_t* rem0 = nullptr;
+  uint8_t* rank = nullptr;
+  float* w_user = nullptr;
+  int* qmm = nullptr;  // [2][D]: min, max of rem0 / D per coordinate
+  SGP_CHECK(tmp.get(&rem0, nD), "alloc rem0");
+  SGP_CHECK(tmp.get(&rank, nD), "alloc rank");
+  SGP_CHECK(tmp.get(&w_user, nD), "alloc w");
+  SGP_CHECK(tmp.get(&qmm, 2 * D), "alloc qmm");
+  {
+    std::vector<int> init(2 * D);
+    for (int c = 0; c < D; ++c) {
+      init[c] = 1 << 30;
+      init[D + c] = -(1 << 30);
+    }
+    SGP_CHECK(cudaMemcpyAsync(qmm, init.data(), 2 * D * sizeof(int), cudaMemcpyHostToDevice, st),
+              "copy qmm");
+  }
+  SGP_CHECK(cudaMemsetAsync(L->err, 0, sizeof(unsigned), st), "memset err");
+  {
+    const int B = 128;
+    SGP_DISPATCH_D(D, k_elevate, (unsigned)ceil_div(n, B), B, st, X, ls, f, n, d, rem0, rank,
+                   w_user, qmm, qmm + D, L->err);
+    SGP_CHECK(cudaGetLastError(), "k_elevate");
+  }
+  unsigned herr = 0;
+  std::vector<int> hq(2 * D);
+  SGP_CHECK(cudaMemcpyAsync(hq.data(), qmm, 2 * D * sizeof(int), cudaMemcpyDeviceToHost, st),
+            "read qmm");
+  SGP_CHECK(cudaMemcpyAsync(&herr, L->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+            "read err");
+  SGP_CHECK(cudaStreamSynchronize(st), "sync elevate");
+  if (herr & ERRBIT_NONFINITE) {
+    set_error("sgp_lattice_build: X holds NaN/Inf or a lengthscale is not a finite positive");
+    return SGP_ERR_NONFINITE;
+  }
+  if (herr & ERRBIT_RANGE) {
+    set_error("sgp_lattice_build: a lattice coordinate exceeds the int16 key range "
+              "(lengthscales too small for the spread of X)");
+    return SGP_ERR_RANGE;
+  }
+
+  // 2. locality order
+  CellPack pk{};
+  {
+    int used = 0;
+    for (int c = 0; c < d && c < kMaxD; ++c) {
+      const int b = bits_for((uint64_t)(hq[D + c] - hq[c]));
+      if (used + b > 32) break;
+      pk.ncoord = c + 1;
+      pk.qmin[c] = hq[c];
+      used += b;
+      pk.shift[c] = b > 0 ? 32 - used : 0;  // a single-valued coordinate packs to 0
+    }
+    uint32_t *ka, *va, *kb, *vb, *rt;
+    SGP_CHECK(tmp.get(&ka, n), "alloc sort");
+    SGP_CHECK(tmp.get(&va, n), "alloc sort");
+    SGP_CHECK(tmp.get(&kb, n), "alloc sort");
+    SGP_CHECK(tmp.get(&vb, n), "alloc sort");
+    SGP_CHECK(tmp.get(&rt, radix_temp_elems(n)), "alloc sort");
+    k_point_key<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(rem0, n, D, pk, ka, va);
+    note_launches(1);
+    // the packed cell occupies the top `used` bits; bits below are zero
+    const bool in_alt = used > 0 ? radix_sort_pairs(ka, va, kb, vb, n, 32, rt, st) : false;
+    SGP_CHECK(dalloc(&L->perm, n, st), "alloc perm");
+    SGP_CHECK(cudaMemcpyAsync(L->perm, in_alt ? vb : va, n * sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, st),
+              "copy perm");
+    L->bytes += n * sizeof(int32_t);
+  }
+
+  // 3. hash insert
+  uint64_t cap = 1024;
+  while (cap < (uint64_t)(2 * nD)) cap <<= 1;
+  const uint64_t mask = cap - 1;
+  unsigned long long* table = nullptr;
+  int32_t* entry_slot = nullptr;
+  SGP_CHECK(tmp.get(&table, cap), "alloc hash table");
+  SGP_CHECK(tmp.get(&entry_slot, nD), "alloc entry slots");
+  SGP_CHECK(cudaMemsetAsync(table, 0xff, cap * sizeof(unsigned long long), st), "memset table");
+  SGP_DISPATCH_D(D, k_insert, (unsigned)ceil_div(nD, 256), 256, st, L->perm, rem0, rank, nD, d,
+                 table, mask, entry_slot, L->err);
+  SGP_CHECK(cudaGetLastError(), "k_insert");
+
+  // 4. numbering
+  uint32_t *flags, *scan_tmp, *total;
+  SGP_CHECK(tmp.get(&flags, nD), "alloc flags");
+  SGP_CHECK(tmp.get(&scan_tmp, scan_temp_elems(nD)), "alloc scan");
+  SGP_CHECK(tmp.get(&total, 1), "alloc total");
+  k_owner_flags<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(entry_slot, table, nD, flags);
+  note_launches(1);
+  exclusive_scan_u32(flags, nD, total, scan_tmp, st);
+  uint32_t hm = 0;
+  SGP_CHECK(cudaMemcpyAsync(&hm, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "read m");
+  SGP_CHECK(cudaMemcpyAsync(&herr, L->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+            "read err");
+  SGP_CHECK(cudaStreamSynchronize(st), "sync insert");
+  if (herr & ERRBIT_HASH_FULL) {
+    set_error("sgp_lattice_build: vertex hash table full");
+    return SGP_ERR_HASH_FULL;
+  }
+  const int64_t m = hm;
+  L->m = m;
+  int32_t* slot_id = nullptr;
+  SGP_CHECK(tmp.get(&slot_id, cap), "alloc slot ids");
+  SGP_CHECK(dalloc(&L->keys, m * D, st), "alloc keys");
+  L->bytes += m * D * sizeof(int16_t);
+  k_assign_ids<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(flags, entry_slot, table, L->perm,
+                                                           rem0, rank, nD, d, slot_id, L->keys);
+  note_launches(1);
+  SGP_CHECK(dalloc(&L->idx, nD, st), "alloc idx");
+  SGP_CHECK(dalloc(&L->w, nD, st), "alloc w");
+  L->bytes += nD * (sizeof(int32_t) + sizeof(float));
+  k_entry_ids<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(entry_slot, slot_id, L->perm, w_user,
+                                                          nD, D, L->idx, L->w);
+  note_launches(1);
+  SGP_CHECK(cudaGetLastError(), "numbering");
+
+  // 5. neighbour table
+  SGP_CHECK(dalloc(&L->nbr, (size_t)D * r * 2 * m, st), "alloc nbr");
+  L->bytes += (size_t)D * r * 2 * m * sizeof(int32_t);
+  SGP_DISPATCH_D(D, k_neighbours, (unsigned)ceil_div(m * D, 256), 256, st, L->keys, m, d, r,
+                 table, mask, slot_id, L->perm, rem0, rank, L->nbr);
+  SGP_CHECK(cudaGetLastError(), "k_neighbours");
+
+  // 6. splat lists: (vertex id, entry) sorted by id, stable in entry order
+  {
+    uint32_t *ka, *va, *kb, *vb, *rt;
+    SGP_CHECK(tmp.get(&ka, nD), "alloc csr");
+    SGP_CHECK(tmp.get(&va, nD), "alloc csr");
+    SGP_CHECK(tmp.get(&kb, nD), "alloc csr");
+    SGP_CHECK(tmp.get(&vb, nD), "alloc csr");
+    SGP_CHECK(tmp.get(&rt, radix_temp_elems(nD)), "alloc csr");
+    SGP_CHECK(cudaMemcpyAsync(ka, L->idx, nD * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st),
+              "copy ids");
+    k_iota<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(va, nD);
+    note_launches(1);
+    const int bits = std::max(1, bits_for((uint64_t)(m > 0 ? m - 1 : 0)));
+    const bool in_alt = radix_sort_pairs(ka, va, kb, vb, nD, bits, rt, st);
+    const uint32_t* sorted_ids = in_alt ? kb : ka;
+    const uint32_t* sorted_entries = in_alt ? vb : va;
+    SGP_CHECK(dalloc(&L->items, nD, st), "alloc items");
+    SGP_CHECK(dalloc(&L->row_ptr, m + 1, st), "alloc row_ptr");
+    L->bytes += nD * sizeof(int2) + (m + 1) * sizeof(int32_t);
+    k_splat_items<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(sorted_entries, L->perm, L->w, nD,
+                                                              D, L->items);
+    note_launches(1);
+    k_row_ptr<<<(unsigned)ceil_div(nD + 1, 256), 256, 0, st>>>(sorted_ids, nD, m, L->row_ptr);
+    note_launches(1);
+    SGP_CHECK(cudaGetLastError(), "splat lists");
+  }
+  SGP_CHECK(cudaStreamSynchronize(st), "sync build");
+  return SGP_OK;
+}
+
+}  // namespace sgp

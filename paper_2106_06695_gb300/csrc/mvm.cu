@@ -1,0 +1,234 @@
+// The lattice MVM  out = alpha * W B W^T V + beta * V  (Sec. 3.2, Eq. ski_to_bf).
+//
+//   k_splat  W^T: each lattice vertex gathers w * V[point] over its list of incident
+//            (point, weight) pairs.  A gather, so the result is deterministic.
+//   k_blur   one lattice direction u_j: out[v] = c_0 in[v] + sum_t c_t (in[v - t u_j] +
+//            in[v + t u_j]) with absent neighbours contributing 0 (Sec. 3.2 "Blur"); the
+//            neighbour ids come from the table built with the lattice.
+//   k_slice  W: each point interpolates its d+1 vertices with its barycentric weights,
+//            fused with the alpha/beta epilogue.
+//
+// All three are bound by memory traffic.  Values are fp32 [rows][k] row-major; a thread
+// owns 4 consecutive columns of one row (16-byte vector loads) when k is a multiple of 4
+// and the caller's buffers are 16-byte aligned, else one column.
+#include "sgp_internal.cuh"
+
+namespace sgp {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int VEC>
+struct Vec;
+template <>
+struct Vec<4> {
+  using T = float4;
+  static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ T ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
+  static __device__ __forceinline__ void st(float* p, T v) { *reinterpret_cast<float4*>(p) = v; }
+  static __device__ __forceinline__ T fma(float a, T x, T y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  }
+  static __device__ __forceinline__ T add(T x, T y) {
+    return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  }
+  static __device__ __forceinline__ T scale(float a, T x) {
+    return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+  }
+};
+template <>
+struct Vec<1> {
+  using T = float;
+  static __device__ __forceinline__ T zero() { return 0.f; }
+  static __device__ __forceinline__ T ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, T v) { *p = v; }
+  static __device__ __forceinline__ T fma(float a, T x, T y) { return fmaf(a, x, y); }
+  static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+  static __device__ __forceinline__ T scale(float a, T x) { return a * x; }
+};
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_splat(int64_t m, int G, int k,
+                                                    const int32_t* __restrict__ row_ptr,
+                                                    const int2* __restrict__ items,
+                                                    const float* __restrict__ V,
+                                                    float* __restrict__ lat) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = gid / G;
+  if (v >= m) return;
+  const int col = (int)(gid - v * G) * VEC;
+  const int b = row_ptr[v], e = row_ptr[v + 1];
+  typename Vt::T acc = Vt::zero();
+  for (int p = b; p < e; ++p) {
+    const int2 it = items[p];
+    acc = Vt::fma(__int_as_float(it.y), Vt::ld(V + (int64_t)it.x * k + col), acc);
+  }
+  Vt::st(lat + v * k + col, acc);
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_blur(int64_t m, int G, int k, int r, Taps tp,
+                                                   const int32_t* __restrict__ nbr,
+                                                   const float* __restrict__ in,
+                                                   float* __restrict__ out) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = gid / G;
+  if (v >= m) return;
+  const int col = (int)(gid - v * G) * VEC;
+  typename Vt::T acc = Vt::scale(tp.t[0], Vt::ld(in + v * k + col));
+  for (int t = 1; t <= r; ++t) {
+    const int a = nbr[(int64_t)(2 * (t - 1)) * m + v];
+    const int c = nbr[(int64_t)(2 * (t - 1) + 1) * m + v];
+    typename Vt::T s = Vt::zero();
+    if (a >= 0) s = Vt::add(s, Vt::ld(in + (int64_t)a * k + col));
+    if (c >= 0) s = Vt::add(s, Vt::ld(in + (int64_t)c * k + col));
+    acc = Vt::fma(tp.t[t], s, acc);
+  }
+  Vt::st(out + v * k + col, acc);
+}
+
+template <int VEC, bool BETA>
+__global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int D,
+                                                    const int32_t* __restrict__ perm,
+                                                    const int32_t* __restrict__ idx,
+                                                    const float* __restrict__ w,
+                                                    const float* __restrict__ lat,
+                                                    const float* __restrict__ V, float alpha,
+                                                    float beta, float* __restrict__ out) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = gid / G;
+  if (p >= n) return;
+  const int col = (int)(gid - p * G) * VEC;
+  typename Vt::T acc = Vt::zero();
+  for (int c = 0; c < D; ++c) {
+    const int64_t e = p * D + c;
+    acc = Vt::fma(w[e], Vt::ld(lat + (int64_t)idx[e] * k + col), acc);
+  }
+  const int64_t i = perm[p];
+  typename Vt::T res = Vt::scale(alpha, acc);
+  if (BETA) res = Vt::fma(beta, Vt::ld(V + i * k + col), res);
+  Vt::st(out + i * k + col, res);
+}
+
+inline bool vec4_ok(int k, const void* a, const void* b) {
+  return (k % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
+}
+
+}  // namespace
+
+sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
+  const size_t need = (size_t)L->m * k;
+  if (L->lat_elems >= need && L->lat[0]) return SGP_OK;
+  for (int b = 0; b < 2; ++b) {
+    if (L->lat[b]) cudaFreeAsync(L->lat[b], st);
+    L->lat[b] = nullptr;
+  }
+  L->bytes -= L->lat_elems * 2 * sizeof(float);
+  L->lat_elems = 0;
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaMallocAsync((void**)&L->lat[b], std::max<size_t>(need, 1) * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
+  }
+  L->lat_elems = need;
+  L->bytes += need * 2 * sizeof(float);
+  return SGP_OK;
+}
+
+void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStream_t st) {
+  if (vec4_ok(k, V, lat)) {
+    const int G = k / 4;
+    k_splat<4><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(L->m, G, k, L->row_ptr,
+                                                                           L->items, V, lat);
+  } else {
+    k_splat<1><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, k, L->row_ptr,
+                                                                           L->items, V, lat);
+  }
+  note_launches(1);
+}
+
+void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
+                      int k, cudaStream_t st) {
+  const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
+  if (k % 4 == 0) {
+    const int G = k / 4;
+    k_blur<4><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(L->m, G, k, L->r, taps,
+                                                                          nbr, in, out);
+  } else {
+    k_blur<1><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, k, L->r, taps,
+                                                                          nbr, in, out);
+  }
+  note_launches(1);
+}
+
+void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
+                  float beta, float* out, cudaStream_t st) {
+  const bool v4 = vec4_ok(k, out, V ? (const void*)V : (const void*)out);
+  const int G = v4 ? k / 4 : k;
+  const unsigned grid = (unsigned)ceil_div(L->n * G, kThreads);
+  const bool use_beta = beta != 0.f && V != nullptr;
+  if (v4) {
+    if (use_beta)
+      k_slice<4, true><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
+                                                  alpha, beta, out);
+    else
+      k_slice<4, false><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
+                                                   alpha, beta, out);
+  } else {
+    if (use_beta)
+      k_slice<1, true><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
+                                                  alpha, beta, out);
+    else
+      k_slice<1, false><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
+                                                   alpha, beta, out);
+  }
+  note_launches(1);
+}
+
+// Enqueue the whole operator on `st`.  Lattice value buffers must already hold m*k.
+int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+                float* out, cudaStream_t st, cudaEvent_t* ev) {
+  Taps c{}, g{};
+  for (int t = 0; t <= L->r; ++t) {
+    c.t[t] = (float)L->coef[t];
+    g.t[t] = (float)L->half[t];
+  }
+  float* a = L->lat[0];
+  float* b = L->lat[1];
+  launch_splat(L, V, k, a, st);
+  if (ev) cudaEventRecord(ev[0], st);
+  const int D = L->D;
+  int passes = 0;
+  auto pass = [&](int j, const Taps& tp) {
+    launch_blur_pass(L, j, tp, a, b, k, st);
+    float* t = a;
+    a = b;
+    b = t;
+    ++passes;
+  };
+  if (blur == SGP_BLUR_SEQUENTIAL) {
+    for (int j = 0; j < D; ++j) pass(j, c);
+  } else if (blur == SGP_BLUR_TRANSPOSE) {
+    for (int j = D - 1; j >= 0; --j) pass(j, c);
+  } else {
+    for (int j = 0; j < D; ++j) pass(j, g);
+    for (int j = D - 1; j >= 0; --j) pass(j, g);
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  launch_slice(L, a, V, k, alpha, beta, out, st);
+  return passes;
+}
+
+sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+                   float* out) {
+  sgp_status s = ensure_lattice_values(L, k, L->stream);
+  if (s != SGP_OK) return s;
+  enqueue_mvm(L, V, k, blur, alpha, beta, out, L->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "launching the lattice MVM");
+  return SGP_OK;
+}
+
+}  // namespace sgp

@@ -1,0 +1,124 @@
+// Internal declarations of the sm_103a Simplex-GP library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sgp.h"
+
+namespace sgp {
+
+// Device error word bits, OR-ed by kernels and read back by the host.
+enum : unsigned {
+  ERRBIT_NONFINITE = 1u,
+  ERRBIT_RANGE = 2u,
+  ERRBIT_HASH_FULL = 4u,
+};
+
+constexpr int kMaxOrder = 4;  // stencil order r
+constexpr int kMaxD = 128;    // d + 1
+constexpr int kMaxK = 256;    // right-hand sides per call
+
+// Stencil taps passed by value to the blur kernels.
+struct Taps {
+  float t[kMaxOrder + 1];
+};
+
+}  // namespace sgp
+
+// The lattice handle: every array below is device memory owned by the handle.
+struct sgp_lattice {
+  int64_t n = 0;
+  int d = 0, D = 0, r = 1;
+  int kernel = 0;
+  int64_t m = 0;
+  double s = 0.0;
+  double coef[sgp::kMaxOrder + 1] = {};
+  double half[sgp::kMaxOrder + 1] = {};
+  float outputscale = 1.f;
+  int value_dtype = 0;
+  int check_every = 8;
+  cudaStream_t stream = nullptr;
+
+  // Points are processed in a locality order p = 0..n-1; perm[p] is the caller's index.
+  int32_t* perm = nullptr;   // [n]
+  int32_t* idx = nullptr;    // [n][D] vertex id of vertex k of point perm[p]
+  float* w = nullptr;        // [n][D] barycentric weight, same order
+  int32_t* row_ptr = nullptr;  // [m+1] splat lists: vertex v gathers items[row_ptr[v]..]
+  int2* items = nullptr;       // [n*D] (caller's point index, weight bits)
+  int32_t* nbr = nullptr;      // [D][r][2][m] neighbour id of v - t u_j (0) / v + t u_j (1)
+  int16_t* keys = nullptr;     // [m][D] vertex coordinates
+  unsigned* err = nullptr;     // device error word
+
+  // Lattice values, allocated on first use and grown on demand.
+  float* lat[2] = {nullptr, nullptr};
+  size_t lat_elems = 0;
+
+  // Optional blur timing: events bracket the blur passes of one MVM inside the CG graph
+  // and are read at every flag check (sgp_profile_blur / sgp_profile_read).
+  int profile = 0;
+  cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+  double prof_ms = 0.0;
+  int64_t prof_passes = 0;
+
+  size_t bytes = 0;
+};
+
+namespace sgp {
+
+using Lattice = ::sgp_lattice;
+
+// ---- error reporting and launch accounting (api.cu) ----
+void set_error(const std::string& msg);
+sgp_status cuda_status(cudaError_t e, const char* what);
+// Count kernels enqueued by this library (graph replays count every kernel node).
+void note_launches(int64_t count);
+int64_t launches_so_far();
+
+// ---- stencils (stencil.cpp) ----
+// Spacing s and taps c[0..r] (kernel values k(t s)) and g[0..r] (half-kernel taps).
+// Returns false when the kernel id or order is invalid.
+bool make_stencil(int kernel, int r, double spacing_override, double* s, double* coef,
+                  double* half);
+
+// ---- primitives (scan_sort.cu) ----
+// Exclusive scan of n uint32 values in place; *total (device, may be null) receives the
+// sum.  `tmp` must hold scan_temp_elems(n) uint32.
+size_t scan_temp_elems(int64_t n);
+void exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, uint32_t* tmp,
+                        cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key.  Uses
+// the *_alt buffers as ping-pong storage; returns true when the result ended in *_alt.
+size_t radix_temp_elems(int64_t n);
+bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                      int64_t n, int bits, uint32_t* tmp, cudaStream_t st);
+
+// ---- lattice construction (build.cu) ----
+sgp_status build_lattice(Lattice* L, const float* X, const float* ls);
+
+// ---- MVM (mvm.cu) ----
+// Make sure the two lattice value buffers hold m * k floats (allocated on `st`).
+sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st);
+void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStream_t st);
+void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
+                      int k, cudaStream_t st);
+void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
+                  float beta, float* out, cudaStream_t st);
+// Enqueue out = alpha * W B W^T V + beta * V on `st` (value buffers must be ready).  When
+// `ev` is given, ev[0] / ev[1] are recorded around the blur passes.  Returns the number
+// of blur passes.
+int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+                float* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
+// Full operator on the handle's stream, allocating value buffers when needed.
+sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+                   float* out);
+
+// ---- CG (cg.cu) ----
+sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
+                  int max_iter, float* X, int* iters, double* rel_res);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace sgp

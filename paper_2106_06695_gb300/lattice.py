@@ -1,0 +1,152 @@
+"""Python handle for the sm_103a Simplex-GP lattice (Sec. 3.2; Eq. ski_to_bf).
+
+Argument marshalling only: tensors are passed to libsgp.so as device pointers, with the
+current torch CUDA stream, and every step of the path runs in the library's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import BLURS, KERNELS, VALUE_DTYPES, check
+
+
+def _f32_cuda(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32" % name)
+    return t.contiguous()
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Lattice:
+    """Permutohedral lattice of the rows of X (n x d) scaled by ARD lengthscales.
+
+    kernel: "rbf_binomial" (default; stencil [.5, 1, .5] at order 1), "rbf_coverage" or
+    "matern32_coverage" (spacing from Eq. balance_coverage); order: stencil order r.
+    """
+
+    def __init__(self, X: torch.Tensor, lengthscales, order: int = 1,
+                 kernel: str = "rbf_binomial", spacing: float = 0.0, outputscale: float = 1.0,
+                 value_dtype: str = "f32", check_every: int = 8):
+        self._lib = _lib.load()
+        X = _f32_cuda(X, "X")
+        if X.dim() != 2:
+            raise ValueError("X must be [n, d]")
+        n, d = X.shape
+        if not isinstance(lengthscales, torch.Tensor):
+            lengthscales = torch.full((d,), float(lengthscales), dtype=torch.float32)
+        ls = lengthscales.to(device=X.device, dtype=torch.float32).reshape(-1)
+        if ls.numel() == 1:
+            ls = ls.expand(d)
+        ls = ls.contiguous()
+        self.device = X.device
+        self.n, self.d = int(n), int(d)
+        opts = _lib.sgp_opts()
+        self._lib.sgp_opts_init(ctypes.byref(opts))
+        opts.order_r = int(order)
+        opts.kernel = KERNELS[kernel]
+        opts.spacing_s = float(spacing)
+        opts.outputscale = float(outputscale)
+        opts.value_dtype = VALUE_DTYPES[value_dtype]
+        opts.check_every = int(check_every)
+        opts.stream = _stream_ptr(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._lib.sgp_lattice_build(X.data_ptr(), ls.data_ptr(), self.n, self.d,
+                                              ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        m = ctypes.c_int64()
+        nbytes = ctypes.c_size_t()
+        check(self._lib.sgp_lattice_info(h, ctypes.byref(m), ctypes.byref(nbytes)))
+        self.m = int(m.value)
+        self.order = int(order)
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.sgp_lattice_free(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("lattice was closed")
+        check(self._lib.sgp_set_stream(self._h, _stream_ptr(self.device)))
+        return self._h
+
+    # -- queries ----------------------------------------------------------------
+    @property
+    def device_bytes(self) -> int:
+        nbytes = ctypes.c_size_t()
+        check(self._lib.sgp_lattice_info(self._h, None, ctypes.byref(nbytes)))
+        return int(nbytes.value)
+
+    def stencil(self):
+        """(s, c[0..r], g[0..r]): spacing, paper taps and symmetric-blur taps."""
+        r = ctypes.c_int()
+        s = ctypes.c_double()
+        c = np.zeros(8, np.float64)
+        g = np.zeros(8, np.float64)
+        check(self._lib.sgp_lattice_stencil(self._h, ctypes.byref(r), ctypes.byref(s),
+                                            c.ctypes.data, g.ctypes.data))
+        return s.value, c[: r.value + 1].copy(), g[: r.value + 1].copy()
+
+    def export(self):
+        """Host copies: keys [m][d+1] int16, idx [n][d+1] int32, w [n][d+1] float32."""
+        D = self.d + 1
+        keys = np.zeros((self.m, D), np.int16)
+        idx = np.zeros((self.n, D), np.int32)
+        w = np.zeros((self.n, D), np.float32)
+        check(self._lib.sgp_lattice_export(self._handle(), keys.ctypes.data, idx.ctypes.data,
+                                           w.ctypes.data))
+        return dict(keys=keys, idx=idx, w=w)
+
+    # -- operators ----------------------------------------------------------------
+    def _rhs(self, V: torch.Tensor, name: str):
+        V = _f32_cuda(V, name)
+        squeeze = V.dim() == 1
+        if squeeze:
+            V = V.unsqueeze(1)
+        if V.dim() != 2 or V.shape[0] != self.n:
+            raise ValueError("%s must be [n] or [n, k]" % name)
+        return V.contiguous(), squeeze
+
+    def mvm(self, V: torch.Tensor, blur: str = "sequential", alpha: float = 1.0,
+            beta: float = 0.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """alpha * W B W^T V + beta * V (B per `blur`: sequential / transpose / symmetric)."""
+        V2, squeeze = self._rhs(V, "V")
+        k = V2.shape[1]
+        if out is None:
+            out = torch.empty_like(V2)
+        check(self._lib.sgp_mvm_ex(self._handle(), V2.data_ptr(), k, BLURS[blur], float(alpha),
+                                   float(beta), out.data_ptr()))
+        return out.squeeze(1) if squeeze else out
+
+    def cg(self, B: torch.Tensor, noise: float, tol: float = 1e-3, max_iter: int = 500,
+           blur: str = "symmetric", out: torch.Tensor | None = None):
+        """Batched CG on (outputscale K~ + noise I) X = B; returns (X, iters, rel_res)."""
+        B2, squeeze = self._rhs(B, "B")
+        k = B2.shape[1]
+        if out is None:
+            out = torch.empty_like(B2)
+        iters = np.zeros(k, np.int32)
+        rel = np.zeros(k, np.float64)
+        check(self._lib.sgp_cg_solve_ex(self._handle(), B2.data_ptr(), k, BLURS[blur],
+                                        float(noise), float(tol), int(max_iter), out.data_ptr(),
+                                        iters.ctypes.data, rel.ctypes.data))
+        return (out.squeeze(1) if squeeze else out), iters, rel

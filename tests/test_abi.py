@@ -1,0 +1,81 @@
+"""The C-ABI boundary on the CPU: the library builds, loads and exports every entry point
+include/sgp.h declares, and fails loudly without a GPU.  No compute call is made here."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+import torch
+
+from paper_2106_06695_gb300 import _lib, build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _lib.declared_functions()
+    for required in ("sgp_lattice_build", "sgp_mvm", "sgp_cg_solve", "sgp_lattice_free",
+                     "sgp_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sgp_\w+)", out))
+    missing = set(_lib.declared_functions()) - exported
+    assert not missing, missing
+    for name in _lib.declared_functions():
+        assert hasattr(lib, name)
+
+
+def test_version_and_defaults(lib):
+    assert lib.sgp_version() == 1
+    o = _lib.sgp_opts()
+    lib.sgp_opts_init(ctypes.byref(o))
+    assert (o.order_r, o.kernel, o.spacing_s, o.outputscale, o.value_dtype, o.check_every) == (
+        1, 0, 0.0, 1.0, 0, 8)
+    assert o.stream is None
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    h = ctypes.c_void_p()
+    rc = lib.sgp_lattice_build(None, None, 10, 3, None, ctypes.byref(h))
+    assert rc == 1 and not h.value
+    assert b"lengthscales" in lib.sgp_last_error()
+    assert lib.sgp_mvm(None, None, 1, None) == 1
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_no_gpu_fails_loudly(lib):
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_float * 4)()
+    rc = lib.sgp_lattice_build(ctypes.addressof(buf), ctypes.addressof(buf), 1, 3, None,
+                               ctypes.byref(h))
+    assert rc == 6
+    assert b"no CUDA device" in lib.sgp_last_error()
+
+
+def test_missing_library_raises(monkeypatch):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "no_such_libsgp.so"))
+    with pytest.raises(ImportError):
+        _lib.load()
+
+
+def test_product_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2106_06695_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+                assert "sgp_oracle" not in text and "liboracle" not in text, f
