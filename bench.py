@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -51,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default 2,000,000)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
+                    help="profiling aid: build once, run R symmetric MVMs, print their time")
     return ap.parse_args(argv)
 
 
@@ -157,14 +160,17 @@ def measured_peak_gbs():
 
 def blur_traffic_per_launch(m: int, k: int):
     """DRAM bytes per blur launch from the committed ncu summary, scaled to this m, if the
-    kernel source has not changed since it was captured; else None."""
+    k_blur source has not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))["blur_pass"]
     except (OSError, KeyError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu"), "rb").read()
-    if hashlib.sha1(src).hexdigest() != rec.get("mvm_cu_sha1") or rec.get("k") != k:
+    src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu")).read()
+    body = re.search(r"template <int VEC>\n__global__ void __launch_bounds__\(kThreads\) "
+                     r"k_blur\(.*?\n}\n", src, re.S)
+    if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("k_blur_src_sha1")
+            or rec.get("k") != k):
         return None
     return float(rec["bytes_per_vertex"]) * m
 
@@ -192,6 +198,17 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     Xd, Vd, lsd = Xh.to(dev), Vh.to(dev), lsh.to(dev)
     out = torch.empty_like(Vd)
+    if args.mvm_only:
+        lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.mvm_only):
+            lat.mvm(Vd, blur=W["blur"], out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mvm_only": True, "n": n, "m": lat.m, "reps": args.mvm_only,
+                          "ms_per_mvm": e0.elapsed_time(e1) / args.mvm_only}), flush=True)
+        return
     prof = {"ms": 0.0, "passes": 0, "m": 0, "iters": [], "build_ms": []}
 
     def step(Xdev, Vdev, ls_dev, profile=False):
@@ -212,6 +229,9 @@ def run_ours(args, world, rank, local):
         prof["m"] = lat.m
         prof["iters"].append(int(iters.max()))
         lat.close()
+        print("step: m=%d build %.1f ms, cg iters %d, %.1f ms total" % (
+            lat.m, prof["build_ms"][-1], int(iters.max()), 1e3 * (time.perf_counter() - t0)),
+            file=sys.stderr, flush=True)
         return int(iters.max()), rel
 
     for _ in range(args.warmup):
@@ -250,8 +270,13 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": bytes_per_pass,
                 "avg_launch_ms": avg_pass_ms, "sampled_launches": prof["passes"]}
 
-    # MVM alone (same lattice, same stream) for context
+    # MVM alone (same lattice, same stream) for context, and the true residual of the
+    # last solve: || V - (K~ + noise I) X || / || V || per column
     lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"])
+    _, _, rel_last = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
+                            blur=W["blur"], out=out)
+    resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
+    true_rel = (resid.norm(dim=0) / Vd.double().norm(dim=0)).max().item()
     for _ in range(3):
         lat.mvm(Vd, blur=W["blur"], out=out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,6 +343,7 @@ def run_ours(args, world, rank, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk.summary(),
+        "cg_final_rel_res_max": float(np.max(rel)), "cg_true_rel_res_max": true_rel,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

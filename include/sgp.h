@@ -95,6 +95,14 @@ typedef struct {
 /* Fill *opts with the defaults listed above. */
 void sgp_opts_init(sgp_opts* opts);
 
+/* Stencil of a kernel without building a lattice (host only, no device needed; Sec. 4.1,
+ * Eq. balance_coverage): spacing *spacing_s, taps coef[0..order_r] = k(t s) and
+ * symmetric-blur taps half_coef[0..order_r] (host arrays of order_r + 1 doubles).
+ * spacing_override > 0 replaces the kernel rule's spacing.  SGP_ERR_INVALID_ARG for an
+ * unknown kernel or order_r outside 1..4. */
+sgp_status sgp_stencil(int kernel, int order_r, double spacing_override, double* spacing_s,
+                       double* coef, double* half_coef);
+
 /* Build the lattice of n points (Sec. 3.2 "Splat"): scale each point by the
  * lengthscales, elevate it into H_d, find its enclosing simplex by rounding and ranking,
  * compute its d+1 barycentric weights, insert the simplex vertices into a device hash
@@ -144,8 +152,10 @@ sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alp
 /* Batched conjugate gradients (Sec. 2; App. A: at most max_iter = 500 iterations) on
  *   (outputscale * W B W^T + noise_var I) X = B,   B = SGP_BLUR_SYMMETRIC,
  * every column independent: column c stops when ||r_c|| / ||b_c|| <= tol (recurrence
- * residual), after max_iter iterations, or when <p_c, A p_c> <= 0.  Vector updates are
- * fp32; dot products and norms are accumulated in fp64.
+ * residual), after max_iter iterations, or when <p_c, A p_c> <= 0.  The iterate and the
+ * residual are kept in fp64 on the device, the search direction and its product in fp32
+ * (the MVM operands); dot products and norms are accumulated in fp64.  Work space:
+ * 24 n k bytes plus the handle's lattice value buffers, allocated per call.
  *   B      device [n][k] fp32;  X device [n][k] fp32 (solution; must not alias B).
  *   iters  host [k] int (iterations per column) or NULL;
  *   rel_res host [k] double (final recurrence residual ratio per column) or NULL.

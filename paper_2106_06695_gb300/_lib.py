@@ -58,6 +58,7 @@ def load():
     I, I64, F, Dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_double
     sigs = {
         "sgp_opts_init": (None, [ctypes.POINTER(sgp_opts)]),
+        "sgp_stencil": (I, [I, I, Dbl, ctypes.POINTER(Dbl), P, P]),
         "sgp_lattice_build": (I, [P, P, I64, I, ctypes.POINTER(sgp_opts), ctypes.POINTER(P)]),
         "sgp_lattice_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]),
         "sgp_lattice_stencil": (I, [P, ctypes.POINTER(I), ctypes.POINTER(Dbl), P, P]),

@@ -1,6 +1,8 @@
 // C-ABI entry points of the lattice library (declared in include/sgp.h): argument
 // validation, handle lifetime and error reporting around the build, MVM and CG paths.
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -22,12 +24,13 @@ void free_lattice(Lattice* L) {
   if (!L) return;
   cudaStream_t st = L->stream;
   void* arrays[] = {L->perm, L->idx, L->w, L->row_ptr, L->items, L->nbr, L->keys, L->err,
-                    L->lat[0], L->lat[1]};
+                    L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial};
   for (void* p : arrays)
-    if (p) cudaFreeAsync(p, st);
+    if (p) (void)cudaFreeAsync(p, st);
   for (cudaEvent_t ev : L->prof_ev)
-    if (ev) cudaEventDestroy(ev);
+    if (ev) (void)cudaEventDestroy(ev);
   delete L;
+  clear_pending_error();
 }
 
 sgp_status check_handle(const sgp_lattice* h) {
@@ -41,6 +44,14 @@ sgp_status check_handle(const sgp_lattice* h) {
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void clear_pending_error() {
+  // SGP_TRACE=1 reports such leftovers on stderr (diagnostics only)
+  static const bool trace = getenv("SGP_TRACE") && getenv("SGP_TRACE")[0] == '1';
+  const cudaError_t e = cudaGetLastError();
+  if (trace && e != cudaSuccess)
+    fprintf(stderr, "[sgp] cleared a pending CUDA error: %s\n", cudaGetErrorName(e));
+}
 
 void note_launches(int64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
@@ -73,6 +84,21 @@ void sgp_opts_init(sgp_opts* o) {
   o->stream = nullptr;
 }
 
+sgp_status sgp_stencil(int kernel, int order_r, double spacing_override, double* spacing_s,
+                       double* coef, double* half_coef) {
+  double s = 0.0, c[kMaxOrder + 1], g[kMaxOrder + 1];
+  if (!make_stencil(kernel, order_r, spacing_override, &s, c, g)) {
+    set_error("sgp_stencil: kernel must be an SGP_KERNEL_* value and 1 <= order_r <= 4");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (spacing_s) *spacing_s = s;
+  for (int t = 0; t <= order_r; ++t) {
+    if (coef) coef[t] = c[t];
+    if (half_coef) half_coef[t] = g[t];
+  }
+  return SGP_OK;
+}
+
 sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t n, int d,
                              const sgp_opts* opts, sgp_lattice** out) {
   if (!out) {
@@ -99,6 +125,7 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
     set_error("sgp_lattice_build: no CUDA device (this library has no CPU path)");
     return SGP_ERR_CUDA;
   }
+  clear_pending_error();
   Lattice* L = new Lattice();
   L->n = n;
   L->d = d;
@@ -202,12 +229,14 @@ static sgp_status check_mvm_args(const sgp_lattice* h, const float* V, int k, in
 
 sgp_status sgp_mvm(sgp_lattice* h, const float* V, int k, float* out) {
   if (sgp_status s = check_mvm_args(h, V, k, SGP_BLUR_SEQUENTIAL, out, "sgp_mvm")) return s;
+  clear_pending_error();
   return run_mvm(h, V, k, SGP_BLUR_SEQUENTIAL, h->outputscale, 0.f, out);
 }
 
 sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alpha, float beta,
                       float* out) {
   if (sgp_status s = check_mvm_args(h, V, k, blur, out, "sgp_mvm_ex")) return s;
+  clear_pending_error();
   return run_mvm(h, V, k, blur, alpha, beta, out);
 }
 
@@ -218,6 +247,7 @@ sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, floa
     set_error("sgp_cg_solve: need noise_var >= 0, tol >= 0 and max_iter >= 0");
     return SGP_ERR_INVALID_ARG;
   }
+  clear_pending_error();
   return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res);
 }
 

@@ -338,6 +338,41 @@ __global__ void k_splat_items(const uint32_t* __restrict__ sorted_entries,
   items[p] = make_int2(perm[e / D], __float_as_int(w[e]));
 }
 
+// Segment counts per vertex: total segments, partial slots, medium / huge flags.
+__global__ void k_seg_count(const int32_t* __restrict__ row_ptr, int64_t m,
+                            uint32_t* __restrict__ nseg, uint32_t* __restrict__ nslot,
+                            uint32_t* __restrict__ med, uint32_t* __restrict__ huge) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const int len = row_ptr[v + 1] - row_ptr[v];
+  const uint32_t c = (uint32_t)((len + kSplatSeg - 1) / kSplatSeg);
+  nseg[v] = c;
+  nslot[v] = c > 1 ? c : 0u;
+  med[v] = (c > 1 && c <= (uint32_t)kSplatMedSegs) ? 1u : 0u;
+  huge[v] = c > (uint32_t)kSplatMedSegs ? 1u : 0u;
+}
+
+// After the exclusive scans: write every segment and the fix-up row lists.
+__global__ void k_seg_fill(const int32_t* __restrict__ row_ptr, int64_t m,
+                           const uint32_t* __restrict__ seg_off,
+                           const uint32_t* __restrict__ slot_off,
+                           const uint32_t* __restrict__ med_off,
+                           const uint32_t* __restrict__ huge_off, int4* __restrict__ seg,
+                           int4* __restrict__ med_rows, int4* __restrict__ huge_rows) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const int b = row_ptr[v], e = row_ptr[v + 1];
+  const int c = (e - b + kSplatSeg - 1) / kSplatSeg;
+  const int s0 = (int)seg_off[v];
+  const int slot0 = c > 1 ? (int)slot_off[v] : -1;
+  for (int j = 0; j < c; ++j) {
+    const int beg = b + j * kSplatSeg;
+    seg[s0 + j] = make_int4((int)v, beg, min(beg + kSplatSeg, e), c > 1 ? slot0 + j : -1);
+  }
+  if (c > 1 && c <= kSplatMedSegs) med_rows[med_off[v]] = make_int4((int)v, slot0, c, 0);
+  if (c > kSplatMedSegs) huge_rows[huge_off[v]] = make_int4((int)v, slot0, c, 0);
+}
+
 __global__ void k_iota(uint32_t* __restrict__ out, int64_t count) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < count) out[p] = (uint32_t)p;
@@ -367,7 +402,8 @@ struct Temps {
   cudaStream_t st;
   std::vector<void*> ptrs;
   ~Temps() {
-    for (void* p : ptrs) cudaFreeAsync(p, st);
+    for (void* p : ptrs) (void)cudaFreeAsync(p, st);
+    clear_pending_error();
   }
   template <class T>
   cudaError_t get(T** p, size_t count) {
@@ -566,6 +602,38 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
     k_row_ptr<<<(unsigned)ceil_div(nD + 1, 256), 256, 0, st>>>(sorted_ids, nD, m, L->row_ptr);
     note_launches(1);
     SGP_CHECK(cudaGetLastError(), "splat lists");
+  }
+
+  // 7. splat segments (load balance)
+  {
+    uint32_t *cnt, *slots, *med, *huge, *tot, *stmp;
+    SGP_CHECK(tmp.get(&cnt, m), "alloc seg");
+    SGP_CHECK(tmp.get(&slots, m), "alloc seg");
+    SGP_CHECK(tmp.get(&med, m), "alloc seg");
+    SGP_CHECK(tmp.get(&huge, m), "alloc seg");
+    SGP_CHECK(tmp.get(&tot, 4), "alloc seg");
+    SGP_CHECK(tmp.get(&stmp, scan_temp_elems(m)), "alloc seg");
+    k_seg_count<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(L->row_ptr, m, cnt, slots, med, huge);
+    note_launches(1);
+    exclusive_scan_u32(cnt, m, tot + 0, stmp, st);
+    exclusive_scan_u32(slots, m, tot + 1, stmp, st);
+    exclusive_scan_u32(med, m, tot + 2, stmp, st);
+    exclusive_scan_u32(huge, m, tot + 3, stmp, st);
+    uint32_t ht[4];
+    SGP_CHECK(cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, st), "read seg");
+    SGP_CHECK(cudaStreamSynchronize(st), "sync seg");
+    L->nseg = ht[0];
+    L->nslots = ht[1];
+    L->nmed = ht[2];
+    L->nhuge = ht[3];
+    SGP_CHECK(dalloc(&L->seg, L->nseg, st), "alloc seg");
+    SGP_CHECK(dalloc(&L->med_rows, L->nmed, st), "alloc seg");
+    SGP_CHECK(dalloc(&L->huge_rows, L->nhuge, st), "alloc seg");
+    L->bytes += (L->nseg + L->nmed + L->nhuge) * sizeof(int4);
+    k_seg_fill<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(L->row_ptr, m, cnt, slots, med, huge,
+                                                          L->seg, L->med_rows, L->huge_rows);
+    note_launches(1);
+    SGP_CHECK(cudaGetLastError(), "splat segments");
   }
   SGP_CHECK(cudaStreamSynchronize(st), "sync build");
   return SGP_OK;

@@ -3,8 +3,10 @@
 //
 // Every right-hand side c is an independent CG with its own scalars; a column that has
 // converged (||r_c|| / ||b_c|| <= tol), hit max_iter or broken down (<p, Ap> <= 0) is
-// frozen by a device-side flag, so extra iterations leave it unchanged.  Vectors are fp32
-// [n][k]; the dot products and norms are accumulated in fp64 per block (fixed column per
+// frozen by a device-side flag, so extra iterations leave it unchanged.  The iterate x and
+// the residual r are kept in fp64 [n][k] (their recurrences are where fp32 rounding makes
+// CG lose orthogonality); the search direction p and A p are fp32, the operands of the
+// lattice MVM.  Dot products and norms are accumulated in fp64 per block (fixed column per
 // thread, shared-memory tree) and the block partials are summed in a fixed order by one
 // small kernel, so the result does not depend on scheduling.  One iteration is captured
 // in a CUDA graph and replayed; the host reads the flags every check_every iterations.
@@ -45,8 +47,8 @@ __device__ __forceinline__ void column_partial(double acc, int k, double* partia
   }
 }
 
-__global__ void k_cg_init(const float* __restrict__ B, float* __restrict__ X,
-                          float* __restrict__ r, float* __restrict__ p, int64_t n, int k,
+__global__ void k_cg_init(const float* __restrict__ B, double* __restrict__ x,
+                          double* __restrict__ r, float* __restrict__ p, int64_t n, int k,
                           double* __restrict__ partial) {
   const int rows_per_block = blockDim.x / k;
   const int c = threadIdx.x % k;
@@ -57,8 +59,8 @@ __global__ void k_cg_init(const float* __restrict__ B, float* __restrict__ X,
          row += (int64_t)gridDim.x * rows_per_block) {
       const int64_t e = row * k + c;
       const float b = B[e];
-      X[e] = 0.f;
-      r[e] = b;
+      x[e] = 0.0;
+      r[e] = (double)b;
       p[e] = b;
       acc += (double)b * (double)b;
     }
@@ -119,7 +121,7 @@ __global__ void k_cg_alpha(int nblk, int k, CgState S) {
   S.alpha[c] = alpha;
 }
 
-__global__ void k_cg_update_xr(float* __restrict__ X, float* __restrict__ r,
+__global__ void k_cg_update_xr(double* __restrict__ x, double* __restrict__ r,
                                const float* __restrict__ p, const float* __restrict__ Ap,
                                int64_t n, int k, CgState S) {
   const int rows_per_block = blockDim.x / k;
@@ -128,17 +130,17 @@ __global__ void k_cg_update_xr(float* __restrict__ X, float* __restrict__ r,
   double acc = 0.0;
   if ((int)threadIdx.x < rows_per_block * k) {
     const bool on = S.active[c] != 0;
-    const float a = (float)S.alpha[c];
+    const double a = S.alpha[c];
     for (int64_t row = (int64_t)blockIdx.x * rows_per_block + row0; row < n;
          row += (int64_t)gridDim.x * rows_per_block) {
       const int64_t e = row * k + c;
-      float rv = r[e];
+      double rv = r[e];
       if (on) {
-        X[e] = fmaf(a, p[e], X[e]);
-        rv = fmaf(-a, Ap[e], rv);
+        x[e] = fma(a, (double)p[e], x[e]);
+        rv = fma(-a, (double)Ap[e], rv);
         r[e] = rv;
       }
-      acc += (double)rv * (double)rv;
+      acc += rv * rv;
     }
   }
   column_partial(acc, k, S.partial);
@@ -162,13 +164,18 @@ __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
   S.rho[c] = rr;
 }
 
-__global__ void k_cg_update_p(float* __restrict__ p, const float* __restrict__ r, int64_t n,
+__global__ void k_cg_update_p(float* __restrict__ p, const double* __restrict__ r, int64_t n,
                               int k, CgState S) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * k) return;
   const int c = (int)(e % k);
   if (!S.active[c]) return;
-  p[e] = fmaf((float)S.beta[c], p[e], r[e]);
+  p[e] = (float)fma(S.beta[c], (double)p[e], r[e]);
+}
+
+__global__ void k_cg_store_x(const double* __restrict__ x, float* __restrict__ X, int64_t count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) X[e] = (float)x[e];
 }
 
 }  // namespace
@@ -191,13 +198,14 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     ~Cleanup() {
-      if (exec) cudaGraphExecDestroy(exec);
-      if (graph) cudaGraphDestroy(graph);
-      for (void* p : ptrs) cudaFreeAsync(p, st);
+      if (exec) (void)cudaGraphExecDestroy(exec);
+      if (graph) (void)cudaGraphDestroy(graph);
+      for (void* p : ptrs) (void)cudaFreeAsync(p, st);
       if (own) {
-        cudaStreamSynchronize(own);
-        cudaStreamDestroy(own);
+        (void)cudaStreamSynchronize(own);
+        (void)cudaStreamDestroy(own);
       }
+      clear_pending_error();
     }
   } cl{st, own, {}};
   auto get = [&](void** p, size_t bytes) {
@@ -211,9 +219,11 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     if (e_ != cudaSuccess) return cuda_status(e_, what);   \
   } while (0)
 
-  float *r, *p, *Ap;
+  double *x, *r;
+  float *p, *Ap;
   CgState S{};
-  CG_CHECK(get((void**)&r, n * k * sizeof(float)), "alloc r");
+  CG_CHECK(get((void**)&x, n * k * sizeof(double)), "alloc x");
+  CG_CHECK(get((void**)&r, n * k * sizeof(double)), "alloc r");
   CG_CHECK(get((void**)&p, n * k * sizeof(float)), "alloc p");
   CG_CHECK(get((void**)&Ap, n * k * sizeof(float)), "alloc Ap");
   CG_CHECK(get((void**)&S.partial, (size_t)kDotBlocks * k * sizeof(double)), "alloc partial");
@@ -235,7 +245,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   const int dot_threads = k * (kDotThreads / k);
   const int64_t rows_per_block = dot_threads / k;
   const int dot_blocks = (int)std::min<int64_t>(kDotBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
-  k_cg_init<<<dot_blocks, dot_threads, 0, st>>>(B, X, r, p, n, k, S.partial);
+  k_cg_init<<<dot_blocks, dot_threads, 0, st>>>(B, x, r, p, n, k, S.partial);
   k_cg_init_scalars<<<1, kMaxK, 0, st>>>(S.partial, dot_blocks, k, tol, max_iter, S);
   note_launches(2);
   CG_CHECK(cudaGetLastError(), "CG init");
@@ -246,7 +256,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     passes = enqueue_mvm(L, p, k, blur, L->outputscale, noise, Ap, st, ev);
     k_coldot<<<dot_blocks, dot_threads, 0, st>>>(p, Ap, n, k, S.partial);
     k_cg_alpha<<<1, kMaxK, 0, st>>>(dot_blocks, k, S);
-    k_cg_update_xr<<<dot_blocks, dot_threads, 0, st>>>(X, r, p, Ap, n, k, S);
+    k_cg_update_xr<<<dot_blocks, dot_threads, 0, st>>>(x, r, p, Ap, n, k, S);
     k_cg_beta<<<1, kMaxK, 0, st>>>(dot_blocks, k, tol, max_iter, S);
     k_cg_update_p<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(p, r, n, k, S);
     note_launches(5);
@@ -277,13 +287,15 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
       CG_CHECK(cudaStreamSynchronize(st), "sync CG");
       if (ev) {  // the events of the last replay bracket one MVM's blur passes
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) {
-          L->prof_ms += ms;
-          L->prof_passes += passes;
-        }
+        CG_CHECK(cudaEventElapsedTime(&ms, ev[0], ev[1]), "reading the blur timing events");
+        L->prof_ms += ms;
+        L->prof_passes += passes;
       }
     }
   }
+  k_cg_store_x<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(x, X, n * k);
+  note_launches(1);
+  CG_CHECK(cudaGetLastError(), "CG result");
   std::vector<double> hrel(k);
   std::vector<int> hit(k);
   CG_CHECK(cudaMemcpyAsync(hrel.data(), S.relres, k * sizeof(double), cudaMemcpyDeviceToHost, st),

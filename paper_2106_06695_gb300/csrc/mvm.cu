@@ -47,24 +47,69 @@ struct Vec<1> {
   static __device__ __forceinline__ T scale(float a, T x) { return a * x; }
 };
 
+// One thread-group of G threads per segment of at most kSplatSeg incidences.
 template <int VEC>
-__global__ void __launch_bounds__(kThreads) k_splat(int64_t m, int G, int k,
-                                                    const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kThreads) k_splat(int64_t nseg, int G, int k,
+                                                    const int4* __restrict__ seg,
                                                     const int2* __restrict__ items,
                                                     const float* __restrict__ V,
-                                                    float* __restrict__ lat) {
+                                                    float* __restrict__ lat,
+                                                    float* __restrict__ partial) {
   using Vt = Vec<VEC>;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t v = gid / G;
-  if (v >= m) return;
-  const int col = (int)(gid - v * G) * VEC;
-  const int b = row_ptr[v], e = row_ptr[v + 1];
+  const int64_t s = gid / G;
+  if (s >= nseg) return;
+  const int col = (int)(gid - s * G) * VEC;
+  const int4 sg = seg[s];
   typename Vt::T acc = Vt::zero();
-  for (int p = b; p < e; ++p) {
+  for (int p = sg.y; p < sg.z; ++p) {
     const int2 it = items[p];
     acc = Vt::fma(__int_as_float(it.y), Vt::ld(V + (int64_t)it.x * k + col), acc);
   }
-  Vt::st(lat + v * k + col, acc);
+  if (sg.w < 0) Vt::st(lat + (int64_t)sg.x * k + col, acc);
+  else Vt::st(partial + (int64_t)sg.w * k + col, acc);
+}
+
+// Fix-up for vertices with 2..kSplatMedSegs segments: one thread-group sums in order.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_splat_med(int64_t nrows, int G, int k,
+                                                        const int4* __restrict__ rows,
+                                                        const float* __restrict__ partial,
+                                                        float* __restrict__ lat) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q = gid / G;
+  if (q >= nrows) return;
+  const int col = (int)(gid - q * G) * VEC;
+  const int4 rw = rows[q];
+  typename Vt::T acc = Vt::zero();
+  for (int j = 0; j < rw.z; ++j) acc = Vt::add(acc, Vt::ld(partial + (int64_t)(rw.y + j) * k + col));
+  Vt::st(lat + (int64_t)rw.x * k + col, acc);
+}
+
+// Fix-up for vertices with more segments: one block per vertex, groups of G threads take
+// strided partials, then a fixed-shape shared-memory tree combines the groups.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_splat_huge(int G, int k, const int4* __restrict__ rows,
+                                                         const float* __restrict__ partial,
+                                                         float* __restrict__ lat) {
+  using Vt = Vec<VEC>;
+  __shared__ typename Vt::T red[kThreads];
+  const int groups = blockDim.x / G;
+  const int g = threadIdx.x / G;
+  const int col = (int)(threadIdx.x % G) * VEC;
+  const int4 rw = rows[blockIdx.x];
+  typename Vt::T acc = Vt::zero();
+  if (g < groups)
+    for (int j = g; j < rw.z; j += groups)
+      acc = Vt::add(acc, Vt::ld(partial + (int64_t)(rw.y + j) * k + col));
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int half = groups / 2; half >= 1; half /= 2) {
+    if (g < half) red[threadIdx.x] = Vt::add(red[threadIdx.x], red[threadIdx.x + half * G]);
+    __syncthreads();
+  }
+  if (g == 0) Vt::st(lat + (int64_t)rw.x * k + col, red[threadIdx.x]);
 }
 
 template <int VEC>
@@ -122,31 +167,54 @@ inline bool vec4_ok(int k, const void* a, const void* b) {
 sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
   const size_t need = (size_t)L->m * k;
   if (L->lat_elems >= need && L->lat[0]) return SGP_OK;
-  for (int b = 0; b < 2; ++b) {
-    if (L->lat[b]) cudaFreeAsync(L->lat[b], st);
-    L->lat[b] = nullptr;
+  float** bufs[3] = {&L->lat[0], &L->lat[1], &L->partial};
+  for (float** b : bufs) {
+    if (*b) cudaFreeAsync(*b, st);
+    *b = nullptr;
   }
-  L->bytes -= L->lat_elems * 2 * sizeof(float);
+  L->bytes -= L->lat_bytes;
+  L->lat_bytes = 0;
   L->lat_elems = 0;
-  for (int b = 0; b < 2; ++b) {
-    cudaError_t e = cudaMallocAsync((void**)&L->lat[b], std::max<size_t>(need, 1) * sizeof(float), st);
+  const size_t sizes[3] = {need, need, (size_t)L->nslots * k};
+  for (int b = 0; b < 3; ++b) {
+    cudaError_t e = cudaMallocAsync((void**)bufs[b], std::max<size_t>(sizes[b], 1) * sizeof(float), st);
     if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
   }
   L->lat_elems = need;
-  L->bytes += need * 2 * sizeof(float);
+  L->lat_bytes = (need * 2 + sizes[2]) * sizeof(float);
+  L->bytes += L->lat_bytes;
   return SGP_OK;
 }
 
 void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStream_t st) {
-  if (vec4_ok(k, V, lat)) {
-    const int G = k / 4;
-    k_splat<4><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(L->m, G, k, L->row_ptr,
-                                                                           L->items, V, lat);
-  } else {
-    k_splat<1><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, k, L->row_ptr,
-                                                                           L->items, V, lat);
-  }
+  const bool v4 = vec4_ok(k, V, lat);
+  const int G = v4 ? k / 4 : k;
+  if (v4)
+    k_splat<4><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat, L->partial);
+  else
+    k_splat<1><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat, L->partial);
   note_launches(1);
+  if (L->nmed > 0) {
+    if (v4)
+      k_splat_med<4><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, L->partial, lat);
+    else
+      k_splat_med<1><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, L->partial, lat);
+    note_launches(1);
+  }
+  if (L->nhuge > 0) {
+    // a power-of-two number of G-thread groups per block for the tree
+    int groups = 1;
+    while (groups * 2 * G <= kThreads) groups *= 2;
+    if (v4)
+      k_splat_huge<4><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, L->partial, lat);
+    else
+      k_splat_huge<1><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, L->partial, lat);
+    note_launches(1);
+  }
 }
 
 void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
@@ -198,7 +266,8 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
   float* a = L->lat[0];
   float* b = L->lat[1];
   launch_splat(L, V, k, a, st);
-  if (ev) cudaEventRecord(ev[0], st);
+  // External: inside a stream capture this becomes an event-record node of the graph
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   const int D = L->D;
   int passes = 0;
   auto pass = [&](int j, const Taps& tp) {
@@ -216,7 +285,7 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
     for (int j = 0; j < D; ++j) pass(j, g);
     for (int j = D - 1; j >= 0; --j) pass(j, g);
   }
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   launch_slice(L, a, V, k, alpha, beta, out, st);
   return passes;
 }

@@ -20,6 +20,8 @@ enum : unsigned {
 constexpr int kMaxOrder = 4;  // stencil order r
 constexpr int kMaxD = 128;    // d + 1
 constexpr int kMaxK = 256;    // right-hand sides per call
+constexpr int kSplatSeg = 32;      // splat items per segment
+constexpr int kSplatMedSegs = 16;  // segments a single thread-group sums in the fix-up
 
 // Stencil taps passed by value to the blur kernels.
 struct Taps {
@@ -48,6 +50,19 @@ struct sgp_lattice {
   float* w = nullptr;        // [n][D] barycentric weight, same order
   int32_t* row_ptr = nullptr;  // [m+1] splat lists: vertex v gathers items[row_ptr[v]..]
   int2* items = nullptr;       // [n*D] (caller's point index, weight bits)
+  // Splat work split into segments of at most kSplatSeg items (load balance: a dense
+  // cluster gives a vertex thousands of points).  seg[s] = (vertex, begin, end, slot):
+  // slot < 0 writes the vertex directly, else the partial goes to partial[slot] and a
+  // fix-up sums a vertex's partials in order.  med_rows / huge_rows: (vertex, first slot,
+  // number of slots) of vertices with 2..kSplatMedSegs / more segments.
+  int4* seg = nullptr;
+  int64_t nseg = 0;
+  int4* med_rows = nullptr;
+  int64_t nmed = 0;
+  int4* huge_rows = nullptr;
+  int64_t nhuge = 0;
+  int64_t nslots = 0;
+  float* partial = nullptr;  // [nslots][k], sized with the lattice values
   int32_t* nbr = nullptr;      // [D][r][2][m] neighbour id of v - t u_j (0) / v + t u_j (1)
   int16_t* keys = nullptr;     // [m][D] vertex coordinates
   unsigned* err = nullptr;     // device error word
@@ -55,6 +70,7 @@ struct sgp_lattice {
   // Lattice values, allocated on first use and grown on demand.
   float* lat[2] = {nullptr, nullptr};
   size_t lat_elems = 0;
+  size_t lat_bytes = 0;  // value buffers + splat partials
 
   // Optional blur timing: events bracket the blur passes of one MVM inside the CG graph
   // and are read at every flag check (sgp_profile_blur / sgp_profile_read).
@@ -73,6 +89,10 @@ using Lattice = ::sgp_lattice;
 // ---- error reporting and launch accounting (api.cu) ----
 void set_error(const std::string& msg);
 sgp_status cuda_status(cudaError_t e, const char* what);
+// Clear a pending non-sticky runtime error left by earlier calls of this thread (ours or
+// the caller's), so that the launch checks of the current call report only its own
+// launches.  A sticky error (a failed context) is returned again by the next call anyway.
+void clear_pending_error();
 // Count kernels enqueued by this library (graph replays count every kernel node).
 void note_launches(int64_t count);
 int64_t launches_so_far();
