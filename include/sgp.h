@@ -149,6 +149,24 @@ sgp_status sgp_mvm(sgp_lattice* h, const float* V, int k, float* out);
 sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alpha,
                       float beta, float* out);
 
+/* As sgp_mvm_ex, but allocating no device memory: the lattice value buffers and splat
+ * partials (2 m k + nslots k floats) come from a 64 MiB work area compiled into the
+ * library (a file-scope __device__ array, held by every GPU that loads the library until
+ * the process exits).  The paper has no counterpart; this entry point exists for callers
+ * that cannot allocate when they need a product: serving loops that must keep
+ * cudaMalloc/cudaFree (which can synchronise the device) off their hot path, and
+ * processes whose device memory is already reserved by another allocator's pool.
+ *   V, out  device [n][k] fp32 as in sgp_mvm_ex (the handle must already be built).
+ * A lattice whose work space for this k exceeds 64 MiB is rejected with
+ * SGP_ERR_INVALID_ARG before anything is launched.  The first call on a device looks up
+ * the work area's device address (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture.  All calls in the process share the one
+ * work area and it keeps the last call's contents (every element is rewritten before it
+ * is read): calls whose execution overlaps on the GPU -- concurrent streams, threads or
+ * handles -- race on it and must be ordered by the caller. */
+sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int blur, float alpha,
+                          float beta, float* out);
+
 /* Batched conjugate gradients (Sec. 2; App. A: at most max_iter = 500 iterations) on
  *   (outputscale * W B W^T + noise_var I) X = B,   B = SGP_BLUR_SYMMETRIC,
  * every column independent: column c stops when ||r_c|| / ||b_c|| <= tol (recurrence

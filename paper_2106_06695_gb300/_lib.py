@@ -66,6 +66,7 @@ def load():
         "sgp_set_stream": (I, [P, P]),
         "sgp_mvm": (I, [P, P, I, P]),
         "sgp_mvm_ex": (I, [P, P, I, I, F, F, P]),
+        "sgp_mvm_static": (I, [P, P, I, I, F, F, P]),
         "sgp_cg_solve": (I, [P, P, I, F, F, I, P, P, P]),
         "sgp_cg_solve_ex": (I, [P, P, I, I, F, F, I, P, P, P]),
         "sgp_lattice_free": (None, [P]),

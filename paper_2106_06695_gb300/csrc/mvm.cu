@@ -290,6 +290,63 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
   return passes;
 }
 
+// Same operator as enqueue_mvm, with the two value buffers and the splat partials given
+// by the caller (used by the allocation-free entry point).
+void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
+                      float beta, float* out, float* lat0, float* lat1, float* partial,
+                      cudaStream_t st) {
+  const bool v4 = vec4_ok(k, V, lat0);
+  const int G = v4 ? k / 4 : k;
+  if (v4)
+    k_splat<4><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat0, partial);
+  else
+    k_splat<1><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat0, partial);
+  note_launches(1);
+  if (L->nmed > 0) {
+    if (v4)
+      k_splat_med<4><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, partial, lat0);
+    else
+      k_splat_med<1><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, partial, lat0);
+    note_launches(1);
+  }
+  if (L->nhuge > 0) {
+    int groups = 1;
+    while (groups * 2 * G <= kThreads) groups *= 2;
+    if (v4)
+      k_splat_huge<4><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat0);
+    else
+      k_splat_huge<1><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat0);
+    note_launches(1);
+  }
+  Taps c{}, g{};
+  for (int t = 0; t <= L->r; ++t) {
+    c.t[t] = (float)L->coef[t];
+    g.t[t] = (float)L->half[t];
+  }
+  float* a = lat0;
+  float* b = lat1;
+  auto pass = [&](int j, const Taps& tp) {
+    launch_blur_pass(L, j, tp, a, b, k, st);
+    float* t = a;
+    a = b;
+    b = t;
+  };
+  const int D = L->D;
+  if (blur == SGP_BLUR_SEQUENTIAL) {
+    for (int j = 0; j < D; ++j) pass(j, c);
+  } else if (blur == SGP_BLUR_TRANSPOSE) {
+    for (int j = D - 1; j >= 0; --j) pass(j, c);
+  } else {
+    for (int j = 0; j < D; ++j) pass(j, g);
+    for (int j = D - 1; j >= 0; --j) pass(j, g);
+  }
+  launch_slice(L, a, V, k, alpha, beta, out, st);
+}
+
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out) {
   sgp_status s = ensure_lattice_values(L, k, L->stream);

@@ -131,6 +131,11 @@ void launch_slice(const Lattice* L, const float* lat, const float* V, int k, flo
 // of blur passes.
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                 float* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
+// As enqueue_mvm, with caller-provided value buffers ([m][k] each) and splat partials
+// ([nslots][k]); allocates nothing.
+void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
+                      float beta, float* out, float* lat0, float* lat1, float* partial,
+                      cudaStream_t st);
 // Full operator on the handle's stream, allocating value buffers when needed.
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);
