@@ -160,15 +160,15 @@ def measured_peak_gbs():
 
 def blur_traffic_per_launch(m: int, k: int):
     """DRAM bytes per blur launch from the committed ncu summary, scaled to this m, if the
-    k_blur source has not changed since it was captured; else None."""
+    k_blur_rows source has not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))["blur_pass"]
     except (OSError, KeyError, ValueError):
         return None
     src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu")).read()
-    body = re.search(r"template <int VEC>\n__global__ void __launch_bounds__\(kThreads\) "
-                     r"k_blur\(.*?\n}\n", src, re.S)
+    body = re.search(r"template <int CH>\n__global__ void __launch_bounds__\(kThreads\) "
+                     r"k_blur_rows\(.*?\n}\n", src, re.S)
     if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("k_blur_src_sha1")
             or rec.get("k") != k):
         return None
@@ -263,7 +263,7 @@ def run_ours(args, world, rank, local):
     avg_pass_ms = prof["ms"] / max(prof["passes"], 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9 if prof["passes"] else None
     traffic = blur_traffic_per_launch(m, k)
-    roofline = {"kernel": "k_blur<4> (one lattice direction)", "bound": "hbm",
+    roofline = {"kernel": "k_blur_rows<2> (one lattice direction)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",

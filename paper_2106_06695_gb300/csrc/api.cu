@@ -24,7 +24,8 @@ void free_lattice(Lattice* L) {
   if (!L) return;
   cudaStream_t st = L->stream;
   void* arrays[] = {L->perm, L->idx, L->w, L->row_ptr, L->items, L->nbr, L->keys, L->err,
-                    L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial};
+                    L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial,
+                    L->vperm};
   for (void* p : arrays)
     if (p) (void)cudaFreeAsync(p, st);
   for (cudaEvent_t ev : L->prof_ev)

@@ -330,12 +330,12 @@ __global__ void __launch_bounds__(256) k_neighbours(
 // 6. Splat lists.
 // ---------------------------------------------------------------------------------
 __global__ void k_splat_items(const uint32_t* __restrict__ sorted_entries,
-                              const int32_t* __restrict__ perm, const float* __restrict__ w,
+                              const float* __restrict__ w,
                               int64_t nD, int D, int2* __restrict__ items) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nD) return;
   const uint32_t e = sorted_entries[p];
-  items[p] = make_int2(perm[e / D], __float_as_int(w[e]));
+  items[p] = make_int2((int)(e / D), __float_as_int(w[e]));
 }
 
 // Segment counts per vertex: total segments, partial slots, medium / huge flags.
@@ -596,8 +596,8 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
     SGP_CHECK(dalloc(&L->items, nD, st), "alloc items");
     SGP_CHECK(dalloc(&L->row_ptr, m + 1, st), "alloc row_ptr");
     L->bytes += nD * sizeof(int2) + (m + 1) * sizeof(int32_t);
-    k_splat_items<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(sorted_entries, L->perm, L->w, nD,
-                                                              D, L->items);
+    k_splat_items<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(sorted_entries, L->w, nD, D,
+                                                              L->items);
     note_launches(1);
     k_row_ptr<<<(unsigned)ceil_div(nD + 1, 256), 256, 0, st>>>(sorted_ids, nD, m, L->row_ptr);
     note_launches(1);

@@ -47,9 +47,11 @@ __device__ __forceinline__ void column_partial(double acc, int k, double* partia
   }
 }
 
-__global__ void k_cg_init(const float* __restrict__ B, double* __restrict__ x,
-                          double* __restrict__ r, float* __restrict__ p, int64_t n, int k,
-                          double* __restrict__ partial) {
+// The solver's vectors live in the lattice's locality order: row p holds the caller's
+// row perm[p], so the MVM's splat gathers and slice writes stay local.
+__global__ void k_cg_init(const float* __restrict__ B, const int32_t* __restrict__ perm,
+                          double* __restrict__ x, double* __restrict__ r, float* __restrict__ p,
+                          int64_t n, int k, double* __restrict__ partial) {
   const int rows_per_block = blockDim.x / k;
   const int c = threadIdx.x % k;
   const int row0 = threadIdx.x / k;
@@ -58,7 +60,7 @@ __global__ void k_cg_init(const float* __restrict__ B, double* __restrict__ x,
     for (int64_t row = (int64_t)blockIdx.x * rows_per_block + row0; row < n;
          row += (int64_t)gridDim.x * rows_per_block) {
       const int64_t e = row * k + c;
-      const float b = B[e];
+      const float b = B[(int64_t)perm[row] * k + c];
       x[e] = 0.0;
       r[e] = (double)b;
       p[e] = b;
@@ -173,9 +175,12 @@ __global__ void k_cg_update_p(float* __restrict__ p, const double* __restrict__ 
   p[e] = (float)fma(S.beta[c], (double)p[e], r[e]);
 }
 
-__global__ void k_cg_store_x(const double* __restrict__ x, float* __restrict__ X, int64_t count) {
+__global__ void k_cg_store_x(const double* __restrict__ x, const int32_t* __restrict__ perm,
+                             float* __restrict__ X, int64_t n, int k) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < count) X[e] = (float)x[e];
+  if (e >= n * k) return;
+  const int64_t row = e / k;
+  X[(int64_t)perm[row] * k + (e - row * k)] = (float)x[e];
 }
 
 }  // namespace
@@ -245,7 +250,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   const int dot_threads = k * (kDotThreads / k);
   const int64_t rows_per_block = dot_threads / k;
   const int dot_blocks = (int)std::min<int64_t>(kDotBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
-  k_cg_init<<<dot_blocks, dot_threads, 0, st>>>(B, x, r, p, n, k, S.partial);
+  k_cg_init<<<dot_blocks, dot_threads, 0, st>>>(B, L->perm, x, r, p, n, k, S.partial);
   k_cg_init_scalars<<<1, kMaxK, 0, st>>>(S.partial, dot_blocks, k, tol, max_iter, S);
   note_launches(2);
   CG_CHECK(cudaGetLastError(), "CG init");
@@ -253,7 +258,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   cudaEvent_t* ev = L->profile ? L->prof_ev : nullptr;
   int passes = 0;
   auto iteration = [&]() {
-    passes = enqueue_mvm(L, p, k, blur, L->outputscale, noise, Ap, st, ev);
+    passes = enqueue_mvm(L, p, k, blur, L->outputscale, noise, Ap, st, ev, /*internal=*/true);
     k_coldot<<<dot_blocks, dot_threads, 0, st>>>(p, Ap, n, k, S.partial);
     k_cg_alpha<<<1, kMaxK, 0, st>>>(dot_blocks, k, S);
     k_cg_update_xr<<<dot_blocks, dot_threads, 0, st>>>(x, r, p, Ap, n, k, S);
@@ -293,7 +298,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
       }
     }
   }
-  k_cg_store_x<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(x, X, n * k);
+  k_cg_store_x<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(x, L->perm, X, n, k);
   note_launches(1);
   CG_CHECK(cudaGetLastError(), "CG result");
   std::vector<double> hrel(k);

@@ -134,7 +134,65 @@ __global__ void __launch_bounds__(kThreads) k_blur(int64_t m, int G, int k, int 
   Vt::st(out + v * k + col, acc);
 }
 
-template <int VEC, bool BETA>
+// Rows of k = 4 CH G floats: each thread owns CH consecutive float4 chunks of one row, so
+// it has 3 CH independent row loads in flight per stencil order after its two id loads.
+template <int CH>
+__global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k, int r,
+                                                        Taps tp,
+                                                        const int32_t* __restrict__ nbr,
+                                                        const float* __restrict__ in,
+                                                        float* __restrict__ out) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = gid / G;
+  if (v >= m) return;
+  const int col = (int)(gid - v * G) * (4 * CH);
+  int ia[kMaxOrder], ic[kMaxOrder];
+#pragma unroll
+  for (int t = 0; t < kMaxOrder; ++t) {
+    if (t < r) {
+      ia[t] = __ldg(nbr + (int64_t)(2 * t) * m + v);
+      ic[t] = __ldg(nbr + (int64_t)(2 * t + 1) * m + v);
+    }
+  }
+  float4 acc[CH];
+  const float4* own = reinterpret_cast<const float4*>(in + v * k + col);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const float4 x = __ldg(own + c);
+    acc[c] = make_float4(tp.t[0] * x.x, tp.t[0] * x.y, tp.t[0] * x.z, tp.t[0] * x.w);
+  }
+#pragma unroll
+  for (int t = 0; t < kMaxOrder; ++t) {
+    if (t >= r) break;
+    float4 sa[CH], sc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sa[c] = sc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ia[t] >= 0) {
+      const float4* pa = reinterpret_cast<const float4*>(in + (int64_t)ia[t] * k + col);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) sa[c] = __ldg(pa + c);
+    }
+    if (ic[t] >= 0) {
+      const float4* pc = reinterpret_cast<const float4*>(in + (int64_t)ic[t] * k + col);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) sc[c] = __ldg(pc + c);
+    }
+    const float w = tp.t[t + 1];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      acc[c].x = fmaf(w, sa[c].x + sc[c].x, acc[c].x);
+      acc[c].y = fmaf(w, sa[c].y + sc[c].y, acc[c].y);
+      acc[c].z = fmaf(w, sa[c].z + sc[c].z, acc[c].z);
+      acc[c].w = fmaf(w, sa[c].w + sc[c].w, acc[c].w);
+    }
+  }
+  float4* dst = reinterpret_cast<float4*>(out + v * k + col);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) dst[c] = acc[c];
+}
+
+// PERM: V and out rows are in the caller's order (row perm[p]); else in locality order.
+template <int VEC, bool BETA, bool PERM>
 __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int D,
                                                     const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ idx,
@@ -152,10 +210,24 @@ __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int
     const int64_t e = p * D + c;
     acc = Vt::fma(w[e], Vt::ld(lat + (int64_t)idx[e] * k + col), acc);
   }
-  const int64_t i = perm[p];
+  const int64_t i = PERM ? (int64_t)perm[p] : p;
   typename Vt::T res = Vt::scale(alpha, acc);
   if (BETA) res = Vt::fma(beta, Vt::ld(V + i * k + col), res);
   Vt::st(out + i * k + col, res);
+}
+
+// Vp[p] = V[perm[p]]: the caller's rows in locality order.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_permute_rows(int64_t n, int G, int k,
+                                                           const int32_t* __restrict__ perm,
+                                                           const float* __restrict__ V,
+                                                           float* __restrict__ Vp) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = gid / G;
+  if (p >= n) return;
+  const int col = (int)(gid - p * G) * VEC;
+  Vt::st(Vp + p * k + col, Vt::ld(V + (int64_t)perm[p] * k + col));
 }
 
 inline bool vec4_ok(int k, const void* a, const void* b) {
@@ -166,8 +238,8 @@ inline bool vec4_ok(int k, const void* a, const void* b) {
 
 sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
   const size_t need = (size_t)L->m * k;
-  if (L->lat_elems >= need && L->lat[0]) return SGP_OK;
-  float** bufs[3] = {&L->lat[0], &L->lat[1], &L->partial};
+  if (L->lat_elems >= need && L->lat[0] && L->vperm_elems >= (size_t)L->n * k) return SGP_OK;
+  float** bufs[4] = {&L->lat[0], &L->lat[1], &L->partial, &L->vperm};
   for (float** b : bufs) {
     if (*b) cudaFreeAsync(*b, st);
     *b = nullptr;
@@ -175,13 +247,15 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
   L->bytes -= L->lat_bytes;
   L->lat_bytes = 0;
   L->lat_elems = 0;
-  const size_t sizes[3] = {need, need, (size_t)L->nslots * k};
-  for (int b = 0; b < 3; ++b) {
+  L->vperm_elems = 0;
+  const size_t sizes[4] = {need, need, (size_t)L->nslots * k, (size_t)L->n * k};
+  for (int b = 0; b < 4; ++b) {
     cudaError_t e = cudaMallocAsync((void**)bufs[b], std::max<size_t>(sizes[b], 1) * sizeof(float), st);
     if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
   }
   L->lat_elems = need;
-  L->lat_bytes = (need * 2 + sizes[2]) * sizeof(float);
+  L->vperm_elems = sizes[3];
+  L->lat_bytes = (sizes[0] + sizes[1] + sizes[2] + sizes[3]) * sizeof(float);
   L->bytes += L->lat_bytes;
   return SGP_OK;
 }
@@ -220,10 +294,14 @@ void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStrea
 void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
                       int k, cudaStream_t st) {
   const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
-  if (k % 4 == 0) {
+  if (k % 8 == 0) {  // two float4 chunks (one 32-byte sector) per thread
+    const int G = k / 8;
+    k_blur_rows<2><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
+        L->m, G, k, L->r, taps, nbr, in, out);
+  } else if (k % 4 == 0) {
     const int G = k / 4;
-    k_blur<4><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(L->m, G, k, L->r, taps,
-                                                                          nbr, in, out);
+    k_blur_rows<1><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
+        L->m, G, k, L->r, taps, nbr, in, out);
   } else {
     k_blur<1><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, k, L->r, taps,
                                                                           nbr, in, out);
@@ -231,33 +309,51 @@ void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in
   note_launches(1);
 }
 
-void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
-                  float beta, float* out, cudaStream_t st) {
+template <bool PERM>
+void launch_slice_t(const Lattice* L, const float* lat, const float* V, int k, float alpha,
+                    float beta, float* out, cudaStream_t st) {
   const bool v4 = vec4_ok(k, out, V ? (const void*)V : (const void*)out);
   const int G = v4 ? k / 4 : k;
   const unsigned grid = (unsigned)ceil_div(L->n * G, kThreads);
   const bool use_beta = beta != 0.f && V != nullptr;
   if (v4) {
     if (use_beta)
-      k_slice<4, true><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
-                                                  alpha, beta, out);
+      k_slice<4, true, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                        lat, V, alpha, beta, out);
     else
-      k_slice<4, false><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
-                                                   alpha, beta, out);
+      k_slice<4, false, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                         lat, V, alpha, beta, out);
   } else {
     if (use_beta)
-      k_slice<1, true><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
-                                                  alpha, beta, out);
+      k_slice<1, true, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                        lat, V, alpha, beta, out);
     else
-      k_slice<1, false><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w, lat, V,
-                                                   alpha, beta, out);
+      k_slice<1, false, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                         lat, V, alpha, beta, out);
+  }
+  note_launches(1);
+}
+
+void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
+                  float beta, float* out, cudaStream_t st) {
+  launch_slice_t<true>(L, lat, V, k, alpha, beta, out, st);
+}
+
+void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStream_t st) {
+  if (vec4_ok(k, V, Vp)) {
+    const int G = k / 4;
+    k_permute_rows<4><<<(unsigned)ceil_div(L->n * G, kThreads), kThreads, 0, st>>>(
+        L->n, G, k, L->perm, V, Vp);
+  } else {
+    k_permute_rows<1><<<(unsigned)ceil_div(L->n * k, kThreads), kThreads, 0, st>>>(
+        L->n, k, k, L->perm, V, Vp);
   }
   note_launches(1);
 }
 
 // Enqueue the whole operator on `st`.  Lattice value buffers must already hold m*k.
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-                float* out, cudaStream_t st, cudaEvent_t* ev) {
+                float* out, cudaStream_t st, cudaEvent_t* ev, bool internal) {
   Taps c{}, g{};
   for (int t = 0; t <= L->r; ++t) {
     c.t[t] = (float)L->coef[t];
@@ -265,7 +361,12 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
   }
   float* a = L->lat[0];
   float* b = L->lat[1];
-  launch_splat(L, V, k, a, st);
+  const float* src = V;
+  if (!internal) {
+    launch_permute(L, V, k, L->vperm, st);
+    src = L->vperm;
+  }
+  launch_splat(L, src, k, a, st);
   // External: inside a stream capture this becomes an event-record node of the graph
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   const int D = L->D;
@@ -286,15 +387,18 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
     for (int j = D - 1; j >= 0; --j) pass(j, g);
   }
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  launch_slice(L, a, V, k, alpha, beta, out, st);
+  if (internal) launch_slice_t<false>(L, a, V, k, alpha, beta, out, st);
+  else launch_slice_t<true>(L, a, V, k, alpha, beta, out, st);
   return passes;
 }
 
 // Same operator as enqueue_mvm, with the two value buffers and the splat partials given
 // by the caller (used by the allocation-free entry point).
-void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
+void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, float alpha,
                       float beta, float* out, float* lat0, float* lat1, float* partial,
-                      cudaStream_t st) {
+                      float* vperm, cudaStream_t st) {
+  launch_permute(L, V_user, k, vperm, st);
+  const float* V = vperm;
   const bool v4 = vec4_ok(k, V, lat0);
   const int G = v4 ? k / 4 : k;
   if (v4)
@@ -344,7 +448,7 @@ void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float a
     for (int j = 0; j < D; ++j) pass(j, g);
     for (int j = D - 1; j >= 0; --j) pass(j, g);
   }
-  launch_slice(L, a, V, k, alpha, beta, out, st);
+  launch_slice(L, a, V_user, k, alpha, beta, out, st);
 }
 
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,

@@ -49,7 +49,7 @@ struct sgp_lattice {
   int32_t* idx = nullptr;    // [n][D] vertex id of vertex k of point perm[p]
   float* w = nullptr;        // [n][D] barycentric weight, same order
   int32_t* row_ptr = nullptr;  // [m+1] splat lists: vertex v gathers items[row_ptr[v]..]
-  int2* items = nullptr;       // [n*D] (caller's point index, weight bits)
+  int2* items = nullptr;       // [n*D] (locality-ordered point index p, weight bits)
   // Splat work split into segments of at most kSplatSeg items (load balance: a dense
   // cluster gives a vertex thousands of points).  seg[s] = (vertex, begin, end, slot):
   // slot < 0 writes the vertex directly, else the partial goes to partial[slot] and a
@@ -63,6 +63,7 @@ struct sgp_lattice {
   int64_t nhuge = 0;
   int64_t nslots = 0;
   float* partial = nullptr;  // [nslots][k], sized with the lattice values
+  float* vperm = nullptr;    // [n][k] the caller's V in locality order (public MVMs)
   int32_t* nbr = nullptr;      // [D][r][2][m] neighbour id of v - t u_j (0) / v + t u_j (1)
   int16_t* keys = nullptr;     // [m][D] vertex coordinates
   unsigned* err = nullptr;     // device error word
@@ -70,7 +71,8 @@ struct sgp_lattice {
   // Lattice values, allocated on first use and grown on demand.
   float* lat[2] = {nullptr, nullptr};
   size_t lat_elems = 0;
-  size_t lat_bytes = 0;  // value buffers + splat partials
+  size_t lat_bytes = 0;  // value buffers + splat partials + permuted input
+  size_t vperm_elems = 0;
 
   // Optional blur timing: events bracket the blur passes of one MVM inside the CG graph
   // and are read at every flag check (sgp_profile_blur / sgp_profile_read).
@@ -126,16 +128,18 @@ void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in
                       int k, cudaStream_t st);
 void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
                   float beta, float* out, cudaStream_t st);
-// Enqueue out = alpha * W B W^T V + beta * V on `st` (value buffers must be ready).  When
+// Enqueue out = alpha * W B W^T V + beta * V on `st` (value buffers must be ready).  With
+// internal = false, V and out are in the caller's point order (V is first permuted into
+// locality order); with internal = true both are already in locality order (CG).  When
 // `ev` is given, ev[0] / ev[1] are recorded around the blur passes.  Returns the number
 // of blur passes.
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-                float* out, cudaStream_t st, cudaEvent_t* ev = nullptr);
-// As enqueue_mvm, with caller-provided value buffers ([m][k] each) and splat partials
-// ([nslots][k]); allocates nothing.
+                float* out, cudaStream_t st, cudaEvent_t* ev = nullptr, bool internal = false);
+// As enqueue_mvm (caller's point order), with caller-provided value buffers ([m][k]
+// each), splat partials ([nslots][k]) and permuted input ([n][k]); allocates nothing.
 void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
                       float beta, float* out, float* lat0, float* lat1, float* partial,
-                      cudaStream_t st);
+                      float* vperm, cudaStream_t st);
 // Full operator on the handle's stream, allocating value buffers when needed.
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);

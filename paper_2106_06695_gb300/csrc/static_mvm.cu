@@ -59,7 +59,7 @@ extern "C" sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int 
               "SGP_BLUR_* operator");
     return SGP_ERR_INVALID_ARG;
   }
-  const size_t need = (2 * (size_t)h->m + (size_t)h->nslots) * (size_t)k;
+  const size_t need = (2 * (size_t)h->m + (size_t)h->nslots + (size_t)h->n) * (size_t)k;
   if (need > kStaticScratchFloats) {
     set_error("sgp_mvm_static: this lattice needs " + std::to_string(need * sizeof(float)) +
               " bytes of work space for k = " + std::to_string(k) +
@@ -77,7 +77,8 @@ extern "C" sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int 
   float* lat0 = base;
   float* lat1 = base + (size_t)h->m * k;
   float* partial = base + 2 * (size_t)h->m * k;
-  enqueue_mvm_into(h, V, k, blur, alpha, beta, out, lat0, lat1, partial, h->stream);
+  float* vperm = partial + (size_t)h->nslots * k;
+  enqueue_mvm_into(h, V, k, blur, alpha, beta, out, lat0, lat1, partial, vperm, h->stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "sgp_mvm_static: launching the lattice MVM");
   return SGP_OK;
