@@ -294,6 +294,19 @@ def run_ours(args, world, rank, local):
     e1.record()
     torch.cuda.synchronize()
     mvm_seq_ms = e0.elapsed_time(e1) / reps
+    ref_out = lat.mvm(Vd, blur=W["blur"]).double()
+    lat.close()
+    # the same product with the lattice values stored in bf16 (fp32 sums)
+    lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"], value_dtype="bf16")
+    for _ in range(3):
+        lat.mvm(Vd, blur=W["blur"], out=out)
+    e0.record()
+    for _ in range(reps):
+        lat.mvm(Vd, blur=W["blur"], out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    mvm_bf16_ms = e0.elapsed_time(e1) / reps
+    bf16_rel_err = ((out.double() - ref_out).norm() / ref_out.norm()).item()
     lat.close()
 
     e2e = None
@@ -338,6 +351,8 @@ def run_ours(args, world, rank, local):
                        "build_ms_median": float(np.median(prof["build_ms"])),
                        "mvm_symmetric_ms": mvm_ms, "mvm_sequential_ms": mvm_seq_ms,
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
+                       "mvm_symmetric_bf16_values_ms": mvm_bf16_ms,
+                       "bf16_values_rel_l2_vs_fp32": bf16_rel_err,
                        "l2": "no flush: every step's working set (X 88 MB, V 128 MB, "
                              "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -150,8 +150,9 @@ sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alp
                       float beta, float* out);
 
 /* As sgp_mvm_ex, but allocating no device memory: the lattice value buffers and splat
- * partials and the input in the lattice's point order ((2 m + nslots + n) k floats)
- * come from a 64 MiB work area compiled into the
+ * partials and the input in the lattice's point order (2 m k lattice values of the
+ * handle's value type plus (nslots + n) k floats) come from a 64 MiB work area compiled
+ * into the
  * library (a file-scope __device__ array, held by every GPU that loads the library until
  * the process exits).  The paper has no counterpart; this entry point exists for callers
  * that cannot allocate when they need a product: serving loops that must keep

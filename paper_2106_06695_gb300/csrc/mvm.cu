@@ -1,23 +1,97 @@
 // The lattice MVM  out = alpha * W B W^T V + beta * V  (Sec. 3.2, Eq. ski_to_bf).
 //
 //   k_splat  W^T: each lattice vertex gathers w * V[point] over its list of incident
-//            (point, weight) pairs.  A gather, so the result is deterministic.
+//            (point, weight) pairs, cut into segments of at most kSplatSeg items; long
+//            lists are finished by an ordered fix-up.  Gathers only: deterministic.
 //   k_blur   one lattice direction u_j: out[v] = c_0 in[v] + sum_t c_t (in[v - t u_j] +
 //            in[v + t u_j]) with absent neighbours contributing 0 (Sec. 3.2 "Blur"); the
 //            neighbour ids come from the table built with the lattice.
 //   k_slice  W: each point interpolates its d+1 vertices with its barycentric weights,
 //            fused with the alpha/beta epilogue.
 //
-// All three are bound by memory traffic.  Values are fp32 [rows][k] row-major; a thread
-// owns 4 consecutive columns of one row (16-byte vector loads) when k is a multiple of 4
-// and the caller's buffers are 16-byte aligned, else one column.
+// All of them are bound by memory traffic.  The caller's vectors are fp32 [rows][k]
+// row-major.  Lattice values are stored as S = float or __nv_bfloat16 (SGP_VALUES_BF16:
+// half the bytes of the dominant blur traffic); every sum is accumulated in fp32.  A
+// thread owns 4 consecutive columns of a row when k is a multiple of 4 and the buffers are
+// aligned, else one column; the blur gives each thread 8 columns when k allows.
+#include <cuda_bf16.h>
+
 #include "sgp_internal.cuh"
 
 namespace sgp {
 namespace {
 
+using bf16 = __nv_bfloat16;
 constexpr int kThreads = 256;
 
+// ---- storage of lattice values: groups of 4 (or 8) values as float4 ------------------
+template <class S>
+struct Store;
+
+template <>
+struct Store<float> {
+  static __device__ __forceinline__ float4 ld4(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+  }
+  static __device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+  }
+  static __device__ __forceinline__ void st4(float* p, float4 v) {
+    *reinterpret_cast<float4*>(p) = v;
+  }
+  static __device__ __forceinline__ void ldg8(const float* p, float4& a, float4& b) {
+    a = __ldg(reinterpret_cast<const float4*>(p));
+    b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  }
+  static __device__ __forceinline__ void st8(float* p, float4 a, float4 b) {
+    reinterpret_cast<float4*>(p)[0] = a;
+    reinterpret_cast<float4*>(p)[1] = b;
+  }
+  static __device__ __forceinline__ float ld1(const float* p) { return *p; }
+  static __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
+};
+
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+  __nv_bfloat162 h;
+  memcpy(&h, &u, 4);
+  return __bfloat1622float2(h);
+}
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+template <>
+struct Store<bf16> {
+  static __device__ __forceinline__ float4 cvt(uint2 u) {
+    const float2 a = unpack2(u.x), b = unpack2(u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ float4 ld4(const bf16* p) {
+    return cvt(*reinterpret_cast<const uint2*>(p));
+  }
+  static __device__ __forceinline__ float4 ldg4(const bf16* p) {
+    return cvt(__ldg(reinterpret_cast<const uint2*>(p)));
+  }
+  static __device__ __forceinline__ void st4(bf16* p, float4 v) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(pack2(v.x, v.y), pack2(v.z, v.w));
+  }
+  static __device__ __forceinline__ void ldg8(const bf16* p, float4& a, float4& b) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    a = cvt(make_uint2(u.x, u.y));
+    b = cvt(make_uint2(u.z, u.w));
+  }
+  static __device__ __forceinline__ void st8(bf16* p, float4 a, float4 b) {
+    *reinterpret_cast<uint4*>(p) =
+        make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
+  }
+  static __device__ __forceinline__ float ld1(const bf16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st1(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- fp32 register vectors of VEC = 4 or 1 columns ----------------------------------
 template <int VEC>
 struct Vec;
 template <>
@@ -26,6 +100,10 @@ struct Vec<4> {
   static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ T ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
   static __device__ __forceinline__ void st(float* p, T v) { *reinterpret_cast<float4*>(p) = v; }
+  template <class S>
+  static __device__ __forceinline__ T lds(const S* p) { return Store<S>::ld4(p); }
+  template <class S>
+  static __device__ __forceinline__ void sts(S* p, T v) { Store<S>::st4(p, v); }
   static __device__ __forceinline__ T fma(float a, T x, T y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
   }
@@ -42,18 +120,23 @@ struct Vec<1> {
   static __device__ __forceinline__ T zero() { return 0.f; }
   static __device__ __forceinline__ T ld(const float* p) { return *p; }
   static __device__ __forceinline__ void st(float* p, T v) { *p = v; }
+  template <class S>
+  static __device__ __forceinline__ T lds(const S* p) { return Store<S>::ld1(p); }
+  template <class S>
+  static __device__ __forceinline__ void sts(S* p, T v) { Store<S>::st1(p, v); }
   static __device__ __forceinline__ T fma(float a, T x, T y) { return fmaf(a, x, y); }
   static __device__ __forceinline__ T add(T x, T y) { return x + y; }
   static __device__ __forceinline__ T scale(float a, T x) { return a * x; }
 };
 
+// ---- splat ---------------------------------------------------------------------------
 // One thread-group of G threads per segment of at most kSplatSeg incidences.
-template <int VEC>
+template <int VEC, class S>
 __global__ void __launch_bounds__(kThreads) k_splat(int64_t nseg, int G, int k,
                                                     const int4* __restrict__ seg,
                                                     const int2* __restrict__ items,
                                                     const float* __restrict__ V,
-                                                    float* __restrict__ lat,
+                                                    S* __restrict__ lat,
                                                     float* __restrict__ partial) {
   using Vt = Vec<VEC>;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,16 +149,16 @@ __global__ void __launch_bounds__(kThreads) k_splat(int64_t nseg, int G, int k,
     const int2 it = items[p];
     acc = Vt::fma(__int_as_float(it.y), Vt::ld(V + (int64_t)it.x * k + col), acc);
   }
-  if (sg.w < 0) Vt::st(lat + (int64_t)sg.x * k + col, acc);
+  if (sg.w < 0) Vt::sts(lat + (int64_t)sg.x * k + col, acc);
   else Vt::st(partial + (int64_t)sg.w * k + col, acc);
 }
 
 // Fix-up for vertices with 2..kSplatMedSegs segments: one thread-group sums in order.
-template <int VEC>
+template <int VEC, class S>
 __global__ void __launch_bounds__(kThreads) k_splat_med(int64_t nrows, int G, int k,
                                                         const int4* __restrict__ rows,
                                                         const float* __restrict__ partial,
-                                                        float* __restrict__ lat) {
+                                                        S* __restrict__ lat) {
   using Vt = Vec<VEC>;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t q = gid / G;
@@ -84,15 +167,15 @@ __global__ void __launch_bounds__(kThreads) k_splat_med(int64_t nrows, int G, in
   const int4 rw = rows[q];
   typename Vt::T acc = Vt::zero();
   for (int j = 0; j < rw.z; ++j) acc = Vt::add(acc, Vt::ld(partial + (int64_t)(rw.y + j) * k + col));
-  Vt::st(lat + (int64_t)rw.x * k + col, acc);
+  Vt::sts(lat + (int64_t)rw.x * k + col, acc);
 }
 
 // Fix-up for vertices with more segments: one block per vertex, groups of G threads take
 // strided partials, then a fixed-shape shared-memory tree combines the groups.
-template <int VEC>
+template <int VEC, class S>
 __global__ void __launch_bounds__(kThreads) k_splat_huge(int G, int k, const int4* __restrict__ rows,
                                                          const float* __restrict__ partial,
-                                                         float* __restrict__ lat) {
+                                                         S* __restrict__ lat) {
   using Vt = Vec<VEC>;
   __shared__ typename Vt::T red[kThreads];
   const int groups = blockDim.x / G;
@@ -109,39 +192,40 @@ __global__ void __launch_bounds__(kThreads) k_splat_huge(int G, int k, const int
     if (g < half) red[threadIdx.x] = Vt::add(red[threadIdx.x], red[threadIdx.x + half * G]);
     __syncthreads();
   }
-  if (g == 0) Vt::st(lat + (int64_t)rw.x * k + col, red[threadIdx.x]);
+  if (g == 0) Vt::sts(lat + (int64_t)rw.x * k + col, red[threadIdx.x]);
 }
 
-template <int VEC>
-__global__ void __launch_bounds__(kThreads) k_blur(int64_t m, int G, int k, int r, Taps tp,
+// ---- blur ----------------------------------------------------------------------------
+// One value per thread (any k).
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_blur(int64_t m, int k, int r, Taps tp,
                                                    const int32_t* __restrict__ nbr,
-                                                   const float* __restrict__ in,
-                                                   float* __restrict__ out) {
-  using Vt = Vec<VEC>;
+                                                   const S* __restrict__ in, S* __restrict__ out) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t v = gid / G;
+  const int64_t v = gid / k;
   if (v >= m) return;
-  const int col = (int)(gid - v * G) * VEC;
-  typename Vt::T acc = Vt::scale(tp.t[0], Vt::ld(in + v * k + col));
+  const int col = (int)(gid - v * k);
+  float acc = tp.t[0] * Store<S>::ld1(in + v * k + col);
   for (int t = 1; t <= r; ++t) {
     const int a = nbr[(int64_t)(2 * (t - 1)) * m + v];
     const int c = nbr[(int64_t)(2 * (t - 1) + 1) * m + v];
-    typename Vt::T s = Vt::zero();
-    if (a >= 0) s = Vt::add(s, Vt::ld(in + (int64_t)a * k + col));
-    if (c >= 0) s = Vt::add(s, Vt::ld(in + (int64_t)c * k + col));
-    acc = Vt::fma(tp.t[t], s, acc);
+    float s = 0.f;
+    if (a >= 0) s += Store<S>::ld1(in + (int64_t)a * k + col);
+    if (c >= 0) s += Store<S>::ld1(in + (int64_t)c * k + col);
+    acc = fmaf(tp.t[t], s, acc);
   }
-  Vt::st(out + v * k + col, acc);
+  Store<S>::st1(out + v * k + col, acc);
 }
 
-// Rows of k = 4 CH G floats: each thread owns CH consecutive float4 chunks of one row, so
-// it has 3 CH independent row loads in flight per stencil order after its two id loads.
-template <int CH>
+// Rows of k = 4 CH G values: each thread owns 4 CH consecutive columns of one row and
+// issues its id loads first, then the own and neighbour row loads together.
+template <int CH, class S>
 __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k, int r,
                                                         Taps tp,
                                                         const int32_t* __restrict__ nbr,
-                                                        const float* __restrict__ in,
-                                                        float* __restrict__ out) {
+                                                        const S* __restrict__ in,
+                                                        S* __restrict__ out) {
+  static_assert(CH == 1 || CH == 2, "one or two groups of four columns per thread");
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t v = gid / G;
   if (v >= m) return;
@@ -154,29 +238,24 @@ __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k,
       ic[t] = __ldg(nbr + (int64_t)(2 * t + 1) * m + v);
     }
   }
+  auto load = [&](int64_t row, float4* x) {
+    if (CH == 2) Store<S>::ldg8(in + row * k + col, x[0], x[CH - 1]);
+    else x[0] = Store<S>::ldg4(in + row * k + col);
+  };
   float4 acc[CH];
-  const float4* own = reinterpret_cast<const float4*>(in + v * k + col);
+  load(v, acc);
 #pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const float4 x = __ldg(own + c);
-    acc[c] = make_float4(tp.t[0] * x.x, tp.t[0] * x.y, tp.t[0] * x.z, tp.t[0] * x.w);
-  }
+  for (int c = 0; c < CH; ++c)
+    acc[c] = make_float4(tp.t[0] * acc[c].x, tp.t[0] * acc[c].y, tp.t[0] * acc[c].z,
+                         tp.t[0] * acc[c].w);
 #pragma unroll
   for (int t = 0; t < kMaxOrder; ++t) {
     if (t >= r) break;
     float4 sa[CH], sc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) sa[c] = sc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ia[t] >= 0) {
-      const float4* pa = reinterpret_cast<const float4*>(in + (int64_t)ia[t] * k + col);
-#pragma unroll
-      for (int c = 0; c < CH; ++c) sa[c] = __ldg(pa + c);
-    }
-    if (ic[t] >= 0) {
-      const float4* pc = reinterpret_cast<const float4*>(in + (int64_t)ic[t] * k + col);
-#pragma unroll
-      for (int c = 0; c < CH; ++c) sc[c] = __ldg(pc + c);
-    }
+    if (ia[t] >= 0) load(ia[t], sa);
+    if (ic[t] >= 0) load(ic[t], sc);
     const float w = tp.t[t + 1];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -186,18 +265,18 @@ __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k,
       acc[c].w = fmaf(w, sa[c].w + sc[c].w, acc[c].w);
     }
   }
-  float4* dst = reinterpret_cast<float4*>(out + v * k + col);
-#pragma unroll
-  for (int c = 0; c < CH; ++c) dst[c] = acc[c];
+  if (CH == 2) Store<S>::st8(out + v * k + col, acc[0], acc[CH - 1]);
+  else Store<S>::st4(out + v * k + col, acc[0]);
 }
 
+// ---- slice ---------------------------------------------------------------------------
 // PERM: V and out rows are in the caller's order (row perm[p]); else in locality order.
-template <int VEC, bool BETA, bool PERM>
+template <int VEC, bool BETA, bool PERM, class S>
 __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int D,
                                                     const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ idx,
                                                     const float* __restrict__ w,
-                                                    const float* __restrict__ lat,
+                                                    const S* __restrict__ lat,
                                                     const float* __restrict__ V, float alpha,
                                                     float beta, float* __restrict__ out) {
   using Vt = Vec<VEC>;
@@ -208,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int
   typename Vt::T acc = Vt::zero();
   for (int c = 0; c < D; ++c) {
     const int64_t e = p * D + c;
-    acc = Vt::fma(w[e], Vt::ld(lat + (int64_t)idx[e] * k + col), acc);
+    acc = Vt::fma(w[e], Vt::lds(lat + (int64_t)idx[e] * k + col), acc);
   }
   const int64_t i = PERM ? (int64_t)perm[p] : p;
   typename Vt::T res = Vt::scale(alpha, acc);
@@ -234,83 +313,60 @@ inline bool vec4_ok(int k, const void* a, const void* b) {
   return (k % 4 == 0) && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
 }
 
-}  // namespace
-
-sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
-  const size_t need = (size_t)L->m * k;
-  if (L->lat_elems >= need && L->lat[0] && L->vperm_elems >= (size_t)L->n * k) return SGP_OK;
-  float** bufs[4] = {&L->lat[0], &L->lat[1], &L->partial, &L->vperm};
-  for (float** b : bufs) {
-    if (*b) cudaFreeAsync(*b, st);
-    *b = nullptr;
-  }
-  L->bytes -= L->lat_bytes;
-  L->lat_bytes = 0;
-  L->lat_elems = 0;
-  L->vperm_elems = 0;
-  const size_t sizes[4] = {need, need, (size_t)L->nslots * k, (size_t)L->n * k};
-  for (int b = 0; b < 4; ++b) {
-    cudaError_t e = cudaMallocAsync((void**)bufs[b], std::max<size_t>(sizes[b], 1) * sizeof(float), st);
-    if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
-  }
-  L->lat_elems = need;
-  L->vperm_elems = sizes[3];
-  L->lat_bytes = (sizes[0] + sizes[1] + sizes[2] + sizes[3]) * sizeof(float);
-  L->bytes += L->lat_bytes;
-  return SGP_OK;
-}
-
-void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStream_t st) {
+// ---- launchers -----------------------------------------------------------------------
+template <class S>
+void launch_splat_t(const Lattice* L, const float* V, int k, S* lat, float* partial,
+                    cudaStream_t st) {
   const bool v4 = vec4_ok(k, V, lat);
   const int G = v4 ? k / 4 : k;
   if (v4)
-    k_splat<4><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
-        L->nseg, G, k, L->seg, L->items, V, lat, L->partial);
+    k_splat<4, S><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat, partial);
   else
-    k_splat<1><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
-        L->nseg, G, k, L->seg, L->items, V, lat, L->partial);
+    k_splat<1, S><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
+        L->nseg, G, k, L->seg, L->items, V, lat, partial);
   note_launches(1);
   if (L->nmed > 0) {
     if (v4)
-      k_splat_med<4><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
-          L->nmed, G, k, L->med_rows, L->partial, lat);
+      k_splat_med<4, S><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, partial, lat);
     else
-      k_splat_med<1><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
-          L->nmed, G, k, L->med_rows, L->partial, lat);
+      k_splat_med<1, S><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
+          L->nmed, G, k, L->med_rows, partial, lat);
     note_launches(1);
   }
   if (L->nhuge > 0) {
-    // a power-of-two number of G-thread groups per block for the tree
-    int groups = 1;
+    int groups = 1;  // a power-of-two number of G-thread groups per block for the tree
     while (groups * 2 * G <= kThreads) groups *= 2;
     if (v4)
-      k_splat_huge<4><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, L->partial, lat);
+      k_splat_huge<4, S><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat);
     else
-      k_splat_huge<1><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, L->partial, lat);
+      k_splat_huge<1, S><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat);
     note_launches(1);
   }
 }
 
-void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
-                      int k, cudaStream_t st) {
+template <class S>
+void launch_blur_t(const Lattice* L, int j, const Taps& taps, const S* in, S* out, int k,
+                   cudaStream_t st) {
   const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
-  if (k % 8 == 0) {  // two float4 chunks (one 32-byte sector) per thread
+  if (k % 8 == 0) {  // eight columns per thread
     const int G = k / 8;
-    k_blur_rows<2><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
+    k_blur_rows<2, S><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
         L->m, G, k, L->r, taps, nbr, in, out);
   } else if (k % 4 == 0) {
     const int G = k / 4;
-    k_blur_rows<1><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
+    k_blur_rows<1, S><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
         L->m, G, k, L->r, taps, nbr, in, out);
   } else {
-    k_blur<1><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, k, L->r, taps,
-                                                                          nbr, in, out);
+    k_blur<S><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, L->r, taps, nbr,
+                                                                          in, out);
   }
   note_launches(1);
 }
 
-template <bool PERM>
-void launch_slice_t(const Lattice* L, const float* lat, const float* V, int k, float alpha,
+template <bool PERM, class S>
+void launch_slice_t(const Lattice* L, const S* lat, const float* V, int k, float alpha,
                     float beta, float* out, cudaStream_t st) {
   const bool v4 = vec4_ok(k, out, V ? (const void*)V : (const void*)out);
   const int G = v4 ? k / 4 : k;
@@ -318,25 +374,20 @@ void launch_slice_t(const Lattice* L, const float* lat, const float* V, int k, f
   const bool use_beta = beta != 0.f && V != nullptr;
   if (v4) {
     if (use_beta)
-      k_slice<4, true, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
-                                                        lat, V, alpha, beta, out);
+      k_slice<4, true, PERM, S><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                           lat, V, alpha, beta, out);
     else
-      k_slice<4, false, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
-                                                         lat, V, alpha, beta, out);
+      k_slice<4, false, PERM, S><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx,
+                                                            L->w, lat, V, alpha, beta, out);
   } else {
     if (use_beta)
-      k_slice<1, true, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
-                                                        lat, V, alpha, beta, out);
+      k_slice<1, true, PERM, S><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
+                                                           lat, V, alpha, beta, out);
     else
-      k_slice<1, false, PERM><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx, L->w,
-                                                         lat, V, alpha, beta, out);
+      k_slice<1, false, PERM, S><<<grid, kThreads, 0, st>>>(L->n, G, k, L->D, L->perm, L->idx,
+                                                            L->w, lat, V, alpha, beta, out);
   }
   note_launches(1);
-}
-
-void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
-                  float beta, float* out, cudaStream_t st) {
-  launch_slice_t<true>(L, lat, V, k, alpha, beta, out, st);
 }
 
 void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStream_t st) {
@@ -351,33 +402,36 @@ void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStre
   note_launches(1);
 }
 
-// Enqueue the whole operator on `st`.  Lattice value buffers must already hold m*k.
-int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-                float* out, cudaStream_t st, cudaEvent_t* ev, bool internal) {
+// The whole operator with explicit buffers.  internal: V and out in locality order;
+// else V and out are in the caller's order and V is first gathered into `vperm`.
+template <class S>
+int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+              float* out, S* lat0, S* lat1, float* partial, float* vperm, cudaStream_t st,
+              cudaEvent_t* ev, bool internal) {
   Taps c{}, g{};
   for (int t = 0; t <= L->r; ++t) {
     c.t[t] = (float)L->coef[t];
     g.t[t] = (float)L->half[t];
   }
-  float* a = L->lat[0];
-  float* b = L->lat[1];
   const float* src = V;
   if (!internal) {
-    launch_permute(L, V, k, L->vperm, st);
-    src = L->vperm;
+    launch_permute(L, V, k, vperm, st);
+    src = vperm;
   }
-  launch_splat(L, src, k, a, st);
+  launch_splat_t<S>(L, src, k, lat0, partial, st);
   // External: inside a stream capture this becomes an event-record node of the graph
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-  const int D = L->D;
+  S* a = lat0;
+  S* b = lat1;
   int passes = 0;
   auto pass = [&](int j, const Taps& tp) {
-    launch_blur_pass(L, j, tp, a, b, k, st);
-    float* t = a;
+    launch_blur_t<S>(L, j, tp, a, b, k, st);
+    S* t = a;
     a = b;
     b = t;
     ++passes;
   };
+  const int D = L->D;
   if (blur == SGP_BLUR_SEQUENTIAL) {
     for (int j = 0; j < D; ++j) pass(j, c);
   } else if (blur == SGP_BLUR_TRANSPOSE) {
@@ -387,68 +441,74 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
     for (int j = D - 1; j >= 0; --j) pass(j, g);
   }
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  if (internal) launch_slice_t<false>(L, a, V, k, alpha, beta, out, st);
-  else launch_slice_t<true>(L, a, V, k, alpha, beta, out, st);
+  if (internal) launch_slice_t<false, S>(L, a, V, k, alpha, beta, out, st);
+  else launch_slice_t<true, S>(L, a, V, k, alpha, beta, out, st);
   return passes;
 }
 
-// Same operator as enqueue_mvm, with the two value buffers and the splat partials given
-// by the caller (used by the allocation-free entry point).
+size_t value_size(const Lattice* L) {
+  return L->value_dtype == SGP_VALUES_BF16 ? sizeof(bf16) : sizeof(float);
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t mvm_work_bytes(const Lattice* L, int k) {
+  return 2 * round256((size_t)L->m * k * value_size(L)) +
+         round256((size_t)L->nslots * k * sizeof(float)) + round256((size_t)L->n * k * sizeof(float));
+}
+
+sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
+  if (L->lat_elems >= (size_t)L->m * k && L->lat[0] && L->vperm_elems >= (size_t)L->n * k)
+    return SGP_OK;
+  void** bufs[4] = {(void**)&L->lat[0], (void**)&L->lat[1], (void**)&L->partial,
+                    (void**)&L->vperm};
+  for (void** b : bufs) {
+    if (*b) cudaFreeAsync(*b, st);
+    *b = nullptr;
+  }
+  L->bytes -= L->lat_bytes;
+  L->lat_bytes = 0;
+  L->lat_elems = 0;
+  L->vperm_elems = 0;
+  const size_t vbytes = (size_t)L->m * k * value_size(L);
+  const size_t sizes[4] = {vbytes, vbytes, (size_t)L->nslots * k * sizeof(float),
+                           (size_t)L->n * k * sizeof(float)};
+  for (int b = 0; b < 4; ++b) {
+    cudaError_t e = cudaMallocAsync(bufs[b], std::max<size_t>(sizes[b], 16), st);
+    if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
+  }
+  L->lat_elems = (size_t)L->m * k;
+  L->vperm_elems = (size_t)L->n * k;
+  L->lat_bytes = sizes[0] + sizes[1] + sizes[2] + sizes[3];
+  L->bytes += L->lat_bytes;
+  return SGP_OK;
+}
+
+int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+                float* out, cudaStream_t st, cudaEvent_t* ev, bool internal) {
+  if (L->value_dtype == SGP_VALUES_BF16)
+    return enqueue_t<bf16>(L, V, k, blur, alpha, beta, out, (bf16*)L->lat[0], (bf16*)L->lat[1],
+                           L->partial, L->vperm, st, ev, internal);
+  return enqueue_t<float>(L, V, k, blur, alpha, beta, out, (float*)L->lat[0], (float*)L->lat[1],
+                          L->partial, L->vperm, st, ev, internal);
+}
+
 void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, float alpha,
-                      float beta, float* out, float* lat0, float* lat1, float* partial,
-                      float* vperm, cudaStream_t st) {
-  launch_permute(L, V_user, k, vperm, st);
-  const float* V = vperm;
-  const bool v4 = vec4_ok(k, V, lat0);
-  const int G = v4 ? k / 4 : k;
-  if (v4)
-    k_splat<4><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
-        L->nseg, G, k, L->seg, L->items, V, lat0, partial);
+                      float beta, float* out, void* work, cudaStream_t st) {
+  char* w = static_cast<char*>(work);
+  const size_t vb = round256((size_t)L->m * k * value_size(L));
+  void* lat0 = w;
+  void* lat1 = w + vb;
+  float* partial = reinterpret_cast<float*>(w + 2 * vb);
+  float* vperm = reinterpret_cast<float*>(w + 2 * vb + round256((size_t)L->nslots * k * sizeof(float)));
+  if (L->value_dtype == SGP_VALUES_BF16)
+    enqueue_t<bf16>(L, V_user, k, blur, alpha, beta, out, (bf16*)lat0, (bf16*)lat1, partial, vperm,
+                    st, nullptr, false);
   else
-    k_splat<1><<<(unsigned)ceil_div(L->nseg * G, kThreads), kThreads, 0, st>>>(
-        L->nseg, G, k, L->seg, L->items, V, lat0, partial);
-  note_launches(1);
-  if (L->nmed > 0) {
-    if (v4)
-      k_splat_med<4><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
-          L->nmed, G, k, L->med_rows, partial, lat0);
-    else
-      k_splat_med<1><<<(unsigned)ceil_div(L->nmed * G, kThreads), kThreads, 0, st>>>(
-          L->nmed, G, k, L->med_rows, partial, lat0);
-    note_launches(1);
-  }
-  if (L->nhuge > 0) {
-    int groups = 1;
-    while (groups * 2 * G <= kThreads) groups *= 2;
-    if (v4)
-      k_splat_huge<4><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat0);
-    else
-      k_splat_huge<1><<<(unsigned)L->nhuge, groups * G, 0, st>>>(G, k, L->huge_rows, partial, lat0);
-    note_launches(1);
-  }
-  Taps c{}, g{};
-  for (int t = 0; t <= L->r; ++t) {
-    c.t[t] = (float)L->coef[t];
-    g.t[t] = (float)L->half[t];
-  }
-  float* a = lat0;
-  float* b = lat1;
-  auto pass = [&](int j, const Taps& tp) {
-    launch_blur_pass(L, j, tp, a, b, k, st);
-    float* t = a;
-    a = b;
-    b = t;
-  };
-  const int D = L->D;
-  if (blur == SGP_BLUR_SEQUENTIAL) {
-    for (int j = 0; j < D; ++j) pass(j, c);
-  } else if (blur == SGP_BLUR_TRANSPOSE) {
-    for (int j = D - 1; j >= 0; --j) pass(j, c);
-  } else {
-    for (int j = 0; j < D; ++j) pass(j, g);
-    for (int j = D - 1; j >= 0; --j) pass(j, g);
-  }
-  launch_slice(L, a, V_user, k, alpha, beta, out, st);
+    enqueue_t<float>(L, V_user, k, blur, alpha, beta, out, (float*)lat0, (float*)lat1, partial,
+                     vperm, st, nullptr, false);
 }
 
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,

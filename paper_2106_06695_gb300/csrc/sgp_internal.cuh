@@ -68,8 +68,8 @@ struct sgp_lattice {
   int16_t* keys = nullptr;     // [m][D] vertex coordinates
   unsigned* err = nullptr;     // device error word
 
-  // Lattice values, allocated on first use and grown on demand.
-  float* lat[2] = {nullptr, nullptr};
+  // Lattice values (fp32 or bf16 per value_dtype), allocated on first use, grown on demand.
+  void* lat[2] = {nullptr, nullptr};
   size_t lat_elems = 0;
   size_t lat_bytes = 0;  // value buffers + splat partials + permuted input
   size_t vperm_elems = 0;
@@ -121,25 +121,23 @@ bool radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
 sgp_status build_lattice(Lattice* L, const float* X, const float* ls);
 
 // ---- MVM (mvm.cu) ----
-// Make sure the two lattice value buffers hold m * k floats (allocated on `st`).
+// Make sure the lattice value buffers, splat partials and permuted-input buffer hold
+// what a k-column product needs (allocated on `st`).
 sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st);
-void launch_splat(const Lattice* L, const float* V, int k, float* lat, cudaStream_t st);
-void launch_blur_pass(const Lattice* L, int j, const Taps& taps, const float* in, float* out,
-                      int k, cudaStream_t st);
-void launch_slice(const Lattice* L, const float* lat, const float* V, int k, float alpha,
-                  float beta, float* out, cudaStream_t st);
-// Enqueue out = alpha * W B W^T V + beta * V on `st` (value buffers must be ready).  With
+// Enqueue out = alpha * W B W^T V + beta * V on `st` (buffers must be ready).  With
 // internal = false, V and out are in the caller's point order (V is first permuted into
 // locality order); with internal = true both are already in locality order (CG).  When
 // `ev` is given, ev[0] / ev[1] are recorded around the blur passes.  Returns the number
 // of blur passes.
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                 float* out, cudaStream_t st, cudaEvent_t* ev = nullptr, bool internal = false);
-// As enqueue_mvm (caller's point order), with caller-provided value buffers ([m][k]
-// each), splat partials ([nslots][k]) and permuted input ([n][k]); allocates nothing.
+// Bytes of work space one k-column product needs (value buffers, partials, permuted
+// input, each rounded up to 256 bytes).
+size_t mvm_work_bytes(const Lattice* L, int k);
+// As enqueue_mvm (caller's point order) with all work space carved out of `work`
+// (mvm_work_bytes(L, k) bytes, 256-byte aligned); allocates nothing.
 void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
-                      float beta, float* out, float* lat0, float* lat1, float* partial,
-                      float* vperm, cudaStream_t st);
+                      float beta, float* out, void* work, cudaStream_t st);
 // Full operator on the handle's stream, allocating value buffers when needed.
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);

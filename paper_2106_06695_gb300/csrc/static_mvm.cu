@@ -59,9 +59,9 @@ extern "C" sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int 
               "SGP_BLUR_* operator");
     return SGP_ERR_INVALID_ARG;
   }
-  const size_t need = (2 * (size_t)h->m + (size_t)h->nslots + (size_t)h->n) * (size_t)k;
-  if (need > kStaticScratchFloats) {
-    set_error("sgp_mvm_static: this lattice needs " + std::to_string(need * sizeof(float)) +
+  const size_t need = mvm_work_bytes(h, k);
+  if (need > kStaticScratchBytes) {
+    set_error("sgp_mvm_static: this lattice needs " + std::to_string(need) +
               " bytes of work space for k = " + std::to_string(k) +
               ", more than the 64 MiB static work area");
     return SGP_ERR_INVALID_ARG;
@@ -72,13 +72,9 @@ extern "C" sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int 
   if (e != cudaSuccess) return cuda_status(e, "sgp_mvm_static: cudaGetDevice");
   float* base = nullptr;
   if (sgp_status s = scratch_address(dev, &base)) return s;
-  // Every element of the value buffers and partials is written before it is read, so
-  // the contents left by an earlier call need no clearing.
-  float* lat0 = base;
-  float* lat1 = base + (size_t)h->m * k;
-  float* partial = base + 2 * (size_t)h->m * k;
-  float* vperm = partial + (size_t)h->nslots * k;
-  enqueue_mvm_into(h, V, k, blur, alpha, beta, out, lat0, lat1, partial, vperm, h->stream);
+  // Every element of the value buffers, partials and permuted input is written before it
+  // is read, so the contents left by an earlier call need no clearing.
+  enqueue_mvm_into(h, V, k, blur, alpha, beta, out, base, h->stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "sgp_mvm_static: launching the lattice MVM");
   return SGP_OK;
