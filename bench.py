@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default 2,000,000)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=WORKLOAD["max_iter"],
+                    help="CG iteration cap (default 500; lower only for profiling runs)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
                     help="profiling aid: build once, run R symmetric MVMs, print their time")
     return ap.parse_args(argv)
@@ -167,9 +169,9 @@ def blur_traffic_per_launch(m: int, k: int):
     except (OSError, KeyError, ValueError):
         return None
     src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu")).read()
-    body = re.search(r"template <int CH>\n__global__ void __launch_bounds__\(kThreads\) "
-                     r"k_blur_rows\(.*?\n}\n", src, re.S)
-    if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("k_blur_src_sha1")
+    body = re.search(r"template <int CH, int U, int R, class S>\n__global__ void "
+                     r"__launch_bounds__\(kThreads\) k_blur_rows\(.*?\n}\n", src, re.S)
+    if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("k_blur_rows_src_sha1")
             or rec.get("k") != k):
         return None
     return float(rec["bytes_per_vertex"]) * m
@@ -190,7 +192,7 @@ def run_ours(args, world, rank, local):
     init_dist(world, "nccl")
     build_lib.build()
     lib = _lib.load()
-    W = dict(WORKLOAD, n=args.n)
+    W = dict(WORKLOAD, n=args.n, max_iter=args.max_iter)
     n, d, k = W["n"], W["d"], W["k"]
     Xh = torch.from_numpy(synth.gmm_points(n, d, W["seed"])).pin_memory()
     Vh = torch.from_numpy(synth.gaussian_values(n, k, W["seed"])).pin_memory()
@@ -263,7 +265,7 @@ def run_ours(args, world, rank, local):
     avg_pass_ms = prof["ms"] / max(prof["passes"], 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9 if prof["passes"] else None
     traffic = blur_traffic_per_launch(m, k)
-    roofline = {"kernel": "k_blur_rows<2> (one lattice direction)", "bound": "hbm",
+    roofline = {"kernel": "k_blur_rows<2,2,1,float> (one lattice direction)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",

@@ -173,9 +173,11 @@ sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int blur, float
  *   (outputscale * W B W^T + noise_var I) X = B,   B = SGP_BLUR_SYMMETRIC,
  * every column independent: column c stops when ||r_c|| / ||b_c|| <= tol (recurrence
  * residual), after max_iter iterations, or when <p_c, A p_c> <= 0.  The iterate and the
- * residual are kept in fp64 on the device, the search direction and its product in fp32
- * (the MVM operands); dot products and norms are accumulated in fp64.  Work space:
- * 24 n k bytes plus the handle's lattice value buffers, allocated per call.
+ * residual are carried on the device as double-float pairs (two fp32 numbers, about 48
+ * significant bits), the search direction and its product in fp32 (the MVM operands);
+ * dot products and norms are accumulated in double-float per thread and fp64 across
+ * threads.  Work space: 24 n k bytes plus the handle's lattice value buffers, allocated
+ * per call.
  *   B      device [n][k] fp32;  X device [n][k] fp32 (solution; must not alias B).
  *   iters  host [k] int (iterations per column) or NULL;
  *   rel_res host [k] double (final recurrence residual ratio per column) or NULL.

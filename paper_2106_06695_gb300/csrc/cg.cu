@@ -4,11 +4,12 @@
 // Every right-hand side c is an independent CG with its own scalars; a column that has
 // converged (||r_c|| / ||b_c|| <= tol), hit max_iter or broken down (<p, Ap> <= 0) is
 // frozen by a device-side flag, so extra iterations leave it unchanged.  The iterate x and
-// the residual r are kept in fp64 [n][k] (their recurrences are where fp32 rounding makes
-// CG lose orthogonality); the search direction p and A p are fp32, the operands of the
-// lattice MVM.  Dot products and norms are accumulated in fp64 per block (fixed column per
-// thread, shared-memory tree) and the block partials are summed in a fixed order by one
-// small kernel, so the result does not depend on scheduling.  One iteration is captured
+// the residual r (whose recurrences are where fp32 rounding makes CG lose orthogonality)
+// carry ~48 bits as double-float pairs (hi + lo fp32, updated with error-free
+// transformations: FP64 arithmetic is slow on this part); the search direction p and A p
+// are fp32, the operands of the lattice MVM.  Dot products are accumulated per thread in
+// double-float, per block and across blocks in fp64 in a fixed order (fixed column per
+// thread, shared-memory tree), so the result does not depend on scheduling.  One iteration is captured
 // in a CUDA graph and replayed; the host reads the flags every check_every iterations.
 #include <algorithm>
 #include <cmath>
@@ -19,11 +20,8 @@
 namespace sgp {
 namespace {
 
-constexpr int kDotThreads = 256;
-constexpr int kDotBlocks = 4 * 152;
-
 struct CgState {
-  double* partial;  // [kDotBlocks][k]
+  double* partial;  // [blocks][k] per-block column sums
   double* rho;      // <r, r> of the current residual
   double* pap;      // <p, A p>
   double* alpha;
@@ -34,48 +32,84 @@ struct CgState {
   int* iters;
 };
 
-// Column-fixed grid-stride mapping: blockDim = k * (kDotThreads / k) threads, so thread t
-// always handles column t % k.
-__device__ __forceinline__ void column_partial(double acc, int k, double* partial) {
-  __shared__ double s[kDotThreads];
-  s[threadIdx.x] = acc;
-  __syncthreads();
-  if ((int)threadIdx.x < k) {
-    double t = 0.0;
-    for (int j = threadIdx.x; j < (int)blockDim.x; j += k) t += s[j];
-    partial[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+// VEC consecutive elements of a row: fp32 (one float4 when VEC = 4) and fp64 (two double2).
+template <int VEC>
+__device__ __forceinline__ void ldf(const float* p, float (&v)[VEC]) {
+  if (VEC == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[VEC - 1] = t.w;
+  } else {
+    v[0] = *p;
   }
 }
+template <int VEC>
+__device__ __forceinline__ void stf(float* p, const float (&v)[VEC]) {
+  if (VEC == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[VEC - 1]);
+  else *p = v[0];
+}
+// Grid-stride over rows with a fixed column group per thread: G = k / VEC threads per row,
+// blockDim.x = a whole number of rows.
+#define SGP_ROWS_LOOP(row)                                                                  \
+  const int G = k / VEC;                                                                    \
+  const int rows_per_block = blockDim.x / G;                                                \
+  const int c0 = (int)(threadIdx.x % G) * VEC;                                              \
+  for (int64_t row = (int64_t)blockIdx.x * rows_per_block + threadIdx.x / G; row < n;       \
+       row += (int64_t)gridDim.x * rows_per_block)
 
 // The solver's vectors live in the lattice's locality order: row p holds the caller's
-// row perm[p], so the MVM's splat gathers and slice writes stay local.
+// row perm[p], so the MVM's splat gathers and slice writes stay local.  B and X are the
+// caller's buffers (any alignment): read and written element by element.
+template <int VEC>
 __global__ void k_cg_init(const float* __restrict__ B, const int32_t* __restrict__ perm,
-                          double* __restrict__ x, double* __restrict__ r, float* __restrict__ p,
+                          float* __restrict__ xh, float* __restrict__ xl,
+                          float* __restrict__ rh, float* __restrict__ rl, float* __restrict__ p,
                           int64_t n, int k, double* __restrict__ partial) {
-  const int rows_per_block = blockDim.x / k;
-  const int c = threadIdx.x % k;
-  const int row0 = threadIdx.x / k;
-  double acc = 0.0;
-  if ((int)threadIdx.x < rows_per_block * k) {
-    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + row0; row < n;
-         row += (int64_t)gridDim.x * rows_per_block) {
-      const int64_t e = row * k + c;
-      const float b = B[(int64_t)perm[row] * k + c];
-      x[e] = 0.0;
-      r[e] = (double)b;
-      p[e] = b;
-      acc += (double)b * (double)b;
+  dfloat acc[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) acc[j] = {0.f, 0.f};
+  SGP_ROWS_LOOP(row) {
+    const float* b = B + (int64_t)perm[row] * k + c0;
+    float bv[VEC], zero[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      bv[j] = b[j];
+      zero[j] = 0.f;
+      acc[j] = df_add(acc[j], df_two_prod(bv[j], bv[j]));
     }
+    const int64_t e = row * k + c0;
+    stf<VEC>(xh + e, zero);
+    stf<VEC>(xl + e, zero);
+    stf<VEC>(rh + e, bv);
+    stf<VEC>(rl + e, zero);
+    stf<VEC>(p + e, bv);
   }
-  column_partial(acc, k, partial);
+  double dd[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) dd[j] = df_to_double(acc[j]);
+  block_column_sums<VEC>(dd, k, partial + (int64_t)blockIdx.x * k);
+}
+
+// Column c's sum over `nblk` block partials, in a fixed order (strided per thread, then a
+// shared-memory tree); blockIdx.x = c, blockDim.x = 256.
+__device__ __forceinline__ double column_total(const double* __restrict__ partial, int nblk, int k) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += partial[(int64_t)b * k + c];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int half = blockDim.x / 2; half >= 1; half /= 2) {
+    if ((int)threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
+    __syncthreads();
+  }
+  return red[0];
 }
 
 __global__ void k_cg_init_scalars(const double* __restrict__ partial, int nblk, int k,
                                   float tol, int max_iter, CgState S) {
-  const int c = threadIdx.x;
-  if (c >= k) return;
-  double rr = 0.0;
-  for (int b = 0; b < nblk; ++b) rr += partial[(int64_t)b * k + c];
+  const double rr = column_total(partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
   S.rho[c] = rr;
   S.bnorm[c] = sqrt(rr);
   S.iters[c] = 0;
@@ -90,27 +124,11 @@ __global__ void k_cg_init_scalars(const double* __restrict__ partial, int nblk, 
   }
 }
 
-__global__ void k_coldot(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
-                         int k, double* __restrict__ partial) {
-  const int rows_per_block = blockDim.x / k;
-  const int c = threadIdx.x % k;
-  const int row0 = threadIdx.x / k;
-  double acc = 0.0;
-  if ((int)threadIdx.x < rows_per_block * k) {
-    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + row0; row < n;
-         row += (int64_t)gridDim.x * rows_per_block) {
-      const int64_t e = row * k + c;
-      acc += (double)a[e] * (double)b[e];
-    }
-  }
-  column_partial(acc, k, partial);
-}
-
+// <p, A p> from the slice's block partials, then alpha = rho / <p, A p>.
 __global__ void k_cg_alpha(int nblk, int k, CgState S) {
-  const int c = threadIdx.x;
-  if (c >= k) return;
-  double pap = 0.0;
-  for (int b = 0; b < nblk; ++b) pap += S.partial[(int64_t)b * k + c];
+  const double pap = column_total(S.partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
   S.pap[c] = pap;
   double alpha = 0.0;
   if (S.active[c]) {
@@ -123,37 +141,60 @@ __global__ void k_cg_alpha(int nblk, int k, CgState S) {
   S.alpha[c] = alpha;
 }
 
-__global__ void k_cg_update_xr(double* __restrict__ x, double* __restrict__ r,
+// x += alpha p, r -= alpha A p on active columns (double-float); block partials of <r, r>.
+template <int VEC>
+__global__ void k_cg_update_xr(float* __restrict__ xh, float* __restrict__ xl,
+                               float* __restrict__ rh, float* __restrict__ rl,
                                const float* __restrict__ p, const float* __restrict__ Ap,
                                int64_t n, int k, CgState S) {
-  const int rows_per_block = blockDim.x / k;
-  const int c = threadIdx.x % k;
-  const int row0 = threadIdx.x / k;
-  double acc = 0.0;
-  if ((int)threadIdx.x < rows_per_block * k) {
-    const bool on = S.active[c] != 0;
-    const double a = S.alpha[c];
-    for (int64_t row = (int64_t)blockIdx.x * rows_per_block + row0; row < n;
-         row += (int64_t)gridDim.x * rows_per_block) {
-      const int64_t e = row * k + c;
-      double rv = r[e];
-      if (on) {
-        x[e] = fma(a, (double)p[e], x[e]);
-        rv = fma(-a, (double)Ap[e], rv);
-        r[e] = rv;
-      }
-      acc += rv * rv;
+  dfloat acc[VEC], a[VEC], na[VEC];
+  bool on[VEC];
+  {
+    const int c = (int)(threadIdx.x % (k / VEC)) * VEC;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      acc[j] = {0.f, 0.f};
+      on[j] = S.active[c + j] != 0;
+      a[j] = df_from_double(S.alpha[c + j]);
+      na[j] = {-a[j].hi, -a[j].lo};
     }
   }
-  column_partial(acc, k, S.partial);
+  SGP_ROWS_LOOP(row) {
+    const int64_t e = row * k + c0;
+    float pv[VEC], qv[VEC], xhv[VEC], xlv[VEC], rhv[VEC], rlv[VEC];
+    ldf<VEC>(p + e, pv);
+    ldf<VEC>(Ap + e, qv);
+    ldf<VEC>(xh + e, xhv);
+    ldf<VEC>(xl + e, xlv);
+    ldf<VEC>(rh + e, rhv);
+    ldf<VEC>(rl + e, rlv);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (on[j]) {
+        const dfloat x = df_add({xhv[j], xlv[j]}, df_mul_f(a[j], pv[j]));
+        const dfloat r = df_add({rhv[j], rlv[j]}, df_mul_f(na[j], qv[j]));
+        xhv[j] = x.hi, xlv[j] = x.lo, rhv[j] = r.hi, rlv[j] = r.lo;
+      }
+      dfloat sq = df_two_prod(rhv[j], rhv[j]);
+      sq = df_fast_two_sum(sq.hi, __fmaf_rn(2.f * rhv[j], rlv[j], sq.lo));
+      acc[j] = df_add(acc[j], sq);
+    }
+    stf<VEC>(xh + e, xhv);
+    stf<VEC>(xl + e, xlv);
+    stf<VEC>(rh + e, rhv);
+    stf<VEC>(rl + e, rlv);
+  }
+  double dd[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) dd[j] = df_to_double(acc[j]);
+  block_column_sums<VEC>(dd, k, S.partial + (int64_t)blockIdx.x * k);
 }
 
 __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
-  const int c = threadIdx.x;
-  if (c >= k) return;
+  const double rr = column_total(S.partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
   if (!S.active[c]) return;
-  double rr = 0.0;
-  for (int b = 0; b < nblk; ++b) rr += S.partial[(int64_t)b * k + c];
   const int it = S.iters[c] + 1;
   S.iters[c] = it;
   const double rel = sqrt(rr) / S.bnorm[c];
@@ -166,21 +207,49 @@ __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
   S.rho[c] = rr;
 }
 
-__global__ void k_cg_update_p(float* __restrict__ p, const double* __restrict__ r, int64_t n,
-                              int k, CgState S) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * k) return;
-  const int c = (int)(e % k);
-  if (!S.active[c]) return;
-  p[e] = (float)fma(S.beta[c], (double)p[e], r[e]);
+// p = r + beta p on active columns (double-float sum, rounded to fp32).
+template <int VEC>
+__global__ void k_cg_update_p(float* __restrict__ p, const float* __restrict__ rh,
+                              const float* __restrict__ rl, int64_t n, int k, CgState S) {
+  dfloat b[VEC];
+  bool on[VEC];
+  {
+    const int c = (int)(threadIdx.x % (k / VEC)) * VEC;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      on[j] = S.active[c + j] != 0;
+      b[j] = df_from_double(S.beta[c + j]);
+    }
+  }
+  SGP_ROWS_LOOP(row) {
+    const int64_t e = row * k + c0;
+    float pv[VEC], rhv[VEC], rlv[VEC];
+    ldf<VEC>(p + e, pv);
+    ldf<VEC>(rh + e, rhv);
+    ldf<VEC>(rl + e, rlv);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (on[j]) {
+        const dfloat t = df_add({rhv[j], rlv[j]}, df_mul_f(b[j], pv[j]));
+        pv[j] = __fadd_rn(t.hi, t.lo);
+      }
+    }
+    stf<VEC>(p + e, pv);
+  }
 }
 
-__global__ void k_cg_store_x(const double* __restrict__ x, const int32_t* __restrict__ perm,
-                             float* __restrict__ X, int64_t n, int k) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * k) return;
-  const int64_t row = e / k;
-  X[(int64_t)perm[row] * k + (e - row * k)] = (float)x[e];
+template <int VEC>
+__global__ void k_cg_store_x(const float* __restrict__ xh, const float* __restrict__ xl,
+                             const int32_t* __restrict__ perm, float* __restrict__ X, int64_t n,
+                             int k) {
+  SGP_ROWS_LOOP(row) {
+    float hv[VEC], lv[VEC];
+    ldf<VEC>(xh + row * k + c0, hv);
+    ldf<VEC>(xl + row * k + c0, lv);
+    float* dst = X + (int64_t)perm[row] * k + c0;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) dst[j] = __fadd_rn(hv[j], lv[j]);
+  }
 }
 
 }  // namespace
@@ -224,14 +293,21 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     if (e_ != cudaSuccess) return cuda_status(e_, what);   \
   } while (0)
 
-  double *x, *r;
-  float *p, *Ap;
+  float *xh, *xl, *rh, *rl, *p, *Ap;
   CgState S{};
-  CG_CHECK(get((void**)&x, n * k * sizeof(double)), "alloc x");
-  CG_CHECK(get((void**)&r, n * k * sizeof(double)), "alloc r");
+  const int vec = k % 4 == 0 ? 4 : 1;
+  const int T = column_block_threads(k, vec);
+  const int64_t rows_per_block = T / (k / vec);
+  const int vblocks = (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
+  const int64_t sblocks = slice_dot_blocks(L, k);
+  CG_CHECK(get((void**)&xh, n * k * sizeof(float)), "alloc x");
+  CG_CHECK(get((void**)&xl, n * k * sizeof(float)), "alloc x");
+  CG_CHECK(get((void**)&rh, n * k * sizeof(float)), "alloc r");
+  CG_CHECK(get((void**)&rl, n * k * sizeof(float)), "alloc r");
   CG_CHECK(get((void**)&p, n * k * sizeof(float)), "alloc p");
   CG_CHECK(get((void**)&Ap, n * k * sizeof(float)), "alloc Ap");
-  CG_CHECK(get((void**)&S.partial, (size_t)kDotBlocks * k * sizeof(double)), "alloc partial");
+  CG_CHECK(get((void**)&S.partial, (size_t)std::max<int64_t>(vblocks, sblocks) * k * sizeof(double)),
+           "alloc partial");
   double* scal;
   CG_CHECK(get((void**)&scal, 6 * (size_t)k * sizeof(double)), "alloc scalars");
   S.rho = scal;
@@ -247,24 +323,25 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   sgp_status s = ensure_lattice_values(L, k, st);
   if (s != SGP_OK) return s;
 
-  const int dot_threads = k * (kDotThreads / k);
-  const int64_t rows_per_block = dot_threads / k;
-  const int dot_blocks = (int)std::min<int64_t>(kDotBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
-  k_cg_init<<<dot_blocks, dot_threads, 0, st>>>(B, L->perm, x, r, p, n, k, S.partial);
-  k_cg_init_scalars<<<1, kMaxK, 0, st>>>(S.partial, dot_blocks, k, tol, max_iter, S);
+  if (vec == 4) k_cg_init<4><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
+  else k_cg_init<1><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
+  k_cg_init_scalars<<<k, 256, 0, st>>>(S.partial, vblocks, k, tol, max_iter, S);
   note_launches(2);
   CG_CHECK(cudaGetLastError(), "CG init");
 
   cudaEvent_t* ev = L->profile ? L->prof_ev : nullptr;
   int passes = 0;
   auto iteration = [&]() {
-    passes = enqueue_mvm(L, p, k, blur, L->outputscale, noise, Ap, st, ev, /*internal=*/true);
-    k_coldot<<<dot_blocks, dot_threads, 0, st>>>(p, Ap, n, k, S.partial);
-    k_cg_alpha<<<1, kMaxK, 0, st>>>(dot_blocks, k, S);
-    k_cg_update_xr<<<dot_blocks, dot_threads, 0, st>>>(x, r, p, Ap, n, k, S);
-    k_cg_beta<<<1, kMaxK, 0, st>>>(dot_blocks, k, tol, max_iter, S);
-    k_cg_update_p<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(p, r, n, k, S);
-    note_launches(5);
+    // Ap = outputscale K~ p + noise p, with the slice also summing <p, Ap> per block
+    passes = enqueue_mvm(L, p, k, blur, L->outputscale, noise, Ap, st, ev, /*internal=*/true,
+                         S.partial);
+    k_cg_alpha<<<k, 256, 0, st>>>((int)sblocks, k, S);
+    if (vec == 4) k_cg_update_xr<4><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
+    else k_cg_update_xr<1><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
+    k_cg_beta<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
+    if (vec == 4) k_cg_update_p<4><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
+    else k_cg_update_p<1><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
+    note_launches(4);
   };
 
   std::vector<int> hact(k);
@@ -298,7 +375,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
       }
     }
   }
-  k_cg_store_x<<<(unsigned)ceil_div(n * k, 256), 256, 0, st>>>(x, L->perm, X, n, k);
+  if (vec == 4) k_cg_store_x<4><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, n, k);
+  else k_cg_store_x<1><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, n, k);
   note_launches(1);
   CG_CHECK(cudaGetLastError(), "CG result");
   std::vector<double> hrel(k);

@@ -217,56 +217,68 @@ __global__ void __launch_bounds__(kThreads) k_blur(int64_t m, int k, int r, Taps
   Store<S>::st1(out + v * k + col, acc);
 }
 
-// Rows of k = 4 CH G values: each thread owns 4 CH consecutive columns of one row and
-// issues its id loads first, then the own and neighbour row loads together.
-template <int CH, class S>
-__global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k, int r,
-                                                        Taps tp,
+// Rows of k = 4 CH G values.  Each thread owns 4 CH consecutive columns of U rows (R =
+// stencil order): it issues all id loads, then all own and neighbour row loads, then the
+// arithmetic, so 3 U row loads per order are in flight at once.  A block covers U
+// consecutive runs of kThreads / G rows (coalesced per run, local per block).
+template <int CH, int U, int R, class S>
+__global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k, Taps tp,
                                                         const int32_t* __restrict__ nbr,
                                                         const S* __restrict__ in,
                                                         S* __restrict__ out) {
   static_assert(CH == 1 || CH == 2, "one or two groups of four columns per thread");
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t v = gid / G;
-  if (v >= m) return;
-  const int col = (int)(gid - v * G) * (4 * CH);
-  int ia[kMaxOrder], ic[kMaxOrder];
+  const int rows_per_run = kThreads / G;
+  const int col = (int)(threadIdx.x % G) * (4 * CH);
+  int64_t v[U];
+  int ia[U][R], ic[U][R];
 #pragma unroll
-  for (int t = 0; t < kMaxOrder; ++t) {
-    if (t < r) {
-      ia[t] = __ldg(nbr + (int64_t)(2 * t) * m + v);
-      ic[t] = __ldg(nbr + (int64_t)(2 * t + 1) * m + v);
+  for (int u = 0; u < U; ++u) {
+    v[u] = ((int64_t)blockIdx.x * U + u) * rows_per_run + threadIdx.x / G;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      ia[u][t] = v[u] < m ? __ldg(nbr + (int64_t)(2 * t) * m + v[u]) : -1;
+      ic[u][t] = v[u] < m ? __ldg(nbr + (int64_t)(2 * t + 1) * m + v[u]) : -1;
     }
   }
   auto load = [&](int64_t row, float4* x) {
     if (CH == 2) Store<S>::ldg8(in + row * k + col, x[0], x[CH - 1]);
     else x[0] = Store<S>::ldg4(in + row * k + col);
   };
-  float4 acc[CH];
-  load(v, acc);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 own[U][CH], sa[U][R][CH], sc[U][R][CH];
 #pragma unroll
-  for (int c = 0; c < CH; ++c)
-    acc[c] = make_float4(tp.t[0] * acc[c].x, tp.t[0] * acc[c].y, tp.t[0] * acc[c].z,
-                         tp.t[0] * acc[c].w);
+  for (int u = 0; u < U; ++u) {
 #pragma unroll
-  for (int t = 0; t < kMaxOrder; ++t) {
-    if (t >= r) break;
-    float4 sa[CH], sc[CH];
+    for (int c = 0; c < CH; ++c) own[u][c] = zero;
+    if (v[u] < m) load(v[u], own[u]);
 #pragma unroll
-    for (int c = 0; c < CH; ++c) sa[c] = sc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ia[t] >= 0) load(ia[t], sa);
-    if (ic[t] >= 0) load(ic[t], sc);
-    const float w = tp.t[t + 1];
+    for (int t = 0; t < R; ++t) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      acc[c].x = fmaf(w, sa[c].x + sc[c].x, acc[c].x);
-      acc[c].y = fmaf(w, sa[c].y + sc[c].y, acc[c].y);
-      acc[c].z = fmaf(w, sa[c].z + sc[c].z, acc[c].z);
-      acc[c].w = fmaf(w, sa[c].w + sc[c].w, acc[c].w);
+      for (int c = 0; c < CH; ++c) sa[u][t][c] = sc[u][t][c] = zero;
+      if (ia[u][t] >= 0) load(ia[u][t], sa[u][t]);
+      if (ic[u][t] >= 0) load(ic[u][t], sc[u][t]);
     }
   }
-  if (CH == 2) Store<S>::st8(out + v * k + col, acc[0], acc[CH - 1]);
-  else Store<S>::st4(out + v * k + col, acc[0]);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (v[u] >= m) continue;
+    float4 acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      acc[c] = make_float4(tp.t[0] * own[u][c].x, tp.t[0] * own[u][c].y, tp.t[0] * own[u][c].z,
+                           tp.t[0] * own[u][c].w);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float w = tp.t[t + 1];
+        acc[c].x = fmaf(w, sa[u][t][c].x + sc[u][t][c].x, acc[c].x);
+        acc[c].y = fmaf(w, sa[u][t][c].y + sc[u][t][c].y, acc[c].y);
+        acc[c].z = fmaf(w, sa[u][t][c].z + sc[u][t][c].z, acc[c].z);
+        acc[c].w = fmaf(w, sa[u][t][c].w + sc[u][t][c].w, acc[c].w);
+      }
+    }
+    if (CH == 2) Store<S>::st8(out + v[u] * k + col, acc[0], acc[CH - 1]);
+    else Store<S>::st4(out + v[u] * k + col, acc[0]);
+  }
 }
 
 // ---- slice ---------------------------------------------------------------------------
@@ -293,6 +305,44 @@ __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int
   typename Vt::T res = Vt::scale(alpha, acc);
   if (BETA) res = Vt::fma(beta, Vt::ld(V + i * k + col), res);
   Vt::st(out + i * k + col, res);
+}
+
+// The CG's slice: V and out in locality order, out = alpha W lat + beta V, and the
+// per-block column sums of V * out for <p, A p> (exact products and double-float
+// accumulation per thread, fp64 across threads).  Grid-stride over points.
+template <int VEC, class S>
+__global__ void __launch_bounds__(kThreads) k_slice_dot(int64_t n, int G, int k, int D,
+                                                        const int32_t* __restrict__ idx,
+                                                        const float* __restrict__ w,
+                                                        const S* __restrict__ lat,
+                                                        const float* __restrict__ V, float alpha,
+                                                        float beta, float* __restrict__ out,
+                                                        double* __restrict__ dot_partial) {
+  using Vt = Vec<VEC>;
+  const int rows = blockDim.x / G;
+  const int col = (int)(threadIdx.x % G) * VEC;
+  dfloat d[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) d[j] = {0.f, 0.f};
+  for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / G; p < n;
+       p += (int64_t)gridDim.x * rows) {
+    typename Vt::T acc = Vt::zero();
+    for (int c = 0; c < D; ++c) {
+      const int64_t e = p * D + c;
+      acc = Vt::fma(w[e], Vt::lds(lat + (int64_t)idx[e] * k + col), acc);
+    }
+    const typename Vt::T v = Vt::ld(V + p * k + col);
+    const typename Vt::T res = Vt::fma(beta, v, Vt::scale(alpha, acc));
+    Vt::st(out + p * k + col, res);
+    const float* vv = reinterpret_cast<const float*>(&v);
+    const float* rr = reinterpret_cast<const float*>(&res);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) d[j] = df_add(d[j], df_two_prod(vv[j], rr[j]));
+  }
+  double dd[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) dd[j] = df_to_double(d[j]);
+  block_column_sums<VEC>(dd, k, dot_partial + (int64_t)blockIdx.x * k);
 }
 
 // Vp[p] = V[perm[p]]: the caller's rows in locality order.
@@ -346,18 +396,28 @@ void launch_splat_t(const Lattice* L, const float* V, int k, S* lat, float* part
   }
 }
 
+template <int CH, int U, class S>
+void launch_blur_rows(const Lattice* L, const int32_t* nbr, const Taps& taps, const S* in,
+                      S* out, int k, cudaStream_t st) {
+  const int G = k / (4 * CH);
+  const int64_t runs = ceil_div(L->m, kThreads / G);
+  const unsigned grid = (unsigned)ceil_div(runs, U);
+  switch (L->r) {
+    case 1: k_blur_rows<CH, U, 1, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    case 2: k_blur_rows<CH, U, 2, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    case 3: k_blur_rows<CH, U, 3, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    default: k_blur_rows<CH, U, 4, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+  }
+}
+
 template <class S>
 void launch_blur_t(const Lattice* L, int j, const Taps& taps, const S* in, S* out, int k,
                    cudaStream_t st) {
   const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
-  if (k % 8 == 0) {  // eight columns per thread
-    const int G = k / 8;
-    k_blur_rows<2, S><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
-        L->m, G, k, L->r, taps, nbr, in, out);
-  } else if (k % 4 == 0) {
-    const int G = k / 4;
-    k_blur_rows<1, S><<<(unsigned)ceil_div(L->m * G, kThreads), kThreads, 0, st>>>(
-        L->m, G, k, L->r, taps, nbr, in, out);
+  if (k % 8 == 0 && kThreads % (k / 8) == 0) {  // eight columns of two rows per thread
+    launch_blur_rows<2, 2, S>(L, nbr, taps, in, out, k, st);
+  } else if (k % 4 == 0 && kThreads % (k / 4) == 0) {
+    launch_blur_rows<1, 2, S>(L, nbr, taps, in, out, k, st);
   } else {
     k_blur<S><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, L->r, taps, nbr,
                                                                           in, out);
@@ -390,6 +450,21 @@ void launch_slice_t(const Lattice* L, const S* lat, const float* V, int k, float
   note_launches(1);
 }
 
+template <class S>
+void launch_slice_dot(const Lattice* L, const S* lat, const float* V, int k, float alpha,
+                      float beta, float* out, double* dot_partial, cudaStream_t st) {
+  const int vec = k % 4 == 0 ? 4 : 1;
+  const int T = column_block_threads(k, vec);
+  const unsigned grid = (unsigned)slice_dot_blocks(L, k);
+  if (vec == 4)
+    k_slice_dot<4, S><<<grid, T, 0, st>>>(L->n, k / 4, k, L->D, L->idx, L->w, lat, V, alpha, beta,
+                                          out, dot_partial);
+  else
+    k_slice_dot<1, S><<<grid, T, 0, st>>>(L->n, k, k, L->D, L->idx, L->w, lat, V, alpha, beta, out,
+                                          dot_partial);
+  note_launches(1);
+}
+
 void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStream_t st) {
   if (vec4_ok(k, V, Vp)) {
     const int G = k / 4;
@@ -407,7 +482,7 @@ void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStre
 template <class S>
 int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
               float* out, S* lat0, S* lat1, float* partial, float* vperm, cudaStream_t st,
-              cudaEvent_t* ev, bool internal) {
+              cudaEvent_t* ev, bool internal, double* dot_partial = nullptr) {
   Taps c{}, g{};
   for (int t = 0; t <= L->r; ++t) {
     c.t[t] = (float)L->coef[t];
@@ -441,7 +516,8 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
     for (int j = D - 1; j >= 0; --j) pass(j, g);
   }
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  if (internal) launch_slice_t<false, S>(L, a, V, k, alpha, beta, out, st);
+  if (internal && dot_partial) launch_slice_dot<S>(L, a, V, k, alpha, beta, out, dot_partial, st);
+  else if (internal) launch_slice_t<false, S>(L, a, V, k, alpha, beta, out, st);
   else launch_slice_t<true, S>(L, a, V, k, alpha, beta, out, st);
   return passes;
 }
@@ -487,12 +563,19 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
 }
 
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-                float* out, cudaStream_t st, cudaEvent_t* ev, bool internal) {
+                float* out, cudaStream_t st, cudaEvent_t* ev, bool internal, double* dot_partial) {
   if (L->value_dtype == SGP_VALUES_BF16)
     return enqueue_t<bf16>(L, V, k, blur, alpha, beta, out, (bf16*)L->lat[0], (bf16*)L->lat[1],
-                           L->partial, L->vperm, st, ev, internal);
+                           L->partial, L->vperm, st, ev, internal, dot_partial);
   return enqueue_t<float>(L, V, k, blur, alpha, beta, out, (float*)L->lat[0], (float*)L->lat[1],
-                          L->partial, L->vperm, st, ev, internal);
+                          L->partial, L->vperm, st, ev, internal, dot_partial);
+}
+
+int64_t slice_dot_blocks(const Lattice* L, int k) {
+  const int vec = k % 4 == 0 ? 4 : 1;
+  const int G = k / vec;
+  return std::min<int64_t>(kVecBlocks,
+                           std::max<int64_t>(1, ceil_div(L->n, column_block_threads(k, vec) / G)));
 }
 
 void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, float alpha,

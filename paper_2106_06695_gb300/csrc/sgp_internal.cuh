@@ -130,7 +130,12 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st);
 // `ev` is given, ev[0] / ev[1] are recorded around the blur passes.  Returns the number
 // of blur passes.
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-                float* out, cudaStream_t st, cudaEvent_t* ev = nullptr, bool internal = false);
+                float* out, cudaStream_t st, cudaEvent_t* ev = nullptr, bool internal = false,
+                double* dot_partial = nullptr);
+// With internal = true and dot_partial set, the slice also writes per-block column sums of
+// V * out (the CG's <p, A p>) to dot_partial[block][k]; this many blocks (grid-stride).
+int64_t slice_dot_blocks(const Lattice* L, int k);
+constexpr int kVecBlocks = 8 * 152;  // blocks of the grid-stride column-owning kernels
 // Bytes of work space one k-column product needs (value buffers, partials, permuted
 // input, each rounded up to 256 bytes).
 size_t mvm_work_bytes(const Lattice* L, int k);
@@ -147,5 +152,74 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
                   int max_iter, float* X, int* iters, double* rel_res);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Per-column sums of per-thread fp64 partials inside one block, for kernels whose threads
+// own VEC consecutive columns of one row: thread t owns columns (t % G) VEC .. + VEC - 1
+// of block row t / G, with G = k / VEC threads per row and blockDim.x a multiple of G.
+// The block's column sums go to out[0..k) in a fixed order (deterministic).  Every
+// thread of the block must call it.
+template <int VEC>
+__device__ __forceinline__ void block_column_sums(const double (&acc)[VEC], int k, double* out) {
+  __shared__ double s[256 * VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) s[threadIdx.x * VEC + j] = acc[j];
+  __syncthreads();
+  const int G = k / VEC;
+  const int rows = blockDim.x / G;
+  for (int col = threadIdx.x; col < k; col += blockDim.x) {
+    const int chunk = col / VEC, lane = col % VEC;
+    double t = 0.0;
+    for (int r = 0; r < rows; ++r) t += s[(r * G + chunk) * VEC + lane];
+    out[col] = t;
+  }
+}
+
+// ---- double-float arithmetic -------------------------------------------------------
+// FP64 throughput on this part is a small fraction of FP32, so quantities that need more
+// than fp32 precision per element (CG iterate and residual, dot-product accumulation) are
+// kept as unevaluated sums hi + lo of two fp32 numbers and updated with error-free
+// transformations: TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|) and TwoProd through a
+// fused multiply-add.  The _rn intrinsics keep the compiler from contracting or
+// reordering the steps.  About 48 significant bits.
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (a.hi + a.lo) + (b.hi + b.lo)
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const dfloat s = df_two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, e);
+}
+// (a.hi + a.lo) * b
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+  const dfloat p = df_two_prod(a.hi, b);
+  return df_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ dfloat df_from_double(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+
+// Threads per block for the column-owning kernels: a whole number of rows of G threads.
+inline int column_block_threads(int k, int vec) {
+  const int G = k / vec;
+  return G * (256 / G);
+}
 
 }  // namespace sgp
