@@ -90,6 +90,9 @@ typedef struct {
   int value_dtype;    /* SGP_VALUES_*; default SGP_VALUES_F32                           */
   int check_every;    /* CG iterations between host reads of the flags; default 8       */
   void* stream;       /* cudaStream_t for all work on this handle; NULL = default stream */
+  int precond_rank;   /* CG preconditioner rank l (0 = none, <= 128); App. A uses 100;
+                         default 0 (see sgp_cg_solve)                                   */
+  unsigned long long precond_seed; /* seed of the preconditioner's random sketch; 0    */
 } sgp_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -187,7 +190,17 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
                         int max_iter, float* X, int* iters, double* rel_res);
 
 /* As sgp_cg_solve with the blur operator chosen by `blur` (SGP_BLUR_*).  CG assumes a
- * symmetric positive-definite matrix; only SGP_BLUR_SYMMETRIC guarantees one. */
+ * symmetric positive-definite matrix; only SGP_BLUR_SYMMETRIC guarantees one.
+ *
+ * Preconditioning (opts->precond_rank = l > 0 at build time, noise_var > 0): CG runs
+ * preconditioned with P = B B^T + noise_var I, a rank-l randomized Nystrom approximation
+ * of outputscale W B W^T built from one l-column product with a Rademacher sketch Omega
+ * (Omega[i][j] = sign bit of SplitMix64 at counter i l + j + 1 from precond_seed, i the
+ * caller's point index): Y = A Omega + nu Omega (nu = 1e-3 noise_var), C = Omega^T Y =
+ * R R^T, B = Y R^-T; P^-1 is applied through the Woodbury identity with the Cholesky
+ * factor of noise_var I + B^T B.  Work space grows by 4 n l + 8 n k bytes.  When a
+ * Cholesky pivot fails the solve runs unpreconditioned.  The stopping rule is unchanged
+ * (unpreconditioned residual ||r_c|| / ||b_c||). */
 sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
                            float tol, int max_iter, float* X, int* iters, double* rel_res);
 

@@ -12,6 +12,8 @@ from .oracle import (  # noqa: F401
     build_oracle,
     dense_rbf,
     elevate,
+    rademacher_sketch,
+    splitmix64,
     simplex,
     fourier_coverage,
     spatial_coverage,

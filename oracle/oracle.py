@@ -108,6 +108,25 @@ def stencil(kind: int = RBF_BINOMIAL, r: int = 1, spacing: float = 0.0):
     return s.value, coef, half
 
 
+def splitmix64(counter, seed: int = 0) -> np.ndarray:
+    """SplitMix64 (Steele, Lea & Flood 2014) output at the given counters (uint64 array):
+    the mixing function applied to seed + counter * 0x9e3779b97f4a7c15."""
+    c = np.asarray(counter, np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + c * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def rademacher_sketch(n: int, l: int, seed: int = 0) -> np.ndarray:
+    """Omega[i][j] = -1 if the top bit of SplitMix64 at counter i l + j + 1 is set, else +1."""
+    c = (np.arange(n, dtype=np.uint64)[:, None] * np.uint64(l)
+         + np.arange(l, dtype=np.uint64)[None, :] + np.uint64(1))
+    return np.where(splitmix64(c, seed) >> np.uint64(63), -1.0, 1.0)
+
+
 def simplex(y):
     """Enclosing simplex of one elevated point y (Sec. 3.2 "Splat"): dict of rem0,
     rank, w ([D]) and keys ([D][D], vertex k in row k)."""
@@ -227,6 +246,70 @@ class OracleLattice:
         if rc != 0:
             raise ValueError("orc_mvm: invalid arguments")
         return out.reshape(shape)
+
+    def nystrom(self, rank: int, noise: float, seed: int = 0, outputscale: float = 1.0,
+                mode: int = 2):
+        """Rank-l randomized Nystrom factor B of A = outputscale K~ (App. A: preconditioner
+        rank), built from products with A only: Y = A Omega + nu Omega (nu = 1e-3 noise),
+        C = Omega^T Y = R R^T, B = Y R^-T.  Returns B and the lower Cholesky factor Q of
+        noise I + B^T B; P = B B^T + noise I."""
+        from scipy.linalg import cholesky, solve_triangular
+
+        om = rademacher_sketch(self.n, rank, seed)
+        Y = self.mvm(om, mode=mode, alpha=outputscale) + 1e-3 * noise * om
+        C = om.T @ Y
+        R = cholesky(0.5 * (C + C.T), lower=True)
+        Bm = solve_triangular(R, Y.T, lower=True).T
+        Q = cholesky(noise * np.eye(rank) + Bm.T @ Bm, lower=True)
+        return Bm, Q
+
+    @staticmethod
+    def nystrom_apply(Bm, Q, noise: float, r):
+        """P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise (Woodbury)."""
+        from scipy.linalg import cho_solve
+
+        return (r - Bm @ cho_solve((Q, True), Bm.T @ r)) / noise
+
+    def pcg(self, B, noise: float, rank: int, tol: float = 1e-3, max_iter: int = 500,
+            seed: int = 0, outputscale: float = 1.0, mode: int = 2):
+        """Preconditioned CG (P = B B^T + noise I from nystrom) on (outputscale K~ + noise I)
+        X = B, every column independent, stopping on ||r|| / ||b|| <= tol."""
+        B2, shape = self._as2d(B)
+        n, k = B2.shape
+        Bm, Q = self.nystrom(rank, noise, seed, outputscale, mode)
+        X = np.zeros_like(B2)
+        r = B2.copy()
+        z = self.nystrom_apply(Bm, Q, noise, r)
+        p = z.copy()
+        rho = (r * z).sum(0)
+        bnorm = np.linalg.norm(B2, axis=0)
+        active = bnorm > 0
+        rel = np.where(active, 1.0, 0.0)
+        iters = np.zeros(k, np.int32)
+        for _ in range(max_iter):
+            if not active.any():
+                break
+            q = self.mvm(p, mode=mode, alpha=outputscale, beta=noise)
+            pq = (p * q).sum(0)
+            for c in np.nonzero(active)[0]:
+                if not pq[c] > 0:
+                    active[c] = False
+                    continue
+                a = rho[c] / pq[c]
+                X[:, c] += a * p[:, c]
+                r[:, c] -= a * q[:, c]
+                iters[c] += 1
+                rel[c] = np.linalg.norm(r[:, c]) / bnorm[c]
+                if rel[c] <= tol or iters[c] >= max_iter:
+                    active[c] = False
+            if not active.any():
+                break
+            z = self.nystrom_apply(Bm, Q, noise, r)
+            rz = (r * z).sum(0)
+            for c in np.nonzero(active)[0]:
+                p[:, c] = z[:, c] + (rz[c] / rho[c]) * p[:, c]
+                rho[c] = rz[c]
+        return X.reshape(shape), iters, rel
 
     def cg(self, B, noise: float, tol: float = 1e-3, max_iter: int = 500,
            outputscale: float = 1.0, mode: int = 0):

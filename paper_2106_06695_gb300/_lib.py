@@ -27,7 +27,8 @@ class sgp_opts(ctypes.Structure):
     _fields_ = [("order_r", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("spacing_s", ctypes.c_double), ("outputscale", ctypes.c_float),
                 ("value_dtype", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("precond_rank", ctypes.c_int),
+                ("precond_seed", ctypes.c_ulonglong)]
 
 
 class SGPError(RuntimeError):

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "build.cu", "mvm.cu", "cg.cu", "scan_sort.cu", "static_mvm.cu", "stencil.cpp"]
+SOURCES = ["api.cu", "build.cu", "mvm.cu", "cg.cu", "scan_sort.cu", "static_mvm.cu", "nystrom.cu",
+           "stencil.cpp"]
 NO_FMA = {"build.cu"}
 
 

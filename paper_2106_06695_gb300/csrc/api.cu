@@ -83,6 +83,8 @@ void sgp_opts_init(sgp_opts* o) {
   o->value_dtype = SGP_VALUES_F32;
   o->check_every = 8;
   o->stream = nullptr;
+  o->precond_rank = 0;
+  o->precond_seed = 0;
 }
 
 sgp_status sgp_stencil(int kernel, int order_r, double spacing_override, double* spacing_s,
@@ -136,6 +138,13 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
   L->outputscale = o.outputscale;
   L->value_dtype = o.value_dtype;
   L->check_every = o.check_every > 0 ? o.check_every : 8;
+  if (o.precond_rank < 0 || o.precond_rank > kMaxRank) {
+    delete L;
+    set_error("sgp_lattice_build: precond_rank must be in 0..128");
+    return SGP_ERR_INVALID_ARG;
+  }
+  L->precond_rank = o.precond_rank;
+  L->precond_seed = o.precond_seed;
   L->stream = (cudaStream_t)o.stream;
   if (!make_stencil(o.kernel, o.order_r, o.spacing_s, &L->s, L->coef, L->half)) {
     delete L;
@@ -249,7 +258,8 @@ sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, floa
     return SGP_ERR_INVALID_ARG;
   }
   clear_pending_error();
-  return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res);
+  return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res, h->precond_rank,
+                h->precond_seed);
 }
 
 sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, float tol,

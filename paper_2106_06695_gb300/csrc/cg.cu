@@ -207,6 +207,74 @@ __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
   S.rho[c] = rr;
 }
 
+// Preconditioned CG: convergence check on <r, r> (no beta yet).
+__global__ void k_cg_check(int nblk, int k, float tol, int max_iter, CgState S) {
+  const double rr = column_total(S.partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
+  if (!S.active[c]) return;
+  const int it = S.iters[c] + 1;
+  S.iters[c] = it;
+  const double rel = sqrt(rr) / S.bnorm[c];
+  S.relres[c] = rel;
+  if (rel <= (double)tol || it >= max_iter || !isfinite(rel)) S.active[c] = 0;
+}
+
+// Preconditioned CG: rho = <r, z> at the start.
+__global__ void k_cg_rho_init(int nblk, int k, CgState S) {
+  const double rz = column_total(S.partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
+  S.rho[c] = rz;
+  if (!(rz > 0.0) || !isfinite(rz)) S.active[c] = 0;
+}
+
+// Preconditioned CG: beta = <r, z>_new / <r, z>_old on active columns.
+__global__ void k_cg_beta_pcg(int nblk, int k, CgState S) {
+  const double rz = column_total(S.partial, nblk, k);
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
+  if (!S.active[c]) return;
+  if (!(rz > 0.0) || !isfinite(rz)) {
+    S.active[c] = 0;
+    return;
+  }
+  S.beta[c] = rz / S.rho[c];
+  S.rho[c] = rz;
+}
+
+// Preconditioned CG: p = z + beta p on active columns (first == true: p = z).
+template <int VEC, bool FIRST>
+__global__ void k_cg_update_p_z(float* __restrict__ p, const float* __restrict__ z, int64_t n,
+                                int k, CgState S) {
+  dfloat b[VEC];
+  bool on[VEC];
+  {
+    const int c = (int)(threadIdx.x % (k / VEC)) * VEC;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      on[j] = S.active[c + j] != 0;
+      b[j] = df_from_double(S.beta[c + j]);
+    }
+  }
+  SGP_ROWS_LOOP(row) {
+    const int64_t e = row * k + c0;
+    float pv[VEC], zv[VEC];
+    ldf<VEC>(p + e, pv);
+    ldf<VEC>(z + e, zv);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (FIRST) {
+        pv[j] = zv[j];
+      } else if (on[j]) {
+        const dfloat t = df_add(df_mul_f(b[j], pv[j]), {zv[j], 0.f});
+        pv[j] = __fadd_rn(t.hi, t.lo);
+      }
+    }
+    stf<VEC>(p + e, pv);
+  }
+}
+
 // p = r + beta p on active columns (double-float sum, rounded to fp32).
 template <int VEC>
 __global__ void k_cg_update_p(float* __restrict__ p, const float* __restrict__ rh,
@@ -255,7 +323,8 @@ __global__ void k_cg_store_x(const float* __restrict__ xh, const float* __restri
 }  // namespace
 
 sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
-                  int max_iter, float* X, int* iters, double* rel_res) {
+                  int max_iter, float* X, int* iters, double* rel_res, int precond_rank,
+                  uint64_t seed) {
   const int64_t n = L->n;
   // CUDA graphs cannot be captured on the legacy default stream: use a private blocking
   // stream then (it is ordered with the legacy stream like any blocking stream).
@@ -271,7 +340,9 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     std::vector<void*> ptrs;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    Nystrom pre;
     ~Cleanup() {
+      pre.release(st);
       if (exec) (void)cudaGraphExecDestroy(exec);
       if (graph) (void)cudaGraphDestroy(graph);
       for (void* p : ptrs) (void)cudaFreeAsync(p, st);
@@ -323,10 +394,27 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   sgp_status s = ensure_lattice_values(L, k, st);
   if (s != SGP_OK) return s;
 
+  // the preconditioner (built before anything is captured); needs noise > 0
+  bool use_pre = false;
+  float* z = nullptr;
+  if (precond_rank > 0 && noise > 0.f) {
+    s = cl.pre.build(L, precond_rank, seed, noise, blur, st);
+    if (s != SGP_OK) return s;
+    use_pre = cl.pre.ok;
+    if (use_pre) CG_CHECK(get((void**)&z, n * k * sizeof(float)), "alloc z");
+  }
+
   if (vec == 4) k_cg_init<4><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
   else k_cg_init<1><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
   k_cg_init_scalars<<<k, 256, 0, st>>>(S.partial, vblocks, k, tol, max_iter, S);
   note_launches(2);
+  if (use_pre) {  // z = P^-1 r, rho = <r, z>, p = z
+    cl.pre.apply(rh, rl, k, z, S.partial, vblocks, T, st);
+    k_cg_rho_init<<<k, 256, 0, st>>>(vblocks, k, S);
+    if (vec == 4) k_cg_update_p_z<4, true><<<vblocks, T, 0, st>>>(p, z, n, k, S);
+    else k_cg_update_p_z<1, true><<<vblocks, T, 0, st>>>(p, z, n, k, S);
+    note_launches(2);
+  }
   CG_CHECK(cudaGetLastError(), "CG init");
 
   cudaEvent_t* ev = L->profile ? L->prof_ev : nullptr;
@@ -338,10 +426,19 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     k_cg_alpha<<<k, 256, 0, st>>>((int)sblocks, k, S);
     if (vec == 4) k_cg_update_xr<4><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
     else k_cg_update_xr<1><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
-    k_cg_beta<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
-    if (vec == 4) k_cg_update_p<4><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
-    else k_cg_update_p<1><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
-    note_launches(4);
+    if (use_pre) {
+      k_cg_check<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
+      cl.pre.apply(rh, rl, k, z, S.partial, vblocks, T, st);
+      k_cg_beta_pcg<<<k, 256, 0, st>>>(vblocks, k, S);
+      if (vec == 4) k_cg_update_p_z<4, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);
+      else k_cg_update_p_z<1, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);
+      note_launches(5);
+    } else {
+      k_cg_beta<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
+      if (vec == 4) k_cg_update_p<4><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
+      else k_cg_update_p<1><<<vblocks, T, 0, st>>>(p, rh, rl, n, k, S);
+      note_launches(4);
+    }
   };
 
   std::vector<int> hact(k);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sgp.h"
 
@@ -42,6 +43,8 @@ struct sgp_lattice {
   float outputscale = 1.f;
   int value_dtype = 0;
   int check_every = 8;
+  int precond_rank = 0;
+  uint64_t precond_seed = 0;
   cudaStream_t stream = nullptr;
 
   // Points are processed in a locality order p = 0..n-1; perm[p] is the caller's index.
@@ -147,11 +150,40 @@ void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float a
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);
 
-// ---- CG (cg.cu) ----
-sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
-                  int max_iter, float* X, int* iters, double* rel_res);
+// ---- rank-l Nystrom preconditioner of the CG (nystrom.cu) ----
+constexpr int kMaxRank = 128;
+struct Nystrom {
+  int l = 0;
+  int64_t n = 0;
+  float noise = 0.f;
+  bool ok = false;             // false when a Cholesky pivot failed (then not used)
+  float* Bm = nullptr;         // [n][l] B = (A Omega + nu Omega) R^-T, locality order
+  double* partial = nullptr;   // per-block partial sums of the tall products
+  double* C = nullptr;         // [l][l] Omega^T Y, then its Cholesky factor R
+  double* Q = nullptr;         // [l][l] Cholesky factor of noise I + B^T B
+  float* T = nullptr;          // [l][l] R^-T
+  double* work = nullptr;
+  double* tvec = nullptr;      // [l][k] B^T r
+  float* u = nullptr;          // [l][k] (noise I + B^T B)^-1 B^T r
+  int* status = nullptr;
+  std::vector<void*> ptrs;
+  // Sketch, factor and keep B, Q for the handle's operator `blur` (enqueued on st, one
+  // synchronisation to read the factorisation status).
+  sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, cudaStream_t st);
+  // z = P^-1 r for r = rh + rl ([n][k], locality order), and the per-block column sums of
+  // r z into dot_partial ([dot_blocks][k]) with the CG's column-owning block shape.
+  void apply(const float* rh, const float* rl, int k, float* z, double* dot_partial,
+             int64_t dot_blocks, int block_threads, cudaStream_t st) const;
+  void release(cudaStream_t st);
+};
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// ---- CG (cg.cu) ----
+// precond_rank > 0: preconditioned CG with a rank-precond_rank Nystrom preconditioner.
+sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
+                  int max_iter, float* X, int* iters, double* rel_res, int precond_rank = 0,
+                  uint64_t seed = 0);
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Per-column sums of per-thread fp64 partials inside one block, for kernels whose threads
 // own VEC consecutive columns of one row: thread t owns columns (t % G) VEC .. + VEC - 1

@@ -31,12 +31,14 @@ class Lattice:
     """Permutohedral lattice of the rows of X (n x d) scaled by ARD lengthscales.
 
     kernel: "rbf_binomial" (default; stencil [.5, 1, .5] at order 1), "rbf_coverage" or
-    "matern32_coverage" (spacing from Eq. balance_coverage); order: stencil order r.
+    "matern32_coverage" (spacing from Eq. balance_coverage); order: stencil order r;
+    precond_rank: rank of the CG's Nystrom preconditioner (0 = plain CG; App. A uses 100).
     """
 
     def __init__(self, X: torch.Tensor, lengthscales, order: int = 1,
                  kernel: str = "rbf_binomial", spacing: float = 0.0, outputscale: float = 1.0,
-                 value_dtype: str = "f32", check_every: int = 8):
+                 value_dtype: str = "f32", check_every: int = 8, precond_rank: int = 0,
+                 precond_seed: int = 0):
         self._lib = _lib.load()
         X = _f32_cuda(X, "X")
         if X.dim() != 2:
@@ -58,6 +60,8 @@ class Lattice:
         opts.outputscale = float(outputscale)
         opts.value_dtype = VALUE_DTYPES[value_dtype]
         opts.check_every = int(check_every)
+        opts.precond_rank = int(precond_rank)
+        opts.precond_seed = int(precond_seed)
         opts.stream = _stream_ptr(self.device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

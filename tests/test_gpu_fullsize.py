@@ -4,7 +4,8 @@ n = 2,000,000, d = 11 (the bench workload): the lattice is compared bit-exactly 
 oracle's, and the MVM on 20,000 seeded rows of the oracle's full FP64 MVM.
 n = 200,000, d = 11, k = 9 (y plus 8 Rademacher probes, noise 0.01, tol 1e-3): the
 residual the solver reports is the true residual of its answer, evaluated with the
-oracle's FP64 operator.
+oracle's FP64 operator; unpreconditioned CG does not reach 1e-3 within 500 iterations
+on this system, the rank-100 preconditioned one (App. A) does.
 """
 
 import numpy as np
@@ -81,9 +82,21 @@ def test_gp_solve_200k_reports_its_true_residual(solve_200k):
     assert np.allclose(true_rel, rel, rtol=0.05), (rel, true_rel)
 
 
-@pytest.mark.xfail(reason="noise 0.01 on this workload is ill-conditioned: unpreconditioned "
-                          "CG stops near 1e-2 after 500 iterations; App. A's CG is "
-                          "preconditioned", strict=False)
-def test_gp_solve_200k_reaches_tolerance(solve_200k):
-    iters, rel, true_rel = solve_200k
-    assert (rel <= 1e-3).all() and (true_rel <= 1.5e-3).all()
+def test_gp_solve_200k_preconditioned_reaches_tolerance():
+    """The same solve with the App. A preconditioner of rank 100 reaches 1e-3."""
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    n, d = 200_000, 11
+    X = synth.gmm_points(n, d, 2)
+    B = synth.solve_rhs(X, 2, probes=8)
+    ls = np.ones(d, np.float32)
+    lat = Lattice(gpu(X), gpu(ls), precond_rank=100, precond_seed=1)
+    xs, iters, rel = lat.cg(gpu(B), noise=0.01, tol=1e-3, max_iter=500)
+    print("preconditioned 200k solve: iterations", iters, "residuals", rel)
+    assert (rel <= 1e-3).all(), (iters, rel)
+    s, _, _ = lat.stencil()
+    ref = OracleLattice(X, ls, spacing=s)
+    Bd = B.astype(np.float64)
+    R = Bd - ref.mvm(xs.cpu().numpy().astype(np.float64), mode=2, beta=0.01)
+    true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bd, axis=0)
+    assert (true_rel <= 1.5e-3).all(), true_rel
