@@ -4,9 +4,14 @@
 One step = the whole path over one batch of synthetic input:
   build the permutohedral lattice of X (elevate, enclosing simplex, barycentric
   weights, hash insert, vertex numbering, neighbour table, splat lists; Sec. 3.2), then
-  solve (K~ + noise I) X = V for all k right-hand sides with batched CG (Sec. 2), each
-  iteration one lattice MVM (splat, 2(d+1) blur passes of the symmetric operator, slice).
-Metric: lattice MVM Mpoint/s = n * (MVMs in the step) / step time, whole job.
+  solve (K~ + noise I) X = V for all k right-hand sides with batched CG (Sec. 2); each
+  CG iteration is one lattice MVM (splat, 2(d+1) blur passes of the symmetric operator,
+  slice).
+Metric: lattice MVM Mpoint/s = n * (k-column MVMs in the step) / step time, whole job,
+iterations counted as the max over columns.  The same solve with the rank-100
+preconditioner of App. A (a randomized Nystrom factor built from one 100-column lattice
+MVM, counted as rank / k MVMs) is timed after the steps and reported in `config.pcg`;
+`--precond-rank 100` makes it the timed step instead.
 
 Workload (default): n = 2,000,000 points, d = 11, standardised 16-component Gaussian
 mixture (the shape of Houseelectric, n=2,049,280 d=11, Sec. 5 Table n_lattice), unit ARD
@@ -29,7 +34,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# The CPU legs time the oracle on one core: keep numpy's BLAS pools single-threaded
+# (set before numpy loads; the GPU arm does no BLAS work).
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -38,7 +48,9 @@ if ROOT not in sys.path:
 METRIC = "lattice MVM Mpoint/s at n=2M,d=11 (%HBM peak)"
 UNIT = "Mpoint/s"
 WORKLOAD = dict(n=2_000_000, d=11, k=16, seed=4, lengthscale=1.0, noise=0.01, tol=1e-3,
-                max_iter=500, kernel="rbf_binomial", order=1, blur="symmetric")
+                max_iter=500, kernel="rbf_binomial", order=1, blur="symmetric",
+                precond_rank=0)
+PCG_RANK = 100  # App. A: CG pre-conditioner of rank 100
 CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg
 REF_SAMPLE = dict(n=50_000, iters=2)    # oracle sample per step for --impl reference
 
@@ -52,6 +64,9 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (default 2,000,000)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precond-rank", type=int, default=WORKLOAD["precond_rank"],
+                    help="rank of the CG preconditioner in the timed step (0 = plain CG, the "
+                         "default; App. A uses 100)")
     ap.add_argument("--max-iter", type=int, default=WORKLOAD["max_iter"],
                     help="CG iteration cap (default 500; lower only for profiling runs)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
@@ -192,7 +207,7 @@ def run_ours(args, world, rank, local):
     init_dist(world, "nccl")
     build_lib.build()
     lib = _lib.load()
-    W = dict(WORKLOAD, n=args.n, max_iter=args.max_iter)
+    W = dict(WORKLOAD, n=args.n, max_iter=args.max_iter, precond_rank=args.precond_rank)
     n, d, k = W["n"], W["d"], W["k"]
     Xh = torch.from_numpy(synth.gmm_points(n, d, W["seed"])).pin_memory()
     Vh = torch.from_numpy(synth.gaussian_values(n, k, W["seed"])).pin_memory()
@@ -215,7 +230,8 @@ def run_ours(args, world, rank, local):
 
     def step(Xdev, Vdev, ls_dev, profile=False):
         t0 = time.perf_counter()
-        lat = Lattice(Xdev, ls_dev, order=W["order"], kernel=W["kernel"])
+        lat = Lattice(Xdev, ls_dev, order=W["order"], kernel=W["kernel"],
+                      precond_rank=W["precond_rank"], precond_seed=W["seed"])
         prof["build_ms"].append(1e3 * (time.perf_counter() - t0))
         if profile:
             _lib.check(lib.sgp_profile_blur(lat._h, 1))
@@ -234,7 +250,7 @@ def run_ours(args, world, rank, local):
         print("step: m=%d build %.1f ms, cg iters %d, %.1f ms total" % (
             lat.m, prof["build_ms"][-1], int(iters.max()), 1e3 * (time.perf_counter() - t0)),
             file=sys.stderr, flush=True)
-        return int(iters.max()), rel
+        return int(iters.max()) + W["precond_rank"] / k, rel
 
     for _ in range(args.warmup):
         step(Xd, Vd, lsd)
@@ -274,7 +290,8 @@ def run_ours(args, world, rank, local):
 
     # MVM alone (same lattice, same stream) for context, and the true residual of the
     # last solve: || V - (K~ + noise I) X || / || V || per column
-    lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"])
+    lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"],
+                  precond_rank=W["precond_rank"], precond_seed=W["seed"])
     _, _, rel_last = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
                             blur=W["blur"], out=out)
     resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
@@ -311,6 +328,26 @@ def run_ours(args, world, rank, local):
     bf16_rel_err = ((out.double() - ref_out).norm() / ref_out.norm()).item()
     lat.close()
 
+    # the same solve with the App. A preconditioner (build + solve timed together)
+    pcg = None
+    if W["precond_rank"] == 0 and PCG_RANK > 0:
+        torch.cuda.synchronize()
+        e0.record()
+        lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"], precond_rank=PCG_RANK,
+                      precond_seed=W["seed"])
+        _, p_iters, p_rel = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
+                                   blur=W["blur"], out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        pcg_ms = e0.elapsed_time(e1)
+        resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
+        p_true = (resid.norm(dim=0) / Vd.double().norm(dim=0)).max().item()
+        lat.close()
+        p_mvms = int(p_iters.max()) + PCG_RANK / k
+        pcg = {"precond_rank": PCG_RANK, "ms": pcg_ms, "cg_iters": int(p_iters.max()),
+               "mpoint_s": n * p_mvms / (pcg_ms / 1e3) / 1e6,
+               "rel_res_max": float(np.max(p_rel)), "true_rel_res_max": p_true}
+
     e2e = None
     if not args.no_e2e:
         Xs_host = torch.empty(n, k, dtype=torch.float32).pin_memory()
@@ -345,11 +382,13 @@ def run_ours(args, world, rank, local):
             "data": "synthetic: standardised 16-component Gaussian mixture (seeded), "
                     "V ~ N(0,1); stands in for the paper's UCI datasets",
             "config": {"workload": "GP solve n=%d d=%d k=%d: lattice build + batched CG "
-                                   "(tol %g, max %d) on the symmetric lattice operator"
-                                   % (n, d, k, W["tol"], W["max_iter"]),
+                                   "(tol %g, max %d, preconditioner rank %d) on the symmetric "
+                                   "lattice operator"
+                                   % (n, d, k, W["tol"], W["max_iter"], W["precond_rank"]),
                        "n": n, "d": d, "k": k, "m": m, "m_over_L": m / (n * (d + 1)),
                        "kernel": "%s r=%d" % (W["kernel"], W["order"]), "noise": W["noise"],
                        "cg_iters_per_step": prof["iters"],
+                       "precond_rank": W["precond_rank"], "pcg": pcg,
                        "build_ms_median": float(np.median(prof["build_ms"])),
                        "mvm_symmetric_ms": mvm_ms, "mvm_sequential_ms": mvm_seq_ms,
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
@@ -373,8 +412,9 @@ def run_ours(args, world, rank, local):
 # the oracle on the host cores
 # ---------------------------------------------------------------------------------------
 def oracle_sample(W, n_sample, iters):
-    """Oracle build + `iters` CG iterations on a seeded n_sample-row subsample; returns
-    (seconds, point-MVMs done)."""
+    """Oracle build + preconditioned CG (same rank) stopped after `iters` iterations, on a
+    seeded n_sample-row subsample; returns (seconds, point-MVMs done, counted as in the
+    GPU arm)."""
     from oracle import OracleLattice
     from paper_2106_06695_gb300 import synth
 
@@ -384,22 +424,28 @@ def oracle_sample(W, n_sample, iters):
     Xs, Vs = X[rows], V[rows].astype(np.float64)
     t0 = time.perf_counter()
     L = OracleLattice(Xs, np.full(W["d"], W["lengthscale"], np.float32), r=W["order"])
-    _, it, _ = L.cg(Vs, W["noise"], tol=0.0, max_iter=iters, mode=2)
-    return time.perf_counter() - t0, float(n_sample) * int(it.max())
+    if W["precond_rank"] > 0:
+        _, it, _ = L.pcg(Vs, W["noise"], rank=W["precond_rank"], tol=0.0, max_iter=iters,
+                         seed=W["seed"])
+    else:
+        _, it, _ = L.cg(Vs, W["noise"], tol=0.0, max_iter=iters, mode=2)
+    mvms = int(it.max()) + W["precond_rank"] / W["k"]
+    return time.perf_counter() - t0, float(n_sample) * mvms
 
 
 def cpu_baseline(W):
     secs, units = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"])
     return {"value": units / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, single thread: lattice build + %d CG iterations (symmetric "
-                      "operator, k=%d) on a seeded %d-row subsample of the workload; %.1f s"
-                      % (CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"], secs)}
+            "sample": "FP64 oracle, single thread: lattice build + rank-%d preconditioner + %d "
+                      "CG iterations (symmetric operator, k=%d) on a seeded %d-row subsample of "
+                      "the workload; %.1f s"
+                      % (W["precond_rank"], CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"], secs)}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    W = dict(WORKLOAD, n=args.n)
+    W = dict(WORKLOAD, n=args.n, precond_rank=args.precond_rank)
     for _ in range(args.warmup):
         oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"])
     secs, units = 0.0, 0.0
@@ -408,9 +454,9 @@ def run_reference(args, world, rank):
         secs += s
         units += u
     value = units / secs / 1e6
-    sample = ("FP64 oracle, single thread, per step: lattice build + %d CG iterations "
-              "(symmetric operator, k=%d) on a seeded %d-row subsample of the workload"
-              % (REF_SAMPLE["iters"], W["k"], REF_SAMPLE["n"]))
+    sample = ("FP64 oracle, single thread, per step: lattice build + rank-%d preconditioner + "
+              "%d CG iterations (symmetric operator, k=%d) on a seeded %d-row subsample of the "
+              "workload" % (W["precond_rank"], REF_SAMPLE["iters"], W["k"], REF_SAMPLE["n"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,

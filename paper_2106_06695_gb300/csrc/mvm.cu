@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k,
                                                         const S* __restrict__ in,
                                                         S* __restrict__ out) {
   static_assert(CH == 1 || CH == 2, "one or two groups of four columns per thread");
-  const int rows_per_run = kThreads / G;
+  const int rows_per_run = blockDim.x / G;
   const int col = (int)(threadIdx.x % G) * (4 * CH);
   int64_t v[U];
   int ia[U][R], ic[U][R];
@@ -400,13 +400,14 @@ template <int CH, int U, class S>
 void launch_blur_rows(const Lattice* L, const int32_t* nbr, const Taps& taps, const S* in,
                       S* out, int k, cudaStream_t st) {
   const int G = k / (4 * CH);
-  const int64_t runs = ceil_div(L->m, kThreads / G);
+  const int threads = G * (kThreads / G);  // a whole number of rows per run
+  const int64_t runs = ceil_div(L->m, threads / G);
   const unsigned grid = (unsigned)ceil_div(runs, U);
   switch (L->r) {
-    case 1: k_blur_rows<CH, U, 1, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
-    case 2: k_blur_rows<CH, U, 2, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
-    case 3: k_blur_rows<CH, U, 3, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
-    default: k_blur_rows<CH, U, 4, S><<<grid, kThreads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    case 1: k_blur_rows<CH, U, 1, S><<<grid, threads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    case 2: k_blur_rows<CH, U, 2, S><<<grid, threads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    case 3: k_blur_rows<CH, U, 3, S><<<grid, threads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
+    default: k_blur_rows<CH, U, 4, S><<<grid, threads, 0, st>>>(L->m, G, k, taps, nbr, in, out); break;
   }
 }
 
@@ -414,9 +415,9 @@ template <class S>
 void launch_blur_t(const Lattice* L, int j, const Taps& taps, const S* in, S* out, int k,
                    cudaStream_t st) {
   const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
-  if (k % 8 == 0 && kThreads % (k / 8) == 0) {  // eight columns of two rows per thread
+  if (k % 8 == 0 && k / 8 <= kThreads) {  // eight columns of two rows per thread
     launch_blur_rows<2, 2, S>(L, nbr, taps, in, out, k, st);
-  } else if (k % 4 == 0 && kThreads % (k / 4) == 0) {
+  } else if (k % 4 == 0 && k / 4 <= kThreads) {
     launch_blur_rows<1, 2, S>(L, nbr, taps, in, out, k, st);
   } else {
     k_blur<S><<<(unsigned)ceil_div(L->m * k, kThreads), kThreads, 0, st>>>(L->m, k, L->r, taps, nbr,

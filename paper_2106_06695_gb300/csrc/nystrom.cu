@@ -13,10 +13,14 @@
 // P is symmetric positive definite for any computed B, so CG stays a CG whatever the
 // rounding in B; the Cholesky factors of the l x l matrices are computed in fp64 by one
 // block, the tall n x l products in fp32 with fixed-order partial sums (deterministic).
-// All row-indexed arrays are in the lattice's locality order.
+// B is stored in fp32 with rows padded to a multiple of 4 columns (zeros) and B^T B is
+// formed from the stored values.  All row-indexed arrays are in the lattice's locality
+// order.
 #include <algorithm>
 #include <cmath>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "sgp_internal.cuh"
 
@@ -25,6 +29,7 @@ namespace {
 
 constexpr int kRowsPerStage = 32;  // rows staged in shared memory per step
 constexpr int kTallBlocks = 2 * 152;
+constexpr int kApplyBlocks = 8 * 152;  // blocks of the per-iteration B^T r reduction
 
 // SplitMix64 (Steele, Lea & Flood 2014) at counter c: one +-1 per (point, column).
 __device__ __forceinline__ float rademacher(uint64_t seed, int64_t i, int j, int l) {
@@ -52,11 +57,15 @@ __global__ void k_shift(const int32_t* __restrict__ perm, int64_t n, int l, uint
   Y[e] = fmaf(nu, rademacher(seed, perm[p], (int)(e - p * l), l), Y[e]);
 }
 
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
 // Per-block partial of L^T X over the block's rows, L = Omega (regenerated) when OMEGA,
-// else L = X.  X: [n][l] fp32.  out: partial[block][l][l] (fp64 of fp32 block sums).
-template <bool OMEGA>
-__global__ void k_gram(const float* __restrict__ X, const int32_t* __restrict__ perm, int64_t n,
-                       int l, uint64_t seed, double* __restrict__ partial) {
+// else L = X.  X: [n][ld] (first l columns used).  out: partial[block][l][l] (fp64 of
+// fp32 block sums).
+template <bool OMEGA, class TX>
+__global__ void k_gram(const TX* __restrict__ X, int ld, const int32_t* __restrict__ perm,
+                       int64_t n, int l, uint64_t seed, double* __restrict__ partial) {
   extern __shared__ float sh[];
   float* xs = sh;                               // [kRowsPerStage][l]
   float* ls = sh + kRowsPerStage * l;           // [kRowsPerStage][l] (OMEGA only)
@@ -73,7 +82,7 @@ __global__ void k_gram(const float* __restrict__ X, const int32_t* __restrict__ 
     __syncthreads();
     for (int e = threadIdx.x; e < rows * l; e += blockDim.x) {
       const int rr = e / l, j = e - rr * l;
-      xs[e] = X[(base + rr) * l + j];
+      xs[e] = to_f(X[(base + rr) * ld + j]);
       if (OMEGA) ls[e] = rademacher(seed, perm[base + rr], j, l);
     }
     __syncthreads();
@@ -154,9 +163,9 @@ __global__ void k_tri_inv_t(const double* __restrict__ R, int l, double* __restr
   for (int i = 0; i < l; ++i) T[c * l + i] = (float)x[i];  // T[c][i] = (R^-1)[i][c]
 }
 
-// In place, row by row: Y[row] <- Y[row] T  (T in shared memory).
-__global__ void k_rows_times(float* __restrict__ Y, const float* __restrict__ T, int64_t n,
-                             int l) {
+// Row by row: Bh[row] = Y[row] T (T in shared memory), columns l..ld-1 zero.
+__global__ void k_rows_times(const float* __restrict__ Y, const float* __restrict__ T, int64_t n,
+                             int l, int ld, float* __restrict__ Bh) {
   extern __shared__ float sh[];
   float* ts = sh;              // [l][l]
   float* ys = sh + l * l;      // [rows_per_block][l]
@@ -171,113 +180,171 @@ __global__ void k_rows_times(float* __restrict__ Y, const float* __restrict__ T,
     if (rr < rows && row < n) {
       float a = 0.f;
       for (int j = 0; j < l; ++j) a = fmaf(ys[rr * l + j], ts[j * l + c], a);
-      Y[row * l + c] = a;
+      Bh[row * ld + c] = a;
+      if (c < ld - l) Bh[row * ld + l + c] = 0.f;
     }
   }
 }
 
-// Per-block partial of B^T r (l x k) with r = rh + rl; blockIdx.y selects a range of
-// kOutsPerBlock outputs, each thread owning up to kOwn of them.
-constexpr int kOwn = 8;
-constexpr int kOutsPerBlock = 256 * kOwn;
-__global__ void k_bt_r(const float* __restrict__ Bm, const float* __restrict__ rh,
-                       const float* __restrict__ rl, int64_t n, int l, int k,
-                       double* __restrict__ partial) {
+// Per-block partial of B^T r for the columns [c_off, c_off + 16) of r = rh + rl (ld x 16
+// outputs, padded rows of B are zero).  Each warp takes a contiguous range of rows; lane
+// `lane` owns the B columns lane, lane + 32, lane + 64, lane + 96 against all 16 r columns
+// (64 accumulators), reading its row of B coalesced; lane c < 16 loads r[row][c_off + c]
+// and shuffles it to the others.  The block's warps are combined in shared memory in a
+// fixed order.
+constexpr int kBtWarps = 8;
+constexpr int kBtRows = 2;
+__global__ void __launch_bounds__(kBtWarps * 32, 2) k_bt_r(const float* __restrict__ Bh, int ld,
+                                                        const float* __restrict__ rh,
+                                                        const float* __restrict__ rl, int64_t n,
+                                                        int k, int c_off,
+                                                        double* __restrict__ partial) {
+  extern __shared__ float red[];  // [kBtWarps][ld][16]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kc = min(16, k - c_off);
+  float acc[4][16];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
+  const int64_t per_warp = ceil_div(n, (int64_t)gridDim.x * kBtWarps);
+  const int64_t r0 = ((int64_t)blockIdx.x * kBtWarps + warp) * per_warp;
+  const int64_t r1 = std::min<int64_t>(n, r0 + per_warp);
+  // kBtRows rows per step: their loads are issued before any of their FMAs
+  for (int64_t row0 = r0; row0 < r1; row0 += kBtRows) {
+    float b[kBtRows][4], rv[kBtRows];
+#pragma unroll
+    for (int q = 0; q < kBtRows; ++q) {
+      const int64_t row = row0 + q;
+      const bool in = row < r1;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int j = lane + 32 * a;
+        b[q][a] = (in && j < ld) ? Bh[row * ld + j] : 0.f;
+      }
+      const int64_t e = row * k + c_off + lane;
+      rv[q] = (in && lane < kc) ? __fadd_rn(rh[e], rl[e]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kBtRows; ++q)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float rc = __shfl_sync(0xffffffffu, rv[q], c);  // r[row][c_off + c]
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][c] = fmaf(b[q][a], rc, acc[a][c]);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int j = lane + 32 * a;
+    if (j < ld)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) red[(warp * ld + j) * 16 + c] = acc[a][c];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < ld * kc; o += blockDim.x) {
+    const int j = o / kc, c = o - j * kc;
+    double sum = 0.0;
+    for (int w = 0; w < kBtWarps; ++w) sum += (double)red[(w * ld + j) * 16 + c];
+    partial[(int64_t)blockIdx.x * ld * k + (int64_t)j * k + c_off + c] = sum;
+  }
+}
+
+// Minv = (Q Q^T)^-1 for lower-triangular Q (fp64): W = Q^-1 by forward substitution per
+// column (thread c), then Minv = W^T W.  `work` holds W ([l][l]).
+__global__ void k_inv_from_cholesky(const double* __restrict__ Q, int l, double* __restrict__ W,
+                                    double* __restrict__ Minv) {
+  for (int c = threadIdx.x; c < l; c += blockDim.x) {
+    for (int i = 0; i < l; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int j = c; j < i; ++j) s -= Q[i * l + j] * W[j * l + c];
+      W[i * l + c] = (i < c) ? 0.0 : s / Q[i * l + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int a = e / l, b = e % l;
+    double s = 0.0;
+    for (int i = max(a, b); i < l; ++i) s += W[i * l + a] * W[i * l + b];
+    Minv[e] = s;
+  }
+}
+
+// u = Minv t (fp64, one output per thread), written as fp32 [ld][k] (rows >= l stay 0).
+__global__ void k_minv_t(const double* __restrict__ Minv, const double* __restrict__ t, int l,
+                         int k, float* __restrict__ u) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= l * k) return;
+  const int i = o / k, c = o - i * k;
+  double s = 0.0;
+  for (int j = 0; j < l; ++j) s += Minv[i * l + j] * t[j * k + c];
+  u[i * k + c] = (float)s;
+}
+
+// z = (r - B u) / noise for the columns [c_off, c_off + 16) and per-block column sums of
+// r z.  One thread per row: it streams its row of B as float4 and reads u ([ld][16] of the
+// chunk, in shared memory) as broadcasts, 64 FMAs per float4 of B.
+constexpr int kZThreads = 256;
+__global__ void __launch_bounds__(kZThreads) k_apply_z(const float* __restrict__ Bh, int ld,
+                                                       const float* __restrict__ u,
+                                                       const float* __restrict__ rh,
+                                                       const float* __restrict__ rl,
+                                                       float inv_noise, int64_t n, int k,
+                                                       int c_off, float* __restrict__ z,
+                                                       double* __restrict__ partial) {
   extern __shared__ float sh[];
-  float* bs = sh;                          // [kRowsPerStage][l]
-  float* rs = sh + kRowsPerStage * l;      // [kRowsPerStage][k]
-  const int outs = l * k;
-  const int o0 = blockIdx.y * kOutsPerBlock;
-  float acc[kOwn];
+  float* us = sh;                                         // [ld][16]
+  double* red = reinterpret_cast<double*>(sh + ld * 16);  // [kZThreads][16]
+  const int kc = min(16, k - c_off);
+  for (int e = threadIdx.x; e < ld * 16; e += blockDim.x) {
+    const int q = e / 16, c = e % 16;
+    us[e] = c < kc ? u[q * k + c_off + c] : 0.f;
+  }
+  __syncthreads();
+  dfloat acc[16];
 #pragma unroll
-  for (int q = 0; q < kOwn; ++q) acc[q] = 0.f;
-  const int64_t rows_per_block = ceil_div(n, gridDim.x);
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t r1 = std::min<int64_t>(n, r0 + rows_per_block);
-  for (int64_t base = r0; base < r1; base += kRowsPerStage) {
-    const int rows = (int)std::min<int64_t>(kRowsPerStage, r1 - base);
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * l; e += blockDim.x) bs[e] = Bm[base * l + e];
-    for (int e = threadIdx.x; e < rows * k; e += blockDim.x)
-      rs[e] = __fadd_rn(rh[base * k + e], rl[base * k + e]);
-    __syncthreads();
+  for (int c = 0; c < 16; ++c) acc[c] = {0.f, 0.f};
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    float s[16];
 #pragma unroll
-    for (int q = 0; q < kOwn; ++q) {
-      const int o = o0 + threadIdx.x + q * blockDim.x;
-      if (o < outs) {
-        const int j = o / k, c = o - j * k;
-        float a = acc[q];
-        for (int rr = 0; rr < rows; ++rr) a = fmaf(bs[rr * l + j], rs[rr * k + c], a);
-        acc[q] = a;
+    for (int c = 0; c < 16; ++c) s[c] = 0.f;
+    const float4* b4 = reinterpret_cast<const float4*>(Bh + row * ld);
+    for (int q4 = 0; q4 < ld / 4; ++q4) {
+      const float4 b = b4[q4];
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4* u4 = reinterpret_cast<const float4*>(us + (q4 * 4 + a) * 16);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float4 uu = u4[g];
+          s[4 * g + 0] = fmaf(bv[a], uu.x, s[4 * g + 0]);
+          s[4 * g + 1] = fmaf(bv[a], uu.y, s[4 * g + 1]);
+          s[4 * g + 2] = fmaf(bv[a], uu.z, s[4 * g + 2]);
+          s[4 * g + 3] = fmaf(bv[a], uu.w, s[4 * g + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c < kc) {
+        const int64_t e = row * k + c_off + c;
+        const float r = __fadd_rn(rh[e], rl[e]);
+        const float zz = (r - s[c]) * inv_noise;
+        z[e] = zz;
+        acc[c] = df_add(acc[c], df_two_prod(r, zz));
       }
     }
   }
 #pragma unroll
-  for (int q = 0; q < kOwn; ++q) {
-    const int o = o0 + threadIdx.x + q * blockDim.x;
-    if (o < outs) partial[(int64_t)blockIdx.x * outs + o] = (double)acc[q];
-  }
-}
-
-// u = (Q Q^T)^-1 t for each of the k columns (Q lower, fp64); one block, one thread per
-// column.  u is written as fp32 [l][k].
-__global__ void k_solve_qqt(const double* __restrict__ Q, const double* __restrict__ t, int l,
-                            int k, double* __restrict__ work, float* __restrict__ u) {
-  const int c = threadIdx.x;
-  if (c >= k) return;
-  double* y = work + (int64_t)c * l;
-  for (int i = 0; i < l; ++i) {  // Q y = t
-    double s = t[i * k + c];
-    for (int j = 0; j < i; ++j) s -= Q[i * l + j] * y[j];
-    y[i] = s / Q[i * l + i];
-  }
-  for (int i = l - 1; i >= 0; --i) {  // Q^T x = y
-    double s = y[i];
-    for (int j = i + 1; j < l; ++j) s -= Q[j * l + i] * y[j];
-    y[i] = s / Q[i * l + i];
-  }
-  for (int i = 0; i < l; ++i) u[i * k + c] = (float)y[i];
-}
-
-// z = (r - B u) / noise per row (u in shared memory) and per-block column sums of r z.
-template <int VEC>
-__global__ void k_apply_z(const float* __restrict__ Bm, const float* __restrict__ u,
-                          const float* __restrict__ rh, const float* __restrict__ rl,
-                          float inv_noise, int64_t n, int l, int k, float* __restrict__ z,
-                          double* __restrict__ partial) {
-  extern __shared__ float us[];  // [l][k]
-  for (int e = threadIdx.x; e < l * k; e += blockDim.x) us[e] = u[e];
+  for (int c = 0; c < 16; ++c) red[threadIdx.x * 16 + c] = df_to_double(acc[c]);
   __syncthreads();
-  const int G = k / VEC;
-  const int rows_per_block = blockDim.x / G;
-  const int c0 = (int)(threadIdx.x % G) * VEC;
-  dfloat acc[VEC];
-#pragma unroll
-  for (int j = 0; j < VEC; ++j) acc[j] = {0.f, 0.f};
-  for (int64_t row = (int64_t)blockIdx.x * rows_per_block + threadIdx.x / G; row < n;
-       row += (int64_t)gridDim.x * rows_per_block) {
-    float s[VEC];
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) s[j] = 0.f;
-    const float* b = Bm + row * l;
-    for (int q = 0; q < l; ++q) {
-      const float bq = b[q];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) s[j] = fmaf(bq, us[q * k + c0 + j], s[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      const int64_t e = row * k + c0 + j;
-      const float r = __fadd_rn(rh[e], rl[e]);
-      const float zz = (r - s[j]) * inv_noise;
-      z[e] = zz;
-      acc[j] = df_add(acc[j], df_two_prod(r, zz));
-    }
+  for (int c = threadIdx.x; c < kc; c += blockDim.x) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += red[i * 16 + c];
+    partial[(int64_t)blockIdx.x * k + c_off + c] = t;
   }
-  double dd[VEC];
-#pragma unroll
-  for (int j = 0; j < VEC; ++j) dd[j] = df_to_double(acc[j]);
-  block_column_sums<VEC>(dd, k, partial + (int64_t)blockIdx.x * k);
 }
 
 }  // namespace
@@ -286,6 +353,7 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
                           cudaStream_t st) {
   const int64_t n = L->n;
   l = rank;
+  ld = (rank + 3) / 4 * 4;
   this->noise = noise;
   this->n = n;
 #define NY_CHECK(expr, what)                                  \
@@ -298,57 +366,69 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   };
-  float* om = nullptr;
-  NY_CHECK(get((void**)&Bm, (size_t)n * l * sizeof(float)), "alloc Nystrom B");
-  NY_CHECK(cudaMallocAsync((void**)&om, (size_t)n * l * sizeof(float), st), "alloc sketch");
-  NY_CHECK(get((void**)&partial, (size_t)kTallBlocks * l * std::max(l, kMaxK) * sizeof(double)),
-           "alloc partial");
-  static bool attrs = false;  // shared-memory sizes beyond the 48 KB default
-  if (!attrs) {
-    const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_rows_times, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_bt_r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_apply_z<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_apply_z<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    attrs = true;
+  {  // shared-memory sizes beyond the 48 KB default, once per device
+    static bool attrs[64] = {};
+    int dev = 0;
+    NY_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev >= 0 && dev < 64 && !attrs[dev]) {
+      const int big = 200 * 1024;
+      cudaFuncSetAttribute(k_gram<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_gram<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_rows_times, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_bt_r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      attrs[dev] = true;
+    }
   }
+  float* Y = nullptr;
+  float* om = nullptr;
+  NY_CHECK(get((void**)&Bh, (size_t)n * ld * sizeof(float)), "alloc Nystrom B");
+  NY_CHECK(cudaMallocAsync((void**)&Y, (size_t)n * l * sizeof(float), st), "alloc Nystrom Y");
+  NY_CHECK(cudaMallocAsync((void**)&om, (size_t)n * l * sizeof(float), st), "alloc sketch");
+  NY_CHECK(get((void**)&partial,
+               std::max((size_t)kTallBlocks * l * l, (size_t)kApplyBlocks * ld * kMaxK) *
+                   sizeof(double)),
+           "alloc partial");
   NY_CHECK(get((void**)&C, (size_t)l * l * sizeof(double)), "alloc C");
   NY_CHECK(get((void**)&Q, (size_t)l * l * sizeof(double)), "alloc Q");
+  NY_CHECK(get((void**)&Minv, (size_t)l * l * sizeof(double)), "alloc Minv");
   NY_CHECK(get((void**)&T, (size_t)l * l * sizeof(float)), "alloc T");
   NY_CHECK(get((void**)&work, (size_t)std::max(l, kMaxK) * l * sizeof(double)), "alloc work");
-  NY_CHECK(get((void**)&tvec, (size_t)l * kMaxK * sizeof(double)), "alloc t");
-  NY_CHECK(get((void**)&u, (size_t)l * kMaxK * sizeof(float)), "alloc u");
+  NY_CHECK(get((void**)&tvec, (size_t)ld * kMaxK * sizeof(double)), "alloc t");
+  NY_CHECK(get((void**)&u, (size_t)ld * kMaxK * sizeof(float)), "alloc u");
   NY_CHECK(get((void**)&status, sizeof(int)), "alloc status");
   NY_CHECK(cudaMemsetAsync(status, 0, sizeof(int), st), "clear status");
+  NY_CHECK(cudaMemsetAsync(u, 0, (size_t)ld * kMaxK * sizeof(float), st), "clear u");
 
   // Y = A Omega (one l-column product in locality order), then Y += nu Omega
   sgp_status s = ensure_lattice_values(L, l, st);
   if (s != SGP_OK) return s;
   const unsigned g1 = (unsigned)ceil_div(n * l, 256);
   k_fill_sketch<<<g1, 256, 0, st>>>(L->perm, n, l, seed, om);
-  enqueue_mvm(L, om, l, blur, L->outputscale, 0.f, Bm, st, nullptr, /*internal=*/true);
+  enqueue_mvm(L, om, l, blur, L->outputscale, 0.f, Y, st, nullptr, /*internal=*/true);
   NY_CHECK(cudaFreeAsync(om, st), "free sketch");
   // nu: a small shift keeps C positive definite when A Omega is rank deficient
   const float nu = 1e-3f * noise;
-  k_shift<<<g1, 256, 0, st>>>(L->perm, n, l, seed, nu, Bm);
+  k_shift<<<g1, 256, 0, st>>>(L->perm, n, l, seed, nu, Y);
   note_launches(2);
   // C = Omega^T Y, Cholesky C = R R^T
   const size_t gram_smem = 2 * (size_t)kRowsPerStage * l * sizeof(float);
-  k_gram<true><<<kTallBlocks, 256, gram_smem, st>>>(Bm, L->perm, n, l, seed, partial);
+  k_gram<true, float><<<kTallBlocks, 256, gram_smem, st>>>(Y, l, L->perm, n, l, seed, partial);
   k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, C);
   k_cholesky<<<1, 1024, 0, st>>>(C, l, 0.0, status);
   // B = Y R^-T
   k_tri_inv_t<<<1, 128, 0, st>>>(C, l, work, T);
   const int rows = std::max(1, 1024 / l);
   const size_t rt_smem = ((size_t)l * l + (size_t)rows * l) * sizeof(float);
-  k_rows_times<<<kTallBlocks, rows * l, rt_smem, st>>>(Bm, T, n, l);
-  // M = noise I + B^T B, Cholesky M = Q Q^T
-  k_gram<false><<<kTallBlocks, 256, gram_smem, st>>>(Bm, L->perm, n, l, seed, partial);
+  k_rows_times<<<kTallBlocks, rows * l, rt_smem, st>>>(Y, T, n, l, ld, (float*)Bh);
+  NY_CHECK(cudaFreeAsync(Y, st), "free Nystrom Y");
+  // M = noise I + B^T B from the stored B, Cholesky M = Q Q^T
+  k_gram<false, float><<<kTallBlocks, 256, gram_smem, st>>>((const float*)Bh, ld, L->perm, n, l,
+                                                            seed, partial);
   k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, Q);
   k_cholesky<<<1, 1024, 0, st>>>(Q, l, (double)noise, status);
-  note_launches(8);
+  k_inv_from_cholesky<<<1, 128, 0, st>>>(Q, l, work, Minv);
+  note_launches(9);
   NY_CHECK(cudaGetLastError(), "building the Nystrom preconditioner");
   int hs = 0;
   NY_CHECK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
@@ -360,19 +440,20 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
 
 void Nystrom::apply(const float* rh, const float* rl, int k, float* z, double* dot_partial,
                     int64_t dot_blocks, int block_threads, cudaStream_t st) const {
-  const size_t bt_smem = (size_t)kRowsPerStage * (l + k) * sizeof(float);
-  const dim3 bt_grid(kTallBlocks, (unsigned)ceil_div((int64_t)l * k, kOutsPerBlock));
-  k_bt_r<<<bt_grid, 256, bt_smem, st>>>(Bm, rh, rl, n, l, k, partial);
-  k_sum_blocks<<<(unsigned)ceil_div(l * k, 256), 256, 0, st>>>(partial, kTallBlocks, l * k, tvec);
-  k_solve_qqt<<<1, kMaxK, 0, st>>>(Q, tvec, l, k, work, u);
-  const size_t z_smem = (size_t)l * k * sizeof(float);
-  if (k % 4 == 0)
-    k_apply_z<4><<<(unsigned)dot_blocks, block_threads, z_smem, st>>>(Bm, u, rh, rl, 1.f / noise, n,
-                                                                      l, k, z, dot_partial);
-  else
-    k_apply_z<1><<<(unsigned)dot_blocks, block_threads, z_smem, st>>>(Bm, u, rh, rl, 1.f / noise, n,
-                                                                      l, k, z, dot_partial);
-  note_launches(4);
+  (void)block_threads;
+  const size_t bt_smem = (size_t)kBtWarps * ld * 16 * sizeof(float);
+  for (int c_off = 0; c_off < k; c_off += 16)
+    k_bt_r<<<kApplyBlocks, kBtWarps * 32, bt_smem, st>>>((const float*)Bh, ld, rh, rl, n, k, c_off,
+                                                         partial);
+  k_sum_blocks<<<(unsigned)ceil_div((int64_t)ld * k, 256), 256, 0, st>>>(partial, kApplyBlocks,
+                                                                       ld * k, tvec);
+  k_minv_t<<<(unsigned)ceil_div((int64_t)l * k, 128), 128, 0, st>>>(Minv, tvec, l, k, u);
+  const size_t z_smem = (size_t)ld * 16 * sizeof(float) + (size_t)kZThreads * 16 * sizeof(double);
+  for (int c_off = 0; c_off < k; c_off += 16)
+    k_apply_z<<<(unsigned)dot_blocks, kZThreads, z_smem, st>>>((const float*)Bh, ld, u, rh, rl,
+                                                               1.f / noise, n, k, c_off, z,
+                                                               dot_partial);
+  note_launches(2 + 2 * ceil_div(k, 16));
 }
 
 void Nystrom::release(cudaStream_t st) {

@@ -154,17 +154,19 @@ sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, flo
 constexpr int kMaxRank = 128;
 struct Nystrom {
   int l = 0;
+  int ld = 0;                  // l rounded up to 8: row stride of Bh
   int64_t n = 0;
   float noise = 0.f;
   bool ok = false;             // false when a Cholesky pivot failed (then not used)
-  float* Bm = nullptr;         // [n][l] B = (A Omega + nu Omega) R^-T, locality order
+  void* Bh = nullptr;          // bf16 [n][ld] B = (A Omega + nu Omega) R^-T, locality order
   double* partial = nullptr;   // per-block partial sums of the tall products
   double* C = nullptr;         // [l][l] Omega^T Y, then its Cholesky factor R
   double* Q = nullptr;         // [l][l] Cholesky factor of noise I + B^T B
+  double* Minv = nullptr;      // [l][l] (noise I + B^T B)^-1
   float* T = nullptr;          // [l][l] R^-T
   double* work = nullptr;
-  double* tvec = nullptr;      // [l][k] B^T r
-  float* u = nullptr;          // [l][k] (noise I + B^T B)^-1 B^T r
+  double* tvec = nullptr;      // [ld][k] B^T r
+  float* u = nullptr;          // [ld][k] (noise I + B^T B)^-1 B^T r, rows >= l zero
   int* status = nullptr;
   std::vector<void*> ptrs;
   // Sketch, factor and keep B, Q for the handle's operator `blur` (enqueued on st, one

@@ -88,7 +88,7 @@ def test_build_bit_exact(case):
     assert_same_lattice(lat, ref)
 
 
-@pytest.mark.parametrize("k", [1, 3, 4, 9, 16])
+@pytest.mark.parametrize("k", [1, 3, 4, 9, 12, 16, 100])
 @pytest.mark.parametrize("blur", ["sequential", "transpose", "symmetric"])
 def test_mvm_parity(blur, k):
     X, L = make_inputs("gmm", 6000, 6, 0.8, seed=5)

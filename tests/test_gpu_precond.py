@@ -22,7 +22,7 @@ def gpu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("n,d,k,rank", [(3000, 5, 4, 100), (5000, 6, 9, 64), (4000, 3, 16, 100)])
+@pytest.mark.parametrize("n,d,k,rank", [(3000, 5, 4, 100), (5000, 6, 9, 64), (4000, 3, 16, 100), (4000, 4, 20, 48)])
 def test_pcg_converges_like_the_oracle(n, d, k, rank):
     from paper_2106_06695_gb300.lattice import Lattice
 
