@@ -1,0 +1,134 @@
+/* sgp_serve.h -- C-ABI of the continuous-batching GP posterior server (sm_103a).
+ *
+ * A request is one exact-GP prediction (Sec. 2, Eq. gp_pred_mean and Eq. gp_pred_cov with
+ * a zero prior mean): training inputs X [n][d] with targets y [n], test inputs Xs
+ * [ns][d], ARD lengthscales, outputscale and noise variance sigma^2.  The server returns
+ *   mean[t] = (K*X (K + sigma^2 I)^-1 y)[t]
+ *   var[t]  = outputscale - (1/S) sum_s z_s[t] (K*X (K + sigma^2 I)^-1 KX* z_s)[t]
+ * where K = outputscale K~ is the lattice kernel (symmetric blur SGP_BLUR_SYMMETRIC) on
+ * one lattice built over the joint point set [X; Xs] (so that K*X is a slice at the test
+ * rows of the same operator), and z_1..z_S are Rademacher probe vectors over the test
+ * points: z_s[t] = -1 if the top bit of SplitMix64 at counter t S + s + 1 (seed =
+ * request seed) is set, else +1.  The variance term is the probe (Hutchinson-type)
+ * estimate of the diagonal of K*X (K + sigma^2 I)^-1 KX*; its expectation over the probes
+ * is that diagonal.  The prior diagonal is outputscale (k(0) = 1 for the kernels here).
+ *
+ * Each request needs one linear solve with k = 1 + S right-hand sides (y and KX* z_s):
+ * batched CG as in sgp_cg_solve (double-float iterate and residual, fp64 dot products,
+ * per-column stopping ||r|| / ||b|| <= tol or max_iter iterations).
+ *
+ * Continuous batching: requests are admitted in arrival order while the number of active
+ * requests is below max_active and the device bytes they may hold stay within
+ * hbm_budget (an upper bound per request from sgp_request_bytes_bound until its lattice
+ * is built, then its actual allocation).  Every CG iteration of all active requests runs
+ * as one sequence of kernels over a device table of the active requests (fixed grids,
+ * per-request and per-column convergence masks), replayed from a CUDA graph; a request
+ * leaves the batch as soon as its columns have stopped, and new requests join at the
+ * next step.  Each request's arithmetic is partitioned by its own sizes only, so its
+ * results are bitwise the same alone and in any mix.  max_active = 1 gives the plain
+ * one-request-at-a-time path with the same kernels.
+ *
+ * Threading: a server is used by one host thread at a time.  Host buffers of a request
+ * (X, y, Xs, lengthscales, mean, var) must stay valid until the request has completed
+ * (sgp_request_stats.done != 0).  Errors follow sgp.h: every call returns an sgp_status
+ * and sgp_last_error() has the message; a request whose build fails completes with its
+ * own status and does not stop the server.
+ */
+#ifndef SGP_SERVE_H_
+#define SGP_SERVE_H_
+
+#include "sgp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgp_server sgp_server; /* opaque; created by sgp_server_create */
+
+typedef struct {
+  unsigned long long hbm_budget; /* device bytes the active requests may hold; default
+                                    half of the device's total memory                    */
+  int max_active;     /* requests in the batch at once, 1..64; default 16 (1 = plain)     */
+  int probes;         /* Rademacher probes S of the variance estimate, 0..31; default 8   */
+  int order_r;        /* stencil order (as sgp_opts); default 1                           */
+  int kernel;         /* SGP_KERNEL_*; default SGP_KERNEL_RBF_BINOMIAL                    */
+  double spacing_s;   /* > 0 overrides the kernel rule's spacing; default 0               */
+  int value_dtype;    /* SGP_VALUES_F32 / SGP_VALUES_BF16 lattice value storage           */
+  double tol;         /* CG tolerance on ||r|| / ||b||; default 1e-3                      */
+  int max_iter;       /* CG iteration cap; default 500                                    */
+  int check_every;    /* CG iterations per sgp_server_step between flag reads; default 8 */
+} sgp_server_opts;
+
+typedef struct {
+  const float* X;            /* host [n][d] training inputs                               */
+  const float* y;            /* host [n] training targets                                 */
+  long long n;               /* >= 1                                                      */
+  const float* Xs;           /* host [ns][d] test inputs                                  */
+  long long ns;              /* >= 1; n + ns <= 2^31 / (d + 1)                            */
+  int d;                     /* 1..127                                                    */
+  const float* lengthscales; /* host [d], each > 0                                        */
+  float outputscale;         /* > 0                                                       */
+  float noise;               /* sigma^2 > 0                                               */
+  unsigned long long seed;   /* probe seed                                                */
+  float* mean;               /* host [ns] output                                          */
+  float* var;                /* host [ns] output (may be NULL when probes = 0)            */
+  double arrival_us;         /* arrival time on the server clock (sgp_server_clock_us), or
+                                < 0 for "now"; latency is measured from it                */
+} sgp_request;
+
+typedef struct {
+  int done;                  /* 1 once mean/var are written (or the request failed)      */
+  int status;                /* sgp_status of the request                                 */
+  int iters;                 /* CG iterations the request ran                             */
+  double rel_res;            /* largest final ||r|| / ||b|| over its columns              */
+  double arrival_us, admit_us, done_us; /* server clock                                   */
+  long long m;               /* lattice vertices                                          */
+  unsigned long long bytes;  /* device bytes the request held while active                */
+} sgp_request_stats;
+
+/* Fill *opts with the defaults listed above (hbm_budget from the current device, or 0
+ * without one). */
+void sgp_server_opts_init(sgp_server_opts* opts);
+
+/* Upper bound of the device bytes one request holds at its peak (lattice build work
+ * space included) for n_points = n + ns points in d dimensions, stencil order r, k
+ * right-hand sides and the value type: every size taken at its bound m = n_points
+ * (d + 1) (Sec. 5.2: at most d + 1 vertices per point).  Host only. */
+unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_r, int k,
+                                           int value_dtype);
+
+/* Create a server on the current device (its own CUDA streams).  opts may be NULL. */
+sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out);
+
+/* Queue a request (nothing is copied or launched yet); *id receives its id.
+ * SGP_ERR_INVALID_ARG for bad sizes or pointers, or a request whose bound exceeds the
+ * whole budget (it could never be admitted). */
+sgp_status sgp_server_submit(sgp_server* srv, const sgp_request* req, long long* id);
+
+/* One scheduling round: enqueue check_every CG iterations of the active batch, admit and
+ * set up queued requests while those run (lattice build, right-hand sides), then read
+ * the convergence flags, finish the requests that stopped (predictive slice, copy of
+ * mean/var to the host) and release their memory.  *completed (may be NULL) receives the
+ * number of requests finished by this call.  Returns at once when nothing is queued or
+ * active. */
+sgp_status sgp_server_step(sgp_server* srv, int* completed);
+
+/* Statistics of request `id` (valid at any time; done = 0 while it is queued/active). */
+sgp_status sgp_server_stats(const sgp_server* srv, long long id, sgp_request_stats* out);
+
+/* Queue and batch state: queued and active request counts, device bytes held by active
+ * requests (as accounted against the budget), and the largest batch seen so far. */
+sgp_status sgp_server_info(const sgp_server* srv, int* queued, int* active,
+                           unsigned long long* bytes_in_use, int* peak_active);
+
+/* Microseconds since the server was created (steady clock). */
+double sgp_server_clock_us(const sgp_server* srv);
+
+/* Wait for the device, release every request's memory, the streams and the graphs. */
+void sgp_server_destroy(sgp_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGP_SERVE_H_ */

@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     build_oracle,
     dense_rbf,
     elevate,
+    gp_posterior,
     rademacher_sketch,
     splitmix64,
     simplex,

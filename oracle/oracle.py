@@ -325,3 +325,79 @@ class OracleLattice:
         if rc != 0:
             raise ValueError("orc_cg: invalid arguments")
         return X.reshape(shape), iters, rel
+
+
+def _cg_columns(apply_A, B, tol: float, max_iter: int):
+    """Textbook CG (Sec. 2), one independent iteration per column of B: x_0 = 0, stop a
+    column when ||r|| / ||b|| <= tol or after max_iter iterations; b = 0 gives x = 0."""
+    n, k = B.shape
+    X = np.zeros((n, k))
+    R = B.copy()
+    P = R.copy()
+    bnorm = np.linalg.norm(B, axis=0)
+    rho = (R * R).sum(0)
+    iters = np.zeros(k, np.int32)
+    rel = np.where(bnorm > 0, 1.0, 0.0)
+    active = (bnorm > 0) & (1.0 > tol) & (max_iter > 0)
+    while active.any():
+        AP = apply_A(P)
+        for c in np.nonzero(active)[0]:
+            pap = P[:, c] @ AP[:, c]
+            if not pap > 0:
+                active[c] = False
+                continue
+            a = rho[c] / pap
+            X[:, c] += a * P[:, c]
+            R[:, c] -= a * AP[:, c]
+            iters[c] += 1
+            rr = R[:, c] @ R[:, c]
+            rel[c] = np.sqrt(rr) / bnorm[c]
+            if rel[c] <= tol or iters[c] >= max_iter:
+                active[c] = False
+                continue
+            P[:, c] = R[:, c] + (rr / rho[c]) * P[:, c]
+            rho[c] = rr
+    return X, iters, rel
+
+
+def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: int = 8,
+                 seed: int = 0, tol: float = 1e-3, max_iter: int = 500,
+                 kind: int = RBF_BINOMIAL, r: int = 1, Z=None):
+    """Posterior mean and probe-estimated variance at the test inputs Xs.
+
+    Eq. gp_pred_mean with a zero prior mean: mean = K*X (K_XX + noise I)^-1 y, and the
+    diagonal of Eq. gp_pred_cov: var = k(x, x) - diag(K*X (K_XX + noise I)^-1 KX*),
+    with k(x, x) = outputscale and the second term estimated from probe vectors z_s over
+    the test points, diag(M) ~ (1/S) sum_s z_s * (M z_s) (its expectation is diag(M) for
+    independent +-1 entries; exact when the z_s run over all sign patterns).  Every
+    covariance is the lattice operator outputscale K~ (symmetric blur) of ONE lattice
+    built over the joint point set [X; Xs]: K_XX, KX* and K*X are its blocks.  Default
+    probes: Z[t][s] from rademacher_sketch(ns, probes, seed).  Returns (mean, var,
+    iterations per column, final relative residual per column); column 0 is y, columns
+    1..S the probes.
+    """
+    X = np.asarray(X, np.float32)
+    Xs = np.asarray(Xs, np.float32)
+    n, ns = X.shape[0], Xs.shape[0]
+    L = OracleLattice(np.vstack([X, Xs]), ls, kind=kind, r=r)
+    Z = rademacher_sketch(ns, probes, seed) if Z is None else np.asarray(Z, np.float64)
+    S = Z.shape[1]
+
+    def K(V):  # outputscale K~ V on the joint point set
+        return L.mvm(V, mode=2, alpha=outputscale)
+
+    def pad(V):  # training-row vector -> joint vector with zero test rows
+        full = np.zeros((n + ns, V.shape[1]))
+        full[:n] = V
+        return full
+
+    B = np.asarray(y, np.float64)[:, None]
+    if S > 0:
+        Vz = np.zeros((n + ns, S))
+        Vz[n:] = Z
+        B = np.concatenate([B, K(Vz)[:n]], 1)
+    W, iters, rel = _cg_columns(lambda V: K(pad(V))[:n] + noise * V, B, tol, max_iter)
+    P = K(pad(W))[n:]
+    mean = P[:, 0]
+    var = outputscale - (Z * P[:, 1:]).mean(1) if S > 0 else np.zeros(ns)
+    return mean, var, iters, rel

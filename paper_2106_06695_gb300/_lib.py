@@ -1,4 +1,5 @@
-"""ctypes loader for libsgp.so, the sm_103a lattice library (C-ABI in include/sgp.h).
+"""ctypes loader for libsgp.so, the sm_103a lattice library (C-ABI in include/sgp.h and
+include/sgp_serve.h).
 
 This module only declares the C signatures.  It never substitutes another
 implementation: if the library is missing, loading fails with an error.
@@ -12,7 +13,8 @@ import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsgp.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "sgp.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+HEADERS = [os.path.join(INCLUDE, "sgp.h"), os.path.join(INCLUDE, "sgp_serve.h")]
 
 SGP_OK = 0
 STATUS_NAMES = {0: "SGP_OK", 1: "SGP_ERR_INVALID_ARG", 2: "SGP_ERR_OOM", 3: "SGP_ERR_RANGE",
@@ -31,6 +33,30 @@ class sgp_opts(ctypes.Structure):
                 ("precond_seed", ctypes.c_ulonglong)]
 
 
+class sgp_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_ulonglong), ("max_active", ctypes.c_int),
+                ("probes", ctypes.c_int), ("order_r", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("spacing_s", ctypes.c_double), ("value_dtype", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("check_every", ctypes.c_int)]
+
+
+class sgp_request(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_longlong),
+                ("Xs", ctypes.c_void_p), ("ns", ctypes.c_longlong), ("d", ctypes.c_int),
+                ("lengthscales", ctypes.c_void_p), ("outputscale", ctypes.c_float),
+                ("noise", ctypes.c_float), ("seed", ctypes.c_ulonglong),
+                ("mean", ctypes.c_void_p), ("var", ctypes.c_void_p),
+                ("arrival_us", ctypes.c_double)]
+
+
+class sgp_request_stats(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("arrival_us", ctypes.c_double),
+                ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong)]
+
+
 class SGPError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
@@ -41,10 +67,12 @@ _lib = None
 
 
 def declared_functions() -> list:
-    """Names of the functions include/sgp.h declares."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sgp_[a-z_0-9]+)\s*\(", text)))
+    """Names of the functions the headers under include/ declare."""
+    names = set()
+    for header in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(header).read(), flags=re.S)
+        names.update(re.findall(r"\b(sgp_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def load():
@@ -76,6 +104,17 @@ def load():
         "sgp_kernel_launches": (I64, []),
         "sgp_last_error": (ctypes.c_char_p, []),
         "sgp_version": (I, []),
+        "sgp_server_opts_init": (None, [ctypes.POINTER(sgp_server_opts)]),
+        "sgp_request_bytes_bound": (ctypes.c_ulonglong, [ctypes.c_longlong, I, I, I, I]),
+        "sgp_server_create": (I, [ctypes.POINTER(sgp_server_opts), ctypes.POINTER(P)]),
+        "sgp_server_submit": (I, [P, ctypes.POINTER(sgp_request),
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+        "sgp_server_step": (I, [P, ctypes.POINTER(I)]),
+        "sgp_server_stats": (I, [P, ctypes.c_longlong, ctypes.POINTER(sgp_request_stats)]),
+        "sgp_server_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(I)]),
+        "sgp_server_clock_us": (Dbl, [P]),
+        "sgp_server_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)

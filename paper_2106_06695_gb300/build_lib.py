@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "build.cu", "mvm.cu", "cg.cu", "scan_sort.cu", "static_mvm.cu", "nystrom.cu",
-           "stencil.cpp"]
+           "serve.cu", "stencil.cpp"]
 NO_FMA = {"build.cu"}
 
 
@@ -46,7 +46,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "sgp.h")]
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+            [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)])
     return any(os.path.getmtime(p) > t for p in deps)
 
 

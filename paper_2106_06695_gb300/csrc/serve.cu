@@ -1,0 +1,1249 @@
+// Continuous-batching server of GP posterior requests (Sec. 2: Eq. gp_pred_mean and
+// Eq. gp_pred_cov, solved with CG that touches the kernel only through lattice MVMs).
+//
+// Per request: one lattice over the joint point set [X; Xs] (Sec. 3.2), so that the
+// cross-covariances K*X and KX* are the same operator sliced at test or training rows.
+// The CG system is (outputscale K~ + noise I) restricted to the training rows: the
+// slice writes zero at test rows, and the right-hand sides are zero there, so every CG
+// vector stays in the training subspace.  Right-hand sides: column 0 = y, columns
+// 1..S = KX* z_s for Rademacher probes z_s over the test points; after the solve one
+// product sliced at the test rows gives the mean (column 0) and the probe estimate of
+// diag(K*X A^-1 KX*) (columns 1..S).
+//
+// Batching: one CG iteration of every active request is a fixed sequence of kernels
+// (splat, two fix-ups, 2 Dmax blur passes, slice with <p, Ap>, alpha, x/r update,
+// convergence check and beta, p update) with fixed grids.  Each kernel walks "virtual
+// blocks" over a device table of the active requests; a request's virtual blocks cover
+// its own rows in a partition fixed by its own sizes, so its results (and reduction
+// order) do not depend on the other requests in the batch.  Requests that have stopped
+// are skipped by a device flag; blur pass t touches only requests with t < 2 (d + 1).
+// Requests are grouped into lanes of similar dimension and per-iteration work; each lane
+// is such a batch with its own table, stream and CUDA graph of one iteration (captured
+// once per Dmax and replayed), rewritten (stream-ordered) when requests join or leave,
+// and the lanes run concurrently.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#include "sgp_internal.cuh"
+#include "values.cuh"
+#include "../../include/sgp_serve.h"
+
+namespace sgp {
+namespace {
+
+constexpr int kMaxSlots = 64;       // requests in one batch
+constexpr int kMaxServeK = 32;      // columns per request (1 + probes, padded to 4)
+constexpr int kST = 256;            // threads of the table-driven kernels
+constexpr int kGrid = 4 * 152;      // their fixed grid (4 blocks per SM)
+constexpr int kBlurU = 2;           // blur rows per thread
+constexpr int kVecRows = 4;         // vector-kernel rows per thread
+
+enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_KINDS };
+
+// One active request as the kernels see it.  Row-indexed arrays are in the lattice's
+// locality order p; perm[p] < n_train marks a training row.
+struct SlotDev {
+  int64_t n, n_train, m;
+  int D, r;
+  int64_t nseg, nmed, nhuge;
+  const int32_t* perm;
+  const int32_t* idx;
+  const float* w;
+  const int2* items;
+  const int4* seg;
+  const int4* med;
+  const int4* huge;
+  const int32_t* nbr;
+  float taps[kMaxOrder + 1];  // symmetric-blur (half-kernel) taps
+  float outputscale, noise;
+  void* lat0;
+  void* lat1;
+  float* spart;  // splat partials
+  float *xh, *xl, *rh, *rl, *p, *ap;  // [n][kp]
+  double* dpart;                      // [virtual blocks][kp]
+  double *rho, *bnorm, *relres, *alpha, *beta;  // [kp]
+  int* active;                        // [kp]
+  int* state;                         // [0] request still iterating, [1] iterations done
+  int max_iter;
+  float tol;
+};
+
+struct Table {
+  int nslots;
+  int kp;
+  int* flags;  // [kMaxSlots][2]: state copied by the check kernel, read by the host
+  int64_t pre[U_KINDS][kMaxSlots + 1];  // prefix sums of virtual blocks per unit kind
+  SlotDev s[kMaxSlots];
+};
+
+__host__ __device__ inline int groups_of(int kp) { return kST / (kp / 4); }
+
+__device__ __forceinline__ int find_slot(const int64_t* pre, int ns, int64_t vb) {
+  int lo = 0, hi = ns - 1;  // largest q with pre[q] <= vb
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= vb) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Walk this block's virtual blocks of one unit kind: q = request, local = its block index.
+#define SLOT_LOOP(KIND)                                                            \
+  const int ns_ = T->nslots;                                                       \
+  const int64_t total_ = T->pre[KIND][ns_];                                        \
+  for (int64_t vb_ = blockIdx.x; vb_ < total_; vb_ += gridDim.x) {                 \
+    const int q = find_slot(T->pre[KIND], ns_, vb_);                               \
+    const SlotDev& s = T->s[q];                                                    \
+    const int64_t local = vb_ - T->pre[KIND][q];
+
+#define SLOT_LOOP_END }
+
+// SplitMix64 (Steele, Lea & Flood 2014) sign at counter i l + j + 1.
+__device__ __forceinline__ float rademacher_pm(uint64_t seed, int64_t i, int j, int l) {
+  uint64_t z = seed + ((uint64_t)(i * l + j) + 1ull) * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return (z >> 63) ? -1.f : 1.f;
+}
+
+// Per-column sums of the block's per-thread partials (thread t owns columns (t % G) 4 ..
+// + 3 of block row t / G), fixed order; out[0..kp).  Uniform call, trailing barrier.
+__device__ __forceinline__ void vb_column_sums(const dfloat (&d)[4], int kp, double* out,
+                                               double* sh) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sh[threadIdx.x * 4 + j] = df_to_double(d[j]);
+  __syncthreads();
+  const int G = kp / 4, rows = kST / G;
+  for (int col = threadIdx.x; col < kp; col += blockDim.x) {
+    const int chunk = col / 4, lane = col % 4;
+    double t = 0.0;
+    for (int r = 0; r < rows; ++r) t += sh[(r * G + chunk) * 4 + lane];
+    out[col] = t;
+  }
+  __syncthreads();
+}
+
+// Column c's total over a request's nvb virtual-block partials (fixed order).
+__device__ __forceinline__ double slot_col_total(const double* part, int64_t nvb, int kp, int c,
+                                                 double* red) {
+  double t = 0.0;
+  for (int64_t b = threadIdx.x; b < nvb; b += blockDim.x) t += part[b * kp + c];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int half = blockDim.x / 2; half >= 1; half /= 2) {
+    if ((int)threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 f4_ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void f4_st(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// ---- one CG iteration over the table --------------------------------------------------
+// Splat W^T p into lat0: one thread-group per segment of a vertex's incidence list.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_splat(const Table* __restrict__ T) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_SPLAT)
+  if (*s.state == 0 || g >= groups) continue;
+  const int64_t sidx = local * groups + g;
+  if (sidx >= s.nseg) continue;
+  const int4 sg = s.seg[sidx];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int it = sg.y; it < sg.z; ++it) {
+    const int2 e = s.items[it];
+    acc = f4_fma(__int_as_float(e.y), f4_ld(s.p + (int64_t)e.x * kp + col), acc);
+  }
+  if (sg.w < 0) Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)sg.x * kp + col, acc);
+  else f4_st(s.spart + (int64_t)sg.w * kp + col, acc);
+  SLOT_LOOP_END
+}
+
+// Vertices with 2..kSplatMedSegs segments: one thread-group sums the partials in order.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_splat_med(const Table* __restrict__ T) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_MED)
+  if (*s.state == 0 || g >= groups) continue;
+  const int64_t ridx = local * groups + g;
+  if (ridx >= s.nmed) continue;
+  const int4 rw = s.med[ridx];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < rw.z; ++j) {
+    const float4 v = f4_ld(s.spart + (int64_t)(rw.y + j) * kp + col);
+    acc = make_float4(acc.x + v.x, acc.y + v.y, acc.z + v.z, acc.w + v.w);
+  }
+  Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)rw.x * kp + col, acc);
+  SLOT_LOOP_END
+}
+
+// Vertices with more segments: one virtual block per vertex, strided partials per group
+// and a fixed shared-memory tree over the groups.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_splat_huge(const Table* __restrict__ T) {
+  __shared__ float4 red[kST];
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  int pow2 = 1;
+  while (pow2 * 2 <= groups) pow2 *= 2;
+  SLOT_LOOP(U_HUGE)
+  if (*s.state == 0) continue;  // uniform over the block
+  const int4 rw = s.huge[local];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (g < pow2)
+    for (int j = g; j < rw.z; j += pow2) {
+      const float4 v = f4_ld(s.spart + (int64_t)(rw.y + j) * kp + col);
+      acc = make_float4(acc.x + v.x, acc.y + v.y, acc.z + v.z, acc.w + v.w);
+    }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int half = pow2 / 2; half >= 1; half /= 2) {
+    if (g < half) {
+      const float4 a = red[threadIdx.x], b = red[threadIdx.x + half * G];
+      red[threadIdx.x] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    }
+    __syncthreads();
+  }
+  if (g == 0) Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)rw.x * kp + col, red[threadIdx.x]);
+  __syncthreads();
+  SLOT_LOOP_END
+}
+
+// Blur pass t of the symmetric operator: direction t for t < D, then 2D - 1 - t; pass t
+// reads lat[t % 2] and writes lat[(t + 1) % 2], so after 2D passes the values are back
+// in lat0.  Each thread owns 4 columns of kBlurU rows (ids first, then rows).
+template <int R, class S>
+__global__ void __launch_bounds__(kST) kb_blur(const Table* __restrict__ T, int t) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_BLUR)
+  if (*s.state == 0 || t >= 2 * s.D || g >= groups) continue;
+  const int j = t < s.D ? t : 2 * s.D - 1 - t;
+  const S* in = static_cast<const S*>((t & 1) ? s.lat1 : s.lat0);
+  S* out = static_cast<S*>((t & 1) ? s.lat0 : s.lat1);
+  const int64_t m = s.m;
+  const int32_t* nbr = s.nbr + (int64_t)j * R * 2 * m;
+  int64_t v[kBlurU];
+  int ia[kBlurU][R], ic[kBlurU][R];
+#pragma unroll
+  for (int u = 0; u < kBlurU; ++u) {
+    v[u] = (local * kBlurU + u) * groups + g;
+#pragma unroll
+    for (int tt = 0; tt < R; ++tt) {
+      ia[u][tt] = v[u] < m ? __ldg(nbr + (int64_t)(2 * tt) * m + v[u]) : -1;
+      ic[u][tt] = v[u] < m ? __ldg(nbr + (int64_t)(2 * tt + 1) * m + v[u]) : -1;
+    }
+  }
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 own[kBlurU], sa[kBlurU][R], sc[kBlurU][R];
+#pragma unroll
+  for (int u = 0; u < kBlurU; ++u) {
+    own[u] = v[u] < m ? Store<S>::ldg4(in + v[u] * kp + col) : zero;
+#pragma unroll
+    for (int tt = 0; tt < R; ++tt) {
+      sa[u][tt] = ia[u][tt] >= 0 ? Store<S>::ldg4(in + (int64_t)ia[u][tt] * kp + col) : zero;
+      sc[u][tt] = ic[u][tt] >= 0 ? Store<S>::ldg4(in + (int64_t)ic[u][tt] * kp + col) : zero;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kBlurU; ++u) {
+    if (v[u] >= m) continue;
+    const float c0 = s.taps[0];
+    float4 acc = make_float4(c0 * own[u].x, c0 * own[u].y, c0 * own[u].z, c0 * own[u].w);
+#pragma unroll
+    for (int tt = 0; tt < R; ++tt) {
+      const float wt = s.taps[tt + 1];
+      acc.x = fmaf(wt, sa[u][tt].x + sc[u][tt].x, acc.x);
+      acc.y = fmaf(wt, sa[u][tt].y + sc[u][tt].y, acc.y);
+      acc.z = fmaf(wt, sa[u][tt].z + sc[u][tt].z, acc.z);
+      acc.w = fmaf(wt, sa[u][tt].w + sc[u][tt].w, acc.w);
+    }
+    Store<S>::st4(out + v[u] * kp + col, acc);
+  }
+  SLOT_LOOP_END
+}
+
+// A p = outputscale W lat0 + noise p on training rows, 0 on test rows; partials of <p, Ap>.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_slice_dot(const Table* __restrict__ T) {
+  __shared__ double sh[kST * 4];
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VEC)
+  if (*s.state == 0) continue;  // uniform over the block
+  dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  const S* lat = static_cast<const S*>(s.lat0);
+  if (g < groups) {
+    for (int i = 0; i < kVecRows; ++i) {
+      const int64_t row = (local * kVecRows + i) * groups + g;
+      if (row >= s.n) break;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < s.D; ++c) {
+        const int64_t e = row * s.D + c;
+        acc = f4_fma(s.w[e], Store<S>::ld4(lat + (int64_t)s.idx[e] * kp + col), acc);
+      }
+      const float4 pv = f4_ld(s.p + row * kp + col);
+      float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s.perm[row] < s.n_train) {
+        const float a = s.outputscale, b = s.noise;
+        res = make_float4(fmaf(b, pv.x, a * acc.x), fmaf(b, pv.y, a * acc.y),
+                          fmaf(b, pv.z, a * acc.z), fmaf(b, pv.w, a * acc.w));
+      }
+      f4_st(s.ap + row * kp + col, res);
+      d[0] = df_add(d[0], df_two_prod(pv.x, res.x));
+      d[1] = df_add(d[1], df_two_prod(pv.y, res.y));
+      d[2] = df_add(d[2], df_two_prod(pv.z, res.z));
+      d[3] = df_add(d[3], df_two_prod(pv.w, res.w));
+    }
+  }
+  vb_column_sums(d, kp, s.dpart + local * kp, sh);
+  SLOT_LOOP_END
+}
+
+// alpha = rho / <p, A p> per active column (a non-positive <p, A p> stops the column).
+__global__ void __launch_bounds__(kST) kb_alpha(const Table* __restrict__ T) {
+  __shared__ double red[kST];
+  const int q = blockIdx.x;
+  if (q >= T->nslots) return;
+  const SlotDev& s = T->s[q];
+  if (*s.state == 0) return;
+  const int kp = T->kp;
+  const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
+  for (int c = 0; c < kp; ++c) {
+    const double pap = slot_col_total(s.dpart, nvb, kp, c, red);
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      if (s.active[c]) {
+        if (pap > 0.0 && isfinite(pap)) a = s.rho[c] / pap;
+        else s.active[c] = 0;
+      }
+      s.alpha[c] = a;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha A p on active columns (double-float); partials of <r, r>.
+__device__ __forceinline__ void xr_row(const SlotDev& s, int64_t e, const bool (&on)[4],
+                                       const dfloat (&a)[4], const dfloat (&na)[4], dfloat (&d)[4]) {
+  const float4 p4 = f4_ld(s.p + e), q4 = f4_ld(s.ap + e);
+  float4 xh = f4_ld(s.xh + e), xl = f4_ld(s.xl + e), rh = f4_ld(s.rh + e), rl = f4_ld(s.rl + e);
+  float* pv = reinterpret_cast<float*>(const_cast<float4*>(&p4));
+  float* qv = reinterpret_cast<float*>(const_cast<float4*>(&q4));
+  float* xhv = reinterpret_cast<float*>(&xh);
+  float* xlv = reinterpret_cast<float*>(&xl);
+  float* rhv = reinterpret_cast<float*>(&rh);
+  float* rlv = reinterpret_cast<float*>(&rl);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (on[j]) {
+      const dfloat x = df_add({xhv[j], xlv[j]}, df_mul_f(a[j], pv[j]));
+      const dfloat r = df_add({rhv[j], rlv[j]}, df_mul_f(na[j], qv[j]));
+      xhv[j] = x.hi, xlv[j] = x.lo, rhv[j] = r.hi, rlv[j] = r.lo;
+    }
+    dfloat sq = df_two_prod(rhv[j], rhv[j]);
+    sq = df_fast_two_sum(sq.hi, __fmaf_rn(2.f * rhv[j], rlv[j], sq.lo));
+    d[j] = df_add(d[j], sq);
+  }
+  f4_st(s.xh + e, xh);
+  f4_st(s.xl + e, xl);
+  f4_st(s.rh + e, rh);
+  f4_st(s.rl + e, rl);
+}
+
+__global__ void __launch_bounds__(kST) kb_update_xr(const Table* __restrict__ T) {
+  __shared__ double sh[kST * 4];
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VEC)
+  if (*s.state == 0) continue;
+  bool on[4];
+  dfloat a[4], na[4];
+  dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    on[j] = s.active[col + j] != 0;
+    a[j] = df_from_double(s.alpha[col + j]);
+    na[j] = {-a[j].hi, -a[j].lo};
+  }
+  if (g < groups) {
+    for (int i = 0; i < kVecRows; ++i) {
+      const int64_t row = (local * kVecRows + i) * groups + g;
+      if (row >= s.n) break;
+      xr_row(s, row * kp + col, on, a, na, d);
+    }
+  }
+  vb_column_sums(d, kp, s.dpart + local * kp, sh);
+  SLOT_LOOP_END
+}
+
+// Convergence check and beta = <r, r>_new / <r, r>_old per active column; the request
+// stops when no column is active.  Its state is copied to the host-read flags.
+__global__ void __launch_bounds__(kST) kb_check_beta(const Table* __restrict__ T) {
+  __shared__ double red[kST];
+  const int q = blockIdx.x;
+  if (q >= T->nslots) return;
+  const SlotDev& s = T->s[q];
+  if (*s.state == 0) {
+    if (threadIdx.x == 0) {
+      T->flags[2 * q] = 0;
+      T->flags[2 * q + 1] = s.state[1];
+    }
+    return;
+  }
+  const int kp = T->kp;
+  const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
+  const int it = s.state[1] + 1;
+  int any = 0;
+  for (int c = 0; c < kp; ++c) {
+    const double rr = slot_col_total(s.dpart, nvb, kp, c, red);
+    if (threadIdx.x == 0 && s.active[c]) {
+      const double rel = sqrt(rr) / s.bnorm[c];
+      s.relres[c] = rel;
+      if (rel <= (double)s.tol || it >= s.max_iter || !isfinite(rel)) {
+        s.active[c] = 0;
+      } else {
+        s.beta[c] = rr / s.rho[c];
+        s.rho[c] = rr;
+        any = 1;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    s.state[1] = it;
+    s.state[0] = any;
+    T->flags[2 * q] = any;
+    T->flags[2 * q + 1] = it;
+  }
+}
+
+// p = r + beta p on active columns (double-float sum rounded to fp32).
+__global__ void __launch_bounds__(kST) kb_update_p(const Table* __restrict__ T) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VEC)
+  if (*s.state == 0 || g >= groups) continue;
+  bool on[4];
+  dfloat b[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    on[j] = s.active[col + j] != 0;
+    b[j] = df_from_double(s.beta[col + j]);
+  }
+  for (int i = 0; i < kVecRows; ++i) {
+    const int64_t row = (local * kVecRows + i) * groups + g;
+    if (row >= s.n) break;
+    const int64_t e = row * kp + col;
+    float4 p4 = f4_ld(s.p + e);
+    const float4 rh = f4_ld(s.rh + e), rl = f4_ld(s.rl + e);
+    float* pv = reinterpret_cast<float*>(&p4);
+    const float* rhv = reinterpret_cast<const float*>(&rh);
+    const float* rlv = reinterpret_cast<const float*>(&rl);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (on[j]) {
+        const dfloat t = df_add({rhv[j], rlv[j]}, df_mul_f(b[j], pv[j]));
+        pv[j] = __fadd_rn(t.hi, t.lo);
+      }
+    }
+    f4_st(s.p + e, p4);
+  }
+  SLOT_LOOP_END
+}
+
+// ---- per-request set-up and read-out (single-request launches) ------------------------
+// Partials of <r, r> for the initial residual (the same virtual blocks as the iteration).
+__global__ void __launch_bounds__(kST) kb_norm(const Table* __restrict__ T) {
+  __shared__ double sh[kST * 4];
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VEC)
+  dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (g < groups) {
+    for (int i = 0; i < kVecRows; ++i) {
+      const int64_t row = (local * kVecRows + i) * groups + g;
+      if (row >= s.n) break;
+      const float4 rh = f4_ld(s.rh + row * kp + col);
+      d[0] = df_add(d[0], df_two_prod(rh.x, rh.x));
+      d[1] = df_add(d[1], df_two_prod(rh.y, rh.y));
+      d[2] = df_add(d[2], df_two_prod(rh.z, rh.z));
+      d[3] = df_add(d[3], df_two_prod(rh.w, rh.w));
+    }
+  }
+  vb_column_sums(d, kp, s.dpart + local * kp, sh);
+  SLOT_LOOP_END
+}
+
+__global__ void __launch_bounds__(kST) kb_init_scalars(const Table* __restrict__ T) {
+  __shared__ double red[kST];
+  const int q = blockIdx.x;
+  if (q >= T->nslots) return;
+  const SlotDev& s = T->s[q];
+  const int kp = T->kp;
+  const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
+  int any = 0;
+  for (int c = 0; c < kp; ++c) {
+    const double rr = slot_col_total(s.dpart, nvb, kp, c, red);
+    if (threadIdx.x == 0) {
+      s.rho[c] = rr;
+      s.bnorm[c] = sqrt(rr);
+      s.alpha[c] = 0.0;
+      s.beta[c] = 0.0;
+      const int on = (rr > 0.0 && 1.0 > (double)s.tol && s.max_iter > 0) ? 1 : 0;
+      s.relres[c] = rr > 0.0 ? 1.0 : 0.0;
+      s.active[c] = on;
+      any |= on;
+    }
+  }
+  if (threadIdx.x == 0) {
+    s.state[0] = any;
+    s.state[1] = 0;
+  }
+}
+
+// Probe right-hand sides in the caller's order: column 1 + s of test row t holds z_s[t].
+__global__ void k_probe_fill(float* __restrict__ V, int64_t n_all, int64_t n_train, int kp,
+                             int S, uint64_t seed) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_all * kp) return;
+  const int64_t i = e / kp;
+  const int c = (int)(e - i * kp);
+  V[e] = (i >= n_train && c >= 1 && c <= S) ? rademacher_pm(seed, i - n_train, c - 1, S) : 0.f;
+}
+
+// b (locality order): training rows [y, (KX* z)_1..S, 0 ...], test rows 0; r = p = b,
+// x = 0.  KZ is the probe product in the caller's order.
+__global__ void k_rhs(const int32_t* __restrict__ perm, const float* __restrict__ y,
+                      const float* __restrict__ KZ, int64_t n_all, int64_t n_train, int kp,
+                      int S, float* __restrict__ xh, float* __restrict__ xl,
+                      float* __restrict__ rh, float* __restrict__ rl, float* __restrict__ p) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_all * kp) return;
+  const int64_t row = e / kp;
+  const int c = (int)(e - row * kp);
+  const int64_t i = perm[row];
+  float b = 0.f;
+  if (i < n_train) b = c == 0 ? y[i] : (c <= S ? KZ[i * kp + c] : 0.f);
+  xh[e] = 0.f;
+  xl[e] = 0.f;
+  rh[e] = b;
+  rl[e] = 0.f;
+  p[e] = b;
+}
+
+__global__ void k_x_sum(const float* __restrict__ xh, const float* __restrict__ xl,
+                        float* __restrict__ out, int64_t count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = __fadd_rn(xh[e], xl[e]);
+}
+
+// mean[t] = (K*X W)[t][0]; var[t] = outputscale - (1/S) sum_s z_s[t] (K*X W)[t][1 + s].
+__global__ void k_predict(const int32_t* __restrict__ perm, const float* __restrict__ KW,
+                          int64_t n_all, int64_t n_train, int kp, int S, uint64_t seed,
+                          float outputscale, float* __restrict__ mean, float* __restrict__ var) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_all) return;
+  const int64_t i = perm[row];
+  if (i < n_train) return;
+  const int64_t t = i - n_train;
+  const float* o = KW + row * kp;
+  mean[t] = o[0];
+  double acc = 0.0;
+  for (int s = 0; s < S; ++s) acc += (double)rademacher_pm(seed, t, s, S) * (double)o[1 + s];
+  var[t] = S > 0 ? (float)((double)outputscale - acc / S) : 0.f;
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace sgp
+
+using namespace sgp;
+
+// ---- host engine ------------------------------------------------------------------------
+// Requests are grouped into lanes by dimension class and per-iteration work class; each
+// lane is its own batch (device table, CUDA graph, stream), so a small request never
+// iterates in lockstep with one a hundred times its size, and lanes run concurrently on
+// the GPU.  sgp_server_step harvests lanes whose round of iterations has finished,
+// admits queued requests, relaunches idle lanes and then waits (briefly) for the next
+// lane to finish.
+namespace {
+
+constexpr int kStepWaitUs = 2000;  // longest wait of one step for a lane to finish
+
+struct Lane;
+
+struct Request {
+  long long id = 0;
+  sgp_request in{};
+  sgp_request_stats st{};
+  unsigned long long bound = 0;
+  unsigned long long held = 0;  // accounted against the budget while active
+  Lattice* L = nullptr;
+  float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr, *p = nullptr, *ap = nullptr;
+  double* dpart = nullptr;
+  double* scal = nullptr;  // rho, bnorm, relres, alpha, beta: [5][kp]
+  int* ints = nullptr;     // active [kp], state [2]
+  float* outd = nullptr;   // mean, var: [2][ns]
+  Table* dtab1 = nullptr;  // one-request table for the set-up kernels
+  cudaEvent_t ready = nullptr;
+  bool waited = false;     // the lane's stream has waited for `ready`
+  int64_t vb[U_KINDS] = {};
+  Lane* lane = nullptr;
+  std::vector<void*> ptrs;
+};
+
+struct Lane {
+  int key = 0;
+  cudaStream_t st = nullptr;
+  Table* dtab = nullptr;
+  int* dflags = nullptr;
+  int* hflags = nullptr;  // pinned
+  cudaEvent_t ev = nullptr;
+  std::unique_ptr<Table> htab;
+  std::vector<Request*> active;  // the first ntab are in the launched table, in order
+  int ntab = 0;
+  bool in_flight = false;
+  bool dirty = true;
+  std::map<int, cudaGraphExec_t> graphs;  // by Dmax
+  std::map<int, int> graph_kernels;
+};
+
+}  // namespace
+
+struct sgp_server {
+  sgp_server_opts o{};
+  int kp = 4, S = 0;
+  cudaStream_t bs = nullptr;  // set-up stream
+  std::chrono::steady_clock::time_point t0;
+  long long next_id = 1;
+  std::deque<Request*> queue;
+  std::map<int, std::unique_ptr<Lane>> lanes;
+  std::map<long long, std::unique_ptr<Request>> reqs;
+  int n_active = 0;
+  unsigned long long in_use = 0;
+  int peak_active = 0;
+  std::unique_ptr<Table> htab1;  // host image of the one-request tables
+};
+
+namespace {
+
+double now_us(const sgp_server* S) { return 1e6 * seconds_since(S->t0); }
+
+#define SRV_CHECK(expr, what)                                \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) return cuda_status(e_, what);     \
+  } while (0)
+
+void fill_slot(const sgp_server* S, const Request* R, SlotDev& s) {
+  const Lattice* L = R->L;
+  s.n = L->n;
+  s.n_train = R->in.n;
+  s.m = L->m;
+  s.D = L->D;
+  s.r = L->r;
+  s.nseg = L->nseg;
+  s.nmed = L->nmed;
+  s.nhuge = L->nhuge;
+  s.perm = L->perm;
+  s.idx = L->idx;
+  s.w = L->w;
+  s.items = L->items;
+  s.seg = L->seg;
+  s.med = L->med_rows;
+  s.huge = L->huge_rows;
+  s.nbr = L->nbr;
+  for (int t = 0; t <= kMaxOrder; ++t) s.taps[t] = t <= L->r ? (float)L->half[t] : 0.f;
+  s.outputscale = L->outputscale;
+  s.noise = R->in.noise;
+  s.lat0 = L->lat[0];
+  s.lat1 = L->lat[1];
+  s.spart = L->partial;
+  s.xh = R->xh;
+  s.xl = R->xl;
+  s.rh = R->rh;
+  s.rl = R->rl;
+  s.p = R->p;
+  s.ap = R->ap;
+  s.dpart = R->dpart;
+  const int kp = S->kp;
+  s.rho = R->scal;
+  s.bnorm = R->scal + kp;
+  s.relres = R->scal + 2 * kp;
+  s.alpha = R->scal + 3 * kp;
+  s.beta = R->scal + 4 * kp;
+  s.active = R->ints;
+  s.state = R->ints + kp;
+  s.max_iter = S->o.max_iter;
+  s.tol = (float)S->o.tol;
+}
+
+void unit_counts(const sgp_server* S, const Lattice* L, int64_t (&vb)[U_KINDS]) {
+  const int groups = groups_of(S->kp);
+  vb[U_SPLAT] = ceil_div(L->nseg, groups);
+  vb[U_MED] = ceil_div(L->nmed, groups);
+  vb[U_HUGE] = L->nhuge;
+  vb[U_BLUR] = ceil_div(L->m, (int64_t)groups * kBlurU);
+  vb[U_VEC] = ceil_div(L->n, (int64_t)groups * kVecRows);
+}
+
+// Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur
+// and slice volume per iteration, classes a factor 8 apart).
+int lane_key(const sgp_server* S, const Lattice* L) {
+  int dclass = 0;
+  while ((4 << dclass) < L->D) ++dclass;
+  const double work = ((double)L->m + (double)L->n) * L->D * S->kp;
+  const int wclass = std::max(0, (int)std::floor(std::log(std::max(work, 1.0)) / std::log(8.0)));
+  return dclass * 64 + std::min(wclass, 63);
+}
+
+void release(sgp_server* S, Request* R, cudaStream_t st) {
+  for (void* p : R->ptrs) (void)cudaFreeAsync(p, st);
+  R->ptrs.clear();
+  if (R->L) {
+    sgp_set_stream(R->L, st);
+    sgp_lattice_free(R->L);
+    R->L = nullptr;
+  }
+  if (R->ready) {
+    cudaEventDestroy(R->ready);
+    R->ready = nullptr;
+  }
+  S->in_use -= R->held;
+  R->held = 0;
+  clear_pending_error();
+}
+
+// Upload, build, right-hand sides and CG start of one request on the set-up stream.
+sgp_status setup(sgp_server* S, Request* R) {
+  cudaStream_t st = S->bs;
+  const sgp_request& in = R->in;
+  const int64_t n_all = in.n + in.ns;
+  const int d = in.d, kp = S->kp;
+  auto get = [&](void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    if (e == cudaSuccess) R->ptrs.push_back(*p);
+    return e;
+  };
+  struct Scratch {  // inputs and probe products, released (stream-ordered) on return
+    cudaStream_t st;
+    std::vector<void*> p;
+    ~Scratch() {
+      for (void* x : p) (void)cudaFreeAsync(x, st);
+    }
+    cudaError_t get(void** x, size_t bytes) {
+      cudaError_t e = cudaMallocAsync(x, std::max<size_t>(bytes, 16), st);
+      if (e == cudaSuccess) p.push_back(*x);
+      return e;
+    }
+  } tmp{st, {}};
+  float *Xd = nullptr, *lsd = nullptr, *yd = nullptr;
+  SRV_CHECK(tmp.get((void**)&Xd, (size_t)n_all * d * sizeof(float)), "alloc X");
+  SRV_CHECK(tmp.get((void**)&lsd, (size_t)d * sizeof(float)), "alloc ls");
+  SRV_CHECK(tmp.get((void**)&yd, (size_t)in.n * sizeof(float)), "alloc y");
+  SRV_CHECK(cudaMemcpyAsync(Xd, in.X, (size_t)in.n * d * sizeof(float), cudaMemcpyHostToDevice, st),
+            "copy X");
+  SRV_CHECK(cudaMemcpyAsync(Xd + in.n * d, in.Xs, (size_t)in.ns * d * sizeof(float),
+                            cudaMemcpyHostToDevice, st),
+            "copy Xs");
+  SRV_CHECK(cudaMemcpyAsync(lsd, in.lengthscales, d * sizeof(float), cudaMemcpyHostToDevice, st),
+            "copy ls");
+  SRV_CHECK(cudaMemcpyAsync(yd, in.y, (size_t)in.n * sizeof(float), cudaMemcpyHostToDevice, st),
+            "copy y");
+  sgp_opts lo;
+  sgp_opts_init(&lo);
+  lo.order_r = S->o.order_r;
+  lo.kernel = S->o.kernel;
+  lo.spacing_s = S->o.spacing_s;
+  lo.outputscale = in.outputscale;
+  lo.value_dtype = S->o.value_dtype;
+  lo.stream = st;
+  sgp_status s = sgp_lattice_build(Xd, lsd, n_all, d, &lo, &R->L);
+  if (s != SGP_OK) return s;
+  Lattice* L = R->L;
+  R->st.m = L->m;
+  s = ensure_lattice_values(L, kp, st);
+  if (s != SGP_OK) return s;
+  unit_counts(S, L, R->vb);
+  const size_t vec = (size_t)n_all * kp * sizeof(float);
+  float** vecs[6] = {&R->xh, &R->xl, &R->rh, &R->rl, &R->p, &R->ap};
+  for (float** v : vecs) SRV_CHECK(get((void**)v, vec), "alloc CG vectors");
+  SRV_CHECK(get((void**)&R->dpart, (size_t)R->vb[U_VEC] * kp * sizeof(double)), "alloc partials");
+  SRV_CHECK(get((void**)&R->scal, 5 * (size_t)kp * sizeof(double)), "alloc scalars");
+  SRV_CHECK(get((void**)&R->ints, ((size_t)kp + 2) * sizeof(int)), "alloc flags");
+  SRV_CHECK(get((void**)&R->outd, 2 * (size_t)in.ns * sizeof(float)), "alloc outputs");
+  SRV_CHECK(get((void**)&R->dtab1, sizeof(Table)), "alloc table");
+  // right-hand sides: y and KX* z_s (one product of the probe columns, caller's order)
+  float *Vz = nullptr, *KZ = nullptr;
+  SRV_CHECK(tmp.get((void**)&Vz, vec), "alloc probes");
+  SRV_CHECK(tmp.get((void**)&KZ, vec), "alloc probes");
+  const unsigned g = (unsigned)ceil_div(n_all * kp, 256);
+  k_probe_fill<<<g, 256, 0, st>>>(Vz, n_all, in.n, kp, S->S, in.seed);
+  note_launches(1);
+  enqueue_mvm(L, Vz, kp, SGP_BLUR_SYMMETRIC, L->outputscale, 0.f, KZ, st);
+  k_rhs<<<g, 256, 0, st>>>(L->perm, yd, KZ, n_all, in.n, kp, S->S, R->xh, R->xl, R->rh, R->rl,
+                           R->p);
+  note_launches(1);
+  // initial residual norms and scalars through a one-request table
+  Table& t1 = *S->htab1;
+  std::memset(&t1, 0, sizeof(Table));
+  t1.nslots = 1;
+  t1.kp = kp;
+  t1.flags = nullptr;
+  fill_slot(S, R, t1.s[0]);
+  for (int u = 0; u < U_KINDS; ++u) t1.pre[u][1] = R->vb[u];
+  SRV_CHECK(cudaMemcpyAsync(R->dtab1, &t1, sizeof(Table), cudaMemcpyHostToDevice, st),
+            "copy table");
+  kb_norm<<<kGrid, kST, 0, st>>>(R->dtab1);
+  kb_init_scalars<<<1, kST, 0, st>>>(R->dtab1);
+  note_launches(2);
+  SRV_CHECK(cudaGetLastError(), "request set-up");
+  SRV_CHECK(cudaEventCreateWithFlags(&R->ready, cudaEventDisableTiming), "event");
+  SRV_CHECK(cudaEventRecord(R->ready, st), "record");
+  R->held = L->bytes + 6 * vec + (size_t)R->vb[U_VEC] * kp * sizeof(double) +
+            2 * (size_t)in.ns * sizeof(float) + sizeof(Table);
+  return SGP_OK;
+}
+
+// Predictive slice, copy to the host, release.  Runs on the (idle) lane's stream.
+sgp_status finish(sgp_server* S, Request* R, cudaStream_t st) {
+  const sgp_request& in = R->in;
+  Lattice* L = R->L;
+  const int kp = S->kp;
+  const int64_t n_all = L->n;
+  const int64_t cnt = n_all * kp;
+  k_x_sum<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(R->xh, R->xl, R->p, cnt);
+  note_launches(1);
+  enqueue_mvm(L, R->p, kp, SGP_BLUR_SYMMETRIC, L->outputscale, 0.f, R->ap, st, nullptr,
+              /*internal=*/true);
+  float* mean_d = R->outd;
+  float* var_d = R->outd + in.ns;
+  k_predict<<<(unsigned)ceil_div(n_all, 256), 256, 0, st>>>(L->perm, R->ap, n_all, in.n, kp,
+                                                           S->S, in.seed, L->outputscale,
+                                                           mean_d, var_d);
+  note_launches(1);
+  SRV_CHECK(cudaMemcpyAsync(in.mean, mean_d, (size_t)in.ns * sizeof(float),
+                            cudaMemcpyDeviceToHost, st),
+            "copy mean");
+  if (in.var)
+    SRV_CHECK(cudaMemcpyAsync(in.var, var_d, (size_t)in.ns * sizeof(float),
+                              cudaMemcpyDeviceToHost, st),
+              "copy var");
+  std::vector<double> relres(kp);
+  std::vector<int> ints(kp + 2);
+  SRV_CHECK(cudaMemcpyAsync(relres.data(), R->scal + 2 * kp, kp * sizeof(double),
+                            cudaMemcpyDeviceToHost, st),
+            "copy residuals");
+  SRV_CHECK(cudaMemcpyAsync(ints.data(), R->ints, (kp + 2) * sizeof(int), cudaMemcpyDeviceToHost,
+                            st),
+            "copy state");
+  SRV_CHECK(cudaStreamSynchronize(st), "finishing a request");
+  double worst = 0.0;
+  for (int c = 0; c <= S->S; ++c) worst = std::max(worst, relres[c]);
+  R->st.iters = ints[kp + 1];
+  R->st.rel_res = worst;
+  R->st.bytes = R->held;
+  R->st.status = SGP_OK;
+  R->st.done_us = now_us(S);
+  R->st.done = 1;
+  release(S, R, st);
+  return SGP_OK;
+}
+
+template <int Rr, class Sv>
+int enqueue_iteration_t(Lane* ln, int dmax) {
+  cudaStream_t st = ln->st;
+  const Table* T = ln->dtab;
+  kb_splat<Sv><<<kGrid, kST, 0, st>>>(T);
+  kb_splat_med<Sv><<<kGrid, kST, 0, st>>>(T);
+  kb_splat_huge<Sv><<<kGrid, kST, 0, st>>>(T);
+  for (int t = 0; t < 2 * dmax; ++t) kb_blur<Rr, Sv><<<kGrid, kST, 0, st>>>(T, t);
+  kb_slice_dot<Sv><<<kGrid, kST, 0, st>>>(T);
+  kb_alpha<<<kMaxSlots, kST, 0, st>>>(T);
+  kb_update_xr<<<kGrid, kST, 0, st>>>(T);
+  kb_check_beta<<<kMaxSlots, kST, 0, st>>>(T);
+  kb_update_p<<<kGrid, kST, 0, st>>>(T);
+  return 8 + 2 * dmax;
+}
+
+template <class Sv>
+int enqueue_iteration_s(const sgp_server* S, Lane* ln, int dmax) {
+  switch (S->o.order_r) {
+    case 1: return enqueue_iteration_t<1, Sv>(ln, dmax);
+    case 2: return enqueue_iteration_t<2, Sv>(ln, dmax);
+    case 3: return enqueue_iteration_t<3, Sv>(ln, dmax);
+    default: return enqueue_iteration_t<4, Sv>(ln, dmax);
+  }
+}
+
+sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, cudaGraphExec_t* out) {
+  auto it = ln->graphs.find(dmax);
+  if (it != ln->graphs.end()) {
+    *out = it->second;
+    return SGP_OK;
+  }
+  SRV_CHECK(cudaStreamBeginCapture(ln->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  const int kernels = S->o.value_dtype == SGP_VALUES_BF16 ? enqueue_iteration_s<bf16>(S, ln, dmax)
+                                                         : enqueue_iteration_s<float>(S, ln, dmax);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ln->st, &g);
+  if (e != cudaSuccess) return cuda_status(e, "capturing the batched CG iteration");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_status(e, "instantiating the batched CG iteration");
+  ln->graphs[dmax] = ex;
+  ln->graph_kernels[dmax] = kernels;
+  *out = ex;
+  return SGP_OK;
+}
+
+sgp_status lane_for(sgp_server* S, int key, Lane** out) {
+  auto it = S->lanes.find(key);
+  if (it != S->lanes.end()) {
+    *out = it->second.get();
+    return SGP_OK;
+  }
+  auto ln = std::make_unique<Lane>();
+  ln->key = key;
+  ln->htab = std::make_unique<Table>();
+  SRV_CHECK(cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking), "lane stream");
+  SRV_CHECK(cudaMalloc((void**)&ln->dtab, sizeof(Table)), "alloc lane table");
+  SRV_CHECK(cudaMalloc((void**)&ln->dflags, 2 * kMaxSlots * sizeof(int)), "alloc lane flags");
+  SRV_CHECK(cudaMallocHost((void**)&ln->hflags, 2 * kMaxSlots * sizeof(int)), "alloc lane flags");
+  SRV_CHECK(cudaEventCreateWithFlags(&ln->ev, cudaEventDisableTiming), "lane event");
+  *out = ln.get();
+  S->lanes[key] = std::move(ln);
+  return SGP_OK;
+}
+
+void destroy_lane(Lane* ln) {
+  if (ln->st) cudaStreamSynchronize(ln->st);
+  for (auto& kv : ln->graphs) cudaGraphExecDestroy(kv.second);
+  if (ln->dtab) cudaFree(ln->dtab);
+  if (ln->dflags) cudaFree(ln->dflags);
+  if (ln->hflags) cudaFreeHost(ln->hflags);
+  if (ln->ev) cudaEventDestroy(ln->ev);
+  if (ln->st) cudaStreamDestroy(ln->st);
+}
+
+sgp_status admit(sgp_server* S) {
+  while (!S->queue.empty() && S->n_active < S->o.max_active) {
+    Request* R = S->queue.front();
+    if (S->in_use + R->bound > S->o.hbm_budget) break;  // strict arrival order
+    S->queue.pop_front();
+    R->st.admit_us = now_us(S);
+    S->in_use += R->bound;  // reserved while the lattice is built
+    sgp_status s = setup(S, R);
+    S->in_use -= R->bound;
+    Lane* ln = nullptr;
+    if (s == SGP_OK) s = lane_for(S, lane_key(S, R->L), &ln);
+    if (s != SGP_OK) {
+      R->st.status = s;
+      R->held = 0;
+      (void)cudaStreamSynchronize(S->bs);
+      release(S, R, S->bs);
+      R->st.done_us = now_us(S);
+      R->st.done = 1;
+      if (s == SGP_ERR_CUDA) return s;  // a failed device call: report it
+      continue;
+    }
+    S->in_use += R->held;
+    R->lane = ln;
+    ln->active.push_back(R);
+    ln->dirty = true;
+    S->n_active += 1;
+    S->peak_active = std::max(S->peak_active, S->n_active);
+  }
+  return SGP_OK;
+}
+
+// Requests of a lane whose round has finished: finish the stopped ones, keep the rest.
+sgp_status harvest(sgp_server* S, Lane* ln, int* done) {
+  std::vector<Request*> keep;
+  for (int q = 0; q < (int)ln->active.size(); ++q) {
+    Request* R = ln->active[q];
+    if (q < ln->ntab && ln->hflags[2 * q] == 0) {
+      if (sgp_status s = finish(S, R, ln->st)) return s;
+      S->n_active -= 1;
+      ++*done;
+    } else {
+      keep.push_back(R);
+    }
+  }
+  if ((int)keep.size() != ln->ntab || keep.size() != ln->active.size()) ln->dirty = true;
+  ln->active.swap(keep);
+  ln->in_flight = false;
+  return SGP_OK;
+}
+
+sgp_status launch(sgp_server* S, Lane* ln) {
+  const int ns = (int)ln->active.size();
+  Table& t = *ln->htab;
+  if (ln->dirty) {
+    std::memset(&t, 0, sizeof(Table));
+    t.nslots = ns;
+    t.kp = S->kp;
+    t.flags = ln->dflags;
+    for (int q = 0; q < ns; ++q) {
+      Request* R = ln->active[q];
+      fill_slot(S, R, t.s[q]);
+      for (int u = 0; u < U_KINDS; ++u) t.pre[u][q + 1] = t.pre[u][q] + R->vb[u];
+      if (!R->waited) {
+        SRV_CHECK(cudaStreamWaitEvent(ln->st, R->ready, 0), "wait for set-up");
+        R->waited = true;
+      }
+    }
+    SRV_CHECK(cudaMemcpyAsync(ln->dtab, &t, sizeof(Table), cudaMemcpyHostToDevice, ln->st),
+              "copy table");
+    ln->ntab = ns;
+    ln->dirty = false;
+  }
+  int dmax = 1;
+  for (Request* R : ln->active) dmax = std::max(dmax, R->L->D);
+  cudaGraphExec_t ex = nullptr;
+  if (sgp_status s = graph_for(S, ln, dmax, &ex)) return s;
+  for (int i = 0; i < S->o.check_every; ++i) {
+    SRV_CHECK(cudaGraphLaunch(ex, ln->st), "launching the batched CG iteration");
+    note_launches(ln->graph_kernels[dmax]);
+  }
+  SRV_CHECK(cudaMemcpyAsync(ln->hflags, ln->dflags, 2 * ns * sizeof(int), cudaMemcpyDeviceToHost,
+                            ln->st),
+            "copy flags");
+  SRV_CHECK(cudaEventRecord(ln->ev, ln->st), "record flags");
+  ln->in_flight = true;
+  return SGP_OK;
+}
+
+sgp_status server_step(sgp_server* S, int* completed) {
+  int done = 0;
+  for (auto& kv : S->lanes) {  // 1. lanes whose round has finished
+    Lane* ln = kv.second.get();
+    if (!ln->in_flight) continue;
+    const cudaError_t q = cudaEventQuery(ln->ev);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return cuda_status(q, "waiting for a lane");
+    if (sgp_status s = harvest(S, ln, &done)) return s;
+  }
+  if (sgp_status s = admit(S)) return s;  // 2. set-up overlaps the lanes in flight
+  bool any = false;
+  for (auto& kv : S->lanes) {  // 3. relaunch idle lanes
+    Lane* ln = kv.second.get();
+    if (!ln->in_flight && !ln->active.empty())
+      if (sgp_status s = launch(S, ln)) return s;
+    any = any || ln->in_flight;
+  }
+  // 4. without a finished request, wait a little for the next lane to finish
+  if (done == 0 && any) {
+    const double deadline = now_us(S) + kStepWaitUs;
+    bool ready = false;
+    while (!ready && now_us(S) < deadline) {
+      for (auto& kv : S->lanes) {
+        Lane* ln = kv.second.get();
+        if (ln->in_flight && cudaEventQuery(ln->ev) != cudaErrorNotReady) ready = true;
+      }
+      if (!ready) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    clear_pending_error();  // cudaEventQuery's not-ready status
+  }
+  if (completed) *completed = done;
+  return SGP_OK;
+}
+
+bool have_device() {
+  int count = 0;
+  return cudaGetDeviceCount(&count) == cudaSuccess && count > 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sgp_server_opts_init(sgp_server_opts* o) {
+  if (!o) return;
+  size_t freeb = 0, total = 0;
+  if (have_device() && cudaMemGetInfo(&freeb, &total) == cudaSuccess) o->hbm_budget = total / 2;
+  else o->hbm_budget = 0;
+  clear_pending_error();
+  o->max_active = 16;
+  o->probes = 8;
+  o->order_r = 1;
+  o->kernel = SGP_KERNEL_RBF_BINOMIAL;
+  o->spacing_s = 0.0;
+  o->value_dtype = SGP_VALUES_F32;
+  o->tol = 1e-3;
+  o->max_iter = 500;
+  o->check_every = 8;
+}
+
+unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_r, int k,
+                                           int value_dtype) {
+  if (n_points < 1 || d < 1 || order_r < 1 || k < 1) return 0;
+  const unsigned long long n = (unsigned long long)n_points, D = (unsigned long long)d + 1;
+  const unsigned long long nD = n * D, m = nD, r = (unsigned long long)order_r;
+  const unsigned long long kp = ((unsigned long long)k + 3) / 4 * 4;
+  const unsigned long long vbytes = value_dtype == SGP_VALUES_BF16 ? 2 : 4;
+  unsigned long long cap = 1024;
+  while (cap < 2 * nD) cap <<= 1;
+  const unsigned long long nseg = nD / kSplatSeg + m;  // segments and fix-up rows
+  // lattice arrays kept by the handle
+  const unsigned long long lattice = 4 * n + 2 * m * D + 8 * nD + 8 * D * r * m + 8 * nD +
+                                     4 * (m + 1) + 16 * (nseg + 2 * m) + 256;
+  // build work space (all counted at once)
+  const unsigned long long build = 7 * nD + 8 * cap + 4 * nD + 4 * nD +
+                                   4 * scan_temp_elems((int64_t)nD) + 4 * cap + 16 * nD +
+                                   4 * radix_temp_elems((int64_t)nD) + 16 * n +
+                                   4 * radix_temp_elems((int64_t)n) + 4 * n * d;
+  // values, splat partials, permuted input; CG vectors and partials; probe products
+  const unsigned long long values = 2 * m * kp * vbytes + nseg * kp * 4 + n * kp * 4;
+  const unsigned long long solve = 6 * n * kp * 4 + (n / 4 + 1) * kp * 8 + 2 * n * kp * 4 +
+                                   n * 4 + sizeof(Table) + 4096;
+  return lattice + build + values + solve;
+}
+
+sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
+  if (!out) {
+    set_error("sgp_server_create: out is null");
+    return SGP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sgp_server_opts o;
+  sgp_server_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.max_active < 1 || o.max_active > kMaxSlots || o.probes < 0 ||
+      o.probes + 1 > kMaxServeK || o.order_r < 1 || o.order_r > kMaxOrder || o.max_iter < 0 ||
+      !(o.tol >= 0.0) || o.check_every < 1 ||
+      (o.value_dtype != SGP_VALUES_F32 && o.value_dtype != SGP_VALUES_BF16)) {
+    set_error("sgp_server_create: need 1 <= max_active <= 64, 0 <= probes <= 31, "
+              "1 <= order_r <= 4, max_iter >= 0, tol >= 0, check_every >= 1");
+    return SGP_ERR_INVALID_ARG;
+  }
+  double sp, c[kMaxOrder + 1], g[kMaxOrder + 1];
+  if (!make_stencil(o.kernel, o.order_r, o.spacing_s, &sp, c, g)) {
+    set_error("sgp_server_create: unknown kernel");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (!have_device()) {
+    set_error("sgp_server_create: no CUDA device (this library has no CPU path)");
+    return SGP_ERR_CUDA;
+  }
+  clear_pending_error();
+  auto S = std::make_unique<sgp_server>();
+  S->o = o;
+  S->S = o.probes;
+  S->kp = (o.probes + 1 + 3) / 4 * 4;
+  S->t0 = std::chrono::steady_clock::now();
+  S->htab1 = std::make_unique<Table>();
+  SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
+  *out = S.release();
+  return SGP_OK;
+}
+
+sgp_status sgp_server_submit(sgp_server* S, const sgp_request* req, long long* id) {
+  if (!S || !req || !id) {
+    set_error("sgp_server_submit: null argument");
+    return SGP_ERR_INVALID_ARG;
+  }
+  const sgp_request& r = *req;
+  if (!r.X || !r.y || !r.Xs || !r.lengthscales || !r.mean || (S->S > 0 && !r.var) || r.n < 1 ||
+      r.ns < 1 || r.d < 1 || r.d + 1 > kMaxD || !(r.outputscale > 0.f) || !(r.noise > 0.f) ||
+      (r.n + r.ns) * (long long)(r.d + 1) > 0x7fffffffLL) {
+    set_error("sgp_server_submit: need X, y, Xs, lengthscales, mean (and var when probes > 0), "
+              "n >= 1, ns >= 1, 1 <= d <= 127, outputscale > 0, noise > 0 and "
+              "(n + ns)(d + 1) < 2^31");
+    return SGP_ERR_INVALID_ARG;
+  }
+  const unsigned long long bound =
+      sgp_request_bytes_bound(r.n + r.ns, r.d, S->o.order_r, S->kp, S->o.value_dtype);
+  if (bound > S->o.hbm_budget) {
+    set_error("sgp_server_submit: the request's memory bound exceeds the server's budget");
+    return SGP_ERR_INVALID_ARG;
+  }
+  auto R = std::make_unique<Request>();
+  R->id = S->next_id++;
+  R->in = r;
+  R->bound = bound;
+  R->st.arrival_us = r.arrival_us >= 0.0 ? r.arrival_us : now_us(S);
+  R->st.status = SGP_OK;
+  *id = R->id;
+  S->queue.push_back(R.get());
+  S->reqs[R->id] = std::move(R);
+  return SGP_OK;
+}
+
+sgp_status sgp_server_step(sgp_server* S, int* completed) {
+  if (completed) *completed = 0;
+  if (!S) {
+    set_error("sgp_server_step: null server");
+    return SGP_ERR_INVALID_ARG;
+  }
+  clear_pending_error();
+  return server_step(S, completed);
+}
+
+sgp_status sgp_server_stats(const sgp_server* S, long long id, sgp_request_stats* out) {
+  if (!S || !out) {
+    set_error("sgp_server_stats: null argument");
+    return SGP_ERR_INVALID_ARG;
+  }
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) {
+    set_error("sgp_server_stats: unknown request id");
+    return SGP_ERR_INVALID_ARG;
+  }
+  *out = it->second->st;
+  return SGP_OK;
+}
+
+sgp_status sgp_server_info(const sgp_server* S, int* queued, int* active,
+                           unsigned long long* bytes_in_use, int* peak_active) {
+  if (!S) {
+    set_error("sgp_server_info: null server");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (queued) *queued = (int)S->queue.size();
+  if (active) *active = S->n_active;
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  if (peak_active) *peak_active = S->peak_active;
+  return SGP_OK;
+}
+
+double sgp_server_clock_us(const sgp_server* S) { return S ? now_us(S) : 0.0; }
+
+void sgp_server_destroy(sgp_server* S) {
+  if (!S) return;
+  cudaStreamSynchronize(S->bs);
+  for (auto& kv : S->lanes) {
+    Lane* ln = kv.second.get();
+    cudaStreamSynchronize(ln->st);
+    for (Request* R : ln->active) release(S, R, ln->st);
+    ln->active.clear();
+  }
+  S->queue.clear();
+  for (auto& kv : S->lanes) destroy_lane(kv.second.get());
+  cudaStreamSynchronize(S->bs);
+  cudaStreamDestroy(S->bs);
+  delete S;
+  clear_pending_error();
+}
+
+}  // extern "C"

@@ -73,3 +73,32 @@ def subsample(n: int, count: int, seed: int) -> np.ndarray:
     """Sorted, distinct row indices drawn by seed (for sampled parity checks)."""
     rng = np.random.default_rng(seed + 15485863)
     return np.sort(rng.choice(n, size=min(count, n), replace=False)).astype(np.int64)
+
+
+def serving_stream(count: int, seed: int, rate_per_s: float = 50.0,
+                   n_range=(5_000, 500_000), dims=(3, 8, 20, 50, 90), test_points: int = 256,
+                   noise: float = 0.01):
+    """GP posterior requests with Poisson arrivals (exponential gaps, mean 1 / rate).
+
+    Each request: n log-uniform in n_range, d uniform over dims, n + test_points points
+    from one standardised Gaussian mixture split into training and test inputs, targets
+    as regression_targets, unit ARD lengthscales, outputscale 1, the given noise, and a
+    probe seed.  Returns a list of dicts (arrival_s, X, y, Xs, lengthscales, outputscale,
+    noise, seed) in arrival order.
+    """
+    rng = np.random.default_rng(seed + 32452843)
+    gaps = rng.exponential(1.0 / rate_per_s, count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(lo, hi)))
+        d = int(dims[rng.integers(0, len(dims))])
+        rs = seed * 1000003 + i
+        P = gmm_points(n + test_points, d, rs)
+        X, Xs = P[:n], P[n:]
+        out.append(dict(arrival_s=float(arrivals[i]), X=np.ascontiguousarray(X),
+                        y=regression_targets(X, rs), Xs=np.ascontiguousarray(Xs),
+                        lengthscales=np.ones(d, np.float32), outputscale=1.0, noise=noise,
+                        seed=rs))
+    return out

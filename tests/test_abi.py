@@ -79,3 +79,28 @@ def test_product_never_touches_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
                 assert "sgp_oracle" not in text and "liboracle" not in text, f
+
+
+def test_request_bytes_bound_is_host_only_and_monotone(lib):
+    b = lambda n, d, k=9, dt=0: lib.sgp_request_bytes_bound(n, d, 1, k, dt)  # noqa: E731
+    assert b(0, 3) == 0 and b(10, 0) == 0
+    assert b(1000, 3) < b(2000, 3) < b(2000, 8)
+    assert b(1000, 3, k=9) < b(1000, 3, k=20)
+    assert b(100_000, 20, dt=1) < b(100_000, 20, dt=0)
+    # at least the lattice arrays at m = n (d + 1): keys, ids, weights, neighbour table
+    n, d = 50_000, 8
+    D = d + 1
+    m = n * D
+    assert b(n, d) >= 2 * m * D + 8 * n * D + 8 * D * m + 2 * m * 12 * 4
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_server_without_gpu_fails_loudly(lib):
+    o = _lib.sgp_server_opts()
+    lib.sgp_server_opts_init(ctypes.byref(o))
+    assert (o.max_active, o.probes, o.max_iter, o.check_every, o.hbm_budget) == (16, 8, 500, 8, 0)
+    h = ctypes.c_void_p()
+    assert lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)) == 6
+    assert not h.value
+    o.max_active = 0
+    assert lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)) == 1
