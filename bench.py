@@ -18,6 +18,9 @@ mixture (the shape of Houseelectric, n=2,049,280 d=11, Sec. 5 Table n_lattice), 
 lengthscales, binomial stencil r = 1, k = 16 right-hand sides ~ N(0, 1), noise 0.01,
 CG tolerance 1e-3, at most 500 iterations.
 
+Serving (`serving` in the JSON line): a Poisson stream of GP posterior requests through the
+continuous-batching server and through the plain one-at-a-time path, solves/s and p50/p99.
+
 `--impl reference` times the FP64 CPU oracle (the reference for this path) on a bounded
 sample of the same workload, on this host's cores.
 """
@@ -51,6 +54,7 @@ WORKLOAD = dict(n=2_000_000, d=11, k=16, seed=4, lengthscale=1.0, noise=0.01, to
                 max_iter=500, kernel="rbf_binomial", order=1, blur="symmetric",
                 precond_rank=0)
 PCG_RANK = 100  # App. A: CG pre-conditioner of rank 100
+SERVING = dict(requests=256, rate_per_s=50.0, seed=5, max_active=16, test_points=256)
 CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg
 REF_SAMPLE = dict(n=50_000, iters=2)    # oracle sample per step for --impl reference
 
@@ -69,6 +73,8 @@ def parse_args(argv=None):
                          "default; App. A uses 100)")
     ap.add_argument("--max-iter", type=int, default=WORKLOAD["max_iter"],
                     help="CG iteration cap (default 500; lower only for profiling runs)")
+    ap.add_argument("--serving-requests", type=int, default=SERVING["requests"],
+                    help="requests in the serving stream (0 = skip the serving comparison)")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
                     help="profiling aid: build once, run R symmetric MVMs, print their time")
     return ap.parse_args(argv)
@@ -369,6 +375,10 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Vh.numel() * 4 + lsh.numel() * 4),
                "d2h_bytes_per_step": int(n * k * 4)}
 
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = run_serving(args.serving_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(W)
@@ -397,7 +407,7 @@ def run_ours(args, world, rank, local):
                        "l2": "no flush: every step's working set (X 88 MB, V 128 MB, "
                              "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
             "gpu_launches": int(launches), "clocks": clk.summary(),
         "cg_final_rel_res_max": float(np.max(rel)), "cg_true_rel_res_max": true_rel,
         }
@@ -406,6 +416,50 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# serving: the same request stream through the batched server and the plain path
+# ---------------------------------------------------------------------------------------
+def run_serving(count: int):
+    """GP posterior requests (mean and probe variance, k = 1 + 8) with Poisson arrivals,
+    replayed in real time through the continuous-batching server and through the plain
+    one-request-at-a-time path (the same server with one slot); latency is completion
+    minus scheduled arrival, solves/s = requests / (last completion - first arrival)."""
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.serve import Server, run_stream
+
+    t0 = time.perf_counter()
+    reqs = synth.serving_stream(count, SERVING["seed"], rate_per_s=SERVING["rate_per_s"],
+                                test_points=SERVING["test_points"])
+    gen_s = time.perf_counter() - t0
+    out, results = {}, {}
+    for name, slots in (("batched", SERVING["max_active"]), ("plain", 1)):
+        with Server(max_active=slots) as srv:
+            res = run_stream(srv, reqs)
+            results[name] = [tuple(a.copy() for a in srv.result(i)) for i in res.ids]
+            rel = [srv.stats(i)["rel_res"] for i in res.ids]
+        out[name] = {"solves_per_s": res.solves_per_s, "p50_s": res.percentile(50),
+                     "p99_s": res.percentile(99), "makespan_s": res.makespan_s,
+                     "max_active": slots, "peak_active": res.peak_active,
+                     "cg_iters_mean": float(np.mean(res.iters)),
+                     "cg_iters_max": int(np.max(res.iters)),
+                     "rel_res_max": float(np.max(rel))}
+        print("serving %s: %.2f solves/s p50 %.3f s p99 %.3f s" % (
+            name, res.solves_per_s, res.percentile(50), res.percentile(99)),
+            file=sys.stderr, flush=True)
+    same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+               for a, b in zip(results["batched"], results["plain"]))
+    out.update({"requests": count, "arrival_rate_per_s": SERVING["rate_per_s"],
+                "identical_results_batched_vs_plain": bool(same),
+                "stream": "n log-uniform [5e3, 5e5], d uniform over {3, 8, 20, 50, 90}, "
+                          "standardised 16-component GMM, y = sum sin(2 x) + N(0, 0.01), "
+                          "%d test points, unit lengthscales, noise 0.01, k = 1 + 8 probes, "
+                          "tol 1e-3, max 500 iterations; generated in %.1f s"
+                          % (SERVING["test_points"], gen_s),
+                "solves_per_s_ratio": out["batched"]["solves_per_s"] / out["plain"]["solves_per_s"],
+                "p99_ratio": out["batched"]["p99_s"] / out["plain"]["p99_s"]})
+    return out
 
 
 # ---------------------------------------------------------------------------------------
