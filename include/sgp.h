@@ -204,6 +204,38 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
 sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
                            float tol, int max_iter, float* X, int* iters, double* rel_res);
 
+/* Input gradients of the backward (sgp_mvm_backward).
+ *   SGP_GRAD_LATTICE  the exact derivative of the product the forward computes, through
+ *                     the barycentric weights (Sec. 3.2): piecewise linear in the elevated
+ *                     points, with ranks and vertex ids piecewise constant.
+ *   SGP_GRAD_FILTER   Sec. 4.2: the kernel's own input gradient estimated with ONE lattice
+ *                     filtering of the 2k(d+1) columns [z (.) G, G, z (.) V, V], z = X / l,
+ *                     with k' = dk/d(d^2) (= -k/2 for the RBF kernels; not available for
+ *                     Matern-3/2). */
+enum {
+  SGP_GRAD_LATTICE = 0,
+  SGP_GRAD_FILTER = 1,
+};
+
+/* Backward of out = alpha * W B W^T V (B per `blur`, as in sgp_mvm_ex) for a scalar loss
+ * with upstream gradient G = dLoss/dout:
+ *   dV   = alpha * W B^T W^T G   (the transpose product on the same lattice)
+ *   dX   = dLoss/dX  and  dls = dLoss/dlengthscales  through the lattice's dependence on
+ *          the scaled points z = X / l, computed as selected by `grad` (SGP_GRAD_*);
+ *          dls_j = -sum_i dX_ij X_ij / l_j.
+ *   X, lengthscales  device, the [n][d] points and [d] lengthscales the handle was built
+ *                    from (needed when dX or dls is requested; may be NULL otherwise).
+ *   V, G     device [n][k] fp32 (V may be NULL when only dV is requested).
+ *   dV       device [n][k], dX device [n][d], dls device [d] fp32; each may be NULL.
+ * Work space: two extra lattice value buffers (SGP_GRAD_LATTICE) or 2 n min(256, 2k(d+1))
+ * floats and the value buffers of that many columns (SGP_GRAD_FILTER), allocated per
+ * call; stream-ordered on the handle's stream, no synchronisation.  1 <= k <= 256.
+ * SGP_ERR_INVALID_ARG for a missing input, an unknown blur or grad, or SGP_GRAD_FILTER on
+ * a Matern-3/2 handle. */
+sgp_status sgp_mvm_backward(sgp_lattice* h, const float* X, const float* lengthscales,
+                            const float* V, const float* G, int k, int blur, float alpha,
+                            int grad, float* dV, float* dX, float* dls);
+
 /* Blur timing for measurement tools.  While enabled, every CG solve on this handle
  * brackets the blur passes of one MVM with CUDA events recorded on the solve's stream (as
  * nodes of its graph) and, at each flag check, adds the elapsed time of the last replay

@@ -72,6 +72,10 @@ def _load():
         lib.orc_mvm.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_double, ctypes.c_double, _c_double_p]
         lib.orc_mvm.restype = ctypes.c_int
+        lib.orc_mvm_backward.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, _c_double_p,
+                                         _c_double_p, _c_double_p]
+        lib.orc_mvm_backward.restype = ctypes.c_int
         lib.orc_cg.argtypes = [ctypes.c_void_p, _c_double_p, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                _c_double_p, _c_int_p, _c_double_p]
@@ -237,6 +241,22 @@ class OracleLattice:
         _lib.orc_slice(self._h, _p(lat, ctypes.c_double), lat.shape[1], _p(out, ctypes.c_double))
         return out
 
+    def mvm_backward(self, V, G, mode: int = 0, alpha: float = 1.0):
+        """Gradients of <G, alpha K~ V> w.r.t. V ([n][k]), the points X ([n][d]) and the
+        lengthscales ([d]) through the barycentric weights (Sec. 3.2)."""
+        V2, _ = self._as2d(V)
+        G2, _ = self._as2d(G)
+        k = V2.shape[1]
+        dV = np.zeros_like(V2)
+        dX = np.zeros((self.n, self.d))
+        dls = np.zeros(self.d)
+        rc = _lib.orc_mvm_backward(self._h, _p(V2, ctypes.c_double), _p(G2, ctypes.c_double),
+                                   k, mode, alpha, _p(dV, ctypes.c_double),
+                                   _p(dX, ctypes.c_double), _p(dls, ctypes.c_double))
+        if rc != 0:
+            raise ValueError("orc_mvm_backward: invalid arguments")
+        return dV, dX, dls
+
     def mvm(self, V, mode: int = 0, alpha: float = 1.0, beta: float = 0.0):
         """alpha K~ V + beta V; mode 0 sequential blur, 1 its transpose, 2 symmetric."""
         V2, shape = self._as2d(V)
@@ -401,3 +421,31 @@ def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: i
     mean = P[:, 0]
     var = outputscale - (Z * P[:, 1:]).mean(1) if S > 0 else np.zeros(ns)
     return mean, var, iters, rel
+
+
+def filter_gradient(apply_K, X, ls, V, G, alpha: float = 1.0, kprime_ratio: float = -0.5):
+    """Sec. 4.2: gradient of L = <G, alpha K V> with respect to the inputs from ONE filtering
+    call.  With k_ij = k(d_ij^2) on z = x / l and k' its derivative in d^2,
+        dL/dz_n = 2 sum_j k'_nj [ (g_n . v_j)(z_n - z_j) + (g_j . v_n)(z_n - z_j) ],
+    which splits into filtering the columns [z (.) g, g, z (.) v, v] with k' and combining
+    the outputs at each point.  For the RBF k(d^2) = exp(-d^2 / 2), k' = -k / 2, so the
+    filter is the kernel operator itself (kprime_ratio = -1/2).  apply_K maps an [n][c]
+    array to K times it.  Returns (dX [n][d], dls [d])."""
+    X = np.asarray(X, np.float64)
+    ls = np.asarray(ls, np.float64)
+    V = np.asarray(V, np.float64)
+    G = np.asarray(G, np.float64)
+    Z = X / ls
+    n, d = Z.shape
+    k = V.shape[1]
+    ZG = (G[:, :, None] * Z[:, None, :]).reshape(n, k * d)  # column c d + t: g_c z_t
+    ZV = (V[:, :, None] * Z[:, None, :]).reshape(n, k * d)
+    F = apply_K(np.concatenate([ZG, G, ZV, V], 1))
+    FZG = F[:, :k * d].reshape(n, k, d)
+    FG = F[:, k * d:k * d + k]
+    FZV = F[:, k * d + k:2 * k * d + k].reshape(n, k, d)
+    FV = F[:, 2 * k * d + k:]
+    dZ = 2.0 * alpha * kprime_ratio * (
+        Z * (G * FV).sum(1)[:, None] - (G[:, :, None] * FZV).sum(1)
+        + Z * (V * FG).sum(1)[:, None] - (V[:, :, None] * FZG).sum(1))
+    return dZ / ls, -(dZ * Z).sum(0) / ls

@@ -68,6 +68,9 @@ struct Lattice {
   std::vector<double> w;     // [n][D] barycentric weight of vertex k
   std::vector<int> idx;      // [n][D] id of vertex k of point i
   std::vector<int> keys;     // [m][D] integer coordinates of each vertex
+  std::vector<double> z;     // [n][d] lengthscale-normalised points x / l
+  std::vector<double> f;     // [d] elevation factors scale / sqrt((j+1)(j+2))
+  std::vector<double> ls;    // [d] lengthscales
   std::unordered_map<std::string, int> table;  // key -> vertex id
   int64_t m = 0;
   // memo of neighbour lookups: nbr[((j * r + (t-1)) * 2 + (sgn > 0)) * m + v] = id of
@@ -363,12 +366,15 @@ int orc_build(const float* X, const float* ls, int64_t n, int d, int r, const do
   L->rank.resize((size_t)n * D);
   L->w.resize((size_t)n * D);
   L->idx.resize((size_t)n * D);
-  std::vector<double> z(d);
+  L->f = f;
+  L->ls.assign(ls, ls + d);
+  L->z.resize((size_t)n * d);
   std::vector<int> key(D);
   for (int64_t i = 0; i < n; ++i) {
+    double* z = &L->z[i * d];
     for (int j = 0; j < d; ++j) z[j] = (double)X[i * d + j] / (double)ls[j];
     double* y = &L->y[i * D];
-    elevate(z.data(), d, f, y);
+    elevate(z, d, f, y);
     enclosing_simplex(y, d, &L->rem0[i * D], &L->rank[i * D], &L->w[i * D]);
     for (int k = 0; k < D; ++k) {
       vertex_key(&L->rem0[i * D], &L->rank[i * D], d, k, key.data());
@@ -520,6 +526,66 @@ void orc_dense_rbf(const float* X, const float* ls, int64_t n, int d, const doub
       for (int c = 0; c < k; ++c) out[i * k + c] += kv * V[j * k + c];
     }
   }
+}
+
+// Gradients of the scalar L = <G, alpha K~ V> (G, V: [n][k]) with respect to V, the
+// points X and the lengthscales.  K~ V = W B W^T V is linear in V and in every weight
+// w_ik; the weights are piecewise linear in the elevated point y (the ranks, remainder-0
+// points and vertex ids are piecewise constant), so:
+//   dV     = alpha W B^T W^T G                                     (mode 0 <-> 1, 2 = 2)
+//   dw_ik  = alpha (<G_i, (B W^T V)[v_ik]> + <V_i, (B^T W^T G)[v_ik]>)
+//   dy_ic  = (dw_i[d - rank_ic] - dw_i[(D - rank_ic) mod D]) / D  (from the weight formula:
+//            (y_c - rem0_c)/D is added to b[d - rank_c] and subtracted from b[D - rank_c],
+//            and b[D] is added to b[0])
+//   dz     from y_0 = sum_l a_l, y_i = sum_{l > i} a_l - i a_i with a_l = z_{l-1} f_{l-1}
+//   dX_ij  = dz_ij / l_j ;  dl_j = -sum_i dz_ij z_ij / l_j.
+// Any output pointer may be null.
+int orc_mvm_backward(void* h, const double* V, const double* G, int k, int mode, double alpha,
+                     double* dV, double* dX, double* dls) {
+  if (k < 1 || mode < 0 || mode > 2) return ORC_ERR_INVALID_ARG;
+  const Lattice& L = *static_cast<Lattice*>(h);
+  const int d = L.d, D = L.D;
+  const int tmode = mode == 2 ? 2 : 1 - mode;
+  // B W^T V and B^T W^T G
+  std::vector<double> BU, BS;
+  splat(L, V, k, BU);
+  if (mode == 2) blur_symmetric(L, k, BU);
+  else blur(L, k, mode, BU);
+  splat(L, G, k, BS);
+  if (tmode == 2) blur_symmetric(L, k, BS);
+  else blur(L, k, tmode, BS);
+  if (dV) {
+    slice(L, BS, k, dV);
+    for (int64_t e = 0; e < L.n * k; ++e) dV[e] *= alpha;
+  }
+  if (!dX && !dls) return ORC_OK;
+  std::vector<double> dw(D), dy(D), dz(d);
+  if (dls) std::fill(dls, dls + d, 0.0);
+  for (int64_t i = 0; i < L.n; ++i) {
+    for (int kk = 0; kk < D; ++kk) {
+      const int64_t v = L.idx[i * D + kk];
+      double t = 0.0;
+      for (int c = 0; c < k; ++c)
+        t += G[i * k + c] * BU[v * k + c] + V[i * k + c] * BS[v * k + c];
+      dw[kk] = alpha * t;
+    }
+    for (int c = 0; c < D; ++c) {
+      const int rk = L.rank[i * D + c];
+      dy[c] = (dw[d - rk] - dw[(D - rk) % D]) / (double)D;
+    }
+    // a_l (l = 1..d) enters y_0 and y_i (i < l) with +1 and y_l with -l
+    double below = dy[0];  // sum of dy_i for i < l
+    for (int l = 1; l <= d; ++l) {
+      const double da = below - (double)l * dy[l];
+      below += dy[l];
+      dz[l - 1] = da * L.f[l - 1];
+    }
+    for (int j = 0; j < d; ++j) {
+      if (dX) dX[i * d + j] = dz[j] / L.ls[j];
+      if (dls) dls[j] -= dz[j] * L.z[i * d + j] / L.ls[j];
+    }
+  }
+  return ORC_OK;
 }
 
 void orc_free(void* h) { delete static_cast<Lattice*>(h); }

@@ -9,8 +9,8 @@ from ._lib import SGPError  # noqa: F401
 
 
 def __getattr__(name):
-    if name == "Lattice":
-        from .lattice import Lattice
+    if name in ("Lattice", "lattice_mvm"):
+        from . import lattice
 
-        return Lattice
+        return getattr(lattice, name)
     raise AttributeError(name)

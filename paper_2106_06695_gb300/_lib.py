@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "SGP_OK", 1: "SGP_ERR_INVALID_ARG", 2: "SGP_ERR_OOM", 3: "SGP
 
 KERNELS = {"rbf_binomial": 0, "rbf_coverage": 1, "matern32_coverage": 2}
 BLURS = {"sequential": 0, "transpose": 1, "symmetric": 2}
+GRADS = {"lattice": 0, "filter": 1}
 VALUE_DTYPES = {"f32": 0, "bf16": 1}
 
 
@@ -97,6 +98,7 @@ def load():
         "sgp_mvm_ex": (I, [P, P, I, I, F, F, P]),
         "sgp_mvm_static": (I, [P, P, I, I, F, F, P]),
         "sgp_cg_solve": (I, [P, P, I, F, F, I, P, P, P]),
+        "sgp_mvm_backward": (I, [P, P, P, P, P, I, I, F, I, P, P, P]),
         "sgp_cg_solve_ex": (I, [P, P, I, I, F, F, I, P, P, P]),
         "sgp_lattice_free": (None, [P]),
         "sgp_profile_blur": (I, [P, I]),

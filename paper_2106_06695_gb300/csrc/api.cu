@@ -23,7 +23,7 @@ bool have_device() {
 void free_lattice(Lattice* L) {
   if (!L) return;
   cudaStream_t st = L->stream;
-  void* arrays[] = {L->perm, L->idx, L->w, L->row_ptr, L->items, L->nbr, L->keys, L->err,
+  void* arrays[] = {L->perm, L->idx, L->w, L->rank, L->row_ptr, L->items, L->nbr, L->keys, L->err,
                     L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial,
                     L->vperm};
   for (void* p : arrays)
@@ -266,6 +266,26 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
                         int max_iter, float* X, int* iters, double* rel_res) {
   return sgp_cg_solve_ex(h, B, k, SGP_BLUR_SYMMETRIC, noise_var, tol, max_iter, X, iters,
                          rel_res);
+}
+
+sgp_status sgp_mvm_backward(sgp_lattice* h, const float* X, const float* lengthscales,
+                            const float* V, const float* G, int k, int blur, float alpha,
+                            int grad, float* dV, float* dX, float* dls) {
+  if (sgp_status s = check_handle(h)) return s;
+  const bool want_x = dX || dls;
+  if (k < 1 || k > kMaxK || blur < SGP_BLUR_SEQUENTIAL || blur > SGP_BLUR_SYMMETRIC ||
+      (grad != SGP_GRAD_LATTICE && grad != SGP_GRAD_FILTER) || !G || (want_x && (!V || !X || !lengthscales))) {
+    set_error("sgp_mvm_backward: need G, 1 <= k <= 256, an SGP_BLUR_* blur, an SGP_GRAD_* "
+              "mode, and V, X and lengthscales when dX or dls is requested");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (grad == SGP_GRAD_FILTER && want_x && h->kernel == SGP_KERNEL_MATERN32_COVERAGE) {
+    set_error("sgp_mvm_backward: SGP_GRAD_FILTER needs an RBF handle (k' = -k / 2)");
+    return SGP_ERR_INVALID_ARG;
+  }
+  if (!dV && !want_x) return SGP_OK;
+  clear_pending_error();
+  return run_mvm_backward(h, X, lengthscales, V, G, k, blur, alpha, grad, dV, dX, dls);
 }
 
 void sgp_lattice_free(sgp_lattice* h) { free_lattice(h); }

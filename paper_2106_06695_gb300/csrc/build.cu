@@ -272,13 +272,16 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
 __global__ void k_entry_ids(const int32_t* __restrict__ entry_slot,
                             const int32_t* __restrict__ slot_id,
                             const int32_t* __restrict__ perm, const float* __restrict__ w_user,
-                            int64_t nD, int D, int32_t* __restrict__ idx,
-                            float* __restrict__ w) {
+                            const uint8_t* __restrict__ rank_user, int64_t nD, int D,
+                            int32_t* __restrict__ idx, float* __restrict__ w,
+                            uint8_t* __restrict__ rank) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nD) return;
   const int32_t s = entry_slot[e];
   idx[e] = s >= 0 ? slot_id[s] : 0;
-  w[e] = w_user[(int64_t)perm[e / D] * D + (e % D)];
+  const int64_t u = (int64_t)perm[e / D] * D + (e % D);
+  w[e] = w_user[u];
+  rank[e] = rank_user[u];
 }
 
 // ---------------------------------------------------------------------------------
@@ -564,9 +567,10 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   note_launches(1);
   SGP_CHECK(dalloc(&L->idx, nD, st), "alloc idx");
   SGP_CHECK(dalloc(&L->w, nD, st), "alloc w");
-  L->bytes += nD * (sizeof(int32_t) + sizeof(float));
+  SGP_CHECK(dalloc(&L->rank, nD, st), "alloc rank");
+  L->bytes += nD * (sizeof(int32_t) + sizeof(float) + sizeof(uint8_t));
   k_entry_ids<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(entry_slot, slot_id, L->perm, w_user,
-                                                          nD, D, L->idx, L->w);
+                                                          rank, nD, D, L->idx, L->w, L->rank);
   note_launches(1);
   SGP_CHECK(cudaGetLastError(), "numbering");
 

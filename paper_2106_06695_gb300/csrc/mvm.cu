@@ -418,6 +418,36 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
   return passes;
 }
 
+// Splat (locality-ordered input) and blur only; returns the buffer holding the result.
+template <class S>
+S* splat_blur_t(const Lattice* L, const float* Vp, int k, int blur, S* lat0, S* lat1,
+                float* partial, cudaStream_t st) {
+  Taps c{}, g{};
+  for (int t = 0; t <= L->r; ++t) {
+    c.t[t] = (float)L->coef[t];
+    g.t[t] = (float)L->half[t];
+  }
+  launch_splat_t<S>(L, Vp, k, lat0, partial, st);
+  S* a = lat0;
+  S* b = lat1;
+  auto pass = [&](int j, const Taps& tp) {
+    launch_blur_t<S>(L, j, tp, a, b, k, st);
+    S* t = a;
+    a = b;
+    b = t;
+  };
+  const int D = L->D;
+  if (blur == SGP_BLUR_SEQUENTIAL) {
+    for (int j = 0; j < D; ++j) pass(j, c);
+  } else if (blur == SGP_BLUR_TRANSPOSE) {
+    for (int j = D - 1; j >= 0; --j) pass(j, c);
+  } else {
+    for (int j = 0; j < D; ++j) pass(j, g);
+    for (int j = D - 1; j >= 0; --j) pass(j, g);
+  }
+  return a;
+}
+
 size_t value_size(const Lattice* L) {
   return L->value_dtype == SGP_VALUES_BF16 ? sizeof(bf16) : sizeof(float);
 }
@@ -489,6 +519,27 @@ void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, fl
     enqueue_t<float>(L, V_user, k, blur, alpha, beta, out, (float*)lat0, (float*)lat1, partial,
                      vperm, st, nullptr, false);
 }
+
+void* enqueue_splat_blur(const Lattice* L, const float* Vp, int k, int blur, void* lat0,
+                         void* lat1, float* partial, cudaStream_t st) {
+  if (L->value_dtype == SGP_VALUES_BF16)
+    return splat_blur_t<bf16>(L, Vp, k, blur, (bf16*)lat0, (bf16*)lat1, partial, st);
+  return splat_blur_t<float>(L, Vp, k, blur, (float*)lat0, (float*)lat1, partial, st);
+}
+
+void enqueue_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStream_t st) {
+  launch_permute(L, V, k, Vp, st);
+}
+
+void enqueue_slice_caller(const Lattice* L, const void* lat, int k, float alpha, float* out,
+                          cudaStream_t st) {
+  if (L->value_dtype == SGP_VALUES_BF16)
+    launch_slice_t<true, bf16>(L, (const bf16*)lat, nullptr, k, alpha, 0.f, out, st);
+  else
+    launch_slice_t<true, float>(L, (const float*)lat, nullptr, k, alpha, 0.f, out, st);
+}
+
+size_t lattice_value_bytes(const Lattice* L, int k) { return (size_t)L->m * k * value_size(L); }
 
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out) {

@@ -58,7 +58,6 @@ __global__ void k_shift(const int32_t* __restrict__ perm, int64_t n, int l, uint
 }
 
 __device__ __forceinline__ float to_f(float x) { return x; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // Per-block partial of L^T X over the block's rows, L = Omega (regenerated) when OMEGA,
 // else L = X.  X: [n][ld] (first l columns used).  out: partial[block][l][l] (fp64 of

@@ -69,6 +69,7 @@ struct sgp_lattice {
   float* vperm = nullptr;    // [n][k] the caller's V in locality order (public MVMs)
   int32_t* nbr = nullptr;      // [D][r][2][m] neighbour id of v - t u_j (0) / v + t u_j (1)
   int16_t* keys = nullptr;     // [m][D] vertex coordinates
+  uint8_t* rank = nullptr;     // [n][D] rank of each elevated coordinate, locality order
   unsigned* err = nullptr;     // device error word
 
   // Lattice values (fp32 or bf16 per value_dtype), allocated on first use, grown on demand.
@@ -146,6 +147,15 @@ size_t mvm_work_bytes(const Lattice* L, int k);
 // (mvm_work_bytes(L, k) bytes, 256-byte aligned); allocates nothing.
 void enqueue_mvm_into(const Lattice* L, const float* V, int k, int blur, float alpha,
                       float beta, float* out, void* work, cudaStream_t st);
+// Pieces of the operator for the backward: splat a locality-ordered Vp and blur it (the
+// result ends in the returned buffer, lat0 or lat1, of the handle's value type); gather
+// the caller's rows into locality order; out (caller's order) = alpha W lat.
+void* enqueue_splat_blur(const Lattice* L, const float* Vp, int k, int blur, void* lat0,
+                         void* lat1, float* partial, cudaStream_t st);
+void enqueue_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStream_t st);
+void enqueue_slice_caller(const Lattice* L, const void* lat, int k, float alpha, float* out,
+                          cudaStream_t st);
+size_t lattice_value_bytes(const Lattice* L, int k);
 // Full operator on the handle's stream, allocating value buffers when needed.
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);
@@ -178,6 +188,11 @@ struct Nystrom {
              int64_t dot_blocks, int block_threads, cudaStream_t st) const;
   void release(cudaStream_t st);
 };
+
+// ---- backward (backward.cu) ----
+sgp_status run_mvm_backward(Lattice* L, const float* X, const float* ls, const float* V,
+                            const float* G, int k, int blur, float alpha, int grad, float* dV,
+                            float* dX, float* dls);
 
 // ---- CG (cg.cu) ----
 // precond_rank > 0: preconditioned CG with a rank-precond_rank Nystrom preconditioner.

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import BLURS, KERNELS, VALUE_DTYPES, check
+from ._lib import BLURS, GRADS, KERNELS, VALUE_DTYPES, check
 
 
 def _f32_cuda(t: torch.Tensor, name: str) -> torch.Tensor:
@@ -141,6 +141,31 @@ class Lattice:
                                    float(beta), out.data_ptr()))
         return out.squeeze(1) if squeeze else out
 
+    def mvm_backward(self, X: torch.Tensor, lengthscales, V: torch.Tensor, G: torch.Tensor,
+                     blur: str = "sequential", alpha: float = 1.0, grad: str = "lattice",
+                     want=("V", "X", "ls")):
+        """(dV, dX, dls) of <G, alpha W B W^T V>: dV = alpha W B^T W^T G, and the input
+        gradients through the lattice (grad="lattice": exact derivative of the product;
+        grad="filter": Sec. 4.2 k'-filter estimate).  X and lengthscales are the build's."""
+        G2, squeeze = self._rhs(G, "G")
+        V2, _ = self._rhs(V, "V")
+        k = G2.shape[1]
+        X = _f32_cuda(X, "X")
+        ls = lengthscales
+        if not isinstance(ls, torch.Tensor):
+            ls = torch.full((self.d,), float(ls), dtype=torch.float32)
+        ls = ls.to(device=X.device, dtype=torch.float32).reshape(-1).expand(self.d).contiguous()
+        dV = torch.empty_like(G2) if "V" in want else None
+        dX = torch.empty_like(X) if "X" in want else None
+        dls = torch.empty(self.d, dtype=torch.float32, device=X.device) if "ls" in want else None
+        ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+        check(self._lib.sgp_mvm_backward(self._handle(), X.data_ptr(), ls.data_ptr(),
+                                         V2.data_ptr(), G2.data_ptr(), k, BLURS[blur],
+                                         float(alpha), GRADS[grad], ptr(dV), ptr(dX), ptr(dls)))
+        if dV is not None and squeeze:
+            dV = dV.squeeze(1)
+        return dV, dX, dls
+
     def cg(self, B: torch.Tensor, noise: float, tol: float = 1e-3, max_iter: int = 500,
            blur: str = "symmetric", out: torch.Tensor | None = None):
         """Batched CG on (outputscale K~ + noise I) X = B; returns (X, iters, rel_res)."""
@@ -154,3 +179,41 @@ class Lattice:
                                         float(noise), float(tol), int(max_iter), out.data_ptr(),
                                         iters.ctypes.data, rel.ctypes.data))
         return (out.squeeze(1) if squeeze else out), iters, rel
+
+
+class _LatticeMVM(torch.autograd.Function):
+    """out = alpha W B W^T V on the lattice of (X, lengthscales), with the hand-written
+    backward of sgp_mvm_backward for V, X and the lengthscales."""
+
+    @staticmethod
+    def forward(ctx, X, lengthscales, V, order, kernel, blur, alpha, grad, value_dtype):
+        lat = Lattice(X.detach(), lengthscales.detach(), order=order, kernel=kernel,
+                      value_dtype=value_dtype)
+        out = lat.mvm(V.detach(), blur=blur, alpha=alpha)
+        ctx.lat, ctx.blur, ctx.alpha, ctx.grad = lat, blur, alpha, grad
+        ctx.save_for_backward(X, lengthscales, V)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        X, ls, V = ctx.saved_tensors
+        want = tuple(name for name, need in zip(("X", "ls", "V"), ctx.needs_input_grad[:3])
+                     if need)
+        dV, dX, dls = ctx.lat.mvm_backward(X.detach(), ls.detach(), V.detach(),
+                                           gout.contiguous(), blur=ctx.blur, alpha=ctx.alpha,
+                                           grad=ctx.grad, want=want)
+        ctx.lat.close()
+        if dls is not None:
+            dls = dls.reshape(ls.shape) if ls.numel() == dls.numel() else dls.sum().reshape(ls.shape)
+        return dX, dls, dV, None, None, None, None, None, None
+
+
+def lattice_mvm(X: torch.Tensor, lengthscales: torch.Tensor, V: torch.Tensor, order: int = 1,
+                kernel: str = "rbf_binomial", blur: str = "symmetric", alpha: float = 1.0,
+                grad: str = "lattice", value_dtype: str = "f32") -> torch.Tensor:
+    """Differentiable lattice MVM alpha K~(X / lengthscales) V (Sec. 3.2) for fp32 CUDA
+    tensors; gradients flow to X, lengthscales and V through the library's backward."""
+    if not isinstance(lengthscales, torch.Tensor):
+        lengthscales = torch.full((X.shape[1],), float(lengthscales), dtype=torch.float32,
+                                  device=X.device)
+    return _LatticeMVM.apply(X, lengthscales, V, order, kernel, blur, alpha, grad, value_dtype)
