@@ -75,6 +75,8 @@ def parse_args(argv=None):
                     help="CG iteration cap (default 500; lower only for profiling runs)")
     ap.add_argument("--serving-requests", type=int, default=SERVING["requests"],
                     help="requests in the serving stream (0 = skip the serving comparison)")
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the forward + backward timing at n=500k, d=20")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
                     help="profiling aid: build once, run R symmetric MVMs, print their time")
     return ap.parse_args(argv)
@@ -302,35 +304,14 @@ def run_ours(args, world, rank, local):
                             blur=W["blur"], out=out)
     resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
     true_rel = (resid.norm(dim=0) / Vd.double().norm(dim=0)).max().item()
-    for _ in range(3):
-        lat.mvm(Vd, blur=W["blur"], out=out)
+    mvm_ms = graph_replay_median_ms(lat, Vd, out, W["blur"])
+    mvm_seq_ms = graph_replay_median_ms(lat, Vd, out, "sequential")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    reps = 10
-    for _ in range(reps):
-        lat.mvm(Vd, blur=W["blur"], out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    mvm_ms = e0.elapsed_time(e1) / reps
-    e0.record()
-    for _ in range(reps):
-        lat.mvm(Vd, blur="sequential", out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    mvm_seq_ms = e0.elapsed_time(e1) / reps
     ref_out = lat.mvm(Vd, blur=W["blur"]).double()
     lat.close()
     # the same product with the lattice values stored in bf16 (fp32 sums)
     lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"], value_dtype="bf16")
-    for _ in range(3):
-        lat.mvm(Vd, blur=W["blur"], out=out)
-    e0.record()
-    for _ in range(reps):
-        lat.mvm(Vd, blur=W["blur"], out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    mvm_bf16_ms = e0.elapsed_time(e1) / reps
+    mvm_bf16_ms = graph_replay_median_ms(lat, Vd, out, W["blur"])
     bf16_rel_err = ((out.double() - ref_out).norm() / ref_out.norm()).item()
     lat.close()
 
@@ -375,6 +356,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Vh.numel() * 4 + lsh.numel() * 4),
                "d2h_bytes_per_step": int(n * k * 4)}
 
+    backward = run_backward_c3() if rank == 0 and not args.no_backward else None
+
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = run_serving(args.serving_requests)
@@ -400,7 +383,10 @@ def run_ours(args, world, rank, local):
                        "cg_iters_per_step": prof["iters"],
                        "precond_rank": W["precond_rank"], "pcg": pcg,
                        "build_ms_median": float(np.median(prof["build_ms"])),
-                       "mvm_symmetric_ms": mvm_ms, "mvm_sequential_ms": mvm_seq_ms,
+                       "mvm_symmetric_ms": mvm_ms,
+                       "mvm_symmetric_ms_note": "median of 50 graph-replayed MVMs",
+                       "mvm_symmetric_mpoint_s": n / (mvm_ms / 1e3) / 1e6,
+                       "mvm_sequential_ms": mvm_seq_ms,
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
                        "mvm_symmetric_bf16_values_ms": mvm_bf16_ms,
                        "bf16_values_rel_l2_vs_fp32": bf16_rel_err,
@@ -408,6 +394,7 @@ def run_ours(args, world, rank, local):
                              "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+            "backward": backward,
             "gpu_launches": int(launches), "clocks": clk.summary(),
         "cg_final_rel_res_max": float(np.max(rel)), "cg_true_rel_res_max": true_rel,
         }
@@ -416,6 +403,70 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def graph_replay_median_ms(lat, V, out, blur, replays=50, warmup=5):
+    """Median time of one MVM captured as a CUDA graph and replayed (events around each
+    replay, on the replaying stream)."""
+    import torch
+
+    lat.mvm(V, blur=blur, out=out)  # buffers allocated outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lat.mvm(V, blur=blur, out=out)
+    for _ in range(warmup):
+        g.replay()
+    times = []
+    for _ in range(replays):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def run_backward_c3():
+    """Forward MVM and hand-written backward on n = 500,000, d = 20 (correlated Gaussian
+    points, ARD lengthscales log-uniform [0.5, 2], k = 8, symmetric blur): median of 5 of
+    each, after a warm-up, with CUDA events on the current stream."""
+    import torch
+
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    n, d, k = 500_000, 20, 8
+    X, ls = synth.correlated_points(n, d, 3)
+    Xd = torch.from_numpy(X).cuda()
+    ld = torch.from_numpy(ls).cuda()
+    Vd = torch.from_numpy(synth.gaussian_values(n, k, 4)).cuda()
+    Gd = torch.from_numpy(synth.gaussian_values(n, k, 5)).cuda()
+    lat = Lattice(Xd, ld)
+    out = torch.empty_like(Vd)
+
+    def timed(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    fwd = timed(lambda: lat.mvm(Vd, blur="symmetric", out=out))
+    bwd = timed(lambda: lat.mvm_backward(Xd, ld, Vd, Gd, blur="symmetric"))
+    bwd_f = timed(lambda: lat.mvm_backward(Xd, ld, Vd, Gd, blur="symmetric", grad="filter"))
+    res = {"workload": "n=%d d=%d k=%d correlated Gaussian, ARD lengthscales, symmetric blur"
+                       % (n, d, k), "m": lat.m, "forward_ms": fwd,
+           "backward_lattice_ms": bwd, "backward_filter_ms": bwd_f,
+           "forward_backward_mpoint_s": n / ((fwd + bwd) / 1e3) / 1e6}
+    lat.close()
+    return res
 
 
 # ---------------------------------------------------------------------------------------
