@@ -204,6 +204,23 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
 sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
                            float tol, int max_iter, float* X, int* iters, double* rel_res);
 
+/* log det(outputscale * W B W^T + noise_var I), B = SGP_BLUR_SYMMETRIC: the second term of
+ * the marginal log-likelihood (Eq. gp_mll), by stochastic Lanczos quadrature.  For each
+ * probe column z_s, plain CG on A x = z_s (at most max_lanczos iterations; App. A uses
+ * 100; stopping early at ||r|| / ||z|| <= tol) gives the Lanczos tridiagonal T_s from its
+ * coefficients (T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T[j+1][j] =
+ * sqrt(beta_j)/alpha_j); quad_s = ||z_s||^2 e1^T log(T_s) e1 (from T_s's eigenvalues and
+ * the first components of its eigenvectors, implicit QL on the GPU), and
+ *   *logdet = (1/s) sum_s quad_s,
+ * an unbiased estimate of tr log A when E[z z^T] = I (e.g. Rademacher probes).
+ *   Z       device [n][s] fp32 probes (caller's order), 1 <= s <= 256.
+ *   max_lanczos 1..256;  noise_var >= 0;  tol >= 0.
+ *   logdet  host double;  quad host [s] doubles or NULL.
+ * Synchronises (CG flag reads and the result).  SGP_ERR_NONFINITE when a tridiagonal is
+ * not positive definite (e.g. noise_var = 0 on a singular operator). */
+sgp_status sgp_logdet(sgp_lattice* h, const float* Z, int s, float noise_var, int max_lanczos,
+                      float tol, double* logdet, double* quad);
+
 /* Input gradients of the backward (sgp_mvm_backward).
  *   SGP_GRAD_LATTICE  the exact derivative of the product the forward computes, through
  *                     the barycentric weights (Sec. 3.2): piecewise linear in the elevated

@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     dense_rbf,
     elevate,
     gp_posterior,
+    lanczos_quadrature,
     rademacher_sketch,
     splitmix64,
     simplex,

@@ -331,6 +331,12 @@ class OracleLattice:
                 rho[c] = rz[c]
         return X.reshape(shape), iters, rel
 
+    def logdet(self, Z, noise: float, outputscale: float = 1.0, max_lanczos: int = 100,
+               tol: float = 0.0):
+        """lanczos_quadrature on A = outputscale K~ + noise I (symmetric blur)."""
+        return lanczos_quadrature(lambda P: self.mvm(P, mode=2, alpha=outputscale, beta=noise),
+                                  Z, max_lanczos, tol)
+
     def cg(self, B, noise: float, tol: float = 1e-3, max_iter: int = 500,
            outputscale: float = 1.0, mode: int = 0):
         """CG on (outputscale K~ + noise I) X = B; returns X, iterations, rel. residuals."""
@@ -347,9 +353,11 @@ class OracleLattice:
         return X.reshape(shape), iters, rel
 
 
-def _cg_columns(apply_A, B, tol: float, max_iter: int):
+def _cg_columns(apply_A, B, tol: float, max_iter: int, history=None):
     """Textbook CG (Sec. 2), one independent iteration per column of B: x_0 = 0, stop a
-    column when ||r|| / ||b|| <= tol or after max_iter iterations; b = 0 gives x = 0."""
+    column when ||r|| / ||b|| <= tol or after max_iter iterations; b = 0 gives x = 0.
+    history: optional dict that receives per column the lists of step sizes alpha_j and
+    ratios beta_j = <r_j+1, r_j+1> / <r_j, r_j> (the latter only while iterating on)."""
     n, k = B.shape
     X = np.zeros((n, k))
     R = B.copy()
@@ -359,6 +367,9 @@ def _cg_columns(apply_A, B, tol: float, max_iter: int):
     iters = np.zeros(k, np.int32)
     rel = np.where(bnorm > 0, 1.0, 0.0)
     active = (bnorm > 0) & (1.0 > tol) & (max_iter > 0)
+    if history is not None:
+        history["alpha"] = [[] for _ in range(k)]
+        history["beta"] = [[] for _ in range(k)]
     while active.any():
         AP = apply_A(P)
         for c in np.nonzero(active)[0]:
@@ -367,6 +378,8 @@ def _cg_columns(apply_A, B, tol: float, max_iter: int):
                 active[c] = False
                 continue
             a = rho[c] / pap
+            if history is not None:
+                history["alpha"][c].append(a)
             X[:, c] += a * P[:, c]
             R[:, c] -= a * AP[:, c]
             iters[c] += 1
@@ -375,9 +388,38 @@ def _cg_columns(apply_A, B, tol: float, max_iter: int):
             if rel[c] <= tol or iters[c] >= max_iter:
                 active[c] = False
                 continue
+            if history is not None:
+                history["beta"][c].append(rr / rho[c])
             P[:, c] = R[:, c] + (rr / rho[c]) * P[:, c]
             rho[c] = rr
     return X, iters, rel
+
+
+def lanczos_quadrature(apply_A, Z, max_iter: int = 100, tol: float = 0.0):
+    """Stochastic Lanczos quadrature of log det A (the log-det term of Eq. gp_mll): for each
+    probe z (a column of Z), CG on A x = z yields the Lanczos tridiagonal T of the Krylov
+    space of z (diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal
+    sqrt(beta_j)/alpha_j), and z^T log(A) z ~ ||z||^2 e1^T log(T) e1 from T's eigenvalues
+    and the first components of its eigenvectors.  Returns (mean over probes, per-probe
+    values)."""
+    from scipy.linalg import eigh_tridiagonal
+
+    Z = np.asarray(Z, np.float64)
+    hist = {}
+    _, iters, _ = _cg_columns(apply_A, Z, tol, max_iter, history=hist)
+    quads = np.zeros(Z.shape[1])
+    for c in range(Z.shape[1]):
+        m = int(iters[c])
+        if m == 0:
+            continue
+        a = np.asarray(hist["alpha"][c][:m])
+        b = np.asarray(hist["beta"][c][:m - 1])
+        diag = 1.0 / a
+        diag[1:] += b / a[:-1]
+        off = np.sqrt(b) / a[:-1]
+        lam, Q = eigh_tridiagonal(diag, off)
+        quads[c] = (Z[:, c] @ Z[:, c]) * float((Q[0] ** 2) @ np.log(lam))
+    return float(quads.mean()), quads
 
 
 def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: int = 8,

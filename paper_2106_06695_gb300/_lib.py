@@ -99,6 +99,7 @@ def load():
         "sgp_mvm_static": (I, [P, P, I, I, F, F, P]),
         "sgp_cg_solve": (I, [P, P, I, F, F, I, P, P, P]),
         "sgp_mvm_backward": (I, [P, P, P, P, P, I, I, F, I, P, P, P]),
+        "sgp_logdet": (I, [P, P, I, F, I, F, ctypes.POINTER(Dbl), P]),
         "sgp_cg_solve_ex": (I, [P, P, I, I, F, F, I, P, P, P]),
         "sgp_lattice_free": (None, [P]),
         "sgp_profile_blur": (I, [P, I]),

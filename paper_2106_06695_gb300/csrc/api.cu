@@ -288,6 +288,19 @@ sgp_status sgp_mvm_backward(sgp_lattice* h, const float* X, const float* lengths
   return run_mvm_backward(h, X, lengthscales, V, G, k, blur, alpha, grad, dV, dX, dls);
 }
 
+sgp_status sgp_logdet(sgp_lattice* h, const float* Z, int s, float noise_var, int max_lanczos,
+                      float tol, double* logdet, double* quad) {
+  if (sgp_status st = check_handle(h)) return st;
+  if (!Z || !logdet || s < 1 || s > kMaxK || max_lanczos < 1 || max_lanczos > 256 ||
+      !(noise_var >= 0.f) || !(tol >= 0.f)) {
+    set_error("sgp_logdet: need Z, logdet, 1 <= s <= 256, 1 <= max_lanczos <= 256, "
+              "noise_var >= 0 and tol >= 0");
+    return SGP_ERR_INVALID_ARG;
+  }
+  clear_pending_error();
+  return run_logdet(h, Z, s, noise_var, max_lanczos, tol, logdet, quad);
+}
+
 void sgp_lattice_free(sgp_lattice* h) { free_lattice(h); }
 
 sgp_status sgp_profile_blur(sgp_lattice* h, int enable) {

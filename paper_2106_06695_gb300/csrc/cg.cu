@@ -30,6 +30,10 @@ struct CgState {
   double* relres;
   int* active;
   int* iters;
+  // optional Lanczos record (plain CG): alpha_j, beta_j of column c at [j][k], j < hcap
+  double* ha;
+  double* hb;
+  int hcap;
 };
 
 // VEC consecutive elements of a row: fp32 (one float4 when VEC = 4) and fp64 (two double2).
@@ -134,6 +138,7 @@ __global__ void k_cg_alpha(int nblk, int k, CgState S) {
   if (S.active[c]) {
     if (pap > 0.0 && isfinite(pap)) {
       alpha = S.rho[c] / pap;
+      if (S.ha && S.iters[c] < S.hcap) S.ha[(int64_t)S.iters[c] * k + c] = alpha;
     } else {
       S.active[c] = 0;  // breakdown: the operator is not positive definite on p
     }
@@ -205,6 +210,7 @@ __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
   }
   S.beta[c] = rr / S.rho[c];
   S.rho[c] = rr;
+  if (S.hb && it - 1 < S.hcap) S.hb[(int64_t)(it - 1) * k + c] = S.beta[c];
 }
 
 // Preconditioned CG: convergence check on <r, r> (no beta yet).
@@ -324,7 +330,7 @@ __global__ void k_cg_store_x(const float* __restrict__ xh, const float* __restri
 
 sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
                   int max_iter, float* X, int* iters, double* rel_res, int precond_rank,
-                  uint64_t seed) {
+                  uint64_t seed, const LanczosRecord* rec) {
   const int64_t n = L->n;
   // CUDA graphs cannot be captured on the legacy default stream: use a private blocking
   // stream then (it is ordered with the legacy stream like any blocking stream).
@@ -391,13 +397,18 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   CG_CHECK(get((void**)&flags, 2 * (size_t)k * sizeof(int)), "alloc flags");
   S.active = flags;
   S.iters = flags + k;
+  if (rec) {
+    S.ha = rec->alpha;
+    S.hb = rec->beta;
+    S.hcap = rec->cap;
+  }
   sgp_status s = ensure_lattice_values(L, k, st);
   if (s != SGP_OK) return s;
 
   // the preconditioner (built before anything is captured); needs noise > 0
   bool use_pre = false;
   float* z = nullptr;
-  if (precond_rank > 0 && noise > 0.f) {
+  if (precond_rank > 0 && noise > 0.f && !rec) {
     s = cl.pre.build(L, precond_rank, seed, noise, blur, st);
     if (s != SGP_OK) return s;
     use_pre = cl.pre.ok;
@@ -485,6 +496,14 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   CG_CHECK(cudaStreamSynchronize(st), "sync CG");
   if (iters) std::copy(hit.begin(), hit.end(), iters);
   if (rel_res) std::copy(hrel.begin(), hrel.end(), rel_res);
+  if (rec) {  // ||b_c|| and the iteration counts stay on the device for the quadrature
+    CG_CHECK(cudaMemcpyAsync(rec->bnorm, S.bnorm, k * sizeof(double), cudaMemcpyDeviceToDevice,
+                             st),
+             "copy norms");
+    CG_CHECK(cudaMemcpyAsync(rec->iters, S.iters, k * sizeof(int), cudaMemcpyDeviceToDevice, st),
+             "copy iterations");
+    CG_CHECK(cudaStreamSynchronize(st), "sync CG");
+  }
   return SGP_OK;
 #undef CG_CHECK
 }

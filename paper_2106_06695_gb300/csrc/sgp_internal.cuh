@@ -195,10 +195,26 @@ sgp_status run_mvm_backward(Lattice* L, const float* X, const float* ls, const f
                             float* dX, float* dls);
 
 // ---- CG (cg.cu) ----
-// precond_rank > 0: preconditioned CG with a rank-precond_rank Nystrom preconditioner.
+// Device buffers that receive the CG coefficients of every column for the Lanczos
+// quadrature: alpha_j / beta_j of column c at [j][k] for j < cap, ||b_c|| and the
+// iteration count per column.
+struct LanczosRecord {
+  double* alpha;
+  double* beta;
+  int cap;
+  double* bnorm;
+  int* iters;
+};
+// precond_rank > 0: preconditioned CG with a rank-precond_rank Nystrom preconditioner
+// (not with a Lanczos record, which needs the plain CG's coefficients).
 sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
                   int max_iter, float* X, int* iters, double* rel_res, int precond_rank = 0,
-                  uint64_t seed = 0);
+                  uint64_t seed = 0, const LanczosRecord* rec = nullptr);
+// log det(outputscale K~ + noise I) by stochastic Lanczos quadrature over the probe
+// columns Z (device [n][s], caller's order); quad (host [s], may be null) receives each
+// probe's ||z||^2 e1^T log(T) e1 (lanczos.cu).
+sgp_status run_logdet(Lattice* L, const float* Z, int s, float noise, int max_lanczos,
+                      float tol, double* logdet, double* quad);
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -166,6 +166,18 @@ class Lattice:
             dV = dV.squeeze(1)
         return dV, dX, dls
 
+    def logdet(self, Z: torch.Tensor, noise: float, max_lanczos: int = 100, tol: float = 1e-6):
+        """Stochastic Lanczos quadrature estimate of log det(outputscale K~ + noise I) with
+        the probe columns Z ([n, s]); returns (estimate, per-probe quadratures)."""
+        Z2, _ = self._rhs(Z, "Z")
+        s = Z2.shape[1]
+        quad = np.zeros(s, np.float64)
+        out = ctypes.c_double()
+        check(self._lib.sgp_logdet(self._handle(), Z2.data_ptr(), s, float(noise),
+                                   int(max_lanczos), float(tol), ctypes.byref(out),
+                                   quad.ctypes.data))
+        return out.value, quad
+
     def cg(self, B: torch.Tensor, noise: float, tol: float = 1e-3, max_iter: int = 500,
            blur: str = "symmetric", out: torch.Tensor | None = None):
         """Batched CG on (outputscale K~ + noise I) X = B; returns (X, iters, rel_res)."""
