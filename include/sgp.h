@@ -22,6 +22,14 @@
  *     failure sgp_last_error() returns a thread-local message, the outputs are
  *     unspecified and an existing handle stays valid.
  *   - There is no CPU fallback: without a CUDA device every call fails with SGP_ERR_CUDA.
+ *   - Fault injection for tests of the error paths, read by sgp_lattice_build from the
+ *     environment variable SGP_FAULT: "oom" (fails as out of memory before allocating),
+ *     "cuda_err" (fails as a CUDA error before any device work), "hash_full" (builds with
+ *     a 1024-slot vertex table, so that the bounded probes of a larger lattice run out and
+ *     the build returns SGP_ERR_HASH_FULL), "nan_input" (the elevation kernel treats the
+ *     first point as NaN: SGP_ERR_NONFINITE).  None of them faults the device.
+ *   - Each stage pushes an NVTX range (sgp_build, sgp_mvm, sgp_cg, sgp_backward,
+ *     sgp_logdet, sgp_serve_step) for timeline profilers.
  */
 #ifndef SGP_H_
 #define SGP_H_
@@ -45,6 +53,7 @@ typedef enum {
   SGP_ERR_HASH_FULL = 4,   /* the vertex hash table ran out of probes               */
   SGP_ERR_NONFINITE = 5,   /* X holds NaN/Inf, or a lengthscale is <= 0 / not finite */
   SGP_ERR_CUDA = 6,        /* a CUDA runtime call failed (message has the CUDA error) */
+  SGP_ERR_TIMEOUT = 7,     /* a served request passed its deadline (sgp_serve.h)     */
 } sgp_status;
 
 /* Stationary kernel and its stencil (Sec. 4.1).  Stencil taps are kernel values at the

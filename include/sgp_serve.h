@@ -20,13 +20,15 @@
  * Continuous batching: requests are admitted in arrival order while the number of active
  * requests is below max_active and the device bytes they may hold stay within
  * hbm_budget (an upper bound per request from sgp_request_bytes_bound until its lattice
- * is built, then its actual allocation).  Every CG iteration of all active requests runs
- * as one sequence of kernels over a device table of the active requests (fixed grids,
- * per-request and per-column convergence masks), replayed from a CUDA graph; a request
- * leaves the batch as soon as its columns have stopped, and new requests join at the
- * next step.  Each request's arithmetic is partitioned by its own sizes only, so its
- * results are bitwise the same alone and in any mix.  max_active = 1 gives the plain
- * one-request-at-a-time path with the same kernels.
+ * is built, then its actual allocation).  Active requests are grouped into lanes of
+ * similar dimension and per-iteration work; every CG iteration of all requests of a lane
+ * runs as one sequence of kernels over a device table of those requests (fixed grids,
+ * per-request and per-column convergence masks), replayed from a CUDA graph, and lanes
+ * run concurrently on their own streams.  A request leaves its lane as soon as its
+ * columns have stopped, and new requests join at the lane's next round.  Each request's
+ * arithmetic is partitioned by its own sizes only, so its results are bitwise the same
+ * alone and in any mix.  max_active = 1 gives the plain one-request-at-a-time path with
+ * the same kernels.
  *
  * Threading: a server is used by one host thread at a time.  Host buffers of a request
  * (X, y, Xs, lengthscales, mean, var) must stay valid until the request has completed
@@ -74,6 +76,9 @@ typedef struct {
   float* var;                /* host [ns] output (may be NULL when probes = 0)            */
   double arrival_us;         /* arrival time on the server clock (sgp_server_clock_us), or
                                 < 0 for "now"; latency is measured from it                */
+  double timeout_us;         /* > 0: deadline arrival_us + timeout_us; a request still
+                                queued or iterating at a step past it completes with
+                                SGP_ERR_TIMEOUT (mean/var not written); <= 0: none        */
 } sgp_request;
 
 typedef struct {
@@ -105,12 +110,14 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out);
  * whole budget (it could never be admitted). */
 sgp_status sgp_server_submit(sgp_server* srv, const sgp_request* req, long long* id);
 
-/* One scheduling round: enqueue check_every CG iterations of the active batch, admit and
- * set up queued requests while those run (lattice build, right-hand sides), then read
- * the convergence flags, finish the requests that stopped (predictive slice, copy of
- * mean/var to the host) and release their memory.  *completed (may be NULL) receives the
- * number of requests finished by this call.  Returns at once when nothing is queued or
- * active. */
+/* One scheduling round: for every lane whose round of check_every CG iterations has
+ * ended, finish the requests that stopped (predictive slice, copy of mean/var to the
+ * host, release of their memory) and cancel those past their deadline; complete queued
+ * requests past their deadline with SGP_ERR_TIMEOUT; admit and set up queued requests
+ * (lattice build, right-hand sides) on a set-up stream while the other lanes run;
+ * relaunch idle lanes; then, if nothing finished, wait up to 2 ms for a lane to end its
+ * round.  *completed (may be NULL) receives the number of requests finished by this
+ * call.  Returns at once when nothing is queued or active. */
 sgp_status sgp_server_step(sgp_server* srv, int* completed);
 
 /* Statistics of request `id` (valid at any time; done = 0 while it is queued/active). */

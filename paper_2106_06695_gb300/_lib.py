@@ -18,7 +18,8 @@ HEADERS = [os.path.join(INCLUDE, "sgp.h"), os.path.join(INCLUDE, "sgp_serve.h")]
 
 SGP_OK = 0
 STATUS_NAMES = {0: "SGP_OK", 1: "SGP_ERR_INVALID_ARG", 2: "SGP_ERR_OOM", 3: "SGP_ERR_RANGE",
-                4: "SGP_ERR_HASH_FULL", 5: "SGP_ERR_NONFINITE", 6: "SGP_ERR_CUDA"}
+                4: "SGP_ERR_HASH_FULL", 5: "SGP_ERR_NONFINITE", 6: "SGP_ERR_CUDA",
+                7: "SGP_ERR_TIMEOUT"}
 
 KERNELS = {"rbf_binomial": 0, "rbf_coverage": 1, "matern32_coverage": 2}
 BLURS = {"sequential": 0, "transpose": 1, "symmetric": 2}
@@ -48,7 +49,7 @@ class sgp_request(ctypes.Structure):
                 ("lengthscales", ctypes.c_void_p), ("outputscale", ctypes.c_float),
                 ("noise", ctypes.c_float), ("seed", ctypes.c_ulonglong),
                 ("mean", ctypes.c_void_p), ("var", ctypes.c_void_p),
-                ("arrival_us", ctypes.c_double)]
+                ("arrival_us", ctypes.c_double), ("timeout_us", ctypes.c_double)]
 
 
 class sgp_request_stats(ctypes.Structure):

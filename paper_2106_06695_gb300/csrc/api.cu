@@ -7,9 +7,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sgp_internal.cuh"
 
 namespace sgp {
+
+int injected_fault() {
+  const char* f = getenv("SGP_FAULT");
+  if (!f || !f[0]) return FAULT_NONE;
+  if (!strcmp(f, "oom")) return FAULT_OOM;
+  if (!strcmp(f, "cuda_err")) return FAULT_CUDA;
+  if (!strcmp(f, "hash_full")) return FAULT_HASH_FULL;
+  if (!strcmp(f, "nan_input")) return FAULT_NAN_INPUT;
+  return FAULT_NONE;
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 namespace {
 thread_local std::string g_last_error;
@@ -129,7 +144,18 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
     return SGP_ERR_CUDA;
   }
   clear_pending_error();
+  NvtxRange nvtx("sgp_build");
+  const int fault = injected_fault();
+  if (fault == FAULT_OOM) {
+    set_error("sgp_lattice_build: out of device memory (injected by SGP_FAULT=oom)");
+    return SGP_ERR_OOM;
+  }
+  if (fault == FAULT_CUDA) {
+    set_error("sgp_lattice_build: CUDA error (injected by SGP_FAULT=cuda_err)");
+    return SGP_ERR_CUDA;
+  }
   Lattice* L = new Lattice();
+  L->fault = fault;
   L->n = n;
   L->d = d;
   L->D = d + 1;
@@ -240,6 +266,7 @@ static sgp_status check_mvm_args(const sgp_lattice* h, const float* V, int k, in
 sgp_status sgp_mvm(sgp_lattice* h, const float* V, int k, float* out) {
   if (sgp_status s = check_mvm_args(h, V, k, SGP_BLUR_SEQUENTIAL, out, "sgp_mvm")) return s;
   clear_pending_error();
+  NvtxRange nvtx("sgp_mvm");
   return run_mvm(h, V, k, SGP_BLUR_SEQUENTIAL, h->outputscale, 0.f, out);
 }
 
@@ -247,6 +274,7 @@ sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alp
                       float* out) {
   if (sgp_status s = check_mvm_args(h, V, k, blur, out, "sgp_mvm_ex")) return s;
   clear_pending_error();
+  NvtxRange nvtx("sgp_mvm");
   return run_mvm(h, V, k, blur, alpha, beta, out);
 }
 
@@ -258,6 +286,7 @@ sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, floa
     return SGP_ERR_INVALID_ARG;
   }
   clear_pending_error();
+  NvtxRange nvtx("sgp_cg");
   return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res, h->precond_rank,
                 h->precond_seed);
 }
@@ -285,6 +314,7 @@ sgp_status sgp_mvm_backward(sgp_lattice* h, const float* X, const float* lengths
   }
   if (!dV && !want_x) return SGP_OK;
   clear_pending_error();
+  NvtxRange nvtx("sgp_backward");
   return run_mvm_backward(h, X, lengthscales, V, G, k, blur, alpha, grad, dV, dX, dls);
 }
 
@@ -298,6 +328,7 @@ sgp_status sgp_logdet(sgp_lattice* h, const float* Z, int s, float noise_var, in
     return SGP_ERR_INVALID_ARG;
   }
   clear_pending_error();
+  NvtxRange nvtx("sgp_logdet");
   return run_logdet(h, Z, s, noise_var, max_lanczos, tol, logdet, quad);
 }
 

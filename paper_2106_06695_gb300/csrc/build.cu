@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128) k_elevate(const float* __restrict__ X,
                                                  uint8_t* __restrict__ rank_out,
                                                  float* __restrict__ w_out,
                                                  int* __restrict__ qmin, int* __restrict__ qmax,
-                                                 unsigned* __restrict__ err) {
+                                                 unsigned* __restrict__ err, int inject_nan) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int D = d + 1;
@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(128) k_elevate(const float* __restrict__ X,
     sm = __dadd_rn(sm, cf);
   }
   y[0] = sm;
+  if (inject_nan && i == 0) bad = true;  // SGP_FAULT=nan_input
   if (bad) {
     atomicOr(err, ERRBIT_NONFINITE);
     for (int c = 0; c < D; ++c) y[c] = 0.0;
@@ -477,7 +478,7 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   {
     const int B = 128;
     SGP_DISPATCH_D(D, k_elevate, (unsigned)ceil_div(n, B), B, st, X, ls, f, n, d, rem0, rank,
-                   w_user, qmm, qmm + D, L->err);
+                   w_user, qmm, qmm + D, L->err, L->fault == FAULT_NAN_INPUT ? 1 : 0);
     SGP_CHECK(cudaGetLastError(), "k_elevate");
   }
   unsigned herr = 0;
@@ -528,7 +529,8 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
 
   // 3. hash insert
   uint64_t cap = 1024;
-  while (cap < (uint64_t)(2 * nD)) cap <<= 1;
+  if (L->fault != FAULT_HASH_FULL)  // SGP_FAULT=hash_full keeps the 1024-slot table
+    while (cap < (uint64_t)(2 * nD)) cap <<= 1;
   const uint64_t mask = cap - 1;
   unsigned long long* table = nullptr;
   int32_t* entry_slot = nullptr;

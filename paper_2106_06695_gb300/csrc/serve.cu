@@ -654,6 +654,10 @@ double now_us(const sgp_server* S) { return 1e6 * seconds_since(S->t0); }
     if (e_ != cudaSuccess) return cuda_status(e_, what);     \
   } while (0)
 
+bool expired(const sgp_server* S, const Request* R) {
+  return R->in.timeout_us > 0.0 && now_us(S) > R->st.arrival_us + R->in.timeout_us;
+}
+
 void fill_slot(const sgp_server* S, const Request* R, SlotDev& s) {
   const Lattice* L = R->L;
   s.n = L->n;
@@ -947,6 +951,17 @@ void destroy_lane(Lane* ln) {
 }
 
 sgp_status admit(sgp_server* S) {
+  for (auto it = S->queue.begin(); it != S->queue.end();) {  // deadlines passed in the queue
+    Request* R = *it;
+    if (!expired(S, R)) {
+      ++it;
+      continue;
+    }
+    R->st.status = SGP_ERR_TIMEOUT;
+    R->st.done_us = now_us(S);
+    R->st.done = 1;
+    it = S->queue.erase(it);
+  }
   while (!S->queue.empty() && S->n_active < S->o.max_active) {
     Request* R = S->queue.front();
     if (S->in_use + R->bound > S->o.hbm_budget) break;  // strict arrival order
@@ -984,6 +999,16 @@ sgp_status harvest(sgp_server* S, Lane* ln, int* done) {
     Request* R = ln->active[q];
     if (q < ln->ntab && ln->hflags[2 * q] == 0) {
       if (sgp_status s = finish(S, R, ln->st)) return s;
+      S->n_active -= 1;
+      ++*done;
+    } else if (expired(S, R)) {  // still iterating past its deadline: cancel
+      (void)cudaStreamSynchronize(ln->st);
+      R->st.status = SGP_ERR_TIMEOUT;
+      R->st.iters = q < ln->ntab ? ln->hflags[2 * q + 1] : 0;
+      R->st.bytes = R->held;
+      R->st.done_us = now_us(S);
+      R->st.done = 1;
+      release(S, R, ln->st);
       S->n_active -= 1;
       ++*done;
     } else {
@@ -1197,6 +1222,7 @@ sgp_status sgp_server_step(sgp_server* S, int* completed) {
     return SGP_ERR_INVALID_ARG;
   }
   clear_pending_error();
+  NvtxRange nvtx("sgp_serve_step");
   return server_step(S, completed);
 }
 

@@ -18,6 +18,16 @@ enum : unsigned {
   ERRBIT_HASH_FULL = 4u,
 };
 
+// Faults injected on the host through SGP_FAULT (tests of the error paths).
+enum { FAULT_NONE = 0, FAULT_OOM, FAULT_CUDA, FAULT_HASH_FULL, FAULT_NAN_INPUT };
+int injected_fault();
+
+// NVTX range for the lifetime of a scope (timeline profilers; no-op without one).
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+};
+
 constexpr int kMaxOrder = 4;  // stencil order r
 constexpr int kMaxD = 128;    // d + 1
 constexpr int kMaxK = 256;    // right-hand sides per call
@@ -45,6 +55,7 @@ struct sgp_lattice {
   int check_every = 8;
   int precond_rank = 0;
   uint64_t precond_seed = 0;
+  int fault = 0;  // sgp::FAULT_* injected by SGP_FAULT for this build
   cudaStream_t stream = nullptr;
 
   // Points are processed in a locality order p = 0..n-1; perm[p] is the caller's index.

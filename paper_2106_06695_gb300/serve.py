@@ -76,7 +76,8 @@ class Server:
 
     # -- requests ---------------------------------------------------------------------
     def submit(self, X, y, Xs, lengthscales, outputscale: float = 1.0, noise: float = 0.01,
-               seed: int = 0, arrival_us: float | None = None) -> int:
+               seed: int = 0, arrival_us: float | None = None,
+               timeout_s: float | None = None) -> int:
         X = _host_f32(X, "X", 2)
         Xs = _host_f32(Xs, "Xs", 2)
         y = _host_f32(y, "y", 1)
@@ -91,6 +92,7 @@ class Server:
         r.outputscale, r.noise, r.seed = float(outputscale), float(noise), int(seed)
         r.mean, r.var = mean.ctypes.data, var.ctypes.data
         r.arrival_us = -1.0 if arrival_us is None else float(arrival_us)
+        r.timeout_us = 0.0 if timeout_s is None else 1e6 * float(timeout_s)
         rid = ctypes.c_longlong()
         check(self._lib.sgp_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
         self._keep[rid.value] = (X, y, Xs, ls, mean, var)
