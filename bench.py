@@ -490,12 +490,13 @@ def run_serving(count: int):
             res = run_stream(srv, reqs)
             results[name] = [tuple(a.copy() for a in srv.result(i)) for i in res.ids]
             rel = [srv.stats(i)["rel_res"] for i in res.ids]
+            setup_s = sum(srv.stats(i)["setup_us"] for i in res.ids) / 1e6
         out[name] = {"solves_per_s": res.solves_per_s, "p50_s": res.percentile(50),
                      "p99_s": res.percentile(99), "makespan_s": res.makespan_s,
                      "max_active": slots, "peak_active": res.peak_active,
                      "cg_iters_mean": float(np.mean(res.iters)),
                      "cg_iters_max": int(np.max(res.iters)),
-                     "rel_res_max": float(np.max(rel))}
+                     "rel_res_max": float(np.max(rel)), "setup_s_total": setup_s}
         print("serving %s: %.2f solves/s p50 %.3f s p99 %.3f s" % (
             name, res.solves_per_s, res.percentile(50), res.percentile(99)),
             file=sys.stderr, flush=True)

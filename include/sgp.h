@@ -134,6 +134,15 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
  * bytes the handle holds.  Either output may be NULL. */
 sgp_status sgp_lattice_info(const sgp_lattice* h, int64_t* m, size_t* device_bytes);
 
+/* Blur work of the handle: *pairs (may be NULL) receives the number of (vertex,
+ * direction) pairs whose vertex has a neighbour along that direction when the lattice is
+ * sparse, else -1; *sparse (may be NULL) is 1 when those pairs are at most 30 % of the
+ * (d+1) m pairs, and the blur then updates
+ * only those vertices in each pass (the others keep their rows; the centre tap's factor
+ * is applied lazily), 0 when every pass sweeps all m vertices.  The operator is the same
+ * either way. */
+sgp_status sgp_lattice_blur_lists(const sgp_lattice* h, int* sparse, int64_t* pairs);
+
 /* Stencil actually used (Sec. 4.1): the spacing s, the paper's taps c[0..r] and the
  * symmetric-blur taps g[0..r] (host arrays of order_r + 1 doubles).  Any may be NULL. */
 sgp_status sgp_lattice_stencil(const sgp_lattice* h, int* order_r, double* spacing_s,

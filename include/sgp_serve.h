@@ -89,6 +89,8 @@ typedef struct {
   double arrival_us, admit_us, done_us; /* server clock                                   */
   long long m;               /* lattice vertices                                          */
   unsigned long long bytes;  /* device bytes the request held while active                */
+  double setup_us;           /* host time of its set-up (upload, lattice build, right-hand
+                                sides), during which this server launched nothing else    */
 } sgp_request_stats;
 
 /* Fill *opts with the defaults listed above (hbm_budget from the current device, or 0

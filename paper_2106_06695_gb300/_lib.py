@@ -56,7 +56,8 @@ class sgp_request_stats(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("arrival_us", ctypes.c_double),
                 ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
-                ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong)]
+                ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong),
+                ("setup_us", ctypes.c_double)]
 
 
 class SGPError(RuntimeError):
@@ -93,6 +94,7 @@ def load():
         "sgp_lattice_build": (I, [P, P, I64, I, ctypes.POINTER(sgp_opts), ctypes.POINTER(P)]),
         "sgp_lattice_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_size_t)]),
         "sgp_lattice_stencil": (I, [P, ctypes.POINTER(I), ctypes.POINTER(Dbl), P, P]),
+        "sgp_lattice_blur_lists": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I64)]),
         "sgp_lattice_export": (I, [P, P, P, P]),
         "sgp_set_stream": (I, [P, P]),
         "sgp_mvm": (I, [P, P, I, P]),

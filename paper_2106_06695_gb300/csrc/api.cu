@@ -39,6 +39,7 @@ void free_lattice(Lattice* L) {
   if (!L) return;
   cudaStream_t st = L->stream;
   void* arrays[] = {L->perm, L->idx, L->w, L->rank, L->row_ptr, L->items, L->nbr, L->keys, L->err,
+                    L->act, L->epoch, L->act_tmp, L->g0pow,
                     L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial,
                     L->vperm};
   for (void* p : arrays)
@@ -195,6 +196,13 @@ sgp_status sgp_lattice_info(const sgp_lattice* h, int64_t* m, size_t* device_byt
   if (sgp_status s = check_handle(h)) return s;
   if (m) *m = h->m;
   if (device_bytes) *device_bytes = h->bytes;
+  return SGP_OK;
+}
+
+sgp_status sgp_lattice_blur_lists(const sgp_lattice* h, int* sparse, int64_t* pairs) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (sparse) *sparse = h->sparse ? 1 : 0;
+  if (pairs) *pairs = h->sparse ? h->act_off.back() : -1;
   return SGP_OK;
 }
 

@@ -38,11 +38,27 @@ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
   return h;
 }
 
-template <int MAXD>
-__device__ __forceinline__ uint64_t hash_key(const int* key, int D) {
-  uint64_t h = 0x243f6a8885a308d3ull;
-  for (int c = 0; c < D; ++c) h = (h ^ (uint64_t)(uint16_t)key[c]) * 0x100000001b3ull;
-  return mix64(h);
+uint64_t host_mix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+uint64_t host_coord_mult(int c) { return host_mix64(0x9e3779b97f4a7c15ull * (uint64_t)(c + 1)) | 1ull; }
+
+// Vertex hash, linear in the integer key: lin(key) = sum_c A_c key_c (mod 2^64) with odd
+// per-coordinate multipliers A_c, then mixed.  A lattice step u_j = (d+1) e_j - 1 moves
+// lin by (d+1) A_j - sum_c A_c, so a neighbour's hash costs O(1) from the vertex's.
+__device__ __forceinline__ uint64_t coord_mult(int c) {
+  return mix64(0x9e3779b97f4a7c15ull * (uint64_t)(c + 1)) | 1ull;
+}
+
+__device__ __forceinline__ uint64_t lin_hash(const int* key, int D) {
+  uint64_t h = 0;
+  for (int c = 0; c < D; ++c) h += coord_mult(c) * (uint64_t)(int64_t)key[c];
+  return h;
 }
 
 // Coordinate c of vertex k of the simplex (rem0, rank): rem0 + k, minus d+1 where the
@@ -217,7 +233,7 @@ __global__ void __launch_bounds__(256) k_insert(const int32_t* __restrict__ perm
   const int k = (int)(e % D);
   int key[MAXD];
   for (int c = 0; c < D; ++c) key[c] = vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
-  const uint64_t h = hash_key<MAXD>(key, D);
+  const uint64_t h = mix64(lin_hash(key, D));
   const uint32_t tag = (uint32_t)(h >> 33);
   const unsigned long long mine = ((unsigned long long)tag << 32) | (uint32_t)e;
   uint64_t slot = h & mask;
@@ -256,7 +272,8 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
                              const unsigned long long* __restrict__ table,
                              const int32_t* __restrict__ perm, const int16_t* __restrict__ rem0,
                              const uint8_t* __restrict__ rank, int64_t nD, int d,
-                             int32_t* __restrict__ slot_id, int16_t* __restrict__ keys) {
+                             int32_t* __restrict__ slot_id, int16_t* __restrict__ keys,
+                             uint64_t* __restrict__ vhash, int2* __restrict__ vrange) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nD) return;
   const int32_t s = entry_slot[e];
@@ -266,8 +283,17 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
   slot_id[s] = (int32_t)id;
   const int64_t i = perm[e / D];
   const int k = (int)(e % D);
-  for (int c = 0; c < D; ++c)
-    keys[(int64_t)id * D + c] = (int16_t)vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
+  uint64_t h = 0;
+  int lo = 1 << 30, hi = -(1 << 30);
+  for (int c = 0; c < D; ++c) {
+    const int x = vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
+    keys[(int64_t)id * D + c] = (int16_t)x;
+    h += coord_mult(c) * (uint64_t)(int64_t)x;
+    lo = min(lo, x);
+    hi = max(hi, x);
+  }
+  vhash[id] = h;
+  vrange[id] = make_int2(lo, hi);
 }
 
 __global__ void k_entry_ids(const int32_t* __restrict__ entry_slot,
@@ -288,9 +314,29 @@ __global__ void k_entry_ids(const int32_t* __restrict__ entry_slot,
 // ---------------------------------------------------------------------------------
 // 5. Neighbour table.
 // ---------------------------------------------------------------------------------
-template <int MAXD>
+// Does the vertex of entry `e` equal keys[v] + step u_j?  (the owner entry's key is
+// recomputed from its point's rem0 and rank)
+__device__ __forceinline__ bool entry_is_neighbour(uint32_t e, const int16_t* __restrict__ kv,
+                                                   int j, int step, int d,
+                                                   const int32_t* __restrict__ perm,
+                                                   const int16_t* __restrict__ rem0,
+                                                   const uint8_t* __restrict__ rank) {
+  const int D = d + 1;
+  const int64_t i = perm[e / D];
+  const int k = (int)(e % D);
+  for (int c = 0; c < D; ++c) {
+    const int want = (int)kv[c] + step * ((c == j ? D : 0) - 1);
+    if (vertex_coord(rem0 + i * D, rank + i * D, d, k, c) != want) return false;
+  }
+  return true;
+}
+
+// One thread per (vertex, direction j): ids of v -+ t u_j, t = 1..r.  The neighbour's hash
+// comes from the vertex's linear hash in O(1) (sum_A = sum_c A_c); the key itself is read
+// only to confirm a tag match.  A neighbour outside the int16 key range does not exist.
 __global__ void __launch_bounds__(256) k_neighbours(
-    const int16_t* __restrict__ keys, int64_t m, int d, int r,
+    const int16_t* __restrict__ keys, const uint64_t* __restrict__ vhash,
+    const int2* __restrict__ vrange, int64_t m, int d, int r, uint64_t sum_A,
     const unsigned long long* __restrict__ table, uint64_t mask,
     const int32_t* __restrict__ slot_id, const int32_t* __restrict__ perm,
     const int16_t* __restrict__ rem0, const uint8_t* __restrict__ rank,
@@ -300,25 +346,32 @@ __global__ void __launch_bounds__(256) k_neighbours(
   if (t_id >= m * D) return;
   const int64_t v = t_id % m;
   const int j = (int)(t_id / m);
-  int key[MAXD];
+  const uint64_t hv = vhash[v];
+  const int2 rg = vrange[v];
+  const uint64_t dj = (uint64_t)D * coord_mult(j) - sum_A;  // lin(u_j)
+  const int16_t* kv = keys + v * D;
   for (int t = 1; t <= r; ++t) {
     for (int sg = 0; sg < 2; ++sg) {
       const int step = sg ? t : -t;
-      bool in_range = true;
-      for (int c = 0; c < D; ++c) {
-        key[c] = (int)keys[v * D + c] + step * ((c == j ? D : 0) - 1);
-        in_range = in_range && key[c] >= -32768 && key[c] <= 32767;
+      // every coordinate moves by -step except j, which moves by d step
+      bool in_range = rg.x - t * d >= -32768 && rg.y + t * d <= 32767;
+      if (!in_range) {
+        in_range = true;
+        for (int c = 0; c < D; ++c) {
+          const int x = (int)kv[c] + step * ((c == j ? D : 0) - 1);
+          in_range = in_range && x >= -32768 && x <= 32767;
+        }
       }
       int32_t found = -1;
       if (in_range) {
-        const uint64_t h = hash_key<MAXD>(key, D);
+        const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * dj);
         const uint32_t tag = (uint32_t)(h >> 33);
         uint64_t slot = h & mask;
         for (uint64_t probe = 0; probe <= mask; ++probe) {
           const unsigned long long cur = table[slot];
           if (cur == kEmpty) break;
           if ((uint32_t)(cur >> 32) == tag &&
-              entry_has_key<MAXD>((uint32_t)cur, key, d, perm, rem0, rank)) {
+              entry_is_neighbour((uint32_t)cur, kv, j, step, d, perm, rem0, rank)) {
             found = slot_id[slot];
             break;
           }
@@ -328,6 +381,35 @@ __global__ void __launch_bounds__(256) k_neighbours(
       nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = found;
     }
   }
+}
+
+// Vertices with at least one neighbour along direction j (the sparse blur's lists).
+__device__ __forceinline__ bool has_neighbour(const int32_t* __restrict__ nbr_j, int64_t m,
+                                              int r, int64_t v) {
+  for (int q = 0; q < 2 * r; ++q)
+    if (nbr_j[(int64_t)q * m + v] >= 0) return true;
+  return false;
+}
+
+__global__ void k_active_count(const int32_t* __restrict__ nbr, int64_t m, int D, int r,
+                               unsigned long long* __restrict__ counts) {
+  const int64_t t_id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t_id >= m * D) return;
+  const int64_t v = t_id % m;
+  const int j = (int)(t_id / m);
+  if (has_neighbour(nbr + (int64_t)j * r * 2 * m, m, r, v)) atomicAdd(&counts[j], 1ull);
+}
+
+__global__ void k_active_flags(const int32_t* __restrict__ nbr_j, int64_t m, int r,
+                               uint32_t* __restrict__ flags) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < m) flags[v] = has_neighbour(nbr_j, m, r, v) ? 1u : 0u;
+}
+
+__global__ void k_active_compact(const int32_t* __restrict__ nbr_j, int64_t m, int r,
+                                 const uint32_t* __restrict__ pos, int32_t* __restrict__ act) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < m && has_neighbour(nbr_j, m, r, v)) act[pos[v]] = (int32_t)v;
 }
 
 // ---------------------------------------------------------------------------------
@@ -564,8 +646,13 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   SGP_CHECK(tmp.get(&slot_id, cap), "alloc slot ids");
   SGP_CHECK(dalloc(&L->keys, m * D, st), "alloc keys");
   L->bytes += m * D * sizeof(int16_t);
+  uint64_t* vhash = nullptr;
+  int2* vrange = nullptr;
+  SGP_CHECK(tmp.get(&vhash, m), "alloc vertex hashes");
+  SGP_CHECK(tmp.get(&vrange, m), "alloc vertex ranges");
   k_assign_ids<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(flags, entry_slot, table, L->perm,
-                                                           rem0, rank, nD, d, slot_id, L->keys);
+                                                           rem0, rank, nD, d, slot_id, L->keys,
+                                                           vhash, vrange);
   note_launches(1);
   SGP_CHECK(dalloc(&L->idx, nD, st), "alloc idx");
   SGP_CHECK(dalloc(&L->w, nD, st), "alloc w");
@@ -579,8 +666,15 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   // 5. neighbour table
   SGP_CHECK(dalloc(&L->nbr, (size_t)D * r * 2 * m, st), "alloc nbr");
   L->bytes += (size_t)D * r * 2 * m * sizeof(int32_t);
-  SGP_DISPATCH_D(D, k_neighbours, (unsigned)ceil_div(m * D, 256), 256, st, L->keys, m, d, r,
-                 table, mask, slot_id, L->perm, rem0, rank, L->nbr);
+  {
+    // sum_c A_c over the D coordinates, as the kernels compute A_c
+    uint64_t sum_A = 0;
+    for (int c = 0; c < D; ++c) sum_A += host_coord_mult(c);
+    k_neighbours<<<(unsigned)ceil_div(m * D, 256), 256, 0, st>>>(
+        L->keys, vhash, vrange, m, d, r, sum_A, table, mask, slot_id, L->perm, rem0, rank,
+        L->nbr);
+    note_launches(1);
+  }
   SGP_CHECK(cudaGetLastError(), "k_neighbours");
 
   // 6. splat lists: (vertex id, entry) sorted by id, stable in entry order
@@ -640,6 +734,53 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
                                                           L->seg, L->med_rows, L->huge_rows);
     note_launches(1);
     SGP_CHECK(cudaGetLastError(), "splat segments");
+  }
+  // 8. direction lists of a sparse lattice
+  {
+    unsigned long long* counts = nullptr;
+    SGP_CHECK(tmp.get(&counts, D), "alloc counts");
+    SGP_CHECK(cudaMemsetAsync(counts, 0, D * sizeof(unsigned long long), st), "clear counts");
+    k_active_count<<<(unsigned)ceil_div(m * D, 256), 256, 0, st>>>(L->nbr, m, D, r, counts);
+    note_launches(1);
+    std::vector<unsigned long long> hc(D);
+    SGP_CHECK(cudaMemcpyAsync(hc.data(), counts, D * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st),
+              "read counts");
+    SGP_CHECK(cudaStreamSynchronize(st), "sync counts");
+    int64_t total = 0, largest = 0;
+    for (int j = 0; j < D; ++j) {
+      total += (int64_t)hc[j];
+      largest = std::max<int64_t>(largest, (int64_t)hc[j]);
+    }
+    if (m > 0 && (double)total <= kSparseFrac * (double)D * (double)m) {
+      L->sparse = true;
+      L->act_max = largest;
+      L->act_off.assign(D + 1, 0);
+      for (int j = 0; j < D; ++j) L->act_off[j + 1] = L->act_off[j] + (int64_t)hc[j];
+      SGP_CHECK(dalloc(&L->act, std::max<int64_t>(total, 1), st), "alloc direction lists");
+      SGP_CHECK(dalloc(&L->epoch, m, st), "alloc epochs");
+      L->bytes += (size_t)total * sizeof(int32_t) + (size_t)m * sizeof(int32_t);
+      uint32_t *pos, *ptmp;
+      SGP_CHECK(tmp.get(&pos, m), "alloc positions");
+      SGP_CHECK(tmp.get(&ptmp, scan_temp_elems(m)), "alloc scan");
+      for (int j = 0; j < D; ++j) {
+        if (hc[j] == 0) continue;
+        const int32_t* nbr_j = L->nbr + (size_t)j * r * 2 * m;
+        const unsigned g = (unsigned)ceil_div(m, 256);
+        k_active_flags<<<g, 256, 0, st>>>(nbr_j, m, r, pos);
+        exclusive_scan_u32(pos, m, nullptr, ptmp, st);
+        k_active_compact<<<g, 256, 0, st>>>(nbr_j, m, r, pos, L->act + L->act_off[j]);
+        note_launches(2);
+      }
+      // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
+      std::vector<float> pw(2 * D + 1);
+      for (int q = 0; q <= 2 * D; ++q) pw[q] = (float)std::pow(L->half[0], (double)q);
+      SGP_CHECK(dalloc(&L->g0pow, 2 * D + 1, st), "alloc tap powers");
+      SGP_CHECK(cudaMemcpyAsync(L->g0pow, pw.data(), pw.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, st),
+                "copy tap powers");
+      SGP_CHECK(cudaGetLastError(), "direction lists");
+    }
   }
   SGP_CHECK(cudaStreamSynchronize(st), "sync build");
   return SGP_OK;

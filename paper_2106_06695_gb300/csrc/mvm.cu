@@ -176,6 +176,76 @@ __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k,
   }
 }
 
+// ---- sparse blur (lattices whose direction lists are short) ------------------------------
+// Stored rows carry a lazy factor: the value of vertex x before pass t is
+// g0^(t - epoch[x]) stored[x] (g0 = the pass's centre tap), since a vertex without a
+// neighbour along a pass's direction is only scaled by the centre tap.  Pass t (direction
+// j) computes the new rows of the vertices on list j into tmp; a second kernel stores them
+// and sets their epoch to t + 1.  After the last pass, k_sparse_finish applies the
+// remaining factors.
+template <int VEC, class S>
+__global__ void __launch_bounds__(kThreads) k_sparse_blur(int64_t count, int G, int k, int r,
+                                                          Taps tp, int t,
+                                                          const int32_t* __restrict__ act,
+                                                          const int32_t* __restrict__ nbr_j,
+                                                          int64_t m,
+                                                          const int32_t* __restrict__ epoch,
+                                                          const float* __restrict__ pw,
+                                                          const S* __restrict__ stored,
+                                                          S* __restrict__ tmp) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t a = gid / G;
+  if (a >= count) return;
+  const int col = (int)(gid - a * G) * VEC;
+  const int64_t v = act[a];
+  auto value = [&](int64_t x) {
+    const float f = pw ? pw[t - epoch[x]] : 1.f;
+    return Vt::scale(f, Vt::lds(stored + x * k + col));
+  };
+  typename Vt::T acc = Vt::scale(tp.t[0], value(v));
+  for (int q = 1; q <= r; ++q) {
+    const int ua = nbr_j[(int64_t)(2 * (q - 1)) * m + v];
+    const int uc = nbr_j[(int64_t)(2 * (q - 1) + 1) * m + v];
+    typename Vt::T sum = Vt::zero();
+    if (ua >= 0) sum = value(ua);
+    if (uc >= 0) sum = Vt::add(sum, value(uc));
+    acc = Vt::fma(tp.t[q], sum, acc);
+  }
+  Vt::sts(tmp + a * k + col, acc);
+}
+
+template <int VEC, class S>
+__global__ void __launch_bounds__(kThreads) k_sparse_store(int64_t count, int G, int k, int t,
+                                                           const int32_t* __restrict__ act,
+                                                           const S* __restrict__ tmp,
+                                                           S* __restrict__ stored,
+                                                           int32_t* __restrict__ epoch) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t a = gid / G;
+  if (a >= count) return;
+  const int col = (int)(gid - a * G) * VEC;
+  const int64_t v = act[a];
+  Vt::sts(stored + v * k + col, Vt::lds(tmp + a * k + col));
+  if (col == 0) epoch[v] = t + 1;
+}
+
+template <int VEC, class S>
+__global__ void __launch_bounds__(kThreads) k_sparse_finish(int64_t m, int G, int k, int P,
+                                                            const int32_t* __restrict__ epoch,
+                                                            const float* __restrict__ pw,
+                                                            S* __restrict__ stored) {
+  using Vt = Vec<VEC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = gid / G;
+  if (v >= m) return;
+  const int e = epoch[v];
+  if (e == P) return;
+  const int col = (int)(gid - v * G) * VEC;
+  Vt::sts(stored + v * k + col, Vt::scale(pw[P - e], Vt::lds(stored + v * k + col)));
+}
+
 // ---- slice ---------------------------------------------------------------------------
 // PERM: V and out rows are in the caller's order (row perm[p]); else in locality order.
 template <int VEC, bool BETA, bool PERM, class S>
@@ -373,17 +443,77 @@ void launch_permute(const Lattice* L, const float* V, int k, float* Vp, cudaStre
   note_launches(1);
 }
 
-// The whole operator with explicit buffers.  internal: V and out in locality order;
-// else V and out are in the caller's order and V is first gathered into `vperm`.
+// The blur passes of `blur` on the splatted values in lat0 (lat1: ping-pong buffer);
+// returns the buffer that holds the result.  Sparse lattices use the direction lists
+// (lat1 unused) unless `dense` is set.
 template <class S>
-int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
-              float* out, S* lat0, S* lat1, float* partial, float* vperm, cudaStream_t st,
-              cudaEvent_t* ev, bool internal, double* dot_partial = nullptr) {
+S* blur_passes_t(const Lattice* L, int blur, S* lat0, S* lat1, int k, cudaStream_t st,
+                 int* passes_out, bool dense) {
   Taps c{}, g{};
   for (int t = 0; t <= L->r; ++t) {
     c.t[t] = (float)L->coef[t];
     g.t[t] = (float)L->half[t];
   }
+  const int D = L->D;
+  const int P = blur == SGP_BLUR_SYMMETRIC ? 2 * D : D;
+  auto dir = [&](int t) {
+    if (blur == SGP_BLUR_SEQUENTIAL) return t;
+    if (blur == SGP_BLUR_TRANSPOSE) return D - 1 - t;
+    return t < D ? t : 2 * D - 1 - t;
+  };
+  const Taps& tp = blur == SGP_BLUR_SYMMETRIC ? g : c;
+  if (passes_out) *passes_out = P;
+  if (!L->sparse || dense) {
+    S* a = lat0;
+    S* b = lat1;
+    for (int t = 0; t < P; ++t) {
+      launch_blur_t<S>(L, dir(t), tp, a, b, k, st);
+      S* x = a;
+      a = b;
+      b = x;
+    }
+    return a;
+  }
+  // sparse: lazy centre-tap factors (none when the centre tap is 1)
+  const float* pw = tp.t[0] == 1.f ? nullptr : L->g0pow;
+  const bool v4 = k % 4 == 0;
+  const int G = v4 ? k / 4 : k;
+  if (pw) cudaMemsetAsync(L->epoch, 0, (size_t)L->m * sizeof(int32_t), st);
+  S* tmp = static_cast<S*>(L->act_tmp);
+  for (int t = 0; t < P; ++t) {
+    const int j = dir(t);
+    const int64_t count = L->act_off[j + 1] - L->act_off[j];
+    if (count == 0) continue;
+    const int32_t* act = L->act + L->act_off[j];
+    const int32_t* nbr_j = L->nbr + (size_t)j * L->r * 2 * L->m;
+    const unsigned grid = (unsigned)ceil_div(count * G, kThreads);
+    if (v4) {
+      k_sparse_blur<4, S><<<grid, kThreads, 0, st>>>(count, G, k, L->r, tp, t, act, nbr_j, L->m,
+                                                     L->epoch, pw, lat0, tmp);
+      k_sparse_store<4, S><<<grid, kThreads, 0, st>>>(count, G, k, t, act, tmp, lat0, L->epoch);
+    } else {
+      k_sparse_blur<1, S><<<grid, kThreads, 0, st>>>(count, G, k, L->r, tp, t, act, nbr_j, L->m,
+                                                     L->epoch, pw, lat0, tmp);
+      k_sparse_store<1, S><<<grid, kThreads, 0, st>>>(count, G, k, t, act, tmp, lat0, L->epoch);
+    }
+    note_launches(2);
+  }
+  if (pw) {
+    const unsigned grid = (unsigned)ceil_div(L->m * G, kThreads);
+    if (v4) k_sparse_finish<4, S><<<grid, kThreads, 0, st>>>(L->m, G, k, P, L->epoch, pw, lat0);
+    else k_sparse_finish<1, S><<<grid, kThreads, 0, st>>>(L->m, G, k, P, L->epoch, pw, lat0);
+    note_launches(1);
+  }
+  return lat0;
+}
+
+// The whole operator with explicit buffers.  internal: V and out in locality order;
+// else V and out are in the caller's order and V is first gathered into `vperm`.
+template <class S>
+int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
+              float* out, S* lat0, S* lat1, float* partial, float* vperm, cudaStream_t st,
+              cudaEvent_t* ev, bool internal, double* dot_partial = nullptr,
+              bool dense = false) {
   const float* src = V;
   if (!internal) {
     launch_permute(L, V, k, vperm, st);
@@ -392,25 +522,8 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
   launch_splat_t<S>(L, src, k, lat0, partial, st);
   // External: inside a stream capture this becomes an event-record node of the graph
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-  S* a = lat0;
-  S* b = lat1;
   int passes = 0;
-  auto pass = [&](int j, const Taps& tp) {
-    launch_blur_t<S>(L, j, tp, a, b, k, st);
-    S* t = a;
-    a = b;
-    b = t;
-    ++passes;
-  };
-  const int D = L->D;
-  if (blur == SGP_BLUR_SEQUENTIAL) {
-    for (int j = 0; j < D; ++j) pass(j, c);
-  } else if (blur == SGP_BLUR_TRANSPOSE) {
-    for (int j = D - 1; j >= 0; --j) pass(j, c);
-  } else {
-    for (int j = 0; j < D; ++j) pass(j, g);
-    for (int j = D - 1; j >= 0; --j) pass(j, g);
-  }
+  S* a = blur_passes_t<S>(L, blur, lat0, lat1, k, st, &passes, dense);
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   if (internal && dot_partial) launch_slice_dot<S>(L, a, V, k, alpha, beta, out, dot_partial, st);
   else if (internal) launch_slice_t<false, S>(L, a, V, k, alpha, beta, out, st);
@@ -422,30 +535,8 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
 template <class S>
 S* splat_blur_t(const Lattice* L, const float* Vp, int k, int blur, S* lat0, S* lat1,
                 float* partial, cudaStream_t st) {
-  Taps c{}, g{};
-  for (int t = 0; t <= L->r; ++t) {
-    c.t[t] = (float)L->coef[t];
-    g.t[t] = (float)L->half[t];
-  }
   launch_splat_t<S>(L, Vp, k, lat0, partial, st);
-  S* a = lat0;
-  S* b = lat1;
-  auto pass = [&](int j, const Taps& tp) {
-    launch_blur_t<S>(L, j, tp, a, b, k, st);
-    S* t = a;
-    a = b;
-    b = t;
-  };
-  const int D = L->D;
-  if (blur == SGP_BLUR_SEQUENTIAL) {
-    for (int j = 0; j < D; ++j) pass(j, c);
-  } else if (blur == SGP_BLUR_TRANSPOSE) {
-    for (int j = D - 1; j >= 0; --j) pass(j, c);
-  } else {
-    for (int j = 0; j < D; ++j) pass(j, g);
-    for (int j = D - 1; j >= 0; --j) pass(j, g);
-  }
-  return a;
+  return blur_passes_t<S>(L, blur, lat0, lat1, k, st, nullptr, false);
 }
 
 size_t value_size(const Lattice* L) {
@@ -462,6 +553,14 @@ size_t mvm_work_bytes(const Lattice* L, int k) {
 }
 
 sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
+  if (L->sparse && L->act_tmp_elems < (size_t)L->act_max * k) {
+    if (L->act_tmp) cudaFreeAsync(L->act_tmp, st);
+    L->act_tmp = nullptr;
+    const size_t bytes = std::max<size_t>((size_t)L->act_max * k * value_size(L), 16);
+    cudaError_t e = cudaMallocAsync(&L->act_tmp, bytes, st);
+    if (e != cudaSuccess) return cuda_status(e, "allocating the sparse blur buffer");
+    L->act_tmp_elems = (size_t)L->act_max * k;
+  }
   if (L->lat_elems >= (size_t)L->m * k && L->lat[0] && L->vperm_elems >= (size_t)L->n * k)
     return SGP_OK;
   void** bufs[4] = {(void**)&L->lat[0], (void**)&L->lat[1], (void**)&L->partial,
@@ -512,12 +611,13 @@ void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, fl
   void* lat1 = w + vb;
   float* partial = reinterpret_cast<float*>(w + 2 * vb);
   float* vperm = reinterpret_cast<float*>(w + 2 * vb + round256((size_t)L->nslots * k * sizeof(float)));
+  // the fixed work area holds no direction-list buffers: dense passes
   if (L->value_dtype == SGP_VALUES_BF16)
     enqueue_t<bf16>(L, V_user, k, blur, alpha, beta, out, (bf16*)lat0, (bf16*)lat1, partial, vperm,
-                    st, nullptr, false);
+                    st, nullptr, false, nullptr, /*dense=*/true);
   else
     enqueue_t<float>(L, V_user, k, blur, alpha, beta, out, (float*)lat0, (float*)lat1, partial,
-                     vperm, st, nullptr, false);
+                     vperm, st, nullptr, false, nullptr, /*dense=*/true);
 }
 
 void* enqueue_splat_blur(const Lattice* L, const float* Vp, int k, int blur, void* lat0,

@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -632,16 +634,25 @@ struct Lane {
 struct sgp_server {
   sgp_server_opts o{};
   int kp = 4, S = 0;
-  cudaStream_t bs = nullptr;  // set-up stream
+  int device = 0;
+  cudaStream_t bs = nullptr;  // set-up stream (used by the set-up thread only)
   std::chrono::steady_clock::time_point t0;
   long long next_id = 1;
   std::deque<Request*> queue;
   std::map<int, std::unique_ptr<Lane>> lanes;
   std::map<long long, std::unique_ptr<Request>> reqs;
-  int n_active = 0;
+  int n_active = 0;  // admitted: in set-up or in a lane
   unsigned long long in_use = 0;
   int peak_active = 0;
-  std::unique_ptr<Table> htab1;  // host image of the one-request tables
+  std::unique_ptr<Table> htab1;  // host image of the one-request tables (set-up thread)
+  // Set-up thread: admitted requests are uploaded, built and given their right-hand sides
+  // there, on `bs`, so that the stepping thread keeps relaunching lanes meanwhile.
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> to_setup;                              // guarded by mu
+  std::vector<std::pair<Request*, sgp_status>> setup_done;    // guarded by mu
+  bool stop = false;                                          // guarded by mu
 };
 
 namespace {
@@ -950,6 +961,59 @@ void destroy_lane(Lane* ln) {
   if (ln->st) cudaStreamDestroy(ln->st);
 }
 
+void setup_worker(sgp_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Request* R = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->to_setup.empty(); });
+      if (S->stop) return;
+      R = S->to_setup.front();
+      S->to_setup.pop_front();
+    }
+    const double t = now_us(S);
+    const sgp_status st = setup(S, R);
+    R->st.setup_us = now_us(S) - t;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->setup_done.emplace_back(R, st);
+    }
+  }
+}
+
+// Requests whose set-up has finished join their lane (or complete with the error).
+sgp_status collect_setups(sgp_server* S, int* done) {
+  std::vector<std::pair<Request*, sgp_status>> ready;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    ready.swap(S->setup_done);
+  }
+  for (auto& rs : ready) {
+    Request* R = rs.first;
+    sgp_status s = rs.second;
+    S->in_use -= R->bound;  // the reservation made at admission
+    Lane* ln = nullptr;
+    if (s == SGP_OK) s = lane_for(S, lane_key(S, R->L), &ln);
+    if (s != SGP_OK) {
+      R->st.status = s;
+      R->held = 0;
+      release(S, R, S->bs);
+      R->st.done_us = now_us(S);
+      R->st.done = 1;
+      S->n_active -= 1;
+      ++*done;
+      if (s == SGP_ERR_CUDA) return s;  // a failed device call: report it
+      continue;
+    }
+    S->in_use += R->held;
+    R->lane = ln;
+    ln->active.push_back(R);
+    ln->dirty = true;
+  }
+  return SGP_OK;
+}
+
 sgp_status admit(sgp_server* S) {
   for (auto it = S->queue.begin(); it != S->queue.end();) {  // deadlines passed in the queue
     Request* R = *it;
@@ -967,29 +1031,21 @@ sgp_status admit(sgp_server* S) {
     if (S->in_use + R->bound > S->o.hbm_budget) break;  // strict arrival order
     S->queue.pop_front();
     R->st.admit_us = now_us(S);
-    S->in_use += R->bound;  // reserved while the lattice is built
-    sgp_status s = setup(S, R);
-    S->in_use -= R->bound;
-    Lane* ln = nullptr;
-    if (s == SGP_OK) s = lane_for(S, lane_key(S, R->L), &ln);
-    if (s != SGP_OK) {
-      R->st.status = s;
-      R->held = 0;
-      (void)cudaStreamSynchronize(S->bs);
-      release(S, R, S->bs);
-      R->st.done_us = now_us(S);
-      R->st.done = 1;
-      if (s == SGP_ERR_CUDA) return s;  // a failed device call: report it
-      continue;
-    }
-    S->in_use += R->held;
-    R->lane = ln;
-    ln->active.push_back(R);
-    ln->dirty = true;
+    S->in_use += R->bound;  // reserved until its set-up reports the actual allocation
     S->n_active += 1;
     S->peak_active = std::max(S->peak_active, S->n_active);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->to_setup.push_back(R);
+    }
+    S->cv.notify_one();
   }
   return SGP_OK;
+}
+
+bool setups_ready(sgp_server* S) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  return !S->setup_done.empty();
 }
 
 // Requests of a lane whose round has finished: finish the stopped ones, keep the rest.
@@ -1061,6 +1117,7 @@ sgp_status launch(sgp_server* S, Lane* ln) {
 
 sgp_status server_step(sgp_server* S, int* completed) {
   int done = 0;
+  if (sgp_status s = collect_setups(S, &done)) return s;  // 0. requests ready to join
   for (auto& kv : S->lanes) {  // 1. lanes whose round has finished
     Lane* ln = kv.second.get();
     if (!ln->in_flight) continue;
@@ -1069,7 +1126,7 @@ sgp_status server_step(sgp_server* S, int* completed) {
     if (q != cudaSuccess) return cuda_status(q, "waiting for a lane");
     if (sgp_status s = harvest(S, ln, &done)) return s;
   }
-  if (sgp_status s = admit(S)) return s;  // 2. set-up overlaps the lanes in flight
+  if (sgp_status s = admit(S)) return s;  // 2. set-up (another thread) overlaps the lanes
   bool any = false;
   for (auto& kv : S->lanes) {  // 3. relaunch idle lanes
     Lane* ln = kv.second.get();
@@ -1077,8 +1134,9 @@ sgp_status server_step(sgp_server* S, int* completed) {
       if (sgp_status s = launch(S, ln)) return s;
     any = any || ln->in_flight;
   }
-  // 4. without a finished request, wait a little for the next lane to finish
-  if (done == 0 && any) {
+  // 4. without a finished request, wait a little for a lane or a set-up to finish
+  const bool setting_up = S->n_active > 0;
+  if (done == 0 && (any || setting_up)) {
     const double deadline = now_us(S) + kStepWaitUs;
     bool ready = false;
     while (!ready && now_us(S) < deadline) {
@@ -1086,6 +1144,7 @@ sgp_status server_step(sgp_server* S, int* completed) {
         Lane* ln = kv.second.get();
         if (ln->in_flight && cudaEventQuery(ln->ev) != cudaErrorNotReady) ready = true;
       }
+      ready = ready || setups_ready(S);
       if (!ready) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     clear_pending_error();  // cudaEventQuery's not-ready status
@@ -1178,7 +1237,10 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->kp = (o.probes + 1 + 3) / 4 * 4;
   S->t0 = std::chrono::steady_clock::now();
   S->htab1 = std::make_unique<Table>();
+  SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
+  sgp_server* raw = S.get();
+  S->worker = std::thread(setup_worker, raw);
   *out = S.release();
   return SGP_OK;
 }
@@ -1257,7 +1319,19 @@ double sgp_server_clock_us(const sgp_server* S) { return S ? now_us(S) : 0.0; }
 
 void sgp_server_destroy(sgp_server* S) {
   if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
   cudaStreamSynchronize(S->bs);
+  for (auto& rs : S->setup_done) {  // set up but never joined a lane
+    S->in_use -= rs.first->bound;
+    release(S, rs.first, S->bs);
+  }
+  S->setup_done.clear();
+  S->to_setup.clear();
   for (auto& kv : S->lanes) {
     Lane* ln = kv.second.get();
     cudaStreamSynchronize(ln->st);

@@ -33,6 +33,9 @@ constexpr int kMaxD = 128;    // d + 1
 constexpr int kMaxK = 256;    // right-hand sides per call
 constexpr int kSplatSeg = 32;      // splat items per segment
 constexpr int kSplatMedSegs = 16;  // segments a single thread-group sums in the fix-up
+// A lattice blurs in sparse mode when the direction lists hold at most this fraction of
+// the D m (vertex, direction) pairs.
+constexpr double kSparseFrac = 0.3;
 
 // Stencil taps passed by value to the blur kernels.
 struct Taps {
@@ -80,6 +83,17 @@ struct sgp_lattice {
   float* vperm = nullptr;    // [n][k] the caller's V in locality order (public MVMs)
   int32_t* nbr = nullptr;      // [D][r][2][m] neighbour id of v - t u_j (0) / v + t u_j (1)
   int16_t* keys = nullptr;     // [m][D] vertex coordinates
+  // Sparse lattices (few vertices with a neighbour along each direction, e.g. isolated
+  // simplices at high d): act[act_off[j] .. act_off[j+1]) lists the vertices with at least
+  // one neighbour along direction j, and the blur updates only those (sgp::kSparseFrac).
+  bool sparse = false;
+  int32_t* act = nullptr;
+  std::vector<int64_t> act_off;  // [D + 1], host
+  int64_t act_max = 0;           // largest list
+  int32_t* epoch = nullptr;      // [m] pass after which a vertex's stored row was written
+  void* act_tmp = nullptr;       // [act_max][k] new values of one pass
+  size_t act_tmp_elems = 0;
+  float* g0pow = nullptr;        // [2D + 1] powers of the symmetric blur's centre tap
   uint8_t* rank = nullptr;     // [n][D] rank of each elevated coordinate, locality order
   unsigned* err = nullptr;     // device error word
 

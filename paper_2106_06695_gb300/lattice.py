@@ -100,6 +100,13 @@ class Lattice:
         check(self._lib.sgp_lattice_info(self._h, None, ctypes.byref(nbytes)))
         return int(nbytes.value)
 
+    @property
+    def sparse_blur(self) -> bool:
+        """True when the blur runs on per-direction vertex lists (sgp_lattice_blur_lists)."""
+        sp = ctypes.c_int()
+        check(self._lib.sgp_lattice_blur_lists(self._h, ctypes.byref(sp), None))
+        return bool(sp.value)
+
     def stencil(self):
         """(s, c[0..r], g[0..r]): spacing, paper taps and symmetric-blur taps."""
         r = ctypes.c_int()

@@ -236,3 +236,28 @@ def test_cg_on_the_sequential_operator_reports_its_state():
     B = synth.solve_rhs(X, 23, probes=2)
     xg, ig, rg = lat.cg(gpu(B), noise=0.01, tol=1e-3, max_iter=40, blur="sequential")
     assert (ig <= 40).all() and np.isfinite(rg).all()
+
+
+SPARSE_CASES = [(3000, 20, 0.5, 1), (2000, 50, 1.0, 1), (1000, 90, 1.0, 1), (2500, 20, 0.5, 2)]
+
+
+@pytest.mark.parametrize("n,d,ls,order", SPARSE_CASES)
+def test_sparse_lattice_mvm_parity(n, d, ls, order):
+    """High-d lattices blur on their per-direction vertex lists (lazy centre-tap factors);
+    the product must match the oracle as the dense sweep does, in every blur mode."""
+    X = synth.gmm_points(n, d, 3)
+    L = np.full(d, ls, np.float32)
+    lat, ref = pair(X, L, "rbf_binomial", order)
+    assert lat.sparse_blur
+    for blur in ("sequential", "transpose", "symmetric"):
+        for k in (1, 4, 9):
+            V = synth.gaussian_values(n, k, 2)
+            out = lat.mvm(gpu(V), blur=blur).cpu().numpy()
+            want = ref.mvm(V.astype(np.float64), mode=MODE[blur])
+            assert rel_l2(out, want) <= MVM_RTOL, (blur, k, rel_l2(out, want))
+
+
+def test_dense_lattice_reports_dense_blur():
+    X = synth.gmm_points(6000, 6, 5)
+    lat, _ = pair(X, np.full(6, 0.8, np.float32))
+    assert not lat.sparse_blur
