@@ -39,7 +39,7 @@ void free_lattice(Lattice* L) {
   if (!L) return;
   cudaStream_t st = L->stream;
   void* arrays[] = {L->perm, L->idx, L->w, L->rank, L->row_ptr, L->items, L->nbr, L->keys, L->err,
-                    L->act, L->epoch, L->act_tmp, L->g0pow,
+                    L->act, L->act_off_dev, L->epoch, L->act_tmp, L->g0pow,
                     L->lat[0], L->lat[1], L->seg, L->med_rows, L->huge_rows, L->partial,
                     L->vperm};
   for (void* p : arrays)

@@ -772,6 +772,10 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
         k_active_compact<<<g, 256, 0, st>>>(nbr_j, m, r, pos, L->act + L->act_off[j]);
         note_launches(2);
       }
+      SGP_CHECK(dalloc(&L->act_off_dev, D + 1, st), "alloc list offsets");
+      SGP_CHECK(cudaMemcpyAsync(L->act_off_dev, L->act_off.data(), (D + 1) * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, st),
+                "copy list offsets");
       // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
       std::vector<float> pw(2 * D + 1);
       for (int q = 0; q <= 2 * D; ++q) pw[q] = (float)std::pow(L->half[0], (double)q);

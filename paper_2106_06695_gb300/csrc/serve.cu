@@ -47,7 +47,7 @@ constexpr int kGrid = 4 * 152;      // their fixed grid (4 blocks per SM)
 constexpr int kBlurU = 2;           // blur rows per thread
 constexpr int kVecRows = 4;         // vector-kernel rows per thread
 
-enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_KINDS };
+enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_KINDS };
 
 // One active request as the kernels see it.  Row-indexed arrays are in the lattice's
 // locality order p; perm[p] < n_train marks a training row.
@@ -75,6 +75,14 @@ struct SlotDev {
   int* state;                         // [0] request still iterating, [1] iterations done
   int max_iter;
   float tol;
+  // sparse lattices: direction lists, per-vertex epochs and the pass buffer (the values
+  // stay in lat0 with lazy centre-tap factors g0pow, as in the library's sparse blur)
+  int sparse;
+  const int32_t* act;
+  const int64_t* act_off;  // [D + 1]
+  int32_t* epoch;
+  void* stmp;
+  const float* g0pow;
 };
 
 struct Table {
@@ -172,8 +180,12 @@ __global__ void __launch_bounds__(kST) kb_splat(const Table* __restrict__ T) {
     const int2 e = s.items[it];
     acc = f4_fma(__int_as_float(e.y), f4_ld(s.p + (int64_t)e.x * kp + col), acc);
   }
-  if (sg.w < 0) Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)sg.x * kp + col, acc);
-  else f4_st(s.spart + (int64_t)sg.w * kp + col, acc);
+  if (sg.w < 0) {
+    Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)sg.x * kp + col, acc);
+    if (s.sparse && col == 0) s.epoch[sg.x] = 0;
+  } else {
+    f4_st(s.spart + (int64_t)sg.w * kp + col, acc);
+  }
   SLOT_LOOP_END
 }
 
@@ -193,6 +205,7 @@ __global__ void __launch_bounds__(kST) kb_splat_med(const Table* __restrict__ T)
     acc = make_float4(acc.x + v.x, acc.y + v.y, acc.z + v.z, acc.w + v.w);
   }
   Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)rw.x * kp + col, acc);
+  if (s.sparse && col == 0) s.epoch[rw.x] = 0;
   SLOT_LOOP_END
 }
 
@@ -224,6 +237,7 @@ __global__ void __launch_bounds__(kST) kb_splat_huge(const Table* __restrict__ T
     __syncthreads();
   }
   if (g == 0) Store<S>::st4(static_cast<S*>(s.lat0) + (int64_t)rw.x * kp + col, red[threadIdx.x]);
+  if (s.sparse && threadIdx.x == 0) s.epoch[rw.x] = 0;
   __syncthreads();
   SLOT_LOOP_END
 }
@@ -238,6 +252,41 @@ __global__ void __launch_bounds__(kST) kb_blur(const Table* __restrict__ T, int 
   SLOT_LOOP(U_BLUR)
   if (*s.state == 0 || t >= 2 * s.D || g >= groups) continue;
   const int j = t < s.D ? t : 2 * s.D - 1 - t;
+  if (s.sparse) {  // the vertices of list j: new rows into stmp, lazy factors on reads
+    const int64_t base = s.act_off[j], count = s.act_off[j + 1] - base;
+    const S* lat = static_cast<const S*>(s.lat0);
+    const int32_t* nbr = s.nbr + (int64_t)j * R * 2 * s.m;
+    for (int u = 0; u < kBlurU; ++u) {
+      const int64_t e = (local * kBlurU + u) * groups + g;
+      if (e >= count) break;
+      const int64_t v = s.act[base + e];
+      const float4 own = Store<S>::ldg4(lat + v * kp + col);
+      const float fo = s.g0pow[t - s.epoch[v]];
+      float4 acc = make_float4(s.taps[0] * fo * own.x, s.taps[0] * fo * own.y,
+                               s.taps[0] * fo * own.z, s.taps[0] * fo * own.w);
+#pragma unroll
+      for (int tt = 0; tt < R; ++tt) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ia = nbr[(int64_t)(2 * tt) * s.m + v];
+        const int ic = nbr[(int64_t)(2 * tt + 1) * s.m + v];
+        if (ia >= 0) {
+          const float f = s.g0pow[t - s.epoch[ia]];
+          const float4 x = Store<S>::ldg4(lat + (int64_t)ia * kp + col);
+          sum = make_float4(f * x.x, f * x.y, f * x.z, f * x.w);
+        }
+        if (ic >= 0) {
+          const float f = s.g0pow[t - s.epoch[ic]];
+          const float4 x = Store<S>::ldg4(lat + (int64_t)ic * kp + col);
+          sum = make_float4(sum.x + f * x.x, sum.y + f * x.y, sum.z + f * x.z, sum.w + f * x.w);
+        }
+        const float wt = s.taps[tt + 1];
+        acc = make_float4(fmaf(wt, sum.x, acc.x), fmaf(wt, sum.y, acc.y), fmaf(wt, sum.z, acc.z),
+                          fmaf(wt, sum.w, acc.w));
+      }
+      Store<S>::st4(static_cast<S*>(s.stmp) + e * kp + col, acc);
+    }
+    continue;
+  }
   const S* in = static_cast<const S*>((t & 1) ? s.lat1 : s.lat0);
   S* out = static_cast<S*>((t & 1) ? s.lat0 : s.lat1);
   const int64_t m = s.m;
@@ -278,6 +327,47 @@ __global__ void __launch_bounds__(kST) kb_blur(const Table* __restrict__ T, int 
       acc.w = fmaf(wt, sa[u][tt].w + sc[u][tt].w, acc.w);
     }
     Store<S>::st4(out + v[u] * kp + col, acc);
+  }
+  SLOT_LOOP_END
+}
+
+// Sparse requests, after kb_blur pass t: list rows back into lat0, epoch t + 1.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_sparse_store(const Table* __restrict__ T, int t) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_BLUR)
+  if (!s.sparse || *s.state == 0 || t >= 2 * s.D || g >= groups) continue;
+  const int j = t < s.D ? t : 2 * s.D - 1 - t;
+  const int64_t base = s.act_off[j], count = s.act_off[j + 1] - base;
+  for (int u = 0; u < kBlurU; ++u) {
+    const int64_t e = (local * kBlurU + u) * groups + g;
+    if (e >= count) break;
+    const int64_t v = s.act[base + e];
+    Store<S>::st4(static_cast<S*>(s.lat0) + v * kp + col,
+                  Store<S>::ld4(static_cast<const S*>(s.stmp) + e * kp + col));
+    if (col == 0) s.epoch[v] = t + 1;
+  }
+  SLOT_LOOP_END
+}
+
+// Sparse requests, after their 2D passes: the remaining centre-tap factors.
+template <class S>
+__global__ void __launch_bounds__(kST) kb_sparse_finish(const Table* __restrict__ T) {
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VERT)
+  if (!s.sparse || *s.state == 0 || g >= groups) continue;
+  const int P = 2 * s.D;
+  for (int u = 0; u < kBlurU; ++u) {
+    const int64_t v = (local * kBlurU + u) * groups + g;
+    if (v >= s.m) break;
+    const int e = s.epoch[v];
+    if (e == P) continue;
+    S* row = static_cast<S*>(s.lat0) + v * kp + col;
+    const float f = s.g0pow[P - e];
+    const float4 x = Store<S>::ld4(row);
+    Store<S>::st4(row, make_float4(f * x.x, f * x.y, f * x.z, f * x.w));
   }
   SLOT_LOOP_END
 }
@@ -710,6 +800,12 @@ void fill_slot(const sgp_server* S, const Request* R, SlotDev& s) {
   s.state = R->ints + kp;
   s.max_iter = S->o.max_iter;
   s.tol = (float)S->o.tol;
+  s.sparse = L->sparse ? 1 : 0;
+  s.act = L->act;
+  s.act_off = L->act_off_dev;
+  s.epoch = L->epoch;
+  s.stmp = L->act_tmp;
+  s.g0pow = L->g0pow;
 }
 
 void unit_counts(const sgp_server* S, const Lattice* L, int64_t (&vb)[U_KINDS]) {
@@ -717,8 +813,9 @@ void unit_counts(const sgp_server* S, const Lattice* L, int64_t (&vb)[U_KINDS]) 
   vb[U_SPLAT] = ceil_div(L->nseg, groups);
   vb[U_MED] = ceil_div(L->nmed, groups);
   vb[U_HUGE] = L->nhuge;
-  vb[U_BLUR] = ceil_div(L->m, (int64_t)groups * kBlurU);
+  vb[U_BLUR] = ceil_div(L->sparse ? L->act_max : L->m, (int64_t)groups * kBlurU);
   vb[U_VEC] = ceil_div(L->n, (int64_t)groups * kVecRows);
+  vb[U_VERT] = L->sparse ? ceil_div(L->m, (int64_t)groups * kBlurU) : 0;
 }
 
 // Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur
@@ -885,40 +982,47 @@ sgp_status finish(sgp_server* S, Request* R, cudaStream_t st) {
 }
 
 template <int Rr, class Sv>
-int enqueue_iteration_t(Lane* ln, int dmax) {
+int enqueue_iteration_t(Lane* ln, int dmax, bool sparse) {
   cudaStream_t st = ln->st;
   const Table* T = ln->dtab;
   kb_splat<Sv><<<kGrid, kST, 0, st>>>(T);
   kb_splat_med<Sv><<<kGrid, kST, 0, st>>>(T);
   kb_splat_huge<Sv><<<kGrid, kST, 0, st>>>(T);
-  for (int t = 0; t < 2 * dmax; ++t) kb_blur<Rr, Sv><<<kGrid, kST, 0, st>>>(T, t);
+  for (int t = 0; t < 2 * dmax; ++t) {
+    kb_blur<Rr, Sv><<<kGrid, kST, 0, st>>>(T, t);
+    if (sparse) kb_sparse_store<Sv><<<kGrid, kST, 0, st>>>(T, t);
+  }
+  if (sparse) kb_sparse_finish<Sv><<<kGrid, kST, 0, st>>>(T);
   kb_slice_dot<Sv><<<kGrid, kST, 0, st>>>(T);
   kb_alpha<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_xr<<<kGrid, kST, 0, st>>>(T);
   kb_check_beta<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_p<<<kGrid, kST, 0, st>>>(T);
-  return 8 + 2 * dmax;
+  return 8 + 2 * dmax + (sparse ? 2 * dmax + 1 : 0);
 }
 
 template <class Sv>
-int enqueue_iteration_s(const sgp_server* S, Lane* ln, int dmax) {
+int enqueue_iteration_s(const sgp_server* S, Lane* ln, int dmax, bool sparse) {
   switch (S->o.order_r) {
-    case 1: return enqueue_iteration_t<1, Sv>(ln, dmax);
-    case 2: return enqueue_iteration_t<2, Sv>(ln, dmax);
-    case 3: return enqueue_iteration_t<3, Sv>(ln, dmax);
-    default: return enqueue_iteration_t<4, Sv>(ln, dmax);
+    case 1: return enqueue_iteration_t<1, Sv>(ln, dmax, sparse);
+    case 2: return enqueue_iteration_t<2, Sv>(ln, dmax, sparse);
+    case 3: return enqueue_iteration_t<3, Sv>(ln, dmax, sparse);
+    default: return enqueue_iteration_t<4, Sv>(ln, dmax, sparse);
   }
 }
 
-sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, cudaGraphExec_t* out) {
-  auto it = ln->graphs.find(dmax);
+// Graph of one iteration of the lane, keyed by Dmax and whether a request blurs sparsely.
+sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, cudaGraphExec_t* out) {
+  const int key = 2 * dmax + (sparse ? 1 : 0);
+  auto it = ln->graphs.find(key);
   if (it != ln->graphs.end()) {
     *out = it->second;
     return SGP_OK;
   }
   SRV_CHECK(cudaStreamBeginCapture(ln->st, cudaStreamCaptureModeThreadLocal), "begin capture");
-  const int kernels = S->o.value_dtype == SGP_VALUES_BF16 ? enqueue_iteration_s<bf16>(S, ln, dmax)
-                                                         : enqueue_iteration_s<float>(S, ln, dmax);
+  const int kernels = S->o.value_dtype == SGP_VALUES_BF16
+                          ? enqueue_iteration_s<bf16>(S, ln, dmax, sparse)
+                          : enqueue_iteration_s<float>(S, ln, dmax, sparse);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(ln->st, &g);
   if (e != cudaSuccess) return cuda_status(e, "capturing the batched CG iteration");
@@ -926,8 +1030,8 @@ sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, cudaGraphExec_t* o
   e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_status(e, "instantiating the batched CG iteration");
-  ln->graphs[dmax] = ex;
-  ln->graph_kernels[dmax] = kernels;
+  ln->graphs[key] = ex;
+  ln->graph_kernels[key] = kernels;
   *out = ex;
   return SGP_OK;
 }
@@ -1100,12 +1204,17 @@ sgp_status launch(sgp_server* S, Lane* ln) {
     ln->dirty = false;
   }
   int dmax = 1;
-  for (Request* R : ln->active) dmax = std::max(dmax, R->L->D);
+  bool sparse = false;
+  for (Request* R : ln->active) {
+    dmax = std::max(dmax, R->L->D);
+    sparse = sparse || R->L->sparse;
+  }
   cudaGraphExec_t ex = nullptr;
-  if (sgp_status s = graph_for(S, ln, dmax, &ex)) return s;
+  if (sgp_status s = graph_for(S, ln, dmax, sparse, &ex)) return s;
+  const int key = 2 * dmax + (sparse ? 1 : 0);
   for (int i = 0; i < S->o.check_every; ++i) {
     SRV_CHECK(cudaGraphLaunch(ex, ln->st), "launching the batched CG iteration");
-    note_launches(ln->graph_kernels[dmax]);
+    note_launches(ln->graph_kernels[key]);
   }
   SRV_CHECK(cudaMemcpyAsync(ln->hflags, ln->dflags, 2 * ns * sizeof(int), cudaMemcpyDeviceToHost,
                             ln->st),

@@ -89,6 +89,7 @@ struct sgp_lattice {
   bool sparse = false;
   int32_t* act = nullptr;
   std::vector<int64_t> act_off;  // [D + 1], host
+  int64_t* act_off_dev = nullptr;  // [D + 1], device copy
   int64_t act_max = 0;           // largest list
   int32_t* epoch = nullptr;      // [m] pass after which a vertex's stored row was written
   void* act_tmp = nullptr;       // [act_max][k] new values of one pass
