@@ -273,7 +273,8 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
                              const int32_t* __restrict__ perm, const int16_t* __restrict__ rem0,
                              const uint8_t* __restrict__ rank, int64_t nD, int d,
                              int32_t* __restrict__ slot_id, int16_t* __restrict__ keys,
-                             uint64_t* __restrict__ vhash, int2* __restrict__ vrange) {
+                             uint64_t* __restrict__ vhash, int2* __restrict__ vrange,
+                             uint32_t* __restrict__ bloom, uint64_t bloom_mask) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nD) return;
   const int32_t s = entry_slot[e];
@@ -294,6 +295,8 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
   }
   vhash[id] = h;
   vrange[id] = make_int2(lo, hi);
+  const uint64_t b = (mix64(h) >> 20) & bloom_mask;  // the vertex's filter bit
+  atomicOr(&bloom[b >> 5], 1u << (b & 31));
 }
 
 __global__ void k_entry_ids(const int32_t* __restrict__ entry_slot,
@@ -331,55 +334,67 @@ __device__ __forceinline__ bool entry_is_neighbour(uint32_t e, const int16_t* __
   return true;
 }
 
-// One thread per (vertex, direction j): ids of v -+ t u_j, t = 1..r.  The neighbour's hash
-// comes from the vertex's linear hash in O(1) (sum_A = sum_c A_c); the key itself is read
-// only to confirm a tag match.  A neighbour outside the int16 key range does not exist.
+// One thread per vertex, all directions j: ids of v -+ t u_j, t = 1..r.  The neighbour's
+// hash comes from the vertex's linear hash in O(1) (sum_A = sum_c A_c); most absent
+// neighbours stop at the vertex filter (one bit per hash, sized to stay in L2); the key
+// itself is read only to confirm a tag match.  A neighbour outside the int16 key range
+// does not exist.  counts[j] accumulates the vertices with a neighbour along j.
 __global__ void __launch_bounds__(256) k_neighbours(
     const int16_t* __restrict__ keys, const uint64_t* __restrict__ vhash,
     const int2* __restrict__ vrange, int64_t m, int d, int r, uint64_t sum_A,
     const unsigned long long* __restrict__ table, uint64_t mask,
     const int32_t* __restrict__ slot_id, const int32_t* __restrict__ perm,
     const int16_t* __restrict__ rem0, const uint8_t* __restrict__ rank,
-    int32_t* __restrict__ nbr) {
-  const int64_t t_id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t* __restrict__ bloom, uint64_t bloom_mask, int32_t* __restrict__ nbr,
+    unsigned long long* __restrict__ counts) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int D = d + 1;
-  if (t_id >= m * D) return;
-  const int64_t v = t_id % m;
-  const int j = (int)(t_id / m);
-  const uint64_t hv = vhash[v];
-  const int2 rg = vrange[v];
-  const uint64_t dj = (uint64_t)D * coord_mult(j) - sum_A;  // lin(u_j)
-  const int16_t* kv = keys + v * D;
-  for (int t = 1; t <= r; ++t) {
-    for (int sg = 0; sg < 2; ++sg) {
-      const int step = sg ? t : -t;
-      // every coordinate moves by -step except j, which moves by d step
-      bool in_range = rg.x - t * d >= -32768 && rg.y + t * d <= 32767;
-      if (!in_range) {
-        in_range = true;
-        for (int c = 0; c < D; ++c) {
-          const int x = (int)kv[c] + step * ((c == j ? D : 0) - 1);
-          in_range = in_range && x >= -32768 && x <= 32767;
-        }
-      }
-      int32_t found = -1;
-      if (in_range) {
-        const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * dj);
-        const uint32_t tag = (uint32_t)(h >> 33);
-        uint64_t slot = h & mask;
-        for (uint64_t probe = 0; probe <= mask; ++probe) {
-          const unsigned long long cur = table[slot];
-          if (cur == kEmpty) break;
-          if ((uint32_t)(cur >> 32) == tag &&
-              entry_is_neighbour((uint32_t)cur, kv, j, step, d, perm, rem0, rank)) {
-            found = slot_id[slot];
-            break;
+  const bool live = v < m;
+  const uint64_t hv = live ? vhash[v] : 0;
+  const int2 rg = live ? vrange[v] : make_int2(0, 0);
+  const int16_t* kv = keys + (live ? v : 0) * D;
+  for (int j = 0; j < D; ++j) {
+    bool any = false;
+    if (live) {
+      const uint64_t dj = (uint64_t)D * coord_mult(j) - sum_A;  // lin(u_j)
+      for (int t = 1; t <= r; ++t) {
+        for (int sg = 0; sg < 2; ++sg) {
+          const int step = sg ? t : -t;
+          // every coordinate moves by -step except j, which moves by d step
+          bool in_range = rg.x - t * d >= -32768 && rg.y + t * d <= 32767;
+          if (!in_range) {
+            in_range = true;
+            for (int c = 0; c < D; ++c) {
+              const int x = (int)kv[c] + step * ((c == j ? D : 0) - 1);
+              in_range = in_range && x >= -32768 && x <= 32767;
+            }
           }
-          slot = (slot + 1) & mask;
+          int32_t found = -1;
+          const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * dj);
+          const uint64_t b = (h >> 20) & bloom_mask;
+          if (in_range && (bloom[b >> 5] >> (b & 31) & 1u)) {
+            const uint32_t tag = (uint32_t)(h >> 33);
+            uint64_t slot = h & mask;
+            for (uint64_t probe = 0; probe <= mask; ++probe) {
+              const unsigned long long cur = table[slot];
+              if (cur == kEmpty) break;
+              if ((uint32_t)(cur >> 32) == tag &&
+                  entry_is_neighbour((uint32_t)cur, kv, j, step, d, perm, rem0, rank)) {
+                found = slot_id[slot];
+                break;
+              }
+              slot = (slot + 1) & mask;
+            }
+          }
+          nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = found;
+          any = any || found >= 0;
         }
       }
-      nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = found;
     }
+    // vertices with a neighbour along j: one atomic per warp
+    const unsigned with = __ballot_sync(0xffffffffu, any);
+    if (with && (int)(threadIdx.x & 31) == __ffs(with) - 1)
+      atomicAdd(&counts[j], (unsigned long long)__popc(with));
   }
 }
 
@@ -391,25 +406,24 @@ __device__ __forceinline__ bool has_neighbour(const int32_t* __restrict__ nbr_j,
   return false;
 }
 
-__global__ void k_active_count(const int32_t* __restrict__ nbr, int64_t m, int D, int r,
-                               unsigned long long* __restrict__ counts) {
-  const int64_t t_id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t_id >= m * D) return;
-  const int64_t v = t_id % m;
-  const int j = (int)(t_id / m);
-  if (has_neighbour(nbr + (int64_t)j * r * 2 * m, m, r, v)) atomicAdd(&counts[j], 1ull);
-}
-
-__global__ void k_active_flags(const int32_t* __restrict__ nbr_j, int64_t m, int r,
-                               uint32_t* __restrict__ flags) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < m) flags[v] = has_neighbour(nbr_j, m, r, v) ? 1u : 0u;
-}
-
-__global__ void k_active_compact(const int32_t* __restrict__ nbr_j, int64_t m, int r,
-                                 const uint32_t* __restrict__ pos, int32_t* __restrict__ act) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < m && has_neighbour(nbr_j, m, r, v)) act[pos[v]] = (int32_t)v;
+// Direction lists: thread per (vertex, direction); a warp's vertices (one direction per
+// block row) take consecutive slots with one atomic.  The order of a list is immaterial to
+// the blur, which updates its vertices independently.
+__global__ void k_active_fill(const int32_t* __restrict__ nbr, int64_t m, int D, int r,
+                              const int64_t* __restrict__ off,
+                              unsigned long long* __restrict__ fill, int32_t* __restrict__ act) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // grid y: direction
+  const int j = (int)blockIdx.y;
+  if (v >= m) return;
+  const bool on = has_neighbour(nbr + (int64_t)j * r * 2 * m, m, r, v);
+  const unsigned with = __ballot_sync(__activemask(), on);
+  if (!on) return;  // the remaining lanes are exactly `with`
+  const int lane = (int)(threadIdx.x & 31);
+  const int leader = __ffs(with) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&fill[j], (unsigned long long)__popc(with));
+  base = __shfl_sync(with, base, leader);
+  act[off[j] + base + __popc(with & ((1u << lane) - 1u))] = (int32_t)v;
 }
 
 // ---------------------------------------------------------------------------------
@@ -650,9 +664,15 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   int2* vrange = nullptr;
   SGP_CHECK(tmp.get(&vhash, m), "alloc vertex hashes");
   SGP_CHECK(tmp.get(&vrange, m), "alloc vertex ranges");
+  // vertex filter: about 8 bits per vertex, 2^16 .. 2^29 bits
+  uint64_t bloom_bits = 1ull << 16;
+  while (bloom_bits < 8ull * (uint64_t)m && bloom_bits < (1ull << 29)) bloom_bits <<= 1;
+  uint32_t* bloom = nullptr;
+  SGP_CHECK(tmp.get(&bloom, bloom_bits / 32), "alloc vertex filter");
+  SGP_CHECK(cudaMemsetAsync(bloom, 0, bloom_bits / 8, st), "clear vertex filter");
   k_assign_ids<<<(unsigned)ceil_div(nD, 256), 256, 0, st>>>(flags, entry_slot, table, L->perm,
                                                            rem0, rank, nD, d, slot_id, L->keys,
-                                                           vhash, vrange);
+                                                           vhash, vrange, bloom, bloom_bits - 1);
   note_launches(1);
   SGP_CHECK(dalloc(&L->idx, nD, st), "alloc idx");
   SGP_CHECK(dalloc(&L->w, nD, st), "alloc w");
@@ -666,13 +686,16 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   // 5. neighbour table
   SGP_CHECK(dalloc(&L->nbr, (size_t)D * r * 2 * m, st), "alloc nbr");
   L->bytes += (size_t)D * r * 2 * m * sizeof(int32_t);
+  unsigned long long* counts = nullptr;
+  SGP_CHECK(tmp.get(&counts, 2 * D), "alloc counts");
+  SGP_CHECK(cudaMemsetAsync(counts, 0, 2 * D * sizeof(unsigned long long), st), "clear counts");
   {
     // sum_c A_c over the D coordinates, as the kernels compute A_c
     uint64_t sum_A = 0;
     for (int c = 0; c < D; ++c) sum_A += host_coord_mult(c);
-    k_neighbours<<<(unsigned)ceil_div(m * D, 256), 256, 0, st>>>(
+    k_neighbours<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(
         L->keys, vhash, vrange, m, d, r, sum_A, table, mask, slot_id, L->perm, rem0, rank,
-        L->nbr);
+        bloom, bloom_bits - 1, L->nbr, counts);
     note_launches(1);
   }
   SGP_CHECK(cudaGetLastError(), "k_neighbours");
@@ -735,13 +758,8 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
     note_launches(1);
     SGP_CHECK(cudaGetLastError(), "splat segments");
   }
-  // 8. direction lists of a sparse lattice
+  // 8. direction lists of a sparse lattice (counts from k_neighbours)
   {
-    unsigned long long* counts = nullptr;
-    SGP_CHECK(tmp.get(&counts, D), "alloc counts");
-    SGP_CHECK(cudaMemsetAsync(counts, 0, D * sizeof(unsigned long long), st), "clear counts");
-    k_active_count<<<(unsigned)ceil_div(m * D, 256), 256, 0, st>>>(L->nbr, m, D, r, counts);
-    note_launches(1);
     std::vector<unsigned long long> hc(D);
     SGP_CHECK(cudaMemcpyAsync(hc.data(), counts, D * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, st),
@@ -760,22 +778,13 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
       SGP_CHECK(dalloc(&L->act, std::max<int64_t>(total, 1), st), "alloc direction lists");
       SGP_CHECK(dalloc(&L->epoch, m, st), "alloc epochs");
       L->bytes += (size_t)total * sizeof(int32_t) + (size_t)m * sizeof(int32_t);
-      uint32_t *pos, *ptmp;
-      SGP_CHECK(tmp.get(&pos, m), "alloc positions");
-      SGP_CHECK(tmp.get(&ptmp, scan_temp_elems(m)), "alloc scan");
-      for (int j = 0; j < D; ++j) {
-        if (hc[j] == 0) continue;
-        const int32_t* nbr_j = L->nbr + (size_t)j * r * 2 * m;
-        const unsigned g = (unsigned)ceil_div(m, 256);
-        k_active_flags<<<g, 256, 0, st>>>(nbr_j, m, r, pos);
-        exclusive_scan_u32(pos, m, nullptr, ptmp, st);
-        k_active_compact<<<g, 256, 0, st>>>(nbr_j, m, r, pos, L->act + L->act_off[j]);
-        note_launches(2);
-      }
       SGP_CHECK(dalloc(&L->act_off_dev, D + 1, st), "alloc list offsets");
       SGP_CHECK(cudaMemcpyAsync(L->act_off_dev, L->act_off.data(), (D + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice, st),
                 "copy list offsets");
+      k_active_fill<<<dim3((unsigned)ceil_div(m, 256), (unsigned)D), 256, 0, st>>>(
+          L->nbr, m, D, r, L->act_off_dev, counts + D, L->act);
+      note_launches(1);
       // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
       std::vector<float> pw(2 * D + 1);
       for (int q = 0; q <= 2 * D; ++q) pw[q] = (float)std::pow(L->half[0], (double)q);
