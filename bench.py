@@ -386,6 +386,7 @@ def run_ours(args, world, rank, local):
                        "mvm_symmetric_ms": mvm_ms,
                        "mvm_symmetric_ms_note": "median of 50 graph-replayed MVMs",
                        "mvm_symmetric_mpoint_s": n / (mvm_ms / 1e3) / 1e6,
+                       "mvm_symmetric_mpoint_columns_s": n * k / (mvm_ms / 1e3) / 1e6,
                        "mvm_sequential_ms": mvm_seq_ms,
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
                        "mvm_symmetric_bf16_values_ms": mvm_bf16_ms,
