@@ -680,6 +680,7 @@ using namespace sgp;
 namespace {
 
 constexpr int kStepWaitUs = 2000;  // longest wait of one step for a lane to finish
+constexpr int kSetupThreads = 3;   // concurrent request set-ups
 
 struct Lane;
 
@@ -725,7 +726,7 @@ struct sgp_server {
   sgp_server_opts o{};
   int kp = 4, S = 0;
   int device = 0;
-  cudaStream_t bs = nullptr;  // set-up stream (used by the set-up thread only)
+  cudaStream_t bs = nullptr;  // stream for releasing requests that failed their set-up
   std::chrono::steady_clock::time_point t0;
   long long next_id = 1;
   std::deque<Request*> queue;
@@ -734,10 +735,11 @@ struct sgp_server {
   int n_active = 0;  // admitted: in set-up or in a lane
   unsigned long long in_use = 0;
   int peak_active = 0;
-  std::unique_ptr<Table> htab1;  // host image of the one-request tables (set-up thread)
-  // Set-up thread: admitted requests are uploaded, built and given their right-hand sides
-  // there, on `bs`, so that the stepping thread keeps relaunching lanes meanwhile.
-  std::thread worker;
+
+  // Set-up threads (kSetupThreads, each with its own stream): admitted requests are
+  // uploaded, built and given their right-hand sides there, so that the stepping thread
+  // keeps relaunching lanes and several builds overlap on the GPU.
+  std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request*> to_setup;                              // guarded by mu
@@ -846,8 +848,7 @@ void release(sgp_server* S, Request* R, cudaStream_t st) {
 }
 
 // Upload, build, right-hand sides and CG start of one request on the set-up stream.
-sgp_status setup(sgp_server* S, Request* R) {
-  cudaStream_t st = S->bs;
+sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   const sgp_request& in = R->in;
   const int64_t n_all = in.n + in.ns;
   const int d = in.d, kp = S->kp;
@@ -916,7 +917,6 @@ sgp_status setup(sgp_server* S, Request* R) {
                            R->p);
   note_launches(1);
   // initial residual norms and scalars through a one-request table
-  Table& t1 = *S->htab1;
   std::memset(&t1, 0, sizeof(Table));
   t1.nslots = 1;
   t1.kp = kp;
@@ -1067,22 +1067,29 @@ void destroy_lane(Lane* ln) {
 
 void setup_worker(sgp_server* S) {
   cudaSetDevice(S->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = S->bs;
+  auto t1 = std::make_unique<Table>();  // host image of the one-request tables
   for (;;) {
     Request* R = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] { return S->stop || !S->to_setup.empty(); });
-      if (S->stop) return;
+      if (S->stop) break;
       R = S->to_setup.front();
       S->to_setup.pop_front();
     }
     const double t = now_us(S);
-    const sgp_status st = setup(S, R);
+    const sgp_status status = setup(S, R, st, *t1);
     R->st.setup_us = now_us(S) - t;
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->setup_done.emplace_back(R, st);
+      S->setup_done.emplace_back(R, status);
     }
+  }
+  if (st != S->bs) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
   }
 }
 
@@ -1345,11 +1352,11 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->S = o.probes;
   S->kp = (o.probes + 1 + 3) / 4 * 4;
   S->t0 = std::chrono::steady_clock::now();
-  S->htab1 = std::make_unique<Table>();
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
   sgp_server* raw = S.get();
-  S->worker = std::thread(setup_worker, raw);
+  const int nthreads = std::min(kSetupThreads, o.max_active);
+  for (int i = 0; i < nthreads; ++i) S->workers.emplace_back(setup_worker, raw);
   *out = S.release();
   return SGP_OK;
 }
@@ -1433,7 +1440,8 @@ void sgp_server_destroy(sgp_server* S) {
     S->stop = true;
   }
   S->cv.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  for (std::thread& w : S->workers)
+    if (w.joinable()) w.join();
   cudaStreamSynchronize(S->bs);
   for (auto& rs : S->setup_done) {  // set up but never joined a lane
     S->in_use -= rs.first->bound;
