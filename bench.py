@@ -503,6 +503,19 @@ def run_serving(count: int):
             file=sys.stderr, flush=True)
     same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
                for a, b in zip(results["batched"], results["plain"]))
+    # repeated solves on resident lattices: 64 requests over 8 point sets, with and
+    # without lattice keys (batched server both times)
+    rep = synth.repeated_stream(64, 8, SERVING["seed"] + 1, rate_per_s=SERVING["rate_per_s"],
+                                test_points=SERVING["test_points"])
+    reuse = {"requests": len(rep), "datasets": 8}
+    for name, keyed in (("with_keys", True), ("without_keys", False)):
+        stream = [dict(r, lattice_key=(r["dataset"] + 1) if keyed else 0) for r in rep]
+        with Server(max_active=SERVING["max_active"]) as srv:
+            res = run_stream(srv, stream)
+            reused = sum(srv.stats(i)["lattice_reused"] for i in res.ids)
+        reuse[name] = {"solves_per_s": res.solves_per_s, "p50_s": res.percentile(50),
+                       "p99_s": res.percentile(99), "lattices_reused": int(reused)}
+    out["reuse"] = reuse
     out.update({"requests": count, "arrival_rate_per_s": SERVING["rate_per_s"],
                 "identical_results_batched_vs_plain": bool(same),
                 "stream": "n log-uniform [5e3, 5e5], d uniform over {3, 8, 20, 50, 90}, "

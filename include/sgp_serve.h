@@ -79,6 +79,11 @@ typedef struct {
   double timeout_us;         /* > 0: deadline arrival_us + timeout_us; a request still
                                 queued or iterating at a step past it completes with
                                 SGP_ERR_TIMEOUT (mean/var not written); <= 0: none        */
+  unsigned long long lattice_key; /* != 0: requests with the same key promise the same X,
+                                Xs, lengthscales and outputscale; the server keeps the
+                                lattice of a finished one resident (within hbm_budget,
+                                least recently used evicted first) and a later one reuses
+                                it instead of uploading and building; 0: no reuse        */
 } sgp_request;
 
 typedef struct {
@@ -90,7 +95,8 @@ typedef struct {
   long long m;               /* lattice vertices                                          */
   unsigned long long bytes;  /* device bytes the request held while active                */
   double setup_us;           /* host time of its set-up (upload, lattice build, right-hand
-                                sides), during which this server launched nothing else    */
+                                sides) on a set-up thread                                 */
+  int lattice_reused;        /* 1 when it ran on a resident lattice (lattice_key)         */
 } sgp_request_stats;
 
 /* Fill *opts with the defaults listed above (hbm_budget from the current device, or 0
@@ -129,6 +135,11 @@ sgp_status sgp_server_stats(const sgp_server* srv, long long id, sgp_request_sta
  * requests (as accounted against the budget), and the largest batch seen so far. */
 sgp_status sgp_server_info(const sgp_server* srv, int* queued, int* active,
                            unsigned long long* bytes_in_use, int* peak_active);
+
+/* Resident lattices kept for reuse (lattice_key) and their device bytes (counted in
+ * bytes_in_use of sgp_server_info). */
+sgp_status sgp_server_cache_info(const sgp_server* srv, int* lattices,
+                                 unsigned long long* bytes);
 
 /* Microseconds since the server was created (steady clock). */
 double sgp_server_clock_us(const sgp_server* srv);

@@ -49,7 +49,8 @@ class sgp_request(ctypes.Structure):
                 ("lengthscales", ctypes.c_void_p), ("outputscale", ctypes.c_float),
                 ("noise", ctypes.c_float), ("seed", ctypes.c_ulonglong),
                 ("mean", ctypes.c_void_p), ("var", ctypes.c_void_p),
-                ("arrival_us", ctypes.c_double), ("timeout_us", ctypes.c_double)]
+                ("arrival_us", ctypes.c_double), ("timeout_us", ctypes.c_double),
+                ("lattice_key", ctypes.c_ulonglong)]
 
 
 class sgp_request_stats(ctypes.Structure):
@@ -57,7 +58,7 @@ class sgp_request_stats(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("arrival_us", ctypes.c_double),
                 ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
                 ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong),
-                ("setup_us", ctypes.c_double)]
+                ("setup_us", ctypes.c_double), ("lattice_reused", ctypes.c_int)]
 
 
 class SGPError(RuntimeError):
@@ -120,6 +121,7 @@ def load():
         "sgp_server_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I),
                                 ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(I)]),
         "sgp_server_clock_us": (Dbl, [P]),
+        "sgp_server_cache_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_ulonglong)]),
         "sgp_server_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():

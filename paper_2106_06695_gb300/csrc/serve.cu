@@ -701,6 +701,7 @@ struct Request {
   bool waited = false;     // the lane's stream has waited for `ready`
   int64_t vb[U_KINDS] = {};
   Lane* lane = nullptr;
+  bool from_cache = false;  // R->L is a resident lattice owned by the server's cache
   std::vector<void*> ptrs;
 };
 
@@ -742,6 +743,17 @@ struct sgp_server {
   std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv;
+  // Resident lattices for reuse (sgp_request.lattice_key).  Set-up threads take an idle
+  // one (busy = true) under mu; the stepping thread inserts, returns and evicts.
+  struct Cached {
+    Lattice* L = nullptr;
+    unsigned long long bytes = 0;
+    float outputscale = 0.f;
+    bool busy = false;
+    double last_us = 0.0;
+  };
+  std::map<unsigned long long, Cached> cache;                // guarded by mu
+  unsigned long long cache_bytes = 0;                         // stepping thread
   std::deque<Request*> to_setup;                              // guarded by mu
   std::vector<std::pair<Request*, sgp_status>> setup_done;    // guarded by mu
   bool stop = false;                                          // guarded by mu
@@ -833,6 +845,16 @@ int lane_key(const sgp_server* S, const Lattice* L) {
 void release(sgp_server* S, Request* R, cudaStream_t st) {
   for (void* p : R->ptrs) (void)cudaFreeAsync(p, st);
   R->ptrs.clear();
+  if (R->from_cache) {  // hand the resident lattice back
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->cache.find(R->in.lattice_key);
+    if (it != S->cache.end()) {
+      it->second.busy = false;
+      it->second.last_us = now_us(S);
+    }
+    R->L = nullptr;
+    R->from_cache = false;
+  }
   if (R->L) {
     sgp_set_stream(R->L, st);
     sgp_lattice_free(R->L);
@@ -869,29 +891,45 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
       return e;
     }
   } tmp{st, {}};
-  float *Xd = nullptr, *lsd = nullptr, *yd = nullptr;
-  SRV_CHECK(tmp.get((void**)&Xd, (size_t)n_all * d * sizeof(float)), "alloc X");
-  SRV_CHECK(tmp.get((void**)&lsd, (size_t)d * sizeof(float)), "alloc ls");
+  float* yd = nullptr;
   SRV_CHECK(tmp.get((void**)&yd, (size_t)in.n * sizeof(float)), "alloc y");
-  SRV_CHECK(cudaMemcpyAsync(Xd, in.X, (size_t)in.n * d * sizeof(float), cudaMemcpyHostToDevice, st),
-            "copy X");
-  SRV_CHECK(cudaMemcpyAsync(Xd + in.n * d, in.Xs, (size_t)in.ns * d * sizeof(float),
-                            cudaMemcpyHostToDevice, st),
-            "copy Xs");
-  SRV_CHECK(cudaMemcpyAsync(lsd, in.lengthscales, d * sizeof(float), cudaMemcpyHostToDevice, st),
-            "copy ls");
   SRV_CHECK(cudaMemcpyAsync(yd, in.y, (size_t)in.n * sizeof(float), cudaMemcpyHostToDevice, st),
             "copy y");
-  sgp_opts lo;
-  sgp_opts_init(&lo);
-  lo.order_r = S->o.order_r;
-  lo.kernel = S->o.kernel;
-  lo.spacing_s = S->o.spacing_s;
-  lo.outputscale = in.outputscale;
-  lo.value_dtype = S->o.value_dtype;
-  lo.stream = st;
-  sgp_status s = sgp_lattice_build(Xd, lsd, n_all, d, &lo, &R->L);
-  if (s != SGP_OK) return s;
+  if (in.lattice_key) {  // a resident lattice of the same points, if idle
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->cache.find(in.lattice_key);
+    if (it != S->cache.end() && !it->second.busy && it->second.L->n == n_all &&
+        it->second.L->d == d && it->second.outputscale == in.outputscale) {
+      it->second.busy = true;
+      R->L = it->second.L;
+      R->from_cache = true;
+      R->st.lattice_reused = 1;
+    }
+  }
+  sgp_status s = SGP_OK;
+  if (!R->from_cache) {
+    float *Xd = nullptr, *lsd = nullptr;
+    SRV_CHECK(tmp.get((void**)&Xd, (size_t)n_all * d * sizeof(float)), "alloc X");
+    SRV_CHECK(tmp.get((void**)&lsd, (size_t)d * sizeof(float)), "alloc ls");
+    SRV_CHECK(cudaMemcpyAsync(Xd, in.X, (size_t)in.n * d * sizeof(float), cudaMemcpyHostToDevice,
+                              st),
+              "copy X");
+    SRV_CHECK(cudaMemcpyAsync(Xd + in.n * d, in.Xs, (size_t)in.ns * d * sizeof(float),
+                              cudaMemcpyHostToDevice, st),
+              "copy Xs");
+    SRV_CHECK(cudaMemcpyAsync(lsd, in.lengthscales, d * sizeof(float), cudaMemcpyHostToDevice, st),
+              "copy ls");
+    sgp_opts lo;
+    sgp_opts_init(&lo);
+    lo.order_r = S->o.order_r;
+    lo.kernel = S->o.kernel;
+    lo.spacing_s = S->o.spacing_s;
+    lo.outputscale = in.outputscale;
+    lo.value_dtype = S->o.value_dtype;
+    lo.stream = st;
+    s = sgp_lattice_build(Xd, lsd, n_all, d, &lo, &R->L);
+    if (s != SGP_OK) return s;
+  }
   Lattice* L = R->L;
   R->st.m = L->m;
   s = ensure_lattice_values(L, kp, st);
@@ -931,7 +969,8 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   SRV_CHECK(cudaGetLastError(), "request set-up");
   SRV_CHECK(cudaEventCreateWithFlags(&R->ready, cudaEventDisableTiming), "event");
   SRV_CHECK(cudaEventRecord(R->ready, st), "record");
-  R->held = L->bytes + 6 * vec + (size_t)R->vb[U_VEC] * kp * sizeof(double) +
+  // a resident lattice's bytes are counted by the cache, not by the request
+  R->held = (R->from_cache ? 0 : L->bytes) + 6 * vec + (size_t)R->vb[U_VEC] * kp * sizeof(double) +
             2 * (size_t)in.ns * sizeof(float) + sizeof(Table);
   return SGP_OK;
 }
@@ -977,8 +1016,46 @@ sgp_status finish(sgp_server* S, Request* R, cudaStream_t st) {
   R->st.status = SGP_OK;
   R->st.done_us = now_us(S);
   R->st.done = 1;
+  if (in.lattice_key && !R->from_cache) {  // keep the lattice resident for reuse
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->cache.find(in.lattice_key) == S->cache.end()) {
+      sgp_server::Cached c;
+      c.L = L;
+      c.bytes = L->bytes;
+      c.outputscale = in.outputscale;
+      c.last_us = now_us(S);
+      S->cache[in.lattice_key] = c;
+      S->cache_bytes += c.bytes;
+      // the lattice's bytes stay in in_use, now counted by the cache rather than the request
+      R->held -= std::min<unsigned long long>(R->held, c.bytes);
+      R->L = nullptr;
+    }
+  }
   release(S, R, st);
   return SGP_OK;
+}
+
+// Free the least recently used idle resident lattice; false when none is idle.
+bool evict_one(sgp_server* S, unsigned long long keep_key) {
+  Lattice* victim = nullptr;
+  unsigned long long bytes = 0;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto best = S->cache.end();
+    for (auto it = S->cache.begin(); it != S->cache.end(); ++it)
+      if (!it->second.busy && it->first != keep_key &&
+          (best == S->cache.end() || it->second.last_us < best->second.last_us))
+        best = it;
+    if (best == S->cache.end()) return false;
+    victim = best->second.L;
+    bytes = best->second.bytes;
+    S->cache.erase(best);
+  }
+  S->cache_bytes -= bytes;
+  S->in_use -= bytes;
+  sgp_set_stream(victim, S->bs);
+  sgp_lattice_free(victim);
+  return true;
 }
 
 template <int Rr, class Sv>
@@ -1139,6 +1216,8 @@ sgp_status admit(sgp_server* S) {
   }
   while (!S->queue.empty() && S->n_active < S->o.max_active) {
     Request* R = S->queue.front();
+    while (S->in_use + R->bound > S->o.hbm_budget && evict_one(S, R->in.lattice_key)) {
+    }
     if (S->in_use + R->bound > S->o.hbm_budget) break;  // strict arrival order
     S->queue.pop_front();
     R->st.admit_us = now_us(S);
@@ -1431,6 +1510,17 @@ sgp_status sgp_server_info(const sgp_server* S, int* queued, int* active,
   return SGP_OK;
 }
 
+sgp_status sgp_server_cache_info(const sgp_server* S, int* lattices, unsigned long long* bytes) {
+  if (!S) {
+    set_error("sgp_server_cache_info: null server");
+    return SGP_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(const_cast<sgp_server*>(S)->mu);
+  if (lattices) *lattices = (int)S->cache.size();
+  if (bytes) *bytes = S->cache_bytes;
+  return SGP_OK;
+}
+
 double sgp_server_clock_us(const sgp_server* S) { return S ? now_us(S) : 0.0; }
 
 void sgp_server_destroy(sgp_server* S) {
@@ -1457,6 +1547,11 @@ void sgp_server_destroy(sgp_server* S) {
   }
   S->queue.clear();
   for (auto& kv : S->lanes) destroy_lane(kv.second.get());
+  for (auto& kv : S->cache) {
+    sgp_set_stream(kv.second.L, S->bs);
+    sgp_lattice_free(kv.second.L);
+  }
+  S->cache.clear();
   cudaStreamSynchronize(S->bs);
   cudaStreamDestroy(S->bs);
   delete S;

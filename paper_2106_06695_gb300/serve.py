@@ -77,7 +77,7 @@ class Server:
     # -- requests ---------------------------------------------------------------------
     def submit(self, X, y, Xs, lengthscales, outputscale: float = 1.0, noise: float = 0.01,
                seed: int = 0, arrival_us: float | None = None,
-               timeout_s: float | None = None) -> int:
+               timeout_s: float | None = None, lattice_key: int = 0) -> int:
         X = _host_f32(X, "X", 2)
         Xs = _host_f32(Xs, "Xs", 2)
         y = _host_f32(y, "y", 1)
@@ -93,6 +93,7 @@ class Server:
         r.mean, r.var = mean.ctypes.data, var.ctypes.data
         r.arrival_us = -1.0 if arrival_us is None else float(arrival_us)
         r.timeout_us = 0.0 if timeout_s is None else 1e6 * float(timeout_s)
+        r.lattice_key = int(lattice_key)
         rid = ctypes.c_longlong()
         check(self._lib.sgp_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
         self._keep[rid.value] = (X, y, Xs, ls, mean, var)
@@ -124,6 +125,11 @@ class Server:
                                         ctypes.byref(b), ctypes.byref(peak)))
         return {"queued": q.value, "active": a.value, "bytes_in_use": b.value,
                 "peak_active": peak.value}
+
+    def cache_info(self) -> dict:
+        n, b = ctypes.c_int(), ctypes.c_ulonglong()
+        check(self._lib.sgp_server_cache_info(self._h, ctypes.byref(n), ctypes.byref(b)))
+        return {"lattices": n.value, "bytes": b.value}
 
     def clock_us(self) -> float:
         return float(self._lib.sgp_server_clock_us(self._h))
@@ -174,7 +180,8 @@ def run_stream(server, requests, sleep=time.sleep) -> StreamResult:
             r = reqs[i]
             ids.append(server.submit(r["X"], r["y"], r["Xs"], r["lengthscales"],
                                      r.get("outputscale", 1.0), r.get("noise", 0.01),
-                                     r.get("seed", 0), t0 + 1e6 * r["arrival_s"]))
+                                     r.get("seed", 0), t0 + 1e6 * r["arrival_s"],
+                                     lattice_key=r.get("lattice_key", 0)))
             i += 1
         info = server.info()
         if info["queued"] + info["active"] > 0:

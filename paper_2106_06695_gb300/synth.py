@@ -102,3 +102,23 @@ def serving_stream(count: int, seed: int, rate_per_s: float = 50.0,
                         lengthscales=np.ones(d, np.float32), outputscale=1.0, noise=noise,
                         seed=rs))
     return out
+
+
+def repeated_stream(count: int, datasets: int, seed: int, rate_per_s: float = 50.0,
+                    n_range=(5_000, 500_000), dims=(3, 8, 20, 50, 90),
+                    test_points: int = 256, noise: float = 0.01):
+    """Requests that reuse `datasets` point sets: each request takes one of them
+    (round-robin over a seeded shuffle) with its own targets (regression_targets with the
+    request's seed) and Poisson arrivals.  Each dict also carries "dataset" (0-based)."""
+    base = serving_stream(datasets, seed, rate_per_s, n_range, dims, test_points, noise)
+    rng = np.random.default_rng(seed + 49979687)
+    gaps = rng.exponential(1.0 / rate_per_s, count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    order = rng.permutation(count) % datasets
+    out = []
+    for i in range(count):
+        b = base[int(order[i])]
+        rs = seed * 1000003 + 500009 + i
+        out.append(dict(b, arrival_s=float(arrivals[i]), y=regression_targets(b["X"], rs),
+                        seed=rs, dataset=int(order[i])))
+    return out

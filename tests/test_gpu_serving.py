@@ -160,3 +160,37 @@ def test_bad_requests_are_rejected():
     with Server(max_active=2, hbm_budget=1 << 20) as srv:
         with pytest.raises(SGPError):
             srv.submit(r["X"], r["y"], r["Xs"], r["lengthscales"])
+
+
+def test_resident_lattice_is_reused_and_evicted_within_the_budget():
+    r = small_requests(1, seed=51, n_range=(3000, 4000), dims=(8,))[0]
+    y2 = synth.regression_targets(r["X"], 99)
+    sub = lambda srv, y, key: srv.submit(r["X"], y, r["Xs"], r["lengthscales"],  # noqa: E731
+                                         seed=r["seed"], lattice_key=key)
+    with Server(max_active=2) as srv:
+        a = sub(srv, r["y"], 7)
+        srv.run_until_idle()
+        b = sub(srv, y2, 7)
+        srv.run_until_idle()
+        assert srv.stats(a)["lattice_reused"] == 0 and srv.stats(b)["lattice_reused"] == 1
+        assert srv.cache_info()["lattices"] == 1 and srv.cache_info()["bytes"] > 0
+        mean_b, var_b = (x.copy() for x in srv.result(b))
+    with Server(max_active=2) as fresh:  # the same request without reuse: the same result
+        c = sub(fresh, y2, 0)
+        fresh.run_until_idle()
+        assert np.array_equal(fresh.result(c)[0], mean_b)
+        assert np.array_equal(fresh.result(c)[1], var_b)
+        assert fresh.cache_info()["lattices"] == 0
+    # a budget for about one request: a second key evicts the first lattice
+    other = small_requests(1, seed=52, n_range=(3000, 4000), dims=(8,))[0]
+    bound = max(request_bytes_bound(len(x["X"]) + len(x["Xs"]), 8, k=9) for x in (r, other))
+    with Server(max_active=1, hbm_budget=int(1.2 * bound)) as srv:
+        sub(srv, r["y"], 1)
+        srv.run_until_idle()
+        srv.submit(other["X"], other["y"], other["Xs"], other["lengthscales"], lattice_key=2)
+        srv.run_until_idle()
+        assert srv.cache_info()["lattices"] == 1
+        again = sub(srv, r["y"], 1)
+        srv.run_until_idle()
+        assert srv.stats(again)["lattice_reused"] == 0 and srv.stats(again)["status"] == 0
+        assert srv.info()["bytes_in_use"] <= int(1.2 * bound)

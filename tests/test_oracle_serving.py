@@ -87,7 +87,7 @@ class FakeServer:
     def clock_us(self):
         return self.t * 1e6
 
-    def submit(self, X, y, Xs, ls, outputscale, noise, seed, arrival_us):
+    def submit(self, X, y, Xs, ls, outputscale, noise, seed, arrival_us, lattice_key=0):
         rid = self.next
         self.next += 1
         self.st[rid] = dict(arrival_us=arrival_us, done_us=None, iters=0, done=0)
