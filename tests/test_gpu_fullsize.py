@@ -1,7 +1,8 @@
 """GPU parity at the benchmark's full sizes, in the launch configuration bench.py times.
 
 n = 2,000,000, d = 11 (the bench workload): the lattice is compared bit-exactly with the
-oracle's, and the MVM on 20,000 seeded rows of the oracle's full FP64 MVM.
+oracle's, and the MVM (fp32 values, and BF16 values with its error stated) on 20,000
+seeded rows of the oracle's full FP64 MVM.
 n = 200,000, d = 11, k = 9 (y plus 8 Rademacher probes, noise 0.01, tol 1e-3): the
 residual the solver reports is the true residual of its answer, evaluated with the
 oracle's FP64 operator; unpreconditioned CG does not reach 1e-3 within 500 iterations
@@ -55,6 +56,23 @@ def test_fullsize_mvm_sampled_rows(bench_workload, blur, mode):
     want = ref.mvm(V.astype(np.float64), mode=mode)[rows]
     rel = np.linalg.norm(out[rows] - want) / np.linalg.norm(want)
     assert rel <= 1e-5
+
+
+def test_fullsize_bf16_values_error_on_sampled_rows(bench_workload):
+    """Precision workload: n = 2M, d = 11, k = 16 with the lattice values stored in BF16
+    (fp32 sums): error against the FP64 oracle on 20,000 seeded rows (stated, bounded)."""
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    W, X, _, ref = bench_workload
+    ls = np.full(W["d"], W["lengthscale"], np.float32)
+    lat = Lattice(gpu(X), gpu(ls), order=W["order"], kernel=W["kernel"], value_dtype="bf16")
+    V = synth.gaussian_values(W["n"], W["k"], W["seed"])
+    out = lat.mvm(gpu(V), blur="symmetric").cpu().numpy()
+    rows = synth.subsample(W["n"], 20000, W["seed"])
+    want = ref.mvm(V.astype(np.float64), mode=2)[rows]
+    rel = np.linalg.norm(out[rows] - want) / np.linalg.norm(want)
+    print("n=2M d=11 k=16 bf16 values: rel L2 error %.2e on 20,000 rows" % rel)
+    assert 1e-6 < rel <= 1e-2
 
 
 @pytest.fixture(scope="module")
