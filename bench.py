@@ -503,6 +503,16 @@ def run_serving(count: int):
             file=sys.stderr, flush=True)
     same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
                for a, b in zip(results["batched"], results["plain"]))
+    # the same stream with the lattice values stored in BF16 (batched)
+    with Server(max_active=SERVING["max_active"], value_dtype="bf16") as srv:
+        res = run_stream(srv, reqs)
+        bf = [tuple(a.copy() for a in srv.result(i)) for i in res.ids]
+    errs = [np.linalg.norm(b[0] - a[0]) / max(np.linalg.norm(a[0]), 1e-30)
+            for a, b in zip(results["batched"], bf)]
+    out["batched_bf16"] = {"solves_per_s": res.solves_per_s, "p50_s": res.percentile(50),
+                           "p99_s": res.percentile(99),
+                           "mean_rel_l2_vs_fp32_median": float(np.median(errs)),
+                           "mean_rel_l2_vs_fp32_max": float(np.max(errs))}
     # repeated solves on resident lattices: 64 requests over 8 point sets, with and
     # without lattice keys (batched server both times)
     rep = synth.repeated_stream(64, 8, SERVING["seed"] + 1, rate_per_s=SERVING["rate_per_s"],
