@@ -76,7 +76,7 @@ def parse_args(argv=None):
     ap.add_argument("--serving-requests", type=int, default=SERVING["requests"],
                     help="requests in the serving stream (0 = skip the serving comparison)")
     ap.add_argument("--no-backward", action="store_true",
-                    help="skip the forward + backward timing at n=500k, d=20")
+                    help="skip the backward (n=500k, d=20) and log-det (n=200k) timings")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
                     help="profiling aid: build once, run R symmetric MVMs, print their time")
     return ap.parse_args(argv)
@@ -357,6 +357,7 @@ def run_ours(args, world, rank, local):
                "d2h_bytes_per_step": int(n * k * 4)}
 
     backward = run_backward_c3() if rank == 0 and not args.no_backward else None
+    logdet = run_logdet_c2() if rank == 0 and not args.no_backward else None
 
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -395,7 +396,7 @@ def run_ours(args, world, rank, local):
                              "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-            "backward": backward,
+            "backward": backward, "logdet": logdet,
             "gpu_launches": int(launches), "clocks": clk.summary(),
         "cg_final_rel_res_max": float(np.max(rel)), "cg_true_rel_res_max": true_rel,
         }
@@ -463,11 +464,39 @@ def run_backward_c3():
     bwd = timed(lambda: lat.mvm_backward(Xd, ld, Vd, Gd, blur="symmetric"))
     bwd_f = timed(lambda: lat.mvm_backward(Xd, ld, Vd, Gd, blur="symmetric", grad="filter"))
     res = {"workload": "n=%d d=%d k=%d correlated Gaussian, ARD lengthscales, symmetric blur"
-                       % (n, d, k), "m": lat.m, "forward_ms": fwd,
-           "backward_lattice_ms": bwd, "backward_filter_ms": bwd_f,
+                       % (n, d, k), "m": lat.m, "sparse_blur": lat.sparse_blur,
+           "forward_ms": fwd, "backward_lattice_ms": bwd, "backward_filter_ms": bwd_f,
+           "backward_over_forward": bwd / fwd,
            "forward_backward_mpoint_s": n / ((fwd + bwd) / 1e3) / 1e6}
     lat.close()
     return res
+
+
+def run_logdet_c2():
+    """log det(K~ + noise I) by stochastic Lanczos quadrature on n = 200,000, d = 11 (the
+    GMM solve workload, noise 0.01): 8 Rademacher probes, 100 Lanczos steps (App. A),
+    median of 3 after a warm-up; Mpoint/s counts n x Lanczos steps x probes / time."""
+    import torch
+
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    n, d, probes, steps = 200_000, 11, 8, 100
+    X = torch.from_numpy(synth.gmm_points(n, d, 2)).cuda()
+    Z = torch.from_numpy(synth.rademacher(n, probes, 2)).cuda()
+    lat = Lattice(X, 1.0)
+    lat.logdet(Z, noise=0.01, max_lanczos=steps, tol=0.0)
+    ts, est = [], None
+    for _ in range(3):
+        t0 = time.perf_counter()
+        est, quad = lat.logdet(Z, noise=0.01, max_lanczos=steps, tol=0.0)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.median(ts))
+    lat.close()
+    return {"workload": "n=%d d=%d, %d probes, %d Lanczos steps, noise 0.01"
+                        % (n, d, probes, steps), "ms": 1e3 * t, "logdet": est,
+            "probe_quadrature_sd": float(np.std(quad, ddof=1)),
+            "mpoint_s": n * steps / t / 1e6}
 
 
 # ---------------------------------------------------------------------------------------
