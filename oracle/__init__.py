@@ -9,11 +9,15 @@ from .oracle import (  # noqa: F401
     MATERN32_COVERAGE,
     RBF_BINOMIAL,
     RBF_COVERAGE,
+    PRECOND_SEED_XOR,
     build_oracle,
+    condition_estimate,
     dense_rbf,
     elevate,
     gp_posterior,
     lanczos_quadrature,
+    nystrom_apply,
+    nystrom_factor,
     rademacher_sketch,
     splitmix64,
     simplex,

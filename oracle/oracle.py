@@ -269,66 +269,25 @@ class OracleLattice:
 
     def nystrom(self, rank: int, noise: float, seed: int = 0, outputscale: float = 1.0,
                 mode: int = 2):
-        """Rank-l randomized Nystrom factor B of A = outputscale K~ (App. A: preconditioner
-        rank), built from products with A only: Y = A Omega + nu Omega (nu = 1e-3 noise),
-        C = Omega^T Y = R R^T, B = Y R^-T.  Returns B and the lower Cholesky factor Q of
-        noise I + B^T B; P = B B^T + noise I."""
-        from scipy.linalg import cholesky, solve_triangular
-
-        om = rademacher_sketch(self.n, rank, seed)
-        Y = self.mvm(om, mode=mode, alpha=outputscale) + 1e-3 * noise * om
-        C = om.T @ Y
-        R = cholesky(0.5 * (C + C.T), lower=True)
-        Bm = solve_triangular(R, Y.T, lower=True).T
-        Q = cholesky(noise * np.eye(rank) + Bm.T @ Bm, lower=True)
-        return Bm, Q
+        """nystrom_factor of A = outputscale K~ on this lattice (App. A: preconditioner
+        rank).  Returns B and the lower Cholesky factor Q of noise I + B^T B."""
+        return nystrom_factor(lambda V: self.mvm(V, mode=mode, alpha=outputscale), self.n,
+                              rank, noise, seed)
 
     @staticmethod
     def nystrom_apply(Bm, Q, noise: float, r):
         """P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise (Woodbury)."""
-        from scipy.linalg import cho_solve
-
-        return (r - Bm @ cho_solve((Q, True), Bm.T @ r)) / noise
+        return nystrom_apply(Bm, Q, noise, r)
 
     def pcg(self, B, noise: float, rank: int, tol: float = 1e-3, max_iter: int = 500,
             seed: int = 0, outputscale: float = 1.0, mode: int = 2):
         """Preconditioned CG (P = B B^T + noise I from nystrom) on (outputscale K~ + noise I)
         X = B, every column independent, stopping on ||r|| / ||b|| <= tol."""
         B2, shape = self._as2d(B)
-        n, k = B2.shape
         Bm, Q = self.nystrom(rank, noise, seed, outputscale, mode)
-        X = np.zeros_like(B2)
-        r = B2.copy()
-        z = self.nystrom_apply(Bm, Q, noise, r)
-        p = z.copy()
-        rho = (r * z).sum(0)
-        bnorm = np.linalg.norm(B2, axis=0)
-        active = bnorm > 0
-        rel = np.where(active, 1.0, 0.0)
-        iters = np.zeros(k, np.int32)
-        for _ in range(max_iter):
-            if not active.any():
-                break
-            q = self.mvm(p, mode=mode, alpha=outputscale, beta=noise)
-            pq = (p * q).sum(0)
-            for c in np.nonzero(active)[0]:
-                if not pq[c] > 0:
-                    active[c] = False
-                    continue
-                a = rho[c] / pq[c]
-                X[:, c] += a * p[:, c]
-                r[:, c] -= a * q[:, c]
-                iters[c] += 1
-                rel[c] = np.linalg.norm(r[:, c]) / bnorm[c]
-                if rel[c] <= tol or iters[c] >= max_iter:
-                    active[c] = False
-            if not active.any():
-                break
-            z = self.nystrom_apply(Bm, Q, noise, r)
-            rz = (r * z).sum(0)
-            for c in np.nonzero(active)[0]:
-                p[:, c] = z[:, c] + (rz[c] / rho[c]) * p[:, c]
-                rho[c] = rz[c]
+        X, iters, rel = _pcg_columns(
+            lambda P: self.mvm(P, mode=mode, alpha=outputscale, beta=noise), B2,
+            lambda R: nystrom_apply(Bm, Q, noise, R), tol, max_iter)
         return X.reshape(shape), iters, rel
 
     def logdet(self, Z, noise: float, outputscale: float = 1.0, max_lanczos: int = 100,
@@ -351,6 +310,72 @@ class OracleLattice:
         if rc != 0:
             raise ValueError("orc_cg: invalid arguments")
         return X.reshape(shape), iters, rel
+
+
+def nystrom_factor(apply_K, n: int, rank: int, noise: float, seed: int = 0):
+    """Rank-l randomized Nystrom factor B of a symmetric positive semi-definite A (App. A:
+    CG preconditioner of rank 100), built from products with A only: Omega = the n x l
+    rademacher_sketch(n, l, seed), Y = A Omega + nu Omega (nu = 1e-3 noise keeps C
+    positive definite when A Omega is rank deficient), C = Omega^T Y = R R^T,
+    B = Y R^-T, so that B B^T = Y C^-1 Y^T.  apply_K maps an [n][c] array to A times it.
+    Returns B and the lower Cholesky factor Q of noise I + B^T B; the preconditioner is
+    P = B B^T + noise I."""
+    from scipy.linalg import cholesky, solve_triangular
+
+    om = rademacher_sketch(n, rank, seed)
+    Y = apply_K(om) + 1e-3 * noise * om
+    C = om.T @ Y
+    R = cholesky(0.5 * (C + C.T), lower=True)
+    Bm = solve_triangular(R, Y.T, lower=True).T
+    Q = cholesky(noise * np.eye(rank) + Bm.T @ Bm, lower=True)
+    return Bm, Q
+
+
+def nystrom_apply(Bm, Q, noise: float, r):
+    """P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise (Woodbury identity)."""
+    from scipy.linalg import cho_solve
+
+    return (r - Bm @ cho_solve((Q, True), Bm.T @ r)) / noise
+
+
+def _pcg_columns(apply_A, B, apply_Pinv, tol: float, max_iter: int):
+    """Preconditioned CG, one independent iteration per column of B: x_0 = 0, r_0 = b,
+    z_0 = P^-1 r_0, p_0 = z_0; each step alpha = <r, z> / <p, A p>, x += alpha p,
+    r -= alpha A p; a column stops when ||r|| / ||b|| <= tol (the unpreconditioned
+    residual) or after max_iter iterations; otherwise z = P^-1 r, beta = <r, z>_new /
+    <r, z>_old, p = z + beta p.  b = 0 gives x = 0."""
+    n, k = B.shape
+    X = np.zeros((n, k))
+    r = np.array(B, np.float64, copy=True)
+    z = apply_Pinv(r)
+    p = z.copy()
+    rho = (r * z).sum(0)
+    bnorm = np.linalg.norm(B, axis=0)
+    active = (bnorm > 0) & (1.0 > tol) & (max_iter > 0)
+    rel = np.where(bnorm > 0, 1.0, 0.0)
+    iters = np.zeros(k, np.int32)
+    while active.any():
+        q = apply_A(p)
+        pq = (p * q).sum(0)
+        for c in np.nonzero(active)[0]:
+            if not pq[c] > 0:
+                active[c] = False
+                continue
+            a = rho[c] / pq[c]
+            X[:, c] += a * p[:, c]
+            r[:, c] -= a * q[:, c]
+            iters[c] += 1
+            rel[c] = np.linalg.norm(r[:, c]) / bnorm[c]
+            if rel[c] <= tol or iters[c] >= max_iter:
+                active[c] = False
+        if not active.any():
+            break
+        z = apply_Pinv(r)
+        rz = (r * z).sum(0)
+        for c in np.nonzero(active)[0]:
+            p[:, c] = z[:, c] + (rz[c] / rho[c]) * p[:, c]
+            rho[c] = rz[c]
+    return X, iters, rel
 
 
 def _cg_columns(apply_A, B, tol: float, max_iter: int, history=None):
@@ -422,9 +447,12 @@ def lanczos_quadrature(apply_A, Z, max_iter: int = 100, tol: float = 0.0):
     return float(quads.mean()), quads
 
 
+PRECOND_SEED_XOR = 0x6A09E667F3BCC909  # sketch seed of a request = its seed XOR this
+
+
 def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: int = 8,
                  seed: int = 0, tol: float = 1e-3, max_iter: int = 500,
-                 kind: int = RBF_BINOMIAL, r: int = 1, Z=None):
+                 kind: int = RBF_BINOMIAL, r: int = 1, Z=None, precond_rank: int = 0):
     """Posterior mean and probe-estimated variance at the test inputs Xs.
 
     Eq. gp_pred_mean with a zero prior mean: mean = K*X (K_XX + noise I)^-1 y, and the
@@ -436,7 +464,9 @@ def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: i
     built over the joint point set [X; Xs]: K_XX, KX* and K*X are its blocks.  Default
     probes: Z[t][s] from rademacher_sketch(ns, probes, seed).  Returns (mean, var,
     iterations per column, final relative residual per column); column 0 is y, columns
-    1..S the probes.
+    1..S the probes.  precond_rank = l > 0 solves with _pcg_columns and the nystrom_factor
+    of the training block outputscale K~_XX (App. A), its sketch over the n training rows
+    drawn with seed XOR PRECOND_SEED_XOR.
     """
     X = np.asarray(X, np.float32)
     Xs = np.asarray(Xs, np.float32)
@@ -458,11 +488,37 @@ def gp_posterior(X, y, Xs, ls, noise: float, outputscale: float = 1.0, probes: i
         Vz = np.zeros((n + ns, S))
         Vz[n:] = Z
         B = np.concatenate([B, K(Vz)[:n]], 1)
-    W, iters, rel = _cg_columns(lambda V: K(pad(V))[:n] + noise * V, B, tol, max_iter)
+    def A(V):  # (outputscale K~ + noise I) on the training rows
+        return K(pad(V))[:n] + noise * V
+
+    if precond_rank > 0:
+        Bm, Q = nystrom_factor(lambda V: K(pad(V))[:n], n, precond_rank, noise,
+                               int(seed) ^ PRECOND_SEED_XOR)
+        W, iters, rel = _pcg_columns(A, B, lambda R: nystrom_apply(Bm, Q, noise, R), tol,
+                                     max_iter)
+    else:
+        W, iters, rel = _cg_columns(A, B, tol, max_iter)
     P = K(pad(W))[n:]
     mean = P[:, 0]
     var = outputscale - (Z * P[:, 1:]).mean(1) if S > 0 else np.zeros(ns)
     return mean, var, iters, rel
+
+
+def condition_estimate(X, Xs, ls, noise: float, outputscale: float = 1.0,
+                       kind: int = RBF_BINOMIAL, r: int = 1) -> float:
+    """Upper estimate of the condition number of A = outputscale K~_XX + noise I (the
+    training block of the joint lattice operator): K~ has non-negative entries, so by
+    Gershgorin's theorem its largest eigenvalue is at most its largest row sum, and the
+    smallest eigenvalue of A is at least noise; returns
+    (outputscale max_i (K~_XX 1)_i + noise) / noise."""
+    X = np.asarray(X, np.float32)
+    Xs = np.asarray(Xs, np.float32)
+    n, ns = X.shape[0], Xs.shape[0]
+    L = OracleLattice(np.vstack([X, Xs]), ls, kind=kind, r=r)
+    ones = np.zeros((n + ns, 1))
+    ones[:n] = 1.0
+    rows = L.mvm(ones, mode=2, alpha=outputscale)[:n, 0]
+    return float((rows.max() + noise) / noise)
 
 
 def filter_gradient(apply_K, X, ls, V, G, alpha: float = 1.0, kprime_ratio: float = -0.5):

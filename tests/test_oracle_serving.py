@@ -11,7 +11,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import OracleLattice, gp_posterior, rademacher_sketch
+from oracle import OracleLattice, condition_estimate, gp_posterior, rademacher_sketch
 from paper_2106_06695_gb300 import synth
 from paper_2106_06695_gb300.serve import run_stream
 
@@ -27,15 +27,17 @@ def all_sign_patterns(ns):
     return np.array(list(itertools.product([-1.0, 1.0], repeat=ns))).T  # [ns][2^ns]
 
 
-@pytest.mark.parametrize("d,outputscale,noise", [(2, 1.0, 0.01), (3, 2.5, 0.1), (5, 0.7, 0.05)])
-def test_posterior_equals_dense_solve_with_exhaustive_probes(d, outputscale, noise):
+@pytest.mark.parametrize("d,outputscale,noise,rank", [(2, 1.0, 0.01, 0), (3, 2.5, 0.1, 0),
+                                                     (5, 0.7, 0.05, 0), (2, 1.0, 0.01, 12),
+                                                     (3, 2.5, 0.1, 25)])
+def test_posterior_equals_dense_solve_with_exhaustive_probes(d, outputscale, noise, rank):
     P = synth.gmm_points(63, d, 3 + d)
     X, Xs = P[:60], P[60:]
     y = synth.regression_targets(X, 7)
     ls = np.full(d, 0.9, np.float32)
     Z = all_sign_patterns(3)
     mean, var, iters, rel = gp_posterior(X, y, Xs, ls, noise, outputscale=outputscale, Z=Z,
-                                         tol=1e-13, max_iter=2000)
+                                         tol=1e-13, max_iter=2000, precond_rank=rank)
     Kd = dense_joint_cov(X, Xs, ls, outputscale)
     A = Kd[:60, :60] + noise * np.eye(60)
     mean_exact = Kd[60:, :60] @ np.linalg.solve(A, y.astype(np.float64))
@@ -64,6 +66,48 @@ def test_probe_estimate_with_random_probes_is_the_sign_weighted_diagonal():
     M = Kd[60:, :60] @ np.linalg.solve(Kd[:60, :60] + noise * np.eye(60), Kd[:60, 60:])
     want = 1.0 - ((M @ Z) * Z).mean(1)
     assert np.abs(var - want).max() <= 1e-8
+
+
+def test_preconditioner_cuts_iterations_on_an_ill_conditioned_request():
+    """d = 2, 400 points on a coarse lattice, noise 1e-3: the training block has a few
+    large eigenvalues (many points per vertex).  The rank-40 preconditioner (App. A)
+    takes far fewer iterations to the same posterior; a wrong sign or a dropped factor
+    in the Woodbury apply would make it slower or stall."""
+    P = synth.gmm_points(416, 2, 17)
+    X, Xs = P[:400], P[400:]
+    y = synth.regression_targets(X, 3)
+    ls = np.full(2, 1.5, np.float32)
+    kw = dict(probes=4, seed=9, tol=1e-8, max_iter=3000)
+    m0, v0, i0, _ = gp_posterior(X, y, Xs, ls, 1e-3, **kw)
+    m1, v1, i1, r1 = gp_posterior(X, y, Xs, ls, 1e-3, precond_rank=40, **kw)
+    assert (r1 <= 1e-8).all()
+    assert i1.max() * 3 <= i0.max(), (i0, i1)
+    assert np.abs(m1 - m0).max() <= 1e-5 * np.abs(m0).max()
+    assert np.abs(v1 - v0).max() <= 1e-5
+
+
+@pytest.mark.parametrize("d,ls,noise", [(2, 1.0, 0.01), (3, 0.5, 0.1), (8, 1.0, 0.01)])
+def test_condition_estimate_bounds_the_condition_number(d, ls, noise):
+    """Gershgorin: the estimate is at least the exact condition number of the training
+    block outputscale K~_XX + noise I, and the mean row sum (a lower bound of the largest
+    eigenvalue of a non-negative symmetric matrix, Rayleigh quotient of the ones vector)
+    keeps it within a factor of the truth."""
+    P = synth.gmm_points(90, d, 23 + d)
+    X, Xs = P[:80], P[80:]
+    lsv = np.full(d, ls, np.float32)
+    os_ = 1.7
+    est = condition_estimate(X, Xs, lsv, noise, outputscale=os_)
+    Kd = dense_joint_cov(X, Xs, lsv, os_)[:80, :80]
+    assert (Kd >= -1e-15).all()
+    ev = np.linalg.eigvalsh(Kd + noise * np.eye(80))
+    kappa = ev[-1] / ev[0]
+    assert kappa <= est * (1 + 1e-12)
+    mean_row = (Kd.sum(1).mean() + noise) / noise
+    assert mean_row <= ev[-1] / noise * (1 + 1e-12)
+    rows = Kd.sum(1)
+    assert est == pytest.approx((rows.max() + noise) / noise, rel=1e-12)
+    # the largest row sum is within the spread max/mean of the largest eigenvalue
+    assert rows.max() <= rows.max() / rows.mean() * ev[-1] * (1 + 1e-12)
 
 
 def test_zero_targets_give_zero_mean_and_no_probes_give_zero_var():
