@@ -17,6 +17,20 @@
  * batched CG as in sgp_cg_solve (double-float iterate and residual, fp64 dot products,
  * per-column stopping ||r|| / ||b|| <= tol or max_iter iterations).
  *
+ * Preconditioning (App. A: CG preconditioner of rank 100): the set-up computes the
+ * condition estimate kappa = (outputscale max_i (K~_XX 1)_i + noise) / noise (Gershgorin:
+ * K~ has non-negative entries, so its largest eigenvalue is at most its largest row sum;
+ * one extra column of the probe product).  When precond_rank > 0 and kappa >=
+ * precond_min_kappa, the request's CG is preconditioned with P = B B^T + noise I, the
+ * rank-l randomized Nystrom approximation of outputscale K~_XX (l = min(precond_rank,
+ * n)): Omega n x l Rademacher over the training points (Omega[i][j] = sign bit of
+ * SplitMix64 at counter i l + j + 1, seed = request seed XOR 0x6A09E667F3BCC909), Y =
+ * A Omega + 1e-3 noise Omega, Omega^T Y = R R^T, B = Y R^-T, and P^-1 r = (r - B (noise I
+ * + B^T B)^-1 B^T r) / noise.  The stopping rule stays on the unpreconditioned residual.
+ * Smooth kernels over many points per lattice vertex (low d, long lengthscales, small
+ * noise) give kappa in the 10^4..10^6 range, where plain CG stalls; isolated points (high
+ * d) give kappa near 1 / noise and converge in a few plain iterations.
+ *
  * Continuous batching: requests are admitted in arrival order while the number of active
  * requests is below max_active and the device bytes they may hold stay within
  * hbm_budget (an upper bound per request from sgp_request_bytes_bound until its lattice
@@ -51,7 +65,7 @@ typedef struct {
   unsigned long long hbm_budget; /* device bytes the active requests may hold; default
                                     half of the device's total memory                    */
   int max_active;     /* requests in the batch at once, 1..64; default 16 (1 = plain)     */
-  int probes;         /* Rademacher probes S of the variance estimate, 0..31; default 8   */
+  int probes;         /* Rademacher probes S of the variance estimate, 0..30; default 8   */
   int order_r;        /* stencil order (as sgp_opts); default 1                           */
   int kernel;         /* SGP_KERNEL_*; default SGP_KERNEL_RBF_BINOMIAL                    */
   double spacing_s;   /* > 0 overrides the kernel rule's spacing; default 0               */
@@ -59,6 +73,10 @@ typedef struct {
   double tol;         /* CG tolerance on ||r|| / ||b||; default 1e-3                      */
   int max_iter;       /* CG iteration cap; default 500                                    */
   int check_every;    /* CG iterations per sgp_server_step between flag reads; default 8 */
+  int precond_rank;   /* rank l of the Nystrom preconditioner, 0..128 (0 = none); default
+                         100 (App. A)                                                     */
+  double precond_min_kappa; /* precondition requests whose condition estimate kappa is at
+                         least this; default 1e3 (0 = every request)                      */
 } sgp_server_opts;
 
 typedef struct {
@@ -97,6 +115,8 @@ typedef struct {
   double setup_us;           /* host time of its set-up (upload, lattice build, right-hand
                                 sides) on a set-up thread                                 */
   int lattice_reused;        /* 1 when it ran on a resident lattice (lattice_key)         */
+  int precond_rank;          /* rank of its preconditioner (0: plain CG)                  */
+  double kappa_est;          /* its condition estimate (0 when precond_rank option is 0)  */
 } sgp_request_stats;
 
 /* Fill *opts with the defaults listed above (hbm_budget from the current device, or 0
@@ -105,10 +125,12 @@ void sgp_server_opts_init(sgp_server_opts* opts);
 
 /* Upper bound of the device bytes one request holds at its peak (lattice build work
  * space included) for n_points = n + ns points in d dimensions, stencil order r, k
- * right-hand sides and the value type: every size taken at its bound m = n_points
- * (d + 1) (Sec. 5.2: at most d + 1 vertices per point).  Host only. */
+ * columns (the server uses k = 1 + probes + 1: y, the probes and the row-sum column),
+ * the value type and the preconditioner rank (0..128; its factor, apply buffers and
+ * factorisation scratch): every size taken at its bound m = n_points (d + 1) (Sec. 5.2:
+ * at most d + 1 vertices per point).  0 for invalid arguments.  Host only. */
 unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_r, int k,
-                                           int value_dtype);
+                                           int value_dtype, int precond_rank);
 
 /* Create a server on the current device (its own CUDA streams).  opts may be NULL. */
 sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out);

@@ -40,7 +40,8 @@ class sgp_server_opts(ctypes.Structure):
                 ("probes", ctypes.c_int), ("order_r", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("spacing_s", ctypes.c_double), ("value_dtype", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("precond_rank", ctypes.c_int),
+                ("precond_min_kappa", ctypes.c_double)]
 
 
 class sgp_request(ctypes.Structure):
@@ -58,7 +59,8 @@ class sgp_request_stats(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("arrival_us", ctypes.c_double),
                 ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
                 ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong),
-                ("setup_us", ctypes.c_double), ("lattice_reused", ctypes.c_int)]
+                ("setup_us", ctypes.c_double), ("lattice_reused", ctypes.c_int),
+                ("precond_rank", ctypes.c_int), ("kappa_est", ctypes.c_double)]
 
 
 class SGPError(RuntimeError):
@@ -112,7 +114,7 @@ def load():
         "sgp_last_error": (ctypes.c_char_p, []),
         "sgp_version": (I, []),
         "sgp_server_opts_init": (None, [ctypes.POINTER(sgp_server_opts)]),
-        "sgp_request_bytes_bound": (ctypes.c_ulonglong, [ctypes.c_longlong, I, I, I, I]),
+        "sgp_request_bytes_bound": (ctypes.c_ulonglong, [ctypes.c_longlong, I, I, I, I, I]),
         "sgp_server_create": (I, [ctypes.POINTER(sgp_server_opts), ctypes.POINTER(P)]),
         "sgp_server_submit": (I, [P, ctypes.POINTER(sgp_request),
                                   ctypes.POINTER(ctypes.c_longlong)]),

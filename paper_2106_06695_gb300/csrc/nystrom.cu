@@ -114,13 +114,27 @@ __global__ void k_sum_blocks(const double* __restrict__ partial, int nblk, int c
   out[e] = t;
 }
 
-// In-place lower Cholesky of the l x l fp64 matrix A (+ shift on the diagonal), one block;
-// the strict upper triangle is zeroed.  *status = 1 when a pivot is not positive.
-__global__ void k_cholesky(double* __restrict__ A, int l, double shift, int* __restrict__ status) {
-  __shared__ double piv;
+// In-place lower Cholesky of the symmetric part (A + A^T) / 2 of the l x l fp64 matrix A,
+// plus shift + rel_shift max_j A[j][j] on the diagonal; one block.  The strict upper
+// triangle is zeroed.  *status = 1 when a pivot is not positive.
+__global__ void k_cholesky(double* __restrict__ A, int l, double shift, double rel_shift,
+                           int* __restrict__ status) {
+  __shared__ double piv, dmax;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e % l;
-    if (i == j) A[e] += shift;
+    if (i > j) A[e] = 0.5 * (A[e] + A[j * l + i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int j = 0; j < l; ++j) m = fmax(m, A[j * l + j]);
+    dmax = m;
+  }
+  __syncthreads();
+  const double sh = shift + rel_shift * dmax;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    if (i == j) A[e] += sh;
     if (j > i) A[e] = 0.0;
   }
   __syncthreads();
@@ -346,6 +360,58 @@ __global__ void __launch_bounds__(kZThreads) k_apply_z(const float* __restrict__
   }
 }
 
+// Masked sketch columns [c0, c0 + kp) in locality order: V[p][c] = Omega[perm[p]][c0 + c]
+// on training rows (perm[p] < n_train) and columns c0 + c < l, else 0.
+__global__ void k_fill_sketch_chunk(const int32_t* __restrict__ perm, int64_t n, int64_t n_train,
+                                    int l, int c0, int kp, uint64_t seed, float* __restrict__ V) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * kp) return;
+  const int64_t p = e / kp;
+  const int c = (int)(e - p * kp);
+  const int32_t i = perm[p];
+  V[e] = (i < n_train && c0 + c < l) ? rademacher(seed, i, c0 + c, l) : 0.f;
+}
+
+// Y[p][c0 + c] = KV[p][c] + nu Omega[perm[p]][c0 + c] on training rows, 0 on masked rows;
+// the last chunk also zeroes the padding columns l..ld-1.
+__global__ void k_gather_chunk(const int32_t* __restrict__ perm, int64_t n, int64_t n_train,
+                               int l, int ld, int c0, int kp, uint64_t seed, float nu,
+                               const float* __restrict__ KV, float* __restrict__ Y) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * kp) return;
+  const int64_t p = e / kp;
+  const int c = (int)(e - p * kp);
+  const int j = c0 + c;
+  if (j >= ld) return;
+  const int32_t i = perm[p];
+  float y = 0.f;
+  if (j < l && i < n_train) y = fmaf(nu, rademacher(seed, i, j, l), KV[e]);
+  Y[p * ld + j] = y;
+}
+
+// In place, row by row: Y[row][0..l) = Y[row][0..l) T (T in shared memory).  Each block
+// stages its rows before it writes any of them, and no other block touches those rows.
+__global__ void k_rows_times_inplace(float* Y, const float* __restrict__ T, int64_t n, int l,
+                                     int ld) {
+  extern __shared__ float sh[];
+  float* ts = sh;              // [l][l]
+  float* ys = sh + l * l;      // [rows_per_block][l]
+  const int rows = blockDim.x / l;  // blockDim.x = rows * l
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) ts[e] = T[e];
+  const int rr = threadIdx.x / l, c = threadIdx.x - rr * l;
+  for (int64_t base = (int64_t)blockIdx.x * rows; base < n; base += (int64_t)gridDim.x * rows) {
+    __syncthreads();
+    const int64_t row = base + rr;
+    if (rr < rows && row < n) ys[rr * l + c] = Y[row * ld + c];
+    __syncthreads();
+    if (rr < rows && row < n) {
+      float a = 0.f;
+      for (int j = 0; j < l; ++j) a = fmaf(ys[rr * l + j], ts[j * l + c], a);
+      Y[row * ld + c] = a;
+    }
+  }
+}
+
 }  // namespace
 
 sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int blur,
@@ -414,7 +480,7 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
   const size_t gram_smem = 2 * (size_t)kRowsPerStage * l * sizeof(float);
   k_gram<true, float><<<kTallBlocks, 256, gram_smem, st>>>(Y, l, L->perm, n, l, seed, partial);
   k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, C);
-  k_cholesky<<<1, 1024, 0, st>>>(C, l, 0.0, status);
+  k_cholesky<<<1, 1024, 0, st>>>(C, l, 0.0, 0.0, status);
   // B = Y R^-T
   k_tri_inv_t<<<1, 128, 0, st>>>(C, l, work, T);
   const int rows = std::max(1, 1024 / l);
@@ -425,7 +491,7 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
   k_gram<false, float><<<kTallBlocks, 256, gram_smem, st>>>((const float*)Bh, ld, L->perm, n, l,
                                                             seed, partial);
   k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, Q);
-  k_cholesky<<<1, 1024, 0, st>>>(Q, l, (double)noise, status);
+  k_cholesky<<<1, 1024, 0, st>>>(Q, l, (double)noise, 0.0, status);
   k_inv_from_cholesky<<<1, 128, 0, st>>>(Q, l, work, Minv);
   note_launches(9);
   NY_CHECK(cudaGetLastError(), "building the Nystrom preconditioner");
@@ -453,6 +519,77 @@ void Nystrom::apply(const float* rh, const float* rl, int k, float* z, double* d
                                                                1.f / noise, n, k, c_off, z,
                                                                dot_partial);
   note_launches(2 + 2 * ceil_div(k, 16));
+}
+
+// Blocks of the masked build's tall products: one per 1024 rows, at most kTallBlocks.
+static int masked_tall_blocks(int64_t n) {
+  return (int)std::min<int64_t>(kTallBlocks, std::max<int64_t>(1, ceil_div(n, 1024)));
+}
+
+size_t nystrom_masked_scratch_bytes(int l, int64_t n) {
+  const size_t ll = (size_t)l * l;
+  // partial [tall blocks][l][l], C, Q, work (fp64); T (fp32)
+  return ((size_t)masked_tall_blocks(n) * ll + 3 * ll) * sizeof(double) + ll * sizeof(float) +
+         1024;
+}
+
+sgp_status nystrom_build_masked(Lattice* L, int64_t n_train, int l, int ld, uint64_t seed,
+                                float noise, int kp, float* V, float* KV, float* Bh,
+                                double* Minv, void* scratch, int* status_dev, cudaStream_t st) {
+  const int64_t n = L->n;
+  const size_t ll = (size_t)l * l;
+  const int tall = masked_tall_blocks(n);
+  double* partial = static_cast<double*>(scratch);
+  double* C = partial + (size_t)tall * ll;
+  double* Q = C + ll;
+  double* work = Q + ll;
+  float* T = reinterpret_cast<float*>(work + ll);
+  {  // shared-memory sizes beyond the 48 KB default, once per device
+    static bool attrs[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    if (dev >= 0 && dev < 64 && !attrs[dev]) {
+      const int big = 200 * 1024;
+      cudaFuncSetAttribute(k_gram<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_gram<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      cudaFuncSetAttribute(k_rows_times_inplace, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+      attrs[dev] = true;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_status(e, "clear Nystrom status");
+  // Y = A Omega + nu Omega, kp sketch columns per lattice product, written into Bh
+  const float nu = 1e-3f * noise;
+  const unsigned g = (unsigned)ceil_div(n * kp, 256);
+  for (int c0 = 0; c0 < ld; c0 += kp) {
+    k_fill_sketch_chunk<<<g, 256, 0, st>>>(L->perm, n, n_train, l, c0, kp, seed, V);
+    enqueue_mvm(L, V, kp, SGP_BLUR_SYMMETRIC, L->outputscale, 0.f, KV, st, nullptr,
+                /*internal=*/true);
+    k_gather_chunk<<<g, 256, 0, st>>>(L->perm, n, n_train, l, ld, c0, kp, seed, nu, KV, Bh);
+    note_launches(2);
+  }
+  // C = Omega^T Y (masked rows of Y are zero), Cholesky C = R R^T, B = Y R^-T in place
+  const size_t gram_smem = 2 * (size_t)kRowsPerStage * l * sizeof(float);
+  k_gram<true, float><<<tall, 256, gram_smem, st>>>(Bh, ld, L->perm, n, l, seed, partial);
+  k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, tall, l * l, C);
+  // BF16 lattice values perturb A Omega by ~2^-8 relative: a relative diagonal shift keeps
+  // C positive definite (any shift leaves P = B B^T + noise I positive definite)
+  const double rel = L->value_dtype == SGP_VALUES_BF16 ? 1e-2 : 0.0;
+  k_cholesky<<<1, 1024, 0, st>>>(C, l, 0.0, rel, status_dev);
+  k_tri_inv_t<<<1, 128, 0, st>>>(C, l, work, T);
+  const int rows = std::max(1, 1024 / l);
+  const size_t rt_smem = ((size_t)l * l + (size_t)rows * l) * sizeof(float);
+  k_rows_times_inplace<<<tall, rows * l, rt_smem, st>>>(Bh, T, n, l, ld);
+  // M = noise I + B^T B from the stored B, Cholesky M = Q Q^T, Minv = M^-1
+  k_gram<false, float><<<tall, 256, gram_smem, st>>>(Bh, ld, L->perm, n, l, seed, partial);
+  k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, tall, l * l, Q);
+  k_cholesky<<<1, 1024, 0, st>>>(Q, l, (double)noise, 0.0, status_dev);
+  k_inv_from_cholesky<<<1, 128, 0, st>>>(Q, l, work, Minv);
+  note_launches(9);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "building the masked Nystrom factor");
+  return SGP_OK;
 }
 
 void Nystrom::release(cudaStream_t st) {

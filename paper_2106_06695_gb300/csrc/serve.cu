@@ -46,8 +46,12 @@ constexpr int kST = 256;            // threads of the table-driven kernels
 constexpr int kGrid = 4 * 152;      // their fixed grid (4 blocks per SM)
 constexpr int kBlurU = 2;           // blur rows per thread
 constexpr int kVecRows = 4;         // vector-kernel rows per thread
+constexpr int kMaxLd = kMaxRank;    // preconditioner: B row stride bound
+constexpr int kBtVbRows = 512;      // rows of one B^T r virtual block (64 per warp)
+constexpr int kBtSeg = 16;          // B^T r partials per first-level sum
+constexpr uint64_t kPrecondSeedXor = 0x6A09E667F3BCC909ull;  // sketch seed = seed ^ this
 
-enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_KINDS };
+enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_BT, U_BTS, U_BTT, U_MINV, U_KINDS };
 
 // One active request as the kernels see it.  Row-indexed arrays are in the lattice's
 // locality order p; perm[p] < n_train marks a training row.
@@ -83,6 +87,16 @@ struct SlotDev {
   int32_t* epoch;
   void* stmp;
   const float* g0pow;
+  // rank-l Nystrom preconditioner (l = 0: plain CG): P = B B^T + noise I
+  int l, ld;
+  float inv_noise;
+  const float* Bh;      // [n][ld] fp32, locality order, zero at test rows
+  const double* Minv;   // [l][l] (noise I + B^T B)^-1
+  float* btpart;        // [U_BT virtual blocks][ld][kp] fp32 partials of B^T r
+  float* bt2;           // [segments][ld][kp] sums of kBtSeg partials
+  double* tvec;         // [ld][kp] B^T r
+  float* u;             // [ld][kp] Minv B^T r (rows >= l zero)
+  double* dpart2;       // [U_VEC virtual blocks][kp] partials of <r, z>
 };
 
 struct Table {
@@ -142,20 +156,25 @@ __device__ __forceinline__ void vb_column_sums(const dfloat (&d)[4], int kp, dou
   __syncthreads();
 }
 
-// Column c's total over a request's nvb virtual-block partials (fixed order).
-__device__ __forceinline__ double slot_col_total(const double* part, int64_t nvb, int kp, int c,
-                                                 double* red) {
-  double t = 0.0;
-  for (int64_t b = threadIdx.x; b < nvb; b += blockDim.x) t += part[b * kp + c];
-  red[threadIdx.x] = t;
+// Totals of all kp columns over a request's nvb virtual-block partials part[b][c], in one
+// coalesced pass: thread t < R kp (R = kST / kp) owns column t % kp and the blocks
+// t / kp, t / kp + R, ... (summed in order), then thread c < kp adds the R sums of its
+// column in order.  out (shared, kp entries); uniform call, trailing barrier.
+__device__ __forceinline__ void slot_cols_total(const double* part, int64_t nvb, int kp,
+                                                double* red, double* out) {
+  const int R = kST / kp;
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  if (t < R * kp)
+    for (int64_t b = t / kp; b < nvb; b += R) acc += part[b * kp + t % kp];
+  red[t] = acc;
   __syncthreads();
-  for (int half = blockDim.x / 2; half >= 1; half /= 2) {
-    if ((int)threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
-    __syncthreads();
+  if (t < kp) {
+    double v = 0.0;
+    for (int r = 0; r < R; ++r) v += red[r * kp + t];
+    out[t] = v;
   }
-  const double r = red[0];
   __syncthreads();
-  return r;
 }
 
 __device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 y) {
@@ -411,23 +430,23 @@ __global__ void __launch_bounds__(kST) kb_slice_dot(const Table* __restrict__ T)
 
 // alpha = rho / <p, A p> per active column (a non-positive <p, A p> stops the column).
 __global__ void __launch_bounds__(kST) kb_alpha(const Table* __restrict__ T) {
-  __shared__ double red[kST];
+  __shared__ double red[kST], tot[kMaxServeK];
   const int q = blockIdx.x;
   if (q >= T->nslots) return;
   const SlotDev& s = T->s[q];
   if (*s.state == 0) return;
   const int kp = T->kp;
   const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
-  for (int c = 0; c < kp; ++c) {
-    const double pap = slot_col_total(s.dpart, nvb, kp, c, red);
-    if (threadIdx.x == 0) {
-      double a = 0.0;
-      if (s.active[c]) {
-        if (pap > 0.0 && isfinite(pap)) a = s.rho[c] / pap;
-        else s.active[c] = 0;
-      }
-      s.alpha[c] = a;
+  slot_cols_total(s.dpart, nvb, kp, red, tot);
+  const int c = threadIdx.x;
+  if (c < kp) {
+    const double pap = tot[c];
+    double a = 0.0;
+    if (s.active[c]) {
+      if (pap > 0.0 && isfinite(pap)) a = s.rho[c] / pap;
+      else s.active[c] = 0;
     }
+    s.alpha[c] = a;
   }
 }
 
@@ -488,7 +507,7 @@ __global__ void __launch_bounds__(kST) kb_update_xr(const Table* __restrict__ T)
 // Convergence check and beta = <r, r>_new / <r, r>_old per active column; the request
 // stops when no column is active.  Its state is copied to the host-read flags.
 __global__ void __launch_bounds__(kST) kb_check_beta(const Table* __restrict__ T) {
-  __shared__ double red[kST];
+  __shared__ double red[kST], trr[kMaxServeK], trz[kMaxServeK];
   const int q = blockIdx.x;
   if (q >= T->nslots) return;
   const SlotDev& s = T->s[q];
@@ -502,21 +521,24 @@ __global__ void __launch_bounds__(kST) kb_check_beta(const Table* __restrict__ T
   const int kp = T->kp;
   const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
   const int it = s.state[1] + 1;
-  int any = 0;
-  for (int c = 0; c < kp; ++c) {
-    const double rr = slot_col_total(s.dpart, nvb, kp, c, red);
-    if (threadIdx.x == 0 && s.active[c]) {
-      const double rel = sqrt(rr) / s.bnorm[c];
-      s.relres[c] = rel;
-      if (rel <= (double)s.tol || it >= s.max_iter || !isfinite(rel)) {
-        s.active[c] = 0;
-      } else {
-        s.beta[c] = rr / s.rho[c];
-        s.rho[c] = rr;
-        any = 1;
-      }
+  slot_cols_total(s.dpart, nvb, kp, red, trr);
+  // preconditioned: beta = <r, z>_new / <r, z>_old; the stopping rule stays on ||r||
+  if (s.l) slot_cols_total(s.dpart2, nvb, kp, red, trz);
+  const int c = threadIdx.x;
+  int go = 0;
+  if (c < kp && s.active[c]) {
+    const double rr = trr[c], rz = s.l ? trz[c] : rr;
+    const double rel = sqrt(rr) / s.bnorm[c];
+    s.relres[c] = rel;
+    if (rel <= (double)s.tol || it >= s.max_iter || !isfinite(rel)) {
+      s.active[c] = 0;
+    } else {
+      s.beta[c] = rz / s.rho[c];
+      s.rho[c] = rz;
+      go = 1;
     }
   }
+  const int any = __syncthreads_or(go);
   if (threadIdx.x == 0) {
     s.state[1] = it;
     s.state[0] = any;
@@ -525,12 +547,14 @@ __global__ void __launch_bounds__(kST) kb_check_beta(const Table* __restrict__ T
   }
 }
 
-// p = r + beta p on active columns (double-float sum rounded to fp32).
+// p = r + beta p on active columns (double-float sum rounded to fp32); p = z + beta p for
+// preconditioned requests (z in ap).
 __global__ void __launch_bounds__(kST) kb_update_p(const Table* __restrict__ T) {
   const int kp = T->kp, G = kp / 4, groups = kST / G;
   const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
   SLOT_LOOP(U_VEC)
   if (*s.state == 0 || g >= groups) continue;
+  const bool pre = s.l > 0;
   bool on[4];
   dfloat b[4];
 #pragma unroll
@@ -543,7 +567,8 @@ __global__ void __launch_bounds__(kST) kb_update_p(const Table* __restrict__ T) 
     if (row >= s.n) break;
     const int64_t e = row * kp + col;
     float4 p4 = f4_ld(s.p + e);
-    const float4 rh = f4_ld(s.rh + e), rl = f4_ld(s.rl + e);
+    const float4 rh = pre ? f4_ld(s.ap + e) : f4_ld(s.rh + e);
+    const float4 rl = pre ? make_float4(0.f, 0.f, 0.f, 0.f) : f4_ld(s.rl + e);
     float* pv = reinterpret_cast<float*>(&p4);
     const float* rhv = reinterpret_cast<const float*>(&rh);
     const float* rlv = reinterpret_cast<const float*>(&rl);
@@ -556,6 +581,175 @@ __global__ void __launch_bounds__(kST) kb_update_p(const Table* __restrict__ T) 
     }
     f4_st(s.p + e, p4);
   }
+  SLOT_LOOP_END
+}
+
+// ---- preconditioner apply z = P^-1 r (requests with l > 0) ----------------------------
+// P^-1 r = (r - B Minv B^T r) / noise (Woodbury), in four table-driven steps.
+
+// Per-virtual-block partial of B^T r (r = rh + rl): each warp takes 64 consecutive rows,
+// four per step; lane owns the B columns lane + 32 a (a < 4) against 16 columns of r at a
+// time (r broadcast by shuffles); fp32 sums, the warps added in a fixed order in shared
+// memory, and the block writes btpart[local][ld][kp].
+__global__ void __launch_bounds__(kST) kb_bt(const Table* __restrict__ T) {
+  __shared__ float red[kMaxLd * 16];
+  constexpr int kWarps = kST / 32, kWarpRows = kBtVbRows / kWarps, kStep = 4;
+  const int kp = T->kp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  SLOT_LOOP(U_BT)
+  if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
+  const int ld = s.ld;
+  const int64_t r0 = local * kBtVbRows + (int64_t)warp * kWarpRows;
+  const int64_t r1 = r0 + kWarpRows < s.n ? r0 + kWarpRows : s.n;
+  for (int c_off = 0; c_off < kp; c_off += 16) {
+    const int kc = kp - c_off < 16 ? kp - c_off : 16;
+    float acc[4][16];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
+    for (int64_t row0 = r0; row0 < r1; row0 += kStep) {
+      float b[kStep][4], rv[kStep];
+#pragma unroll
+      for (int q2 = 0; q2 < kStep; ++q2) {
+        const int64_t row = row0 + q2;
+        const bool in = row < r1;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int j = lane + 32 * a;
+          b[q2][a] = (in && j < ld) ? s.Bh[row * ld + j] : 0.f;
+        }
+        const int64_t e = row * kp + c_off + lane;
+        rv[q2] = (in && lane < kc) ? __fadd_rn(s.rh[e], s.rl[e]) : 0.f;
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < kStep; ++q2)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float rc = __shfl_sync(0xffffffffu, rv[q2], c);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) acc[a][c] = fmaf(b[q2][a], rc, acc[a][c]);
+        }
+    }
+    for (int w = 0; w < kWarps; ++w) {
+      if (warp == w)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int j = lane + 32 * a;
+          if (j < ld)
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              red[j * 16 + c] = (w == 0 ? 0.f : red[j * 16 + c]) + acc[a][c];
+        }
+      __syncthreads();
+    }
+    for (int o = threadIdx.x; o < ld * kc; o += kST) {
+      const int j = o / kc, c = o - j * kc;
+      s.btpart[(local * ld + j) * kp + c_off + c] = red[j * 16 + c];
+    }
+    __syncthreads();
+  }
+  SLOT_LOOP_END
+}
+
+// First-level sums of the B^T r partials: virtual block (segment g, chunk h) adds the
+// partials g kBtSeg .. g kBtSeg + kBtSeg - 1 of outputs h kST .. h kST + kST - 1 in order.
+__global__ void __launch_bounds__(kST) kb_bt_seg(const Table* __restrict__ T) {
+  const int kp = T->kp;
+  SLOT_LOOP(U_BTS)
+  if (*s.state == 0 || s.l == 0) continue;
+  const int cnt = s.ld * kp;
+  const int nch = (cnt + kST - 1) / kST;
+  const int64_t g = local / nch;
+  const int o = (int)(local - g * nch) * kST + threadIdx.x;
+  if (o >= cnt) continue;
+  const int64_t nvb = T->pre[U_BT][q + 1] - T->pre[U_BT][q];
+  const int64_t b0 = g * kBtSeg, b1 = b0 + kBtSeg < nvb ? b0 + kBtSeg : nvb;
+  float t = 0.f;
+  for (int64_t b = b0; b < b1; ++b) t += s.btpart[b * cnt + o];
+  s.bt2[g * cnt + o] = t;
+  SLOT_LOOP_END
+}
+
+// t = B^T r: the segment sums added in order in fp64, one output per thread.
+__global__ void __launch_bounds__(kST) kb_bt_total(const Table* __restrict__ T) {
+  const int kp = T->kp;
+  SLOT_LOOP(U_BTT)
+  if (*s.state == 0 || s.l == 0) continue;
+  const int cnt = s.ld * kp;
+  const int o = (int)local * kST + threadIdx.x;
+  if (o >= cnt) continue;
+  const int64_t nseg = ceil_div(T->pre[U_BT][q + 1] - T->pre[U_BT][q], kBtSeg);
+  double t = 0.0;
+  for (int64_t g = 0; g < nseg; ++g) t += (double)s.bt2[g * cnt + o];
+  s.tvec[o] = t;
+  SLOT_LOOP_END
+}
+
+// u = Minv t (fp64) on the first l rows, 0 below; stored fp32 [ld][kp].  Four lanes per
+// output, each a quarter of the dot product, combined by shuffles in a fixed order.
+__global__ void __launch_bounds__(kST) kb_minv(const Table* __restrict__ T) {
+  const int kp = T->kp;
+  SLOT_LOOP(U_MINV)
+  if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
+  const int o = (int)(local * kST + threadIdx.x) / 4, part = threadIdx.x & 3;
+  const int cnt = s.ld * kp;
+  const int j = o / kp, c = o - j * kp;
+  double a = 0.0;
+  if (o < cnt && j < s.l)
+    for (int i = part; i < s.l; i += 4) a += s.Minv[j * s.l + i] * s.tvec[i * kp + c];
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  a += __shfl_xor_sync(0xffffffffu, a, 2);
+  if (o < cnt && part == 0) s.u[o] = (float)a;
+  SLOT_LOOP_END
+}
+
+// z = (r - B u) / noise, written into ap (free between the x, r update and the next
+// product), and the virtual block's column sums of r z into dpart2, with the layout of the
+// other vector kernels (thread g, col: 4 columns of rows ... + g; u in shared memory; the
+// threads of one row read the same B row, a broadcast).  Test rows have zero B rows and
+// zero r, so z = 0 there.
+__global__ void __launch_bounds__(kST) kb_apply_z(const Table* __restrict__ T) {
+  __shared__ __align__(16) float us[kMaxLd * kMaxServeK];
+  __shared__ double sh[kST * 4];
+  const int kp = T->kp, G = kp / 4, groups = kST / G;
+  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  SLOT_LOOP(U_VEC)
+  if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
+  const int ld = s.ld;
+  __syncthreads();
+  for (int e = threadIdx.x; e < ld * kp; e += kST) us[e] = s.u[e];
+  __syncthreads();
+  dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (g < groups) {
+    for (int i = 0; i < kVecRows; ++i) {
+      const int64_t row = (local * kVecRows + i) * groups + g;
+      if (row >= s.n) break;
+      const float4* b4 = reinterpret_cast<const float4*>(s.Bh + row * ld);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q4 = 0; q4 < ld / 4; ++q4) {
+        const float4 bb = b4[q4];
+        const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float4 uu = *reinterpret_cast<const float4*>(us + (q4 * 4 + a) * kp + col);
+          acc = f4_fma(bv[a], uu, acc);
+        }
+      }
+      const int64_t e = row * kp + col;
+      const float4 rh = f4_ld(s.rh + e), rl = f4_ld(s.rl + e);
+      const float r0 = __fadd_rn(rh.x, rl.x), r1 = __fadd_rn(rh.y, rl.y);
+      const float r2 = __fadd_rn(rh.z, rl.z), r3 = __fadd_rn(rh.w, rl.w);
+      const float4 z = make_float4((r0 - acc.x) * s.inv_noise, (r1 - acc.y) * s.inv_noise,
+                                   (r2 - acc.z) * s.inv_noise, (r3 - acc.w) * s.inv_noise);
+      f4_st(s.ap + e, z);
+      d[0] = df_add(d[0], df_two_prod(r0, z.x));
+      d[1] = df_add(d[1], df_two_prod(r1, z.y));
+      d[2] = df_add(d[2], df_two_prod(r2, z.z));
+      d[3] = df_add(d[3], df_two_prod(r3, z.w));
+    }
+  }
+  vb_column_sums(d, kp, s.dpart2 + local * kp, sh);
   SLOT_LOOP_END
 }
 
@@ -583,40 +777,66 @@ __global__ void __launch_bounds__(kST) kb_norm(const Table* __restrict__ T) {
 }
 
 __global__ void __launch_bounds__(kST) kb_init_scalars(const Table* __restrict__ T) {
-  __shared__ double red[kST];
+  __shared__ double red[kST], trr[kMaxServeK], trz[kMaxServeK];
   const int q = blockIdx.x;
   if (q >= T->nslots) return;
   const SlotDev& s = T->s[q];
   const int kp = T->kp;
   const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
-  int any = 0;
-  for (int c = 0; c < kp; ++c) {
-    const double rr = slot_col_total(s.dpart, nvb, kp, c, red);
-    if (threadIdx.x == 0) {
-      s.rho[c] = rr;
-      s.bnorm[c] = sqrt(rr);
-      s.alpha[c] = 0.0;
-      s.beta[c] = 0.0;
-      const int on = (rr > 0.0 && 1.0 > (double)s.tol && s.max_iter > 0) ? 1 : 0;
-      s.relres[c] = rr > 0.0 ? 1.0 : 0.0;
-      s.active[c] = on;
-      any |= on;
-    }
+  slot_cols_total(s.dpart, nvb, kp, red, trr);
+  if (s.l) slot_cols_total(s.dpart2, nvb, kp, red, trz);
+  const int c = threadIdx.x;
+  int on = 0;
+  if (c < kp) {
+    const double rr = trr[c];
+    s.rho[c] = s.l ? trz[c] : rr;
+    s.bnorm[c] = sqrt(rr);
+    s.alpha[c] = 0.0;
+    s.beta[c] = 0.0;
+    on = (rr > 0.0 && 1.0 > (double)s.tol && s.max_iter > 0) ? 1 : 0;
+    s.relres[c] = rr > 0.0 ? 1.0 : 0.0;
+    s.active[c] = on;
   }
+  const int any = __syncthreads_or(on);
   if (threadIdx.x == 0) {
     s.state[0] = any;
     s.state[1] = 0;
   }
 }
 
-// Probe right-hand sides in the caller's order: column 1 + s of test row t holds z_s[t].
+// Probe right-hand sides in the caller's order: column 1 + s of test row t holds z_s[t];
+// the last column (kp - 1 > S) holds 1 on the training rows, for the row sums of K~_XX.
 __global__ void k_probe_fill(float* __restrict__ V, int64_t n_all, int64_t n_train, int kp,
                              int S, uint64_t seed) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_all * kp) return;
   const int64_t i = e / kp;
   const int c = (int)(e - i * kp);
-  V[e] = (i >= n_train && c >= 1 && c <= S) ? rademacher_pm(seed, i - n_train, c - 1, S) : 0.f;
+  float v = 0.f;
+  if (i >= n_train) {
+    if (c >= 1 && c <= S) v = rademacher_pm(seed, i - n_train, c - 1, S);
+  } else if (c == kp - 1) {
+    v = 1.f;
+  }
+  V[e] = v;
+}
+
+// Largest training-row sum max_i KZ[i][kp - 1] (i < n_train) of outputscale K~_XX; the
+// entries are non-negative, so the float bits order like the values (*out preset to 0).
+__global__ void k_rowsum_max(const float* __restrict__ KZ, int64_t n_train, int kp,
+                             int* __restrict__ out) {
+  __shared__ float red[256];
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_train;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, KZ[i * kp + kp - 1]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h >= 1; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, __float_as_int(fmaxf(red[0], 0.f)));
 }
 
 // b (locality order): training rows [y, (KX* z)_1..S, 0 ...], test rows 0; r = p = b,
@@ -702,6 +922,13 @@ struct Request {
   int64_t vb[U_KINDS] = {};
   Lane* lane = nullptr;
   bool from_cache = false;  // R->L is a resident lattice owned by the server's cache
+  // rank-l Nystrom preconditioner (l = 0: none) and the condition estimate behind it
+  int l = 0, ld = 0;
+  double kappa = 0.0;
+  float* Bh = nullptr;
+  double* Minv = nullptr;
+  float *btpart = nullptr, *bt2 = nullptr, *u = nullptr;
+  double *tvec = nullptr, *dpart2 = nullptr;
   std::vector<void*> ptrs;
 };
 
@@ -820,9 +1047,20 @@ void fill_slot(const sgp_server* S, const Request* R, SlotDev& s) {
   s.epoch = L->epoch;
   s.stmp = L->act_tmp;
   s.g0pow = L->g0pow;
+  s.l = R->l;
+  s.ld = R->ld;
+  s.inv_noise = 1.f / R->in.noise;
+  s.Bh = R->Bh;
+  s.Minv = R->Minv;
+  s.btpart = R->btpart;
+  s.bt2 = R->bt2;
+  s.tvec = R->tvec;
+  s.u = R->u;
+  s.dpart2 = R->dpart2;
 }
 
-void unit_counts(const sgp_server* S, const Lattice* L, int64_t (&vb)[U_KINDS]) {
+void unit_counts(const sgp_server* S, const Request* R, int64_t (&vb)[U_KINDS]) {
+  const Lattice* L = R->L;
   const int groups = groups_of(S->kp);
   vb[U_SPLAT] = ceil_div(L->nseg, groups);
   vb[U_MED] = ceil_div(L->nmed, groups);
@@ -830,14 +1068,20 @@ void unit_counts(const sgp_server* S, const Lattice* L, int64_t (&vb)[U_KINDS]) 
   vb[U_BLUR] = ceil_div(L->sparse ? L->act_max : L->m, (int64_t)groups * kBlurU);
   vb[U_VEC] = ceil_div(L->n, (int64_t)groups * kVecRows);
   vb[U_VERT] = L->sparse ? ceil_div(L->m, (int64_t)groups * kBlurU) : 0;
+  const int64_t nch = ceil_div((int64_t)R->ld * S->kp, kST);  // output chunks of B^T r
+  vb[U_BT] = R->l ? ceil_div(L->n, kBtVbRows) : 0;
+  vb[U_BTS] = R->l ? nch * ceil_div(vb[U_BT], kBtSeg) : 0;
+  vb[U_BTT] = R->l ? nch : 0;
+  vb[U_MINV] = R->l ? ceil_div((int64_t)R->ld * S->kp * 4, kST) : 0;
 }
 
-// Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur
-// and slice volume per iteration, classes a factor 8 apart).
-int lane_key(const sgp_server* S, const Lattice* L) {
+// Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur,
+// slice and preconditioner volume per iteration, classes a factor 8 apart).
+int lane_key(const sgp_server* S, const Request* R) {
+  const Lattice* L = R->L;
   int dclass = 0;
   while ((4 << dclass) < L->D) ++dclass;
-  const double work = ((double)L->m + (double)L->n) * L->D * S->kp;
+  const double work = ((double)L->m + (double)L->n) * L->D * S->kp + 2.0 * L->n * R->ld;
   const int wclass = std::max(0, (int)std::floor(std::log(std::max(work, 1.0)) / std::log(8.0)));
   return dclass * 64 + std::min(wclass, 63);
 }
@@ -934,7 +1178,8 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   R->st.m = L->m;
   s = ensure_lattice_values(L, kp, st);
   if (s != SGP_OK) return s;
-  unit_counts(S, L, R->vb);
+  R->l = R->ld = 0;
+  unit_counts(S, R, R->vb);
   const size_t vec = (size_t)n_all * kp * sizeof(float);
   float** vecs[6] = {&R->xh, &R->xl, &R->rh, &R->rl, &R->p, &R->ap};
   for (float** v : vecs) SRV_CHECK(get((void**)v, vec), "alloc CG vectors");
@@ -954,6 +1199,62 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   k_rhs<<<g, 256, 0, st>>>(L->perm, yd, KZ, n_all, in.n, kp, S->S, R->xh, R->xl, R->rh, R->rl,
                            R->p);
   note_launches(1);
+  // App. A preconditioner, for requests whose condition estimate (Gershgorin: largest
+  // training-row sum of outputscale K~ over noise) reaches precond_min_kappa
+  size_t pre_bytes = 0;
+  if (S->o.precond_rank > 0) {
+    int* rowmax_d = nullptr;
+    SRV_CHECK(tmp.get((void**)&rowmax_d, sizeof(int)), "alloc row sum");
+    SRV_CHECK(cudaMemsetAsync(rowmax_d, 0, sizeof(int), st), "clear row sum");
+    k_rowsum_max<<<152, 256, 0, st>>>(KZ, in.n, kp, rowmax_d);
+    note_launches(1);
+    int rowmax_bits = 0;
+    SRV_CHECK(cudaMemcpyAsync(&rowmax_bits, rowmax_d, sizeof(int), cudaMemcpyDeviceToHost, st),
+              "read row sum");
+    SRV_CHECK(cudaStreamSynchronize(st), "condition estimate");
+    float rowmax = 0.f;
+    std::memcpy(&rowmax, &rowmax_bits, sizeof(float));
+    R->kappa = ((double)rowmax + (double)in.noise) / (double)in.noise;
+    if (R->kappa >= S->o.precond_min_kappa) {
+      const int l = (int)std::min<long long>(S->o.precond_rank, in.n);
+      const int ld = (l + 3) / 4 * 4;
+      R->l = l;
+      R->ld = ld;
+      unit_counts(S, R, R->vb);
+      SRV_CHECK(get((void**)&R->Bh, (size_t)n_all * ld * sizeof(float)), "alloc Nystrom B");
+      SRV_CHECK(get((void**)&R->Minv, (size_t)l * l * sizeof(double)), "alloc Nystrom Minv");
+      const size_t nseg = (size_t)ceil_div(R->vb[U_BT], kBtSeg);
+      SRV_CHECK(get((void**)&R->btpart, (size_t)R->vb[U_BT] * ld * kp * sizeof(float)),
+                "alloc B^T r partials");
+      SRV_CHECK(get((void**)&R->bt2, nseg * ld * kp * sizeof(float)), "alloc B^T r sums");
+      SRV_CHECK(get((void**)&R->tvec, (size_t)ld * kp * sizeof(double)), "alloc B^T r");
+      SRV_CHECK(get((void**)&R->u, (size_t)ld * kp * sizeof(float)), "alloc Minv B^T r");
+      SRV_CHECK(get((void**)&R->dpart2, (size_t)R->vb[U_VEC] * kp * sizeof(double)),
+                "alloc <r, z> partials");
+      pre_bytes = (size_t)n_all * ld * sizeof(float) + (size_t)l * l * sizeof(double) +
+                  ((size_t)R->vb[U_BT] + nseg) * ld * kp * sizeof(float) +
+                  (size_t)ld * kp * (sizeof(double) + sizeof(float)) +
+                  (size_t)R->vb[U_VEC] * kp * sizeof(double);
+      void* scratch = nullptr;
+      int* status_d = nullptr;
+      SRV_CHECK(tmp.get(&scratch, nystrom_masked_scratch_bytes(l, n_all)),
+                "alloc Nystrom scratch");
+      SRV_CHECK(tmp.get((void**)&status_d, sizeof(int)), "alloc Nystrom status");
+      s = nystrom_build_masked(L, in.n, l, ld, in.seed ^ kPrecondSeedXor, in.noise, kp, Vz, KZ,
+                               R->Bh, R->Minv, scratch, status_d, st);
+      if (s != SGP_OK) return s;
+      int failed = 0;
+      SRV_CHECK(cudaMemcpyAsync(&failed, status_d, sizeof(int), cudaMemcpyDeviceToHost, st),
+                "read Nystrom status");
+      SRV_CHECK(cudaStreamSynchronize(st), "Nystrom factor");
+      if (failed) {  // a Cholesky pivot failed: plain CG (the buffers are released at the end)
+        R->l = R->ld = 0;
+        unit_counts(S, R, R->vb);
+      }
+    }
+  }
+  R->st.precond_rank = R->l;
+  R->st.kappa_est = R->kappa;
   // initial residual norms and scalars through a one-request table
   std::memset(&t1, 0, sizeof(Table));
   t1.nslots = 1;
@@ -964,14 +1265,28 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   SRV_CHECK(cudaMemcpyAsync(R->dtab1, &t1, sizeof(Table), cudaMemcpyHostToDevice, st),
             "copy table");
   kb_norm<<<kGrid, kST, 0, st>>>(R->dtab1);
+  note_launches(1);
+  if (R->l) {  // z_0 = P^-1 r_0 (the kernels run for a request whose state is set)
+    static const int kOne = 1;
+    SRV_CHECK(cudaMemcpyAsync(R->ints + kp, &kOne, sizeof(int), cudaMemcpyHostToDevice, st),
+              "mark the request active");
+    kb_bt<<<kGrid, kST, 0, st>>>(R->dtab1);
+    kb_bt_seg<<<kGrid, kST, 0, st>>>(R->dtab1);
+    kb_bt_total<<<kGrid, kST, 0, st>>>(R->dtab1);
+    kb_minv<<<kGrid, kST, 0, st>>>(R->dtab1);
+    kb_apply_z<<<kGrid, kST, 0, st>>>(R->dtab1);
+    note_launches(5);
+  }
   kb_init_scalars<<<1, kST, 0, st>>>(R->dtab1);
-  note_launches(2);
+  note_launches(1);
+  if (R->l)  // p_0 = z_0
+    SRV_CHECK(cudaMemcpyAsync(R->p, R->ap, vec, cudaMemcpyDeviceToDevice, st), "p = z");
   SRV_CHECK(cudaGetLastError(), "request set-up");
   SRV_CHECK(cudaEventCreateWithFlags(&R->ready, cudaEventDisableTiming), "event");
   SRV_CHECK(cudaEventRecord(R->ready, st), "record");
   // a resident lattice's bytes are counted by the cache, not by the request
   R->held = (R->from_cache ? 0 : L->bytes) + 6 * vec + (size_t)R->vb[U_VEC] * kp * sizeof(double) +
-            2 * (size_t)in.ns * sizeof(float) + sizeof(Table);
+            2 * (size_t)in.ns * sizeof(float) + sizeof(Table) + pre_bytes;
   return SGP_OK;
 }
 
@@ -1059,7 +1374,7 @@ bool evict_one(sgp_server* S, unsigned long long keep_key) {
 }
 
 template <int Rr, class Sv>
-int enqueue_iteration_t(Lane* ln, int dmax, bool sparse) {
+int enqueue_iteration_t(Lane* ln, int dmax, bool sparse, bool pre) {
   cudaStream_t st = ln->st;
   const Table* T = ln->dtab;
   kb_splat<Sv><<<kGrid, kST, 0, st>>>(T);
@@ -1073,24 +1388,37 @@ int enqueue_iteration_t(Lane* ln, int dmax, bool sparse) {
   kb_slice_dot<Sv><<<kGrid, kST, 0, st>>>(T);
   kb_alpha<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_xr<<<kGrid, kST, 0, st>>>(T);
+  if (pre) {
+    kb_bt<<<kGrid, kST, 0, st>>>(T);
+    kb_bt_seg<<<kGrid, kST, 0, st>>>(T);
+    kb_bt_total<<<kGrid, kST, 0, st>>>(T);
+    kb_minv<<<kGrid, kST, 0, st>>>(T);
+    kb_apply_z<<<kGrid, kST, 0, st>>>(T);
+  }
   kb_check_beta<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_p<<<kGrid, kST, 0, st>>>(T);
-  return 8 + 2 * dmax + (sparse ? 2 * dmax + 1 : 0);
+  return 8 + 2 * dmax + (sparse ? 2 * dmax + 1 : 0) + (pre ? 5 : 0);
 }
 
 template <class Sv>
-int enqueue_iteration_s(const sgp_server* S, Lane* ln, int dmax, bool sparse) {
+int enqueue_iteration_s(const sgp_server* S, Lane* ln, int dmax, bool sparse, bool pre) {
   switch (S->o.order_r) {
-    case 1: return enqueue_iteration_t<1, Sv>(ln, dmax, sparse);
-    case 2: return enqueue_iteration_t<2, Sv>(ln, dmax, sparse);
-    case 3: return enqueue_iteration_t<3, Sv>(ln, dmax, sparse);
-    default: return enqueue_iteration_t<4, Sv>(ln, dmax, sparse);
+    case 1: return enqueue_iteration_t<1, Sv>(ln, dmax, sparse, pre);
+    case 2: return enqueue_iteration_t<2, Sv>(ln, dmax, sparse, pre);
+    case 3: return enqueue_iteration_t<3, Sv>(ln, dmax, sparse, pre);
+    default: return enqueue_iteration_t<4, Sv>(ln, dmax, sparse, pre);
   }
 }
 
-// Graph of one iteration of the lane, keyed by Dmax and whether a request blurs sparsely.
-sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, cudaGraphExec_t* out) {
-  const int key = 2 * dmax + (sparse ? 1 : 0);
+int graph_key(int dmax, bool sparse, bool pre) {
+  return 4 * dmax + (pre ? 2 : 0) + (sparse ? 1 : 0);
+}
+
+// Graph of one iteration of the lane, keyed by Dmax, whether a request blurs sparsely and
+// whether one is preconditioned.
+sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, bool pre,
+                     cudaGraphExec_t* out) {
+  const int key = graph_key(dmax, sparse, pre);
   auto it = ln->graphs.find(key);
   if (it != ln->graphs.end()) {
     *out = it->second;
@@ -1098,8 +1426,8 @@ sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, cudaG
   }
   SRV_CHECK(cudaStreamBeginCapture(ln->st, cudaStreamCaptureModeThreadLocal), "begin capture");
   const int kernels = S->o.value_dtype == SGP_VALUES_BF16
-                          ? enqueue_iteration_s<bf16>(S, ln, dmax, sparse)
-                          : enqueue_iteration_s<float>(S, ln, dmax, sparse);
+                          ? enqueue_iteration_s<bf16>(S, ln, dmax, sparse, pre)
+                          : enqueue_iteration_s<float>(S, ln, dmax, sparse, pre);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(ln->st, &g);
   if (e != cudaSuccess) return cuda_status(e, "capturing the batched CG iteration");
@@ -1182,7 +1510,7 @@ sgp_status collect_setups(sgp_server* S, int* done) {
     sgp_status s = rs.second;
     S->in_use -= R->bound;  // the reservation made at admission
     Lane* ln = nullptr;
-    if (s == SGP_OK) s = lane_for(S, lane_key(S, R->L), &ln);
+    if (s == SGP_OK) s = lane_for(S, lane_key(S, R), &ln);
     if (s != SGP_OK) {
       R->st.status = s;
       R->held = 0;
@@ -1290,14 +1618,15 @@ sgp_status launch(sgp_server* S, Lane* ln) {
     ln->dirty = false;
   }
   int dmax = 1;
-  bool sparse = false;
+  bool sparse = false, pre = false;
   for (Request* R : ln->active) {
     dmax = std::max(dmax, R->L->D);
     sparse = sparse || R->L->sparse;
+    pre = pre || R->l > 0;
   }
   cudaGraphExec_t ex = nullptr;
-  if (sgp_status s = graph_for(S, ln, dmax, sparse, &ex)) return s;
-  const int key = 2 * dmax + (sparse ? 1 : 0);
+  if (sgp_status s = graph_for(S, ln, dmax, sparse, pre, &ex)) return s;
+  const int key = graph_key(dmax, sparse, pre);
   for (int i = 0; i < S->o.check_every; ++i) {
     SRV_CHECK(cudaGraphLaunch(ex, ln->st), "launching the batched CG iteration");
     note_launches(ln->graph_kernels[key]);
@@ -1372,11 +1701,15 @@ void sgp_server_opts_init(sgp_server_opts* o) {
   o->tol = 1e-3;
   o->max_iter = 500;
   o->check_every = 8;
+  o->precond_rank = 100;
+  o->precond_min_kappa = 1e3;
 }
 
 unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_r, int k,
-                                           int value_dtype) {
-  if (n_points < 1 || d < 1 || order_r < 1 || k < 1) return 0;
+                                           int value_dtype, int precond_rank) {
+  if (n_points < 1 || d < 1 || order_r < 1 || k < 1 || precond_rank < 0 ||
+      precond_rank > kMaxRank)
+    return 0;
   const unsigned long long n = (unsigned long long)n_points, D = (unsigned long long)d + 1;
   const unsigned long long nD = n * D, m = nD, r = (unsigned long long)order_r;
   const unsigned long long kp = ((unsigned long long)k + 3) / 4 * 4;
@@ -1396,7 +1729,15 @@ unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_
   const unsigned long long values = 2 * m * kp * vbytes + nseg * kp * 4 + n * kp * 4;
   const unsigned long long solve = 6 * n * kp * 4 + (n / 4 + 1) * kp * 8 + 2 * n * kp * 4 +
                                    n * 4 + sizeof(Table) + 4096;
-  return lattice + build + values + solve;
+  // preconditioner: B, Minv, apply partials, and the factorisation's scratch
+  unsigned long long pre = 0;
+  if (precond_rank > 0) {
+    const unsigned long long l = (unsigned long long)precond_rank, ld = (l + 3) / 4 * 4;
+    const unsigned long long nbt = n / kBtVbRows + 1;
+    pre = n * ld * 4 + l * l * 8 + (nbt + nbt / kBtSeg + 1) * ld * kp * 4 + ld * kp * 12 +
+          (n / 4 + 1) * kp * 8 + nystrom_masked_scratch_bytes((int)l, (int64_t)n) + 1024;
+  }
+  return lattice + build + values + solve + pre;
 }
 
 sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
@@ -1409,11 +1750,13 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   sgp_server_opts_init(&o);
   if (opts) o = *opts;
   if (o.max_active < 1 || o.max_active > kMaxSlots || o.probes < 0 ||
-      o.probes + 1 > kMaxServeK || o.order_r < 1 || o.order_r > kMaxOrder || o.max_iter < 0 ||
+      o.probes + 2 > kMaxServeK || o.order_r < 1 || o.order_r > kMaxOrder || o.max_iter < 0 ||
       !(o.tol >= 0.0) || o.check_every < 1 ||
-      (o.value_dtype != SGP_VALUES_F32 && o.value_dtype != SGP_VALUES_BF16)) {
-    set_error("sgp_server_create: need 1 <= max_active <= 64, 0 <= probes <= 31, "
-              "1 <= order_r <= 4, max_iter >= 0, tol >= 0, check_every >= 1");
+      (o.value_dtype != SGP_VALUES_F32 && o.value_dtype != SGP_VALUES_BF16) ||
+      o.precond_rank < 0 || o.precond_rank > kMaxRank || !(o.precond_min_kappa >= 0.0)) {
+    set_error("sgp_server_create: need 1 <= max_active <= 64, 0 <= probes <= 30, "
+              "1 <= order_r <= 4, max_iter >= 0, tol >= 0, check_every >= 1, "
+              "0 <= precond_rank <= 128, precond_min_kappa >= 0");
     return SGP_ERR_INVALID_ARG;
   }
   double sp, c[kMaxOrder + 1], g[kMaxOrder + 1];
@@ -1429,7 +1772,7 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   auto S = std::make_unique<sgp_server>();
   S->o = o;
   S->S = o.probes;
-  S->kp = (o.probes + 1 + 3) / 4 * 4;
+  S->kp = (o.probes + 2 + 3) / 4 * 4;  // y, S probes, the ones column, padding
   S->t0 = std::chrono::steady_clock::now();
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
@@ -1455,7 +1798,8 @@ sgp_status sgp_server_submit(sgp_server* S, const sgp_request* req, long long* i
     return SGP_ERR_INVALID_ARG;
   }
   const unsigned long long bound =
-      sgp_request_bytes_bound(r.n + r.ns, r.d, S->o.order_r, S->kp, S->o.value_dtype);
+      sgp_request_bytes_bound(r.n + r.ns, r.d, S->o.order_r, S->kp, S->o.value_dtype,
+                              S->o.precond_rank);
   if (bound > S->o.hbm_budget) {
     set_error("sgp_server_submit: the request's memory bound exceeds the server's budget");
     return SGP_ERR_INVALID_ARG;

@@ -190,11 +190,11 @@ sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, flo
 constexpr int kMaxRank = 128;
 struct Nystrom {
   int l = 0;
-  int ld = 0;                  // l rounded up to 8: row stride of Bh
+  int ld = 0;                  // l rounded up to 4: row stride of Bh
   int64_t n = 0;
   float noise = 0.f;
   bool ok = false;             // false when a Cholesky pivot failed (then not used)
-  void* Bh = nullptr;          // bf16 [n][ld] B = (A Omega + nu Omega) R^-T, locality order
+  void* Bh = nullptr;          // fp32 [n][ld] B = (A Omega + nu Omega) R^-T, locality order
   double* partial = nullptr;   // per-block partial sums of the tall products
   double* C = nullptr;         // [l][l] Omega^T Y, then its Cholesky factor R
   double* Q = nullptr;         // [l][l] Cholesky factor of noise I + B^T B
@@ -214,6 +214,20 @@ struct Nystrom {
              int64_t dot_blocks, int block_threads, cudaStream_t st) const;
   void release(cudaStream_t st);
 };
+
+// Nystrom factor of the training block of a joint lattice's operator, for the GP
+// posterior server: A = outputscale K~ restricted to the rows p with perm[p] < n_train
+// (the other rows are masked: zero sketch rows, zero rows of Y and B).  The l sketch
+// columns go through the lattice kp at a time (V, KV: [n][kp] device scratch, lattice
+// values already sized for kp columns), so that no l-column value buffer is needed.
+// Writes B (fp32 [n][ld], locality order, columns l..ld-1 zero) into Bh and
+// (noise I + B^T B)^-1 (fp64 [l][l]) into Minv; scratch: nystrom_masked_scratch_bytes(l, n)
+// device bytes.  Enqueued on st; *status_dev (device int) is set to 1 when a Cholesky
+// pivot fails (the factor must then not be used); the caller reads it.
+size_t nystrom_masked_scratch_bytes(int l, int64_t n);
+sgp_status nystrom_build_masked(Lattice* L, int64_t n_train, int l, int ld, uint64_t seed,
+                                float noise, int kp, float* V, float* KV, float* Bh,
+                                double* Minv, void* scratch, int* status_dev, cudaStream_t st);
 
 // ---- backward (backward.cu) ----
 sgp_status run_mvm_backward(Lattice* L, const float* X, const float* ls, const float* V,

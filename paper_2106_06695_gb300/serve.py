@@ -30,11 +30,14 @@ class Server:
 
     max_active = 1 is the plain one-request-at-a-time path (same kernels); probes is the
     number S of Rademacher probes of the variance estimate (k = 1 + S right-hand sides).
+    precond_rank: rank of the Nystrom CG preconditioner (App. A; 0 = none), used for the
+    requests whose condition estimate reaches precond_min_kappa.
     """
 
     def __init__(self, max_active: int = 16, probes: int = 8, hbm_budget: int | None = None,
                  order: int = 1, kernel: str = "rbf_binomial", value_dtype: str = "f32",
-                 tol: float = 1e-3, max_iter: int = 500, check_every: int = 8):
+                 tol: float = 1e-3, max_iter: int = 500, check_every: int = 8,
+                 precond_rank: int = 100, precond_min_kappa: float = 1e3):
         self._lib = _lib.load()
         o = _lib.sgp_server_opts()
         self._lib.sgp_server_opts_init(ctypes.byref(o))
@@ -48,6 +51,8 @@ class Server:
         o.tol = float(tol)
         o.max_iter = int(max_iter)
         o.check_every = int(check_every)
+        o.precond_rank = int(precond_rank)
+        o.precond_min_kappa = float(precond_min_kappa)
         self.opts = o
         h = ctypes.c_void_p()
         check(self._lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)))
@@ -142,11 +147,13 @@ class Server:
             self.step()
 
 
-def request_bytes_bound(n_points: int, d: int, order: int = 1, k: int = 9,
-                        value_dtype: str = "f32") -> int:
-    """Upper bound of one request's device bytes (sgp_request_bytes_bound)."""
+def request_bytes_bound(n_points: int, d: int, order: int = 1, k: int = 10,
+                        value_dtype: str = "f32", precond_rank: int = 100) -> int:
+    """Upper bound of one request's device bytes (sgp_request_bytes_bound); k = 1 + probes
+    + 1 columns, precond_rank as the server's option."""
     return int(_lib.load().sgp_request_bytes_bound(int(n_points), int(d), int(order), int(k),
-                                                  VALUE_DTYPES[value_dtype]))
+                                                  VALUE_DTYPES[value_dtype],
+                                                  int(precond_rank)))
 
 
 @dataclass

@@ -82,11 +82,13 @@ def test_product_never_touches_the_oracle():
 
 
 def test_request_bytes_bound_is_host_only_and_monotone(lib):
-    b = lambda n, d, k=9, dt=0: lib.sgp_request_bytes_bound(n, d, 1, k, dt)  # noqa: E731
-    assert b(0, 3) == 0 and b(10, 0) == 0
+    b = lambda n, d, k=9, dt=0, l=0: lib.sgp_request_bytes_bound(n, d, 1, k, dt, l)  # noqa: E731
+    assert b(0, 3) == 0 and b(10, 0) == 0 and b(10, 3, l=-1) == 0 and b(10, 3, l=129) == 0
     assert b(1000, 3) < b(2000, 3) < b(2000, 8)
     assert b(1000, 3, k=9) < b(1000, 3, k=20)
     assert b(100_000, 20, dt=1) < b(100_000, 20, dt=0)
+    # the preconditioner adds at least its factor B (n x l fp32)
+    assert b(100_000, 3, l=100) >= b(100_000, 3) + 100_000 * 100 * 4
     # at least the lattice arrays at m = n (d + 1): keys, ids, weights, neighbour table
     n, d = 50_000, 8
     D = d + 1
@@ -99,6 +101,7 @@ def test_server_without_gpu_fails_loudly(lib):
     o = _lib.sgp_server_opts()
     lib.sgp_server_opts_init(ctypes.byref(o))
     assert (o.max_active, o.probes, o.max_iter, o.check_every, o.hbm_budget) == (16, 8, 500, 8, 0)
+    assert (o.precond_rank, o.precond_min_kappa) == (100, 1e3)
     h = ctypes.c_void_p()
     assert lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)) == 6
     assert not h.value

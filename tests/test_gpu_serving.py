@@ -6,7 +6,7 @@ batched one on a request stream, admission by the memory budget, and argument ch
 import numpy as np
 import pytest
 
-from oracle import gp_posterior
+from oracle import condition_estimate, gp_posterior
 from paper_2106_06695_gb300 import SGPError, synth
 from paper_2106_06695_gb300.serve import Server, request_bytes_bound, run_stream
 
@@ -30,41 +30,88 @@ def results(srv, ids):
     return out
 
 
-def test_posterior_matches_oracle():
+@pytest.mark.parametrize("min_kappa", [1e3, 0.0, None])
+def test_posterior_matches_oracle(min_kappa):
+    """Default rule (precondition when the condition estimate reaches 1e3), every request
+    preconditioned (min_kappa 0), and none (precond_rank 0); the oracle solves with the
+    rank the server chose, and the condition estimate matches the oracle's."""
     reqs = small_requests(4, seed=5)
     tol = 1e-5
-    with Server(max_active=4, tol=tol, max_iter=2000) as srv:
+    kw = dict(precond_rank=0) if min_kappa is None else dict(precond_min_kappa=min_kappa)
+    with Server(max_active=4, tol=tol, max_iter=2000, **kw) as srv:
         ids = submit_all(srv, reqs)
         srv.run_until_idle()
         for r, rid in zip(reqs, ids):
             mean, var = srv.result(rid)
             st = srv.stats(rid)
+            if min_kappa is None:
+                assert st["precond_rank"] == 0 and st["kappa_est"] == 0.0
+            else:
+                kappa = condition_estimate(r["X"], r["Xs"], r["lengthscales"], r["noise"])
+                assert st["kappa_est"] == pytest.approx(kappa, rel=1e-4)
+                want = min(100, len(r["X"])) if kappa >= min_kappa * (1 + 1e-3) else 0
+                if abs(kappa - min_kappa) > 1e-3 * max(min_kappa, 1.0):
+                    assert st["precond_rank"] == want
             m_ref, v_ref, it_ref, _ = gp_posterior(r["X"], r["y"], r["Xs"], r["lengthscales"],
                                                    r["noise"], probes=8, seed=r["seed"],
-                                                   tol=tol, max_iter=2000)
+                                                   tol=tol, max_iter=2000,
+                                                   precond_rank=st["precond_rank"])
             err_m = np.linalg.norm(mean - m_ref) / np.linalg.norm(m_ref)
             err_v = np.abs(var - v_ref).max()
-            print("n=%d d=%d iters gpu %d oracle %d: mean rel L2 %.2e, var max abs %.2e"
-                  % (len(r["X"]), r["X"].shape[1], st["iters"], it_ref.max(), err_m, err_v))
+            print("n=%d d=%d kappa %.3g rank %d iters gpu %d oracle %d: mean rel L2 %.2e, "
+                  "var max abs %.2e" % (len(r["X"]), r["X"].shape[1], st["kappa_est"],
+                                        st["precond_rank"], st["iters"], it_ref.max(), err_m,
+                                        err_v))
             assert st["status"] == 0 and st["rel_res"] <= tol
             assert err_m <= 1e-3
             assert err_v <= 1e-3
 
 
-def test_sparse_lattice_requests_match_oracle():
+def test_preconditioner_makes_an_ill_conditioned_request_converge():
+    """d = 3, n = 20,000 on a coarse lattice (hundreds of points per vertex), noise 0.01:
+    the condition estimate is far above 1e3.  Preconditioned (App. A, rank 100) the solve
+    reaches tol in far fewer iterations than plain CG and matches the oracle's
+    preconditioned posterior."""
+    r = synth.serving_stream(1, 77, n_range=(20_000, 20_001), dims=(3,), test_points=64)[0]
+    tol = 1e-4
+    out = {}
+    for name, rank in (("plain", 0), ("pcg", 100)):
+        with Server(max_active=1, tol=tol, max_iter=1500, precond_rank=rank) as srv:
+            rid = submit_all(srv, [r])[0]
+            srv.run_until_idle()
+            st = srv.stats(rid)
+            out[name] = (st, *[a.copy() for a in srv.result(rid)])
+    st_p, mean, var = out["pcg"]
+    print("kappa %.3g: plain %d iters (rel %.2e), preconditioned %d iters (rel %.2e)"
+          % (st_p["kappa_est"], out["plain"][0]["iters"], out["plain"][0]["rel_res"],
+             st_p["iters"], st_p["rel_res"]))
+    assert st_p["kappa_est"] > 1e3 and st_p["precond_rank"] == 100
+    assert st_p["rel_res"] <= tol
+    assert 3 * st_p["iters"] <= out["plain"][0]["iters"]
+    m_ref, v_ref, _, _ = gp_posterior(r["X"], r["y"], r["Xs"], r["lengthscales"], r["noise"],
+                                      probes=8, seed=r["seed"], tol=tol, max_iter=1500,
+                                      precond_rank=100)
+    assert np.linalg.norm(mean - m_ref) / np.linalg.norm(m_ref) <= 1e-3
+    assert np.abs(var - v_ref).max() <= 1e-3
+
+
+@pytest.mark.parametrize("min_kappa", [1e3, 0.0])
+def test_sparse_lattice_requests_match_oracle(min_kappa):
     """d = 20 and 50: the requests' lattices blur on direction lists inside the batched
     iteration (lazy centre-tap factors); mixed with a dense d = 3 request."""
     reqs = (small_requests(2, seed=41, n_range=(1500, 2500), dims=(20, 50))
             + small_requests(1, seed=42, n_range=(1500, 2500), dims=(3,)))
     tol = 1e-5
-    with Server(max_active=4, tol=tol, max_iter=2000) as srv:
+    with Server(max_active=4, tol=tol, max_iter=2000, precond_min_kappa=min_kappa) as srv:
         ids = submit_all(srv, reqs)
         srv.run_until_idle()
         for r, rid in zip(reqs, ids):
             mean, var = srv.result(rid)
+            rank = srv.stats(rid)["precond_rank"]
+            assert rank == 100 or min_kappa > 0
             m_ref, v_ref, _, _ = gp_posterior(r["X"], r["y"], r["Xs"], r["lengthscales"],
                                               r["noise"], probes=8, seed=r["seed"], tol=tol,
-                                              max_iter=2000)
+                                              max_iter=2000, precond_rank=rank)
             # at d = 50 the test points share no vertex with the training points: the
             # lattice's K*X is exactly 0 there, and so is the mean on both sides
             assert np.isfinite(mean).all() and np.isfinite(var).all()
@@ -74,15 +121,16 @@ def test_sparse_lattice_requests_match_oracle():
             assert err_m <= 1e-3 and np.abs(var - v_ref).max() <= 1e-3
 
 
-def test_alone_equals_in_the_mix_bitwise():
+@pytest.mark.parametrize("min_kappa", [1e3, 0.0])
+def test_alone_equals_in_the_mix_bitwise(min_kappa):
     reqs = small_requests(6, seed=9) + small_requests(2, seed=10, dims=(20, 50))
-    with Server(max_active=8) as srv:
+    with Server(max_active=8, precond_min_kappa=min_kappa) as srv:
         ids = submit_all(srv, reqs)
         srv.run_until_idle()
         mix = results(srv, ids)
         assert srv.info()["peak_active"] == 8
     for r, (m, v, it) in zip(reqs, mix):
-        with Server(max_active=1) as one:
+        with Server(max_active=1, precond_min_kappa=min_kappa) as one:
             rid = submit_all(one, [r])[0]
             one.run_until_idle()
             m1, v1 = one.result(rid)
@@ -108,7 +156,7 @@ def test_stream_plain_and_batched_give_identical_results():
 
 def test_admission_respects_the_memory_budget():
     reqs = small_requests(5, seed=21)
-    bounds = [request_bytes_bound(len(r["X"]) + len(r["Xs"]), r["X"].shape[1], k=9)
+    bounds = [request_bytes_bound(len(r["X"]) + len(r["Xs"]), r["X"].shape[1], k=10)
               for r in reqs]
     with Server(max_active=8, hbm_budget=sum(bounds)) as srv:
         ids = submit_all(srv, reqs)
@@ -181,16 +229,24 @@ def test_resident_lattice_is_reused_and_evicted_within_the_budget():
         assert np.array_equal(fresh.result(c)[0], mean_b)
         assert np.array_equal(fresh.result(c)[1], var_b)
         assert fresh.cache_info()["lattices"] == 0
-    # a budget for about one request: a second key evicts the first lattice
-    other = small_requests(1, seed=52, n_range=(3000, 4000), dims=(8,))[0]
-    bound = max(request_bytes_bound(len(x["X"]) + len(x["Xs"]), 8, k=9) for x in (r, other))
-    with Server(max_active=1, hbm_budget=int(1.2 * bound)) as srv:
+    # a budget of one request's bound plus half a resident lattice: a second key (a request
+    # of the same size) evicts the first lattice
+    other = small_requests(1, seed=52, n_range=(len(r["X"]), len(r["X"]) + 1), dims=(8,))[0]
+    assert len(other["X"]) == len(r["X"])
+    bound = request_bytes_bound(len(r["X"]) + len(r["Xs"]), 8, k=10)
+    with Server(max_active=1) as srv:
         sub(srv, r["y"], 1)
         srv.run_until_idle()
+        resident = srv.cache_info()["bytes"]
+    budget = bound + resident // 2
+    with Server(max_active=1, hbm_budget=budget) as srv:
+        sub(srv, r["y"], 1)
+        srv.run_until_idle()
+        assert srv.cache_info()["lattices"] == 1
         srv.submit(other["X"], other["y"], other["Xs"], other["lengthscales"], lattice_key=2)
         srv.run_until_idle()
         assert srv.cache_info()["lattices"] == 1
         again = sub(srv, r["y"], 1)
         srv.run_until_idle()
         assert srv.stats(again)["lattice_reused"] == 0 and srv.stats(again)["status"] == 0
-        assert srv.info()["bytes_in_use"] <= int(1.2 * bound)
+        assert srv.info()["bytes_in_use"] <= budget
