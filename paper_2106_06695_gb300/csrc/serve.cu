@@ -47,8 +47,13 @@ constexpr int kGrid = 4 * 152;      // their fixed grid (4 blocks per SM)
 constexpr int kBlurU = 2;           // blur rows per thread
 constexpr int kVecRows = 4;         // vector-kernel rows per thread
 constexpr int kMaxLd = kMaxRank;    // preconditioner: B row stride bound
-constexpr int kBtVbRows = 512;      // rows of one B^T r virtual block (64 per warp)
+constexpr int kBtVbRows = 512;      // rows of one B^T r virtual block
 constexpr int kBtSeg = 16;          // B^T r partials per first-level sum
+constexpr int kStages = 3;          // bulk-copied chunks in flight per block
+constexpr int kRingBytes = 192 * 1024;  // shared memory of the chunk ring
+constexpr int kRingRowsMax = 96;    // rows of one chunk at most
+constexpr int kRingGrid = 152;      // persistent grid of the ring kernels (one block per SM)
+constexpr int kSpinLimit = 1 << 20; // bounded mbarrier waits (about a second at most)
 constexpr uint64_t kPrecondSeedXor = 0x6A09E667F3BCC909ull;  // sketch seed = seed ^ this
 
 enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_BT, U_BTS, U_BTT, U_MINV, U_KINDS };
@@ -103,6 +108,7 @@ struct Table {
   int nslots;
   int kp;
   int* flags;  // [kMaxSlots][2]: state copied by the check kernel, read by the host
+  int* err;    // set to 1 when a bulk-copy wait gave up (the round's results are void)
   int64_t pre[U_KINDS][kMaxSlots + 1];  // prefix sums of virtual blocks per unit kind
   SlotDev s[kMaxSlots];
 };
@@ -584,68 +590,193 @@ __global__ void __launch_bounds__(kST) kb_update_p(const Table* __restrict__ T) 
   SLOT_LOOP_END
 }
 
+// ---- bulk copies (TMA) into a shared-memory ring, completed on mbarriers -------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// One contiguous global -> shared copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when the limit is reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Rows of one stage of the chunk ring for kp columns: a stage holds rows x (kMaxLd + 2 kp)
+// floats, kStages stages in kRingBytes.
+__host__ __device__ inline int ring_rows_cap(int kp) {
+  const int r = kRingBytes / kStages / ((kMaxLd + 2 * kp) * 4);
+  return r < kRingRowsMax ? r : kRingRowsMax;
+}
+
+// Chunks of rows [r0, r1) of one request: B ([rows][ld]), rh and, with `lo`, rl ([rows][kp]
+// each) land in stage st of the ring, back to back.
+struct ChunkRing {
+  float* base;       // dynamic shared memory, kStages stages
+  int stage_floats;  // ring_rows_cap(kp) (kMaxLd + 2 kp)
+  int rows;          // rows per chunk (<= ring_rows_cap(kp))
+  bool lo;           // rl is copied too
+  uint64_t* bar;     // [kStages]
+  uint32_t phase;    // bit st: parity of stage st's next completion
+  __device__ float* B(int st) const { return base + (size_t)st * stage_floats; }
+};
+
+// Issue chunk k of rows [r0, r1) into stage st (one thread).
+__device__ __forceinline__ void ring_issue(const ChunkRing& ring, int st, const SlotDev& s,
+                                           int kp, int64_t r0, int64_t r1, int k) {
+  const int64_t a = r0 + (int64_t)k * ring.rows;
+  const int rows = (int)(r1 - a < ring.rows ? r1 - a : ring.rows);
+  const uint32_t bB = (uint32_t)rows * s.ld * 4, bR = (uint32_t)rows * kp * 4;
+  float* dst = ring.B(st);
+  mbar_expect_tx(&ring.bar[st], bB + (ring.lo ? 2 : 1) * bR);
+  bulk_g2s(dst, s.Bh + a * s.ld, bB, &ring.bar[st]);
+  bulk_g2s(dst + rows * s.ld, s.rh + a * kp, bR, &ring.bar[st]);
+  if (ring.lo) bulk_g2s(dst + rows * s.ld + rows * kp, s.rl + a * kp, bR, &ring.bar[st]);
+}
+
+// After a failed wait on chunk k0: record the error, then wait (bounded) for this block's
+// chunks k0 .. k1 - 1 still in flight, so that no copy lands after the block has exited.
+__device__ void ring_abort(ChunkRing& ring, const Table* T, int k0, int k1) {
+  if (threadIdx.x == 0) atomicExch(T->err, 1);
+  for (int k = k0; k < k1; ++k) {
+    const int st = k % kStages;
+    (void)mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u);
+    ring.phase ^= 1u << st;
+  }
+}
+
+__device__ __forceinline__ void ring_init(ChunkRing& ring, float* base, uint64_t* bar, int kp,
+                                          bool lo) {
+  ring.base = base;
+  ring.stage_floats = ring_rows_cap(kp) * (kMaxLd + 2 * kp);
+  ring.rows = ring_rows_cap(kp);
+  ring.lo = lo;
+  ring.bar = bar;
+  ring.phase = 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+}
+
 // ---- preconditioner apply z = P^-1 r (requests with l > 0) ----------------------------
 // P^-1 r = (r - B Minv B^T r) / noise (Woodbury), in four table-driven steps.
 
-// Per-virtual-block partial of B^T r (r = rh + rl): each warp takes 64 consecutive rows,
-// four per step; lane owns the B columns lane + 32 a (a < 4) against 16 columns of r at a
-// time (r broadcast by shuffles); fp32 sums, the warps added in a fixed order in shared
-// memory, and the block writes btpart[local][ld][kp].
-__global__ void __launch_bounds__(kST) kb_bt(const Table* __restrict__ T) {
-  __shared__ float red[kMaxLd * 16];
-  constexpr int kWarps = kST / 32, kWarpRows = kBtVbRows / kWarps, kStep = 4;
+// Per-virtual-block partial of B^T r over kBtVbRows rows, with r taken as its fp32 part
+// rh (the low part rl is below the preconditioner's own rounding): the rows stream through
+// the chunk ring (bulk copies, kStages chunks in flight); warp w takes rows w, w + 8, ...
+// of each chunk, lane owns the B columns 4 lane .. 4 lane + 3 (one float4 of the row)
+// against KC columns of r broadcast from shared memory (fp32 sums).  The warps are added in
+// a fixed order in shared memory and the block writes btpart[local][ld][kp].  kp > KC: one
+// pass per KC columns (B streamed again).
+template <int KC>
+__global__ void __launch_bounds__(kST, 1) kb_bt(const Table* __restrict__ T) {
+  extern __shared__ __align__(128) float dsm[];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ __align__(16) float red[KC * kMaxLd];  // [c][j]
+  constexpr int kWarps = kST / 32;
   const int kp = T->kp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  ChunkRing ring;
+  ring_init(ring, dsm, bar, kp, false);
   SLOT_LOOP(U_BT)
   if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
   const int ld = s.ld;
-  const int64_t r0 = local * kBtVbRows + (int64_t)warp * kWarpRows;
-  const int64_t r1 = r0 + kWarpRows < s.n ? r0 + kWarpRows : s.n;
-  for (int c_off = 0; c_off < kp; c_off += 16) {
-    const int kc = kp - c_off < 16 ? kp - c_off : 16;
-    float acc[4][16];
+  const int64_t r0 = local * kBtVbRows;
+  const int64_t r1 = r0 + kBtVbRows < s.n ? r0 + kBtVbRows : s.n;
+  const int nch = (int)ceil_div(r1 - r0, ring.rows);
+  const bool mine = 4 * lane < ld;
+  for (int c_off = 0; c_off < kp; c_off += KC) {
+    const int kc = kp - c_off < KC ? kp - c_off : KC;
+    float acc[4][KC];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
-    for (int64_t row0 = r0; row0 < r1; row0 += kStep) {
-      float b[kStep][4], rv[kStep];
-#pragma unroll
-      for (int q2 = 0; q2 < kStep; ++q2) {
-        const int64_t row = row0 + q2;
-        const bool in = row < r1;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int j = lane + 32 * a;
-          b[q2][a] = (in && j < ld) ? s.Bh[row * ld + j] : 0.f;
-        }
-        const int64_t e = row * kp + c_off + lane;
-        rv[q2] = (in && lane < kc) ? __fadd_rn(s.rh[e], s.rl[e]) : 0.f;
+      for (int c = 0; c < KC; ++c) acc[a][c] = 0.f;
+    if (threadIdx.x == 0)
+      for (int k = 0; k < nch && k < kStages; ++k) ring_issue(ring, k, s, kp, r0, r1, k);
+    for (int k = 0; k < nch; ++k) {
+      const int st = k % kStages;
+      const bool ok = __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u));
+      if (!ok) {
+        ring_abort(ring, T, k, k + kStages < nch ? k + kStages : nch);
+        return;
       }
+      ring.phase ^= 1u << st;
+      const int64_t a0 = r0 + (int64_t)k * ring.rows;
+      const int rows = (int)(r1 - a0 < ring.rows ? r1 - a0 : ring.rows);
+      const float* Bs = ring.B(st);
+      const float* Hs = Bs + rows * ld;
+#pragma unroll 2
+      for (int rr = warp; rr < rows; rr += kWarps) {
+        const float4 b = mine ? *reinterpret_cast<const float4*>(Bs + rr * ld + 4 * lane)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        float rv[KC];
 #pragma unroll
-      for (int q2 = 0; q2 < kStep; ++q2)
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float rc = __shfl_sync(0xffffffffu, rv[q2], c);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) acc[a][c] = fmaf(b[q2][a], rc, acc[a][c]);
+        for (int g = 0; g < KC / 4; ++g) {
+          const float4 h = 4 * g < kc
+                               ? *reinterpret_cast<const float4*>(Hs + rr * kp + c_off + 4 * g)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          rv[4 * g + 0] = h.x;
+          rv[4 * g + 1] = h.y;
+          rv[4 * g + 2] = h.z;
+          rv[4 * g + 3] = h.w;
         }
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          acc[0][c] = fmaf(b.x, rv[c], acc[0][c]);
+          acc[1][c] = fmaf(b.y, rv[c], acc[1][c]);
+          acc[2][c] = fmaf(b.z, rv[c], acc[2][c]);
+          acc[3][c] = fmaf(b.w, rv[c], acc[3][c]);
+        }
+      }
+      __syncthreads();  // stage st is free again
+      if (threadIdx.x == 0 && k + kStages < nch) ring_issue(ring, st, s, kp, r0, r1, k + kStages);
     }
     for (int w = 0; w < kWarps; ++w) {
-      if (warp == w)
+      if (warp == w && mine)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int j = lane + 32 * a;
-          if (j < ld)
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-              red[j * 16 + c] = (w == 0 ? 0.f : red[j * 16 + c]) + acc[a][c];
+        for (int c = 0; c < KC; ++c) {
+          float4* dst = reinterpret_cast<float4*>(red + c * kMaxLd + 4 * lane);
+          const float4 prev = w == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *dst;
+          *dst = make_float4(prev.x + acc[0][c], prev.y + acc[1][c], prev.z + acc[2][c],
+                             prev.w + acc[3][c]);
         }
       __syncthreads();
     }
     for (int o = threadIdx.x; o < ld * kc; o += kST) {
       const int j = o / kc, c = o - j * kc;
-      s.btpart[(local * ld + j) * kp + c_off + c] = red[j * 16 + c];
+      s.btpart[(local * ld + j) * kp + c_off + c] = red[c * kMaxLd + j];
     }
     __syncthreads();
   }
@@ -705,52 +836,116 @@ __global__ void __launch_bounds__(kST) kb_minv(const Table* __restrict__ T) {
 }
 
 // z = (r - B u) / noise, written into ap (free between the x, r update and the next
-// product), and the virtual block's column sums of r z into dpart2, with the layout of the
-// other vector kernels (thread g, col: 4 columns of rows ... + g; u in shared memory; the
-// threads of one row read the same B row, a broadcast).  Test rows have zero B rows and
-// zero r, so z = 0 there.
-__global__ void __launch_bounds__(kST) kb_apply_z(const Table* __restrict__ T) {
-  __shared__ __align__(16) float us[kMaxLd * kMaxServeK];
+// product), and the virtual block's column sums of r z into dpart2.  The block's rows
+// (groups kVecRows of them, as in the other vector kernels) stream through the chunk
+// ring; thread (g, col) computes 4 columns of one row per pass from the staged B row and
+// u (in shared memory).  Test rows have zero B rows and zero r, so z = 0 there.
+__global__ void __launch_bounds__(kST, 1) kb_apply_z(const Table* __restrict__ T) {
+  extern __shared__ __align__(128) float dsm[];
+  __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ double sh[kST * 4];
   const int kp = T->kp, G = kp / 4, groups = kST / G;
   const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
+  float* us = dsm;  // [kMaxLd][kp]
+  ChunkRing ring;
+  ring_init(ring, dsm + kMaxLd * kp, bar, kp, true);
+  if (groups < ring.rows) ring.rows = groups;  // one row per thread and chunk
   SLOT_LOOP(U_VEC)
   if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
   const int ld = s.ld;
-  __syncthreads();
+  const int64_t r0 = local * (int64_t)groups * kVecRows;
+  const int64_t r1 = r0 + (int64_t)groups * kVecRows < s.n ? r0 + (int64_t)groups * kVecRows : s.n;
+  const int nch = (int)ceil_div(r1 - r0, ring.rows);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nch && k < kStages; ++k) ring_issue(ring, k, s, kp, r0, r1, k);
   for (int e = threadIdx.x; e < ld * kp; e += kST) us[e] = s.u[e];
-  __syncthreads();
   dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  if (g < groups) {
-    for (int i = 0; i < kVecRows; ++i) {
-      const int64_t row = (local * kVecRows + i) * groups + g;
-      if (row >= s.n) break;
-      const float4* b4 = reinterpret_cast<const float4*>(s.Bh + row * ld);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int q4 = 0; q4 < ld / 4; ++q4) {
-        const float4 bb = b4[q4];
-        const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float4 uu = *reinterpret_cast<const float4*>(us + (q4 * 4 + a) * kp + col);
-          acc = f4_fma(bv[a], uu, acc);
-        }
-      }
-      const int64_t e = row * kp + col;
-      const float4 rh = f4_ld(s.rh + e), rl = f4_ld(s.rl + e);
-      const float r0 = __fadd_rn(rh.x, rl.x), r1 = __fadd_rn(rh.y, rl.y);
-      const float r2 = __fadd_rn(rh.z, rl.z), r3 = __fadd_rn(rh.w, rl.w);
-      const float4 z = make_float4((r0 - acc.x) * s.inv_noise, (r1 - acc.y) * s.inv_noise,
-                                   (r2 - acc.z) * s.inv_noise, (r3 - acc.w) * s.inv_noise);
-      f4_st(s.ap + e, z);
-      d[0] = df_add(d[0], df_two_prod(r0, z.x));
-      d[1] = df_add(d[1], df_two_prod(r1, z.y));
-      d[2] = df_add(d[2], df_two_prod(r2, z.z));
-      d[3] = df_add(d[3], df_two_prod(r3, z.w));
+  for (int k = 0; k < nch; ++k) {
+    const int st = k % kStages;
+    const bool ok = __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u));
+    if (!ok) {
+      ring_abort(ring, T, k, k + kStages < nch ? k + kStages : nch);
+      return;
     }
+    ring.phase ^= 1u << st;
+    const int64_t a = r0 + (int64_t)k * ring.rows;
+    const int rows = (int)(r1 - a < ring.rows ? r1 - a : ring.rows);
+    const float* Bs = ring.B(st);
+    const float* Hs = Bs + rows * ld;
+    const float* Ls = Hs + rows * kp;
+    if (g < groups)
+      for (int rr = g; rr < rows; rr += groups) {
+        const float* brow = Bs + rr * ld;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc;
+        int q4 = 0;
+        for (; q4 + 2 <= ld / 4; q4 += 2) {  // two independent chains
+          const float4 b0 = *reinterpret_cast<const float4*>(brow + 4 * q4);
+          const float4 b1 = *reinterpret_cast<const float4*>(brow + 4 * q4 + 4);
+          const float* u0 = us + 4 * q4 * kp + col;
+          const float* u1 = u0 + 4 * kp;
+          acc = f4_fma(b0.x, *reinterpret_cast<const float4*>(u0), acc);
+          acc2 = f4_fma(b1.x, *reinterpret_cast<const float4*>(u1), acc2);
+          acc = f4_fma(b0.y, *reinterpret_cast<const float4*>(u0 + kp), acc);
+          acc2 = f4_fma(b1.y, *reinterpret_cast<const float4*>(u1 + kp), acc2);
+          acc = f4_fma(b0.z, *reinterpret_cast<const float4*>(u0 + 2 * kp), acc);
+          acc2 = f4_fma(b1.z, *reinterpret_cast<const float4*>(u1 + 2 * kp), acc2);
+          acc = f4_fma(b0.w, *reinterpret_cast<const float4*>(u0 + 3 * kp), acc);
+          acc2 = f4_fma(b1.w, *reinterpret_cast<const float4*>(u1 + 3 * kp), acc2);
+        }
+        if (q4 < ld / 4) {
+          const float4 b0 = *reinterpret_cast<const float4*>(brow + 4 * q4);
+          const float* u0 = us + 4 * q4 * kp + col;
+          acc = f4_fma(b0.x, *reinterpret_cast<const float4*>(u0), acc);
+          acc = f4_fma(b0.y, *reinterpret_cast<const float4*>(u0 + kp), acc);
+          acc = f4_fma(b0.z, *reinterpret_cast<const float4*>(u0 + 2 * kp), acc);
+          acc = f4_fma(b0.w, *reinterpret_cast<const float4*>(u0 + 3 * kp), acc);
+        }
+        acc = make_float4(acc.x + acc2.x, acc.y + acc2.y, acc.z + acc2.z, acc.w + acc2.w);
+        const float4 h = *reinterpret_cast<const float4*>(Hs + rr * kp + col);
+        const float4 lo = *reinterpret_cast<const float4*>(Ls + rr * kp + col);
+        const float x0 = __fadd_rn(h.x, lo.x), x1 = __fadd_rn(h.y, lo.y);
+        const float x2 = __fadd_rn(h.z, lo.z), x3 = __fadd_rn(h.w, lo.w);
+        const float4 z = make_float4((x0 - acc.x) * s.inv_noise, (x1 - acc.y) * s.inv_noise,
+                                     (x2 - acc.z) * s.inv_noise, (x3 - acc.w) * s.inv_noise);
+        f4_st(s.ap + (a + rr) * kp + col, z);
+        d[0] = df_add(d[0], df_two_prod(x0, z.x));
+        d[1] = df_add(d[1], df_two_prod(x1, z.y));
+        d[2] = df_add(d[2], df_two_prod(x2, z.z));
+        d[3] = df_add(d[3], df_two_prod(x3, z.w));
+      }
+    __syncthreads();  // stage st is free again
+    if (threadIdx.x == 0 && k + kStages < nch) ring_issue(ring, st, s, kp, r0, r1, k + kStages);
   }
   vb_column_sums(d, kp, s.dpart2 + local * kp, sh);
   SLOT_LOOP_END
+}
+
+// Dynamic shared memory of kb_bt and kb_apply_z for kp columns.
+size_t ring_smem_bytes(int kp) {
+  return (size_t)kStages * ring_rows_cap(kp) * (kMaxLd + 2 * kp) * 4;
+}
+size_t apply_z_smem_bytes(int kp) { return ring_smem_bytes(kp) + (size_t)kMaxLd * kp * 4; }
+
+// kb_bt for the server's kp: KC = min(kp, 16) columns per pass.
+void launch_bt(int kp, const Table* T, cudaStream_t st) {
+  const size_t sm = ring_smem_bytes(kp);
+  switch (kp < 16 ? kp : 16) {
+    case 4: kb_bt<4><<<kRingGrid, kST, sm, st>>>(T); break;
+    case 8: kb_bt<8><<<kRingGrid, kST, sm, st>>>(T); break;
+    case 12: kb_bt<12><<<kRingGrid, kST, sm, st>>>(T); break;
+    default: kb_bt<16><<<kRingGrid, kST, sm, st>>>(T); break;
+  }
+}
+cudaError_t bt_smem_attributes(int kp) {
+  const int sm = (int)ring_smem_bytes(kp);
+  cudaError_t e = cudaFuncSetAttribute(kb_bt<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_bt<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_bt<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_bt<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
 }
 
 // ---- per-request set-up and read-out (single-request launches) ------------------------
@@ -914,7 +1109,7 @@ struct Request {
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr, *p = nullptr, *ap = nullptr;
   double* dpart = nullptr;
   double* scal = nullptr;  // rho, bnorm, relres, alpha, beta: [5][kp]
-  int* ints = nullptr;     // active [kp], state [2]
+  int* ints = nullptr;     // active [kp], state [2], bulk-copy error [1]
   float* outd = nullptr;   // mean, var: [2][ns]
   Table* dtab1 = nullptr;  // one-request table for the set-up kernels
   cudaEvent_t ready = nullptr;
@@ -1185,7 +1380,8 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   for (float** v : vecs) SRV_CHECK(get((void**)v, vec), "alloc CG vectors");
   SRV_CHECK(get((void**)&R->dpart, (size_t)R->vb[U_VEC] * kp * sizeof(double)), "alloc partials");
   SRV_CHECK(get((void**)&R->scal, 5 * (size_t)kp * sizeof(double)), "alloc scalars");
-  SRV_CHECK(get((void**)&R->ints, ((size_t)kp + 2) * sizeof(int)), "alloc flags");
+  SRV_CHECK(get((void**)&R->ints, ((size_t)kp + 3) * sizeof(int)), "alloc flags");
+  SRV_CHECK(cudaMemsetAsync(R->ints, 0, ((size_t)kp + 3) * sizeof(int), st), "clear flags");
   SRV_CHECK(get((void**)&R->outd, 2 * (size_t)in.ns * sizeof(float)), "alloc outputs");
   SRV_CHECK(get((void**)&R->dtab1, sizeof(Table)), "alloc table");
   // right-hand sides: y and KX* z_s (one product of the probe columns, caller's order)
@@ -1260,6 +1456,7 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   t1.nslots = 1;
   t1.kp = kp;
   t1.flags = nullptr;
+  t1.err = R->ints + kp + 2;
   fill_slot(S, R, t1.s[0]);
   for (int u = 0; u < U_KINDS; ++u) t1.pre[u][1] = R->vb[u];
   SRV_CHECK(cudaMemcpyAsync(R->dtab1, &t1, sizeof(Table), cudaMemcpyHostToDevice, st),
@@ -1270,11 +1467,11 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
     static const int kOne = 1;
     SRV_CHECK(cudaMemcpyAsync(R->ints + kp, &kOne, sizeof(int), cudaMemcpyHostToDevice, st),
               "mark the request active");
-    kb_bt<<<kGrid, kST, 0, st>>>(R->dtab1);
+    launch_bt(kp, R->dtab1, st);
     kb_bt_seg<<<kGrid, kST, 0, st>>>(R->dtab1);
     kb_bt_total<<<kGrid, kST, 0, st>>>(R->dtab1);
     kb_minv<<<kGrid, kST, 0, st>>>(R->dtab1);
-    kb_apply_z<<<kGrid, kST, 0, st>>>(R->dtab1);
+    kb_apply_z<<<kRingGrid, kST, apply_z_smem_bytes(kp), st>>>(R->dtab1);
     note_launches(5);
   }
   kb_init_scalars<<<1, kST, 0, st>>>(R->dtab1);
@@ -1315,11 +1512,11 @@ sgp_status finish(sgp_server* S, Request* R, cudaStream_t st) {
                               cudaMemcpyDeviceToHost, st),
               "copy var");
   std::vector<double> relres(kp);
-  std::vector<int> ints(kp + 2);
+  std::vector<int> ints(kp + 3);
   SRV_CHECK(cudaMemcpyAsync(relres.data(), R->scal + 2 * kp, kp * sizeof(double),
                             cudaMemcpyDeviceToHost, st),
             "copy residuals");
-  SRV_CHECK(cudaMemcpyAsync(ints.data(), R->ints, (kp + 2) * sizeof(int), cudaMemcpyDeviceToHost,
+  SRV_CHECK(cudaMemcpyAsync(ints.data(), R->ints, (kp + 3) * sizeof(int), cudaMemcpyDeviceToHost,
                             st),
             "copy state");
   SRV_CHECK(cudaStreamSynchronize(st), "finishing a request");
@@ -1329,6 +1526,10 @@ sgp_status finish(sgp_server* S, Request* R, cudaStream_t st) {
   R->st.rel_res = worst;
   R->st.bytes = R->held;
   R->st.status = SGP_OK;
+  if (ints[kp + 2]) {  // a bulk copy of its set-up never completed: the result is void
+    set_error("sgp_server: a bulk-copy wait of the preconditioner gave up");
+    R->st.status = SGP_ERR_CUDA;
+  }
   R->st.done_us = now_us(S);
   R->st.done = 1;
   if (in.lattice_key && !R->from_cache) {  // keep the lattice resident for reuse
@@ -1389,11 +1590,12 @@ int enqueue_iteration_t(Lane* ln, int dmax, bool sparse, bool pre) {
   kb_alpha<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_xr<<<kGrid, kST, 0, st>>>(T);
   if (pre) {
-    kb_bt<<<kGrid, kST, 0, st>>>(T);
+    const int kp = ln->htab->kp;
+    launch_bt(kp, T, st);
     kb_bt_seg<<<kGrid, kST, 0, st>>>(T);
     kb_bt_total<<<kGrid, kST, 0, st>>>(T);
     kb_minv<<<kGrid, kST, 0, st>>>(T);
-    kb_apply_z<<<kGrid, kST, 0, st>>>(T);
+    kb_apply_z<<<kRingGrid, kST, apply_z_smem_bytes(kp), st>>>(T);
   }
   kb_check_beta<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_p<<<kGrid, kST, 0, st>>>(T);
@@ -1452,8 +1654,10 @@ sgp_status lane_for(sgp_server* S, int key, Lane** out) {
   ln->htab = std::make_unique<Table>();
   SRV_CHECK(cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking), "lane stream");
   SRV_CHECK(cudaMalloc((void**)&ln->dtab, sizeof(Table)), "alloc lane table");
-  SRV_CHECK(cudaMalloc((void**)&ln->dflags, 2 * kMaxSlots * sizeof(int)), "alloc lane flags");
-  SRV_CHECK(cudaMallocHost((void**)&ln->hflags, 2 * kMaxSlots * sizeof(int)), "alloc lane flags");
+  SRV_CHECK(cudaMalloc((void**)&ln->dflags, (2 * kMaxSlots + 1) * sizeof(int)), "alloc lane flags");
+  SRV_CHECK(cudaMemset(ln->dflags, 0, (2 * kMaxSlots + 1) * sizeof(int)), "clear lane flags");
+  SRV_CHECK(cudaMallocHost((void**)&ln->hflags, (2 * kMaxSlots + 1) * sizeof(int)),
+            "alloc lane flags");
   SRV_CHECK(cudaEventCreateWithFlags(&ln->ev, cudaEventDisableTiming), "lane event");
   *out = ln.get();
   S->lanes[key] = std::move(ln);
@@ -1569,9 +1773,27 @@ bool setups_ready(sgp_server* S) {
 // Requests of a lane whose round has finished: finish the stopped ones, keep the rest.
 sgp_status harvest(sgp_server* S, Lane* ln, int* done) {
   std::vector<Request*> keep;
+  const bool voided = ln->hflags[2 * kMaxSlots] != 0;  // a bulk-copy wait gave up
+  if (voided) {
+    set_error("sgp_server: a bulk-copy wait of the preconditioner gave up; the requests of "
+              "that round completed with SGP_ERR_CUDA");
+    ln->hflags[2 * kMaxSlots] = 0;
+    SRV_CHECK(cudaMemsetAsync(ln->dflags + 2 * kMaxSlots, 0, sizeof(int), ln->st),
+              "clear lane error");
+  }
   for (int q = 0; q < (int)ln->active.size(); ++q) {
     Request* R = ln->active[q];
-    if (q < ln->ntab && ln->hflags[2 * q] == 0) {
+    if (voided && q < ln->ntab) {
+      (void)cudaStreamSynchronize(ln->st);
+      R->st.status = SGP_ERR_CUDA;
+      R->st.iters = ln->hflags[2 * q + 1];
+      R->st.bytes = R->held;
+      R->st.done_us = now_us(S);
+      R->st.done = 1;
+      release(S, R, ln->st);
+      S->n_active -= 1;
+      ++*done;
+    } else if (q < ln->ntab && ln->hflags[2 * q] == 0) {
       if (sgp_status s = finish(S, R, ln->st)) return s;
       S->n_active -= 1;
       ++*done;
@@ -1603,6 +1825,7 @@ sgp_status launch(sgp_server* S, Lane* ln) {
     t.nslots = ns;
     t.kp = S->kp;
     t.flags = ln->dflags;
+    t.err = ln->dflags + 2 * kMaxSlots;
     for (int q = 0; q < ns; ++q) {
       Request* R = ln->active[q];
       fill_slot(S, R, t.s[q]);
@@ -1634,6 +1857,9 @@ sgp_status launch(sgp_server* S, Lane* ln) {
   SRV_CHECK(cudaMemcpyAsync(ln->hflags, ln->dflags, 2 * ns * sizeof(int), cudaMemcpyDeviceToHost,
                             ln->st),
             "copy flags");
+  SRV_CHECK(cudaMemcpyAsync(ln->hflags + 2 * kMaxSlots, ln->dflags + 2 * kMaxSlots, sizeof(int),
+                            cudaMemcpyDeviceToHost, ln->st),
+            "copy lane error");
   SRV_CHECK(cudaEventRecord(ln->ev, ln->st), "record flags");
   ln->in_flight = true;
   return SGP_OK;
@@ -1775,6 +2001,10 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->kp = (o.probes + 2 + 3) / 4 * 4;  // y, S probes, the ones column, padding
   S->t0 = std::chrono::steady_clock::now();
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
+  SRV_CHECK(bt_smem_attributes(S->kp), "shared memory of the preconditioner kernels");
+  SRV_CHECK(cudaFuncSetAttribute(kb_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)apply_z_smem_bytes(S->kp)),
+            "shared memory of the preconditioner kernels");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
   sgp_server* raw = S.get();
   const int nthreads = std::min(kSetupThreads, o.max_active);
