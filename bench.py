@@ -79,6 +79,9 @@ def parse_args(argv=None):
                     help="skip the backward (n=500k, d=20) and log-det (n=200k) timings")
     ap.add_argument("--mvm-only", type=int, default=0, metavar="R",
                     help="profiling aid: build once, run R symmetric MVMs, print their time")
+    ap.add_argument("--serve-single", action="store_true",
+                    help="profiling aid: serve two ill-conditioned requests (d = 3, n = 240k "
+                         "and d = 8, n = 100k) one at a time and print their statistics")
     return ap.parse_args(argv)
 
 
@@ -629,9 +632,36 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serve_single():
+    """Two preconditioned requests served alone (one slot), for the launch list and the
+    counters of the preconditioner's kernels: d = 3 with n = 240k (363 vertices, condition
+    estimate ~1e7) and d = 8 with n = 100k; 256 test points each, k = 1 + 8."""
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.serve import Server
+
+    reqs = (synth.serving_stream(1, 901, n_range=(240_000, 240_001), dims=(3,))
+            + synth.serving_stream(1, 902, n_range=(100_000, 100_001), dims=(8,)))
+    out = []
+    for r in reqs:
+        with Server(max_active=1) as srv:
+            rid = srv.submit(r["X"], r["y"], r["Xs"], r["lengthscales"], r["outputscale"],
+                             r["noise"], r["seed"])
+            srv.run_until_idle()
+            st = srv.stats(rid)
+        out.append({"d": r["X"].shape[1], "n": len(r["X"]), "m": st["m"],
+                    "kappa_est": st["kappa_est"], "precond_rank": st["precond_rank"],
+                    "iters": st["iters"], "rel_res": st["rel_res"],
+                    "setup_ms": st["setup_us"] / 1e3,
+                    "total_ms": (st["done_us"] - st["arrival_us"]) / 1e3})
+    print(json.dumps({"serve_single": out}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
+    if args.serve_single:
+        run_serve_single()
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
