@@ -49,6 +49,7 @@ constexpr int kVecRows = 4;         // vector-kernel rows per thread
 constexpr int kMaxLd = kMaxRank;    // preconditioner: B row stride bound
 constexpr int kBtVbRows = 512;      // rows of one B^T r virtual block
 constexpr int kBtSeg = 16;          // B^T r partials per first-level sum
+constexpr int kZVbRows = 576;       // rows of one z virtual block
 constexpr int kStages = 3;          // bulk-copied chunks in flight per block
 constexpr int kRingBytes = 192 * 1024;  // shared memory of the chunk ring
 constexpr int kRingRowsMax = 96;    // rows of one chunk at most
@@ -56,7 +57,8 @@ constexpr int kRingGrid = 152;      // persistent grid of the ring kernels (one 
 constexpr int kSpinLimit = 1 << 20; // bounded mbarrier waits (about a second at most)
 constexpr uint64_t kPrecondSeedXor = 0x6A09E667F3BCC909ull;  // sketch seed = seed ^ this
 
-enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_BT, U_BTS, U_BTT, U_MINV, U_KINDS };
+enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_BT, U_BTS, U_BTT, U_MINV, U_Z,
+       U_KINDS };
 
 // One active request as the kernels see it.  Row-indexed arrays are in the lattice's
 // locality order p; perm[p] < n_train marks a training row.
@@ -101,7 +103,7 @@ struct SlotDev {
   float* bt2;           // [segments][ld][kp] sums of kBtSeg partials
   double* tvec;         // [ld][kp] B^T r
   float* u;             // [ld][kp] Minv B^T r (rows >= l zero)
-  double* dpart2;       // [U_VEC virtual blocks][kp] partials of <r, z>
+  double* dpart2;       // [U_Z virtual blocks][kp] partials of <r, z>
 };
 
 struct Table {
@@ -526,10 +528,11 @@ __global__ void __launch_bounds__(kST) kb_check_beta(const Table* __restrict__ T
   }
   const int kp = T->kp;
   const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
+  const int64_t nvz = T->pre[U_Z][q + 1] - T->pre[U_Z][q];
   const int it = s.state[1] + 1;
   slot_cols_total(s.dpart, nvb, kp, red, trr);
   // preconditioned: beta = <r, z>_new / <r, z>_old; the stopping rule stays on ||r||
-  if (s.l) slot_cols_total(s.dpart2, nvb, kp, red, trz);
+  if (s.l) slot_cols_total(s.dpart2, nvz, kp, red, trz);
   const int c = threadIdx.x;
   int go = 0;
   if (c < kp && s.active[c]) {
@@ -835,31 +838,63 @@ __global__ void __launch_bounds__(kST) kb_minv(const Table* __restrict__ T) {
   SLOT_LOOP_END
 }
 
+// TF32 tensor-core pieces: round to tf32 (nearest, ties away), the 3xTF32 split x = hi + lo
+// (hi·hi + hi·lo + lo·hi keeps about fp32 accuracy), and one m16n8k8 MMA with fp32 sums.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+// D (16 x 8) += A (16 x 8, row-major) B (8 x 8, column-major); lane = 4 g + t holds
+// A[g][t], A[g + 8][t], A[g][t + 4], A[g + 8][t + 4]; B[t][g], B[t + 4][g];
+// D[g][2t], D[g][2t + 1], D[g + 8][2t], D[g + 8][2t + 1].
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // z = (r - B u) / noise, written into ap (free between the x, r update and the next
-// product), and the virtual block's column sums of r z into dpart2.  The block's rows
-// (groups kVecRows of them, as in the other vector kernels) stream through the chunk
-// ring; thread (g, col) computes 4 columns of one row per pass from the staged B row and
-// u (in shared memory).  Test rows have zero B rows and zero r, so z = 0 there.
+// product), and the virtual block's column sums of r z into dpart2.  The block's kZVbRows
+// rows stream through the chunk ring; warp w takes the 16-row tiles w, w + 8, ... of each
+// chunk and forms B u on the tensor cores (m16n8k8, 3xTF32 split, NT tiles of 8 columns),
+// A fragments from the staged B rows, B fragments from u split once into shared memory.  The epilogue
+// reads r from the stage.  The column sums of r z are double-float per lane, combined over
+// the lanes of a column by a fixed butterfly and over the warps in order.  Test rows have
+// zero B rows and zero r, so z = 0 there.
+template <int NT>
 __global__ void __launch_bounds__(kST, 1) kb_apply_z(const Table* __restrict__ T) {
   extern __shared__ __align__(128) float dsm[];
   __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ double sh[kST * 4];
-  const int kp = T->kp, G = kp / 4, groups = kST / G;
-  const int g = threadIdx.x / G, col = (int)(threadIdx.x % G) * 4;
-  float* us = dsm;  // [kMaxLd][kp]
+  __shared__ double red[kST / 32][8 * NT];
+  constexpr int kWarps = kST / 32;
+  const int kp = T->kp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // u split once per virtual block: uh = tf32(u), ul = tf32(u - uh), [kMaxLd][kp] each
+  uint32_t* uh = reinterpret_cast<uint32_t*>(dsm);
+  uint32_t* ul = uh + kMaxLd * kp;
   ChunkRing ring;
-  ring_init(ring, dsm + kMaxLd * kp, bar, kp, true);
-  if (groups < ring.rows) ring.rows = groups;  // one row per thread and chunk
-  SLOT_LOOP(U_VEC)
+  ring_init(ring, dsm + 2 * kMaxLd * kp, bar, kp, true);
+  ring.rows = ring.rows / 16 * 16;
+  SLOT_LOOP(U_Z)
   if (*s.state == 0 || s.l == 0) continue;  // uniform over the block
-  const int ld = s.ld;
-  const int64_t r0 = local * (int64_t)groups * kVecRows;
-  const int64_t r1 = r0 + (int64_t)groups * kVecRows < s.n ? r0 + (int64_t)groups * kVecRows : s.n;
+  const int ld = s.ld, ksteps = (ld + 7) / 8;
+  const int64_t r0 = local * kZVbRows;
+  const int64_t r1 = r0 + kZVbRows < s.n ? r0 + kZVbRows : s.n;
   const int nch = (int)ceil_div(r1 - r0, ring.rows);
   if (threadIdx.x == 0)
     for (int k = 0; k < nch && k < kStages; ++k) ring_issue(ring, k, s, kp, r0, r1, k);
-  for (int e = threadIdx.x; e < ld * kp; e += kST) us[e] = s.u[e];
-  dfloat d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int e = threadIdx.x; e < ld * kp; e += kST) tf32_split(s.u[e], uh[e], ul[e]);
+  dfloat acc[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = {0.f, 0.f};
   for (int k = 0; k < nch; ++k) {
     const int st = k % kStages;
     const bool ok = __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u));
@@ -868,55 +903,80 @@ __global__ void __launch_bounds__(kST, 1) kb_apply_z(const Table* __restrict__ T
       return;
     }
     ring.phase ^= 1u << st;
-    const int64_t a = r0 + (int64_t)k * ring.rows;
-    const int rows = (int)(r1 - a < ring.rows ? r1 - a : ring.rows);
+    const int64_t a0 = r0 + (int64_t)k * ring.rows;
+    const int rows = (int)(r1 - a0 < ring.rows ? r1 - a0 : ring.rows);
     const float* Bs = ring.B(st);
     const float* Hs = Bs + rows * ld;
     const float* Ls = Hs + rows * kp;
-    if (g < groups)
-      for (int rr = g; rr < rows; rr += groups) {
-        const float* brow = Bs + rr * ld;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), acc2 = acc;
-        int q4 = 0;
-        for (; q4 + 2 <= ld / 4; q4 += 2) {  // two independent chains
-          const float4 b0 = *reinterpret_cast<const float4*>(brow + 4 * q4);
-          const float4 b1 = *reinterpret_cast<const float4*>(brow + 4 * q4 + 4);
-          const float* u0 = us + 4 * q4 * kp + col;
-          const float* u1 = u0 + 4 * kp;
-          acc = f4_fma(b0.x, *reinterpret_cast<const float4*>(u0), acc);
-          acc2 = f4_fma(b1.x, *reinterpret_cast<const float4*>(u1), acc2);
-          acc = f4_fma(b0.y, *reinterpret_cast<const float4*>(u0 + kp), acc);
-          acc2 = f4_fma(b1.y, *reinterpret_cast<const float4*>(u1 + kp), acc2);
-          acc = f4_fma(b0.z, *reinterpret_cast<const float4*>(u0 + 2 * kp), acc);
-          acc2 = f4_fma(b1.z, *reinterpret_cast<const float4*>(u1 + 2 * kp), acc2);
-          acc = f4_fma(b0.w, *reinterpret_cast<const float4*>(u0 + 3 * kp), acc);
-          acc2 = f4_fma(b1.w, *reinterpret_cast<const float4*>(u1 + 3 * kp), acc2);
+    for (int rt = warp * 16; rt < rows; rt += kWarps * 16) {
+      float d[NT][4];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
+      // rows past the chunk read stale stage data; their outputs are not stored
+      const float* ra = Bs + (rt + g) * ld;
+      const float* rb = ra + 8 * ld;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int j0 = ks * 8 + t, j1 = j0 + 4;
+        const bool in0 = j0 < ld, in1 = j1 < ld;
+        uint32_t ah[4], al[4];
+        tf32_split(in0 ? ra[j0] : 0.f, ah[0], al[0]);
+        tf32_split(in0 ? rb[j0] : 0.f, ah[1], al[1]);
+        tf32_split(in1 ? ra[j1] : 0.f, ah[2], al[2]);
+        tf32_split(in1 ? rb[j1] : 0.f, ah[3], al[3]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int n = 8 * nt + g;
+          const bool n_in = n < kp;
+          const uint32_t bh0 = in0 && n_in ? uh[j0 * kp + n] : 0u;
+          const uint32_t bl0 = in0 && n_in ? ul[j0 * kp + n] : 0u;
+          const uint32_t bh1 = in1 && n_in ? uh[j1 * kp + n] : 0u;
+          const uint32_t bl1 = in1 && n_in ? ul[j1 * kp + n] : 0u;
+          mma_tf32(d[nt], ah, bh0, bh1);
+          mma_tf32(d[nt], ah, bl0, bl1);
+          mma_tf32(d[nt], al, bh0, bh1);
         }
-        if (q4 < ld / 4) {
-          const float4 b0 = *reinterpret_cast<const float4*>(brow + 4 * q4);
-          const float* u0 = us + 4 * q4 * kp + col;
-          acc = f4_fma(b0.x, *reinterpret_cast<const float4*>(u0), acc);
-          acc = f4_fma(b0.y, *reinterpret_cast<const float4*>(u0 + kp), acc);
-          acc = f4_fma(b0.z, *reinterpret_cast<const float4*>(u0 + 2 * kp), acc);
-          acc = f4_fma(b0.w, *reinterpret_cast<const float4*>(u0 + 3 * kp), acc);
-        }
-        acc = make_float4(acc.x + acc2.x, acc.y + acc2.y, acc.z + acc2.z, acc.w + acc2.w);
-        const float4 h = *reinterpret_cast<const float4*>(Hs + rr * kp + col);
-        const float4 lo = *reinterpret_cast<const float4*>(Ls + rr * kp + col);
-        const float x0 = __fadd_rn(h.x, lo.x), x1 = __fadd_rn(h.y, lo.y);
-        const float x2 = __fadd_rn(h.z, lo.z), x3 = __fadd_rn(h.w, lo.w);
-        const float4 z = make_float4((x0 - acc.x) * s.inv_noise, (x1 - acc.y) * s.inv_noise,
-                                     (x2 - acc.z) * s.inv_noise, (x3 - acc.w) * s.inv_noise);
-        f4_st(s.ap + (a + rr) * kp + col, z);
-        d[0] = df_add(d[0], df_two_prod(x0, z.x));
-        d[1] = df_add(d[1], df_two_prod(x1, z.y));
-        d[2] = df_add(d[2], df_two_prod(x2, z.z));
-        d[3] = df_add(d[3], df_two_prod(x3, z.w));
       }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int c = 8 * nt + 2 * t;
+        if (c >= kp) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int row = rt + g + 8 * half;
+          if (row >= rows) continue;
+          const float2 h = *reinterpret_cast<const float2*>(Hs + row * kp + c);
+          const float2 lo = *reinterpret_cast<const float2*>(Ls + row * kp + c);
+          const float x0 = __fadd_rn(h.x, lo.x), x1 = __fadd_rn(h.y, lo.y);
+          const float z0 = (x0 - d[nt][2 * half]) * s.inv_noise;
+          const float z1 = (x1 - d[nt][2 * half + 1]) * s.inv_noise;
+          *reinterpret_cast<float2*>(s.ap + (a0 + row) * kp + c) = make_float2(z0, z1);
+          acc[nt][0] = df_add(acc[nt][0], df_two_prod(x0, z0));
+          acc[nt][1] = df_add(acc[nt][1], df_two_prod(x1, z1));
+        }
+      }
+    }
     __syncthreads();  // stage st is free again
     if (threadIdx.x == 0 && k + kStages < nch) ring_issue(ring, st, s, kp, r0, r1, k + kStages);
   }
-  vb_column_sums(d, kp, s.dpart2 + local * kp, sh);
+  // column sums: the 8 lanes of a column (same t) by a fixed butterfly, then the warps in order
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      double v = df_to_double(acc[nt][e]);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      const int c = 8 * nt + 2 * t + e;
+      if (g == 0 && c < kp) red[warp][c] = v;
+    }
+  __syncthreads();
+  if ((int)threadIdx.x < kp) {
+    double v = 0.0;
+    for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
+    s.dpart2[local * kp + threadIdx.x] = v;
+  }
+  __syncthreads();
   SLOT_LOOP_END
 }
 
@@ -924,7 +984,30 @@ __global__ void __launch_bounds__(kST, 1) kb_apply_z(const Table* __restrict__ T
 size_t ring_smem_bytes(int kp) {
   return (size_t)kStages * ring_rows_cap(kp) * (kMaxLd + 2 * kp) * 4;
 }
-size_t apply_z_smem_bytes(int kp) { return ring_smem_bytes(kp) + (size_t)kMaxLd * kp * 4; }
+size_t apply_z_smem_bytes(int kp) { return ring_smem_bytes(kp) + 2 * (size_t)kMaxLd * kp * 4; }
+
+// kb_apply_z for the server's kp: NT = kp / 8 rounded up tiles of 8 columns.
+void launch_apply_z(int kp, const Table* T, cudaStream_t st) {
+  const size_t sm = apply_z_smem_bytes(kp);
+  switch ((kp + 7) / 8) {
+    case 1: kb_apply_z<1><<<kRingGrid, kST, sm, st>>>(T); break;
+    case 2: kb_apply_z<2><<<kRingGrid, kST, sm, st>>>(T); break;
+    case 3: kb_apply_z<3><<<kRingGrid, kST, sm, st>>>(T); break;
+    default: kb_apply_z<4><<<kRingGrid, kST, sm, st>>>(T); break;
+  }
+}
+cudaError_t apply_z_smem_attributes(int kp) {
+  const int sm = (int)apply_z_smem_bytes(kp);
+  cudaError_t e =
+      cudaFuncSetAttribute(kb_apply_z<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_apply_z<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_apply_z<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_apply_z<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
 
 // kb_bt for the server's kp: KC = min(kp, 16) columns per pass.
 void launch_bt(int kp, const Table* T, cudaStream_t st) {
@@ -978,8 +1061,9 @@ __global__ void __launch_bounds__(kST) kb_init_scalars(const Table* __restrict__
   const SlotDev& s = T->s[q];
   const int kp = T->kp;
   const int64_t nvb = T->pre[U_VEC][q + 1] - T->pre[U_VEC][q];
+  const int64_t nvz = T->pre[U_Z][q + 1] - T->pre[U_Z][q];
   slot_cols_total(s.dpart, nvb, kp, red, trr);
-  if (s.l) slot_cols_total(s.dpart2, nvb, kp, red, trz);
+  if (s.l) slot_cols_total(s.dpart2, nvz, kp, red, trz);
   const int c = threadIdx.x;
   int on = 0;
   if (c < kp) {
@@ -1268,6 +1352,7 @@ void unit_counts(const sgp_server* S, const Request* R, int64_t (&vb)[U_KINDS]) 
   vb[U_BTS] = R->l ? nch * ceil_div(vb[U_BT], kBtSeg) : 0;
   vb[U_BTT] = R->l ? nch : 0;
   vb[U_MINV] = R->l ? ceil_div((int64_t)R->ld * S->kp * 4, kST) : 0;
+  vb[U_Z] = R->l ? ceil_div(L->n, kZVbRows) : 0;
 }
 
 // Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur,
@@ -1425,12 +1510,12 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
       SRV_CHECK(get((void**)&R->bt2, nseg * ld * kp * sizeof(float)), "alloc B^T r sums");
       SRV_CHECK(get((void**)&R->tvec, (size_t)ld * kp * sizeof(double)), "alloc B^T r");
       SRV_CHECK(get((void**)&R->u, (size_t)ld * kp * sizeof(float)), "alloc Minv B^T r");
-      SRV_CHECK(get((void**)&R->dpart2, (size_t)R->vb[U_VEC] * kp * sizeof(double)),
+      SRV_CHECK(get((void**)&R->dpart2, (size_t)R->vb[U_Z] * kp * sizeof(double)),
                 "alloc <r, z> partials");
       pre_bytes = (size_t)n_all * ld * sizeof(float) + (size_t)l * l * sizeof(double) +
                   ((size_t)R->vb[U_BT] + nseg) * ld * kp * sizeof(float) +
                   (size_t)ld * kp * (sizeof(double) + sizeof(float)) +
-                  (size_t)R->vb[U_VEC] * kp * sizeof(double);
+                  (size_t)R->vb[U_Z] * kp * sizeof(double);
       void* scratch = nullptr;
       int* status_d = nullptr;
       SRV_CHECK(tmp.get(&scratch, nystrom_masked_scratch_bytes(l, n_all)),
@@ -1471,7 +1556,7 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
     kb_bt_seg<<<kGrid, kST, 0, st>>>(R->dtab1);
     kb_bt_total<<<kGrid, kST, 0, st>>>(R->dtab1);
     kb_minv<<<kGrid, kST, 0, st>>>(R->dtab1);
-    kb_apply_z<<<kRingGrid, kST, apply_z_smem_bytes(kp), st>>>(R->dtab1);
+    launch_apply_z(kp, R->dtab1, st);
     note_launches(5);
   }
   kb_init_scalars<<<1, kST, 0, st>>>(R->dtab1);
@@ -1595,7 +1680,7 @@ int enqueue_iteration_t(Lane* ln, int dmax, bool sparse, bool pre) {
     kb_bt_seg<<<kGrid, kST, 0, st>>>(T);
     kb_bt_total<<<kGrid, kST, 0, st>>>(T);
     kb_minv<<<kGrid, kST, 0, st>>>(T);
-    kb_apply_z<<<kRingGrid, kST, apply_z_smem_bytes(kp), st>>>(T);
+    launch_apply_z(kp, T, st);
   }
   kb_check_beta<<<kMaxSlots, kST, 0, st>>>(T);
   kb_update_p<<<kGrid, kST, 0, st>>>(T);
@@ -1655,7 +1740,10 @@ sgp_status lane_for(sgp_server* S, int key, Lane** out) {
   SRV_CHECK(cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking), "lane stream");
   SRV_CHECK(cudaMalloc((void**)&ln->dtab, sizeof(Table)), "alloc lane table");
   SRV_CHECK(cudaMalloc((void**)&ln->dflags, (2 * kMaxSlots + 1) * sizeof(int)), "alloc lane flags");
-  SRV_CHECK(cudaMemset(ln->dflags, 0, (2 * kMaxSlots + 1) * sizeof(int)), "clear lane flags");
+  // on the lane's own stream: a legacy-stream memset is not ordered with the lane's kernels
+  // and could land after the first round has written its flags
+  SRV_CHECK(cudaMemsetAsync(ln->dflags, 0, (2 * kMaxSlots + 1) * sizeof(int), ln->st),
+            "clear lane flags");
   SRV_CHECK(cudaMallocHost((void**)&ln->hflags, (2 * kMaxSlots + 1) * sizeof(int)),
             "alloc lane flags");
   SRV_CHECK(cudaEventCreateWithFlags(&ln->ev, cudaEventDisableTiming), "lane event");
@@ -2002,9 +2090,7 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->t0 = std::chrono::steady_clock::now();
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
   SRV_CHECK(bt_smem_attributes(S->kp), "shared memory of the preconditioner kernels");
-  SRV_CHECK(cudaFuncSetAttribute(kb_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)apply_z_smem_bytes(S->kp)),
-            "shared memory of the preconditioner kernels");
+  SRV_CHECK(apply_z_smem_attributes(S->kp), "shared memory of the preconditioner kernels");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
   sgp_server* raw = S.get();
   const int nthreads = std::min(kSetupThreads, o.max_active);

@@ -198,6 +198,25 @@ def test_bf16_values_error_against_fp32():
         assert err <= 0.3
 
 
+def test_every_request_stops_at_tol_or_max_iter_in_fresh_lanes():
+    """A request may stop only at the tolerance or at max_iter (a non-positive <p, A p>
+    cannot occur on these SPD systems).  Eight dimension classes open a new lane each, so
+    every request's first round runs in a lane created just before it: the lane's flag
+    buffer must be cleared in order with the lane's own work."""
+    reqs = []
+    for i, d in enumerate((2, 3, 5, 9, 17, 33, 65, 100)):
+        reqs += synth.serving_stream(2, 60 + i, n_range=(2000, 4000), dims=(d,), test_points=32)
+    tol, max_iter = 1e-4, 3000
+    for rep in range(3):
+        with Server(max_active=16, tol=tol, max_iter=max_iter) as srv:
+            ids = submit_all(srv, reqs)
+            srv.run_until_idle()
+            for r, rid in zip(reqs, ids):
+                st = srv.stats(rid)
+                assert st["status"] == 0
+                assert st["rel_res"] <= tol or st["iters"] == max_iter, (r["X"].shape, st)
+
+
 def test_bad_requests_are_rejected():
     r = small_requests(1, seed=1)[0]
     with Server(max_active=2) as srv:
