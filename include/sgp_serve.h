@@ -48,7 +48,10 @@
  * (X, y, Xs, lengthscales, mean, var) must stay valid until the request has completed
  * (sgp_request_stats.done != 0).  Errors follow sgp.h: every call returns an sgp_status
  * and sgp_last_error() has the message; a request whose build fails completes with its
- * own status and does not stop the server.
+ * own status and does not stop the server.  The preconditioner's kernels wait on
+ * bulk-copy barriers with a bounded number of polls; should a wait give up, the kernel
+ * records it and returns, and the requests of that round complete with SGP_ERR_CUDA
+ * (their mean/var are not written) while the server keeps running.
  */
 #ifndef SGP_SERVE_H_
 #define SGP_SERVE_H_
