@@ -8,10 +8,14 @@
 // vector stays in the training subspace.  Right-hand sides: column 0 = y, columns
 // 1..S = KX* z_s for Rademacher probes z_s over the test points; after the solve one
 // product sliced at the test rows gives the mean (column 0) and the probe estimate of
-// diag(K*X A^-1 KX*) (columns 1..S).
+// diag(K*X A^-1 KX*) (columns 1..S).  The probe product also carries a ones column over
+// the training rows (column kp - 1): its largest entry is the Gershgorin bound behind
+// the request's condition estimate, which decides whether its CG is preconditioned with
+// the rank-l Nystrom factor of App. A.
 //
 // Batching: one CG iteration of every active request is a fixed sequence of kernels
-// (splat, two fix-ups, 2 Dmax blur passes, slice with <p, Ap>, alpha, x/r update,
+// (splat, two fix-ups, 2 Dmax blur passes, slice with <p, Ap>, alpha, x/r update; for
+// preconditioned requests B^T r, its two ordered sums, Minv B^T r and z = P^-1 r; then
 // convergence check and beta, p update) with fixed grids.  Each kernel walks "virtual
 // blocks" over a device table of the active requests; a request's virtual blocks cover
 // its own rows in a partition fixed by its own sizes, so its results (and reduction
@@ -19,8 +23,8 @@
 // are skipped by a device flag; blur pass t touches only requests with t < 2 (d + 1).
 // Requests are grouped into lanes of similar dimension and per-iteration work; each lane
 // is such a batch with its own table, stream and CUDA graph of one iteration (captured
-// once per Dmax and replayed), rewritten (stream-ordered) when requests join or leave,
-// and the lanes run concurrently.
+// once per Dmax, sparse blur and preconditioning, then replayed), rewritten
+// (stream-ordered) when requests join or leave, and the lanes run concurrently.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
