@@ -107,3 +107,34 @@ def test_server_without_gpu_fails_loudly(lib):
     assert not h.value
     o.max_active = 0
     assert lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)) == 1
+
+
+def test_struct_layouts_match_the_headers(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets: a C
+    program compiled against include/*.h prints them and they are compared with ctypes."""
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_lib.sgp_opts, _lib.sgp_server_opts, _lib.sgp_request, _lib.sgp_request_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sgp_serve.h"',
+             "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in st._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out.strip().splitlines())}
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
