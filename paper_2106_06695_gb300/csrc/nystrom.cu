@@ -17,6 +17,7 @@
 // formed from the stored values.  All row-indexed arrays are in the lattice's locality
 // order.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -432,17 +433,17 @@ sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int 
     return e;
   };
   {  // shared-memory sizes beyond the 48 KB default, once per device
-    static bool attrs[64] = {};
+    static std::atomic<bool> attrs[64];  // several host threads may arrive here at once
     int dev = 0;
     NY_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
-    if (dev >= 0 && dev < 64 && !attrs[dev]) {
+    if (dev >= 0 && dev < 64 && !attrs[dev].load()) {
       const int big = 200 * 1024;
       cudaFuncSetAttribute(k_gram<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_gram<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_rows_times, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_bt_r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      attrs[dev] = true;
+      attrs[dev].store(true);
     }
   }
   float* Y = nullptr;
@@ -545,16 +546,16 @@ sgp_status nystrom_build_masked(Lattice* L, int64_t n_train, int l, int ld, uint
   double* work = Q + ll;
   float* T = reinterpret_cast<float*>(work + ll);
   {  // shared-memory sizes beyond the 48 KB default, once per device
-    static bool attrs[64] = {};
+    static std::atomic<bool> attrs[64];  // several host threads may arrive here at once
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
-    if (dev >= 0 && dev < 64 && !attrs[dev]) {
+    if (dev >= 0 && dev < 64 && !attrs[dev].load()) {
       const int big = 200 * 1024;
       cudaFuncSetAttribute(k_gram<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_gram<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
       cudaFuncSetAttribute(k_rows_times_inplace, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      attrs[dev] = true;
+      attrs[dev].store(true);
     }
   }
   cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), st);
