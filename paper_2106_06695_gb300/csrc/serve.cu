@@ -30,6 +30,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <mutex>
+#include <string>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -1213,6 +1214,7 @@ struct Request {
   float *btpart = nullptr, *bt2 = nullptr, *u = nullptr;
   double *tvec = nullptr, *dpart2 = nullptr;
   std::vector<void*> ptrs;
+  std::string setup_error;  // message of a failed set-up (set on the set-up thread)
 };
 
 struct Lane {
@@ -1783,6 +1785,8 @@ void setup_worker(sgp_server* S) {
     const double t = now_us(S);
     const sgp_status status = setup(S, R, st, *t1);
     R->st.setup_us = now_us(S) - t;
+    // error messages are per host thread: carry this one to the stepping thread
+    if (status != SGP_OK) R->setup_error = sgp_last_error();
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->setup_done.emplace_back(R, status);
@@ -1808,6 +1812,7 @@ sgp_status collect_setups(sgp_server* S, int* done) {
     Lane* ln = nullptr;
     if (s == SGP_OK) s = lane_for(S, lane_key(S, R), &ln);
     if (s != SGP_OK) {
+      if (!R->setup_error.empty()) set_error("request set-up: " + R->setup_error);
       R->st.status = s;
       R->held = 0;
       release(S, R, S->bs);
