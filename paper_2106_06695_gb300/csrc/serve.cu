@@ -698,7 +698,8 @@ __device__ __forceinline__ void ring_init(ChunkRing& ring, float* base, uint64_t
 }
 
 // ---- preconditioner apply z = P^-1 r (requests with l > 0) ----------------------------
-// P^-1 r = (r - B Minv B^T r) / noise (Woodbury), in four table-driven steps.
+// P^-1 r = (r - B Minv B^T r) / noise (Woodbury), in five table-driven kernels: B^T r
+// partials, two ordered sums, Minv (B^T r), and z with the <r, z> partials.
 
 // Per-virtual-block partial of B^T r over kBtVbRows rows, with r taken as its fp32 part
 // rh (the low part rl is below the preconditioner's own rounding): the rows stream through
