@@ -2099,8 +2099,9 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->kp = (o.probes + 2 + 3) / 4 * 4;  // y, S probes, the ones column, padding
   S->t0 = std::chrono::steady_clock::now();
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
-  SRV_CHECK(bt_smem_attributes(S->kp), "shared memory of the preconditioner kernels");
-  SRV_CHECK(apply_z_smem_attributes(S->kp), "shared memory of the preconditioner kernels");
+  // the attribute is per kernel, shared by every server: allow the largest kp
+  SRV_CHECK(bt_smem_attributes(kMaxServeK), "shared memory of the preconditioner kernels");
+  SRV_CHECK(apply_z_smem_attributes(kMaxServeK), "shared memory of the preconditioner kernels");
   SRV_CHECK(cudaStreamCreateWithFlags(&S->bs, cudaStreamNonBlocking), "stream");
   sgp_server* raw = S.get();
   const int nthreads = std::min(kSetupThreads, o.max_active);

@@ -217,6 +217,29 @@ def test_every_request_stops_at_tol_or_max_iter_in_fresh_lanes():
                 assert st["rel_res"] <= tol or st["iters"] == max_iter, (r["X"].shape, st)
 
 
+def test_servers_with_different_probe_counts_coexist():
+    """The preconditioner kernels' shared-memory limit is a per-kernel attribute shared by
+    all servers: a server with 30 probes (kp = 32) keeps working after one with 2 probes
+    (kp = 4) has been created, and both give the oracle's posterior."""
+    r = small_requests(1, seed=71, n_range=(3000, 3001), dims=(3,), ns=32)[0]
+    out = {}
+    with Server(max_active=2, probes=30, precond_min_kappa=0.0, tol=1e-5, max_iter=2000) as big:
+        with Server(max_active=2, probes=2, precond_min_kappa=0.0, tol=1e-5,
+                    max_iter=2000) as small:
+            a = submit_all(small, [r])[0]
+            small.run_until_idle()
+            out[2] = (small.stats(a), small.result(a)[0].copy())
+        b = submit_all(big, [r])[0]
+        big.run_until_idle()
+        out[30] = (big.stats(b), big.result(b)[0].copy())
+    m_ref, _, _, _ = gp_posterior(r["X"], r["y"], r["Xs"], r["lengthscales"], r["noise"],
+                                  probes=2, seed=r["seed"], tol=1e-5, max_iter=2000,
+                                  precond_rank=out[2][0]["precond_rank"])
+    for probes, (st, mean) in out.items():
+        assert st["status"] == 0 and st["precond_rank"] > 0, (probes, st)
+        assert np.linalg.norm(mean - m_ref) / np.linalg.norm(m_ref) <= 1e-3, probes
+
+
 def test_bad_requests_are_rejected():
     r = small_requests(1, seed=1)[0]
     with Server(max_active=2) as srv:
