@@ -85,3 +85,26 @@ def test_pcg_solves_the_same_system_in_fewer_iterations():
     assert np.allclose(xp, exact, rtol=0, atol=1e-5 * np.abs(exact).max())
     true_rel = np.linalg.norm(B - A @ xp, axis=0) / np.linalg.norm(B, axis=0)
     assert np.allclose(true_rel, rp, rtol=1e-3, atol=1e-12)
+
+
+def test_pcg_columns_edge_cases():
+    """The preconditioned CG's start rule, as the device applies it: a zero right-hand
+    side gives x = 0 with no iterations, tol >= 1 or max_iter = 0 run none, and an
+    identity preconditioner reproduces plain CG's iterates and counts."""
+    from oracle.oracle import _cg_columns, _pcg_columns
+
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((30, 30))
+    A = M @ M.T + 30 * np.eye(30)
+    B = rng.standard_normal((30, 3))
+    B[:, 1] = 0.0
+    apply_A = lambda V: A @ V  # noqa: E731
+    X, it, rel = _pcg_columns(apply_A, B, lambda R: R.copy(), 1e-10, 200)
+    assert it[1] == 0 and np.all(X[:, 1] == 0.0) and rel[1] == 0.0
+    assert np.allclose(A @ X, B, atol=1e-8)
+    Xc, itc, _ = _cg_columns(apply_A, B, 1e-10, 200)
+    assert np.array_equal(it, itc) and np.allclose(X, Xc, atol=1e-12)
+    for tol, mi in ((1.0, 200), (1e-10, 0)):
+        X0, it0, rel0 = _pcg_columns(apply_A, B, lambda R: R.copy(), tol, mi)
+        assert np.all(it0 == 0) and np.all(X0 == 0.0)
+        assert np.array_equal(rel0, np.where(np.linalg.norm(B, axis=0) > 0, 1.0, 0.0))
