@@ -16,9 +16,13 @@ from .oracle import (  # noqa: F401
     elevate,
     gp_posterior,
     lanczos_quadrature,
+    max_threads,
     nystrom_apply,
     nystrom_factor,
+    nystrom_shifted,
+    nystrom_shifted_apply,
     rademacher_sketch,
+    set_threads,
     splitmix64,
     simplex,
     fourier_coverage,

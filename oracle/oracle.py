@@ -28,14 +28,17 @@ _c_int_p = ctypes.POINTER(ctypes.c_int)
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile the oracle with g++ (-O2, no FMA contraction, no fast-math)."""
+    """Compile the oracle with g++ (-O2, no FMA contraction, no fast-math), with OpenMP
+    when the compiler supports it (else the thread count stays 1)."""
     with _lock:
         stale = not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
         if force or stale:
             tmp = _LIB + ".%d.tmp" % os.getpid()
             cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
                    "-fPIC", "-shared", "-o", tmp, _SRC]
-            subprocess.run(cmd, check=True)
+            if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:],
+                              stderr=subprocess.DEVNULL).returncode != 0:
+                subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -80,6 +83,12 @@ def _load():
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                _c_double_p, _c_int_p, _c_double_p]
         lib.orc_cg.restype = ctypes.c_int
+        lib.orc_cg_history.argtypes = lib.orc_cg.argtypes + [_c_double_p]
+        lib.orc_cg_history.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_max_threads.argtypes = []
+        lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_dense_rbf.argtypes = [_c_float_p, _c_float_p, ctypes.c_int64, ctypes.c_int,
                                       _c_double_p, ctypes.c_int, _c_double_p]
         lib.orc_dense_rbf.restype = None
@@ -96,6 +105,17 @@ def _load():
 
 def _p(a, t):
     return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's parallel loops (results are bit-identical for any count);
+    returns the count in effect (1 when the library was built without OpenMP)."""
+    return _load().orc_set_threads(int(t))
+
+
+def max_threads() -> int:
+    """Processors the oracle's parallel loops can use."""
+    return _load().orc_max_threads()
 
 
 def stencil(kind: int = RBF_BINOMIAL, r: int = 1, spacing: float = 0.0):
@@ -279,6 +299,19 @@ class OracleLattice:
         """P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise (Woodbury)."""
         return nystrom_apply(Bm, Q, noise, r)
 
+    def pcg_shifted(self, B, noise: float, rank: int, tol: float = 1e-3, max_iter: int = 500,
+                    seed: int = 0, outputscale: float = 1.0, power_iters: int = 1):
+        """Preconditioned CG with the nystrom_shifted preconditioner of outputscale K~
+        (symmetric blur) on (outputscale K~ + noise I) X = B, every column independent,
+        stopping on ||r|| / ||b|| <= tol.  Returns X, iterations, rel. residuals, tau."""
+        B2, shape = self._as2d(B)
+        Bm, tau, Minv = nystrom_shifted(lambda V: self.mvm(V, mode=2, alpha=outputscale),
+                                        self.n, rank, noise, seed, power_iters)
+        X, iters, rel = _pcg_columns(
+            lambda P: self.mvm(P, mode=2, alpha=outputscale, beta=noise), B2,
+            lambda R: nystrom_shifted_apply(Bm, tau, Minv, R), tol, max_iter)
+        return X.reshape(shape), iters, rel, tau
+
     def pcg(self, B, noise: float, rank: int, tol: float = 1e-3, max_iter: int = 500,
             seed: int = 0, outputscale: float = 1.0, mode: int = 2):
         """Preconditioned CG (P = B B^T + noise I from nystrom) on (outputscale K~ + noise I)
@@ -297,18 +330,24 @@ class OracleLattice:
                                   Z, max_lanczos, tol)
 
     def cg(self, B, noise: float, tol: float = 1e-3, max_iter: int = 500,
-           outputscale: float = 1.0, mode: int = 0):
-        """CG on (outputscale K~ + noise I) X = B; returns X, iterations, rel. residuals."""
+           outputscale: float = 1.0, mode: int = 0, history: bool = False):
+        """CG on (outputscale K~ + noise I) X = B; returns X, iterations, rel. residuals
+        (and, with history=True, the [max_iter][k] relative residual after every iteration,
+        NaN where a column had stopped)."""
         B2, shape = self._as2d(B)
         k = B2.shape[1]
         X = np.zeros_like(B2)
         iters = np.zeros(k, np.int32)
         rel = np.zeros(k, np.float64)
-        rc = _lib.orc_cg(self._h, _p(B2, ctypes.c_double), k, outputscale, noise, tol,
-                         max_iter, mode, _p(X, ctypes.c_double), _p(iters, ctypes.c_int),
-                         _p(rel, ctypes.c_double))
+        hist = np.full((max(max_iter, 1), k), np.nan) if history else None
+        rc = _lib.orc_cg_history(self._h, _p(B2, ctypes.c_double), k, outputscale, noise, tol,
+                                 max_iter, mode, _p(X, ctypes.c_double),
+                                 _p(iters, ctypes.c_int), _p(rel, ctypes.c_double),
+                                 _p(hist, ctypes.c_double) if history else None)
         if rc != 0:
             raise ValueError("orc_cg: invalid arguments")
+        if history:
+            return X.reshape(shape), iters, rel, hist[:max_iter]
         return X.reshape(shape), iters, rel
 
 
@@ -329,6 +368,45 @@ def nystrom_factor(apply_K, n: int, rank: int, noise: float, seed: int = 0):
     Bm = solve_triangular(R, Y.T, lower=True).T
     Q = cholesky(noise * np.eye(rank) + Bm.T @ Bm, lower=True)
     return Bm, Q
+
+
+def nystrom_shifted(apply_K, n: int, rank: int, noise: float, seed: int = 0,
+                    power_iters: int = 1, rel_shift: float = 1e-6):
+    """Randomized Nystrom preconditioner of large rank for A = K + noise I (App. A: CG
+    pre-conditioner; the rank grows with the system's conditioning), built from products
+    with the symmetric positive semi-definite K only:
+      Omega   the n x l rademacher_sketch(n, l, seed);
+      Q       Omega, or after `power_iters` subspace iterations an orthonormal basis of
+              K^q Omega (numpy QR of each product; the approximation depends only on the
+              subspace);
+      Y       = K Q;  C = (Q^T Y + Y^T Q) / 2 + eps I,  eps = rel_shift max_j C_jj;
+      B       = Y R^-T with C = R R^T, so that B B^T = Y C^-1 Y^T ~ K;
+      tau     = lambda_min(B^T B) + noise (the smallest retained eigenvalue of the
+              approximation, plus the noise);
+      P       = B B^T + tau I, applied as P^-1 r = (r - B (tau I + B^T B)^-1 B^T r) / tau.
+    On the captured subspace P ~ K + tau I and elsewhere P = tau I, so P^-1 A has its
+    spectrum in [noise / tau, ~1]: the condition number is about tau / noise.  Returns
+    (B, tau, Minv) with Minv = (tau I + B^T B)^-1."""
+    from scipy.linalg import cholesky, solve_triangular
+
+    Q = rademacher_sketch(n, rank, seed)
+    for _ in range(power_iters):
+        Q, _ = np.linalg.qr(apply_K(Q))
+    Y = apply_K(Q)
+    C = Q.T @ Y
+    C = 0.5 * (C + C.T)
+    C += rel_shift * np.max(np.diag(C)) * np.eye(rank)
+    R = cholesky(C, lower=True)
+    Bm = solve_triangular(R, Y.T, lower=True).T
+    G = Bm.T @ Bm
+    tau = float(np.linalg.eigvalsh(G)[0]) + noise
+    Minv = np.linalg.inv(tau * np.eye(rank) + G)
+    return Bm, tau, Minv
+
+
+def nystrom_shifted_apply(Bm, tau: float, Minv, r):
+    """P^-1 r for P = B B^T + tau I (Woodbury identity)."""
+    return (r - Bm @ (Minv @ (Bm.T @ r))) / tau
 
 
 def nystrom_apply(Bm, Q, noise: float, r):

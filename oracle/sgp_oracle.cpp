@@ -40,6 +40,15 @@
 //
 // Built with -O2 -ffp-contract=off (no fused multiply-add, no fast-math) so that every
 // floating-point operation of the lattice construction is one IEEE-rounded operation.
+//
+// Threads (orc_set_threads, OpenMP when the compiler has it): with more than one thread
+// the per-point elevation, the per-vertex blur, the per-point slice, the CG's per-column
+// updates and the neighbour lookups run in parallel, each output computed by exactly the
+// same operations in the same order as with one thread; the splat becomes a per-vertex
+// gather over the vertex's incidences in increasing point order, which is the order in
+// which the sequential scatter adds them.  Results are therefore bit-identical for every
+// thread count (pinned by a test).  Vertex insertion stays sequential (first-occurrence
+// ids).
 
 #include <cmath>
 #include <cstdint>
@@ -48,9 +57,15 @@
 #include <unordered_map>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace {
 
 enum { ORC_OK = 0, ORC_ERR_INVALID_ARG = 1 };
+
+int g_threads = 1;  // threads of the parallel loops (orc_set_threads)
 
 enum { ORC_RBF_BINOMIAL = 0, ORC_RBF_COVERAGE = 1, ORC_MATERN32_COVERAGE = 2 };
 
@@ -76,6 +91,11 @@ struct Lattice {
   // memo of neighbour lookups: nbr[((j * r + (t-1)) * 2 + (sgn > 0)) * m + v] = id of
   // key_v + sgn t u_j or -1, filled on first use
   std::vector<int> nbr;
+  // memo of the splat incidences grouped by vertex (used with more than one thread):
+  // the incidences (point i, vertex slot kk) of vertex v are inc[inc_ptr[v] .. inc_ptr[v+1])
+  // as i * D + kk, in increasing i
+  std::vector<int64_t> inc_ptr;
+  std::vector<int64_t> inc;
 };
 
 std::string key_bytes(const int* key, int D) {
@@ -225,16 +245,18 @@ const std::vector<int>& neighbours(const Lattice& L) {
   if (M.nbr.empty() && L.m > 0) {
     const int D = L.D;
     M.nbr.assign((size_t)D * L.r * 2 * L.m, -1);
-    std::vector<int> nk(D);
     for (int j = 0; j < D; ++j)
       for (int t = 1; t <= L.r; ++t)
-        for (int sgn = -1; sgn <= 1; sgn += 2)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
           for (int64_t v = 0; v < L.m; ++v) {
+            std::vector<int> nk(D);
             const int* key = &L.keys[v * D];
             for (int i = 0; i < D; ++i) nk[i] = key[i] + sgn * t * ((i == j ? D : 0) - 1);
             M.nbr[(((size_t)j * L.r + (t - 1)) * 2 + (sgn > 0)) * L.m + v] =
                 find_vertex(L, nk.data());
           }
+        }
   }
   return M.nbr;
 }
@@ -242,6 +264,7 @@ const std::vector<int>& neighbours(const Lattice& L) {
 void blur_direction(const Lattice& L, int j, int k, const std::vector<double>& in,
                     std::vector<double>& out) {
   const std::vector<int>& nbr = neighbours(L);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t v = 0; v < L.m; ++v) {
     for (int c = 0; c < k; ++c) out[v * k + c] = L.coef[0] * in[v * k + c];
     for (int t = 1; t <= L.r; ++t) {
@@ -271,8 +294,35 @@ void blur_symmetric(const Lattice& L, int k, std::vector<double>& lat) {
   G.coef = saved;
 }
 
+// Incidences grouped by vertex, in increasing point order (built once, sequentially).
+const Lattice& incidences(const Lattice& L) {
+  Lattice& M = const_cast<Lattice&>(L);
+  if (M.inc_ptr.empty()) {
+    M.inc_ptr.assign((size_t)L.m + 1, 0);
+    for (int64_t e = 0; e < L.n * L.D; ++e) ++M.inc_ptr[(size_t)L.idx[e] + 1];
+    for (int64_t v = 0; v < L.m; ++v) M.inc_ptr[v + 1] += M.inc_ptr[v];
+    M.inc.assign((size_t)L.n * L.D, 0);
+    std::vector<int64_t> fill(M.inc_ptr.begin(), M.inc_ptr.end() - 1);
+    for (int64_t e = 0; e < L.n * L.D; ++e) M.inc[fill[L.idx[e]]++] = e;
+  }
+  return M;
+}
+
 void splat(const Lattice& L, const double* V, int k, std::vector<double>& lat) {
   lat.assign((size_t)L.m * k, 0.0);
+  if (g_threads > 1) {
+    // the same sums as the scatter below, each vertex's terms added in increasing i
+    const Lattice& I = incidences(L);
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1024)
+    for (int64_t v = 0; v < L.m; ++v)
+      for (int64_t q = I.inc_ptr[v]; q < I.inc_ptr[v + 1]; ++q) {
+        const int64_t e = I.inc[q];
+        const int64_t i = e / L.D;
+        const double wt = L.w[e];
+        for (int c = 0; c < k; ++c) lat[v * k + c] += wt * V[i * k + c];
+      }
+    return;
+  }
   for (int64_t i = 0; i < L.n; ++i)
     for (int kk = 0; kk < L.D; ++kk) {
       const int64_t v = L.idx[i * L.D + kk];
@@ -291,6 +341,7 @@ void blur(const Lattice& L, int k, int transpose, std::vector<double>& lat) {
 }
 
 void slice(const Lattice& L, const std::vector<double>& lat, int k, double* out) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t i = 0; i < L.n; ++i)
     for (int c = 0; c < k; ++c) {
       double acc = 0.0;
@@ -310,12 +361,33 @@ void apply(const Lattice& L, const double* V, int k, int mode, double alpha, dou
   if (mode == 2) blur_symmetric(L, k, lat);
   else blur(L, k, mode == 1 ? 1 : 0, lat);
   slice(L, lat, k, a.data());
+#pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t e = 0; e < L.n * k; ++e) out[e] = alpha * a[e] + beta * V[e];
 }
 
 }  // namespace
 
 extern "C" {
+
+// Threads used by the parallel loops (clamped to 1 without OpenMP); returns the count set.
+int orc_set_threads(int t) {
+#ifdef _OPENMP
+  g_threads = t < 1 ? 1 : t;
+#else
+  (void)t;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
+
+// Processors available to the parallel loops (1 without OpenMP).
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_num_procs();
+#else
+  return 1;
+#endif
+}
 
 // Stencil taps c_0..c_r = k(t s), the symmetric-blur taps g_0..g_r and the spacing s
 // (Sec. 4.1).  kind: 0 RBF with
@@ -369,13 +441,18 @@ int orc_build(const float* X, const float* ls, int64_t n, int d, int r, const do
   L->f = f;
   L->ls.assign(ls, ls + d);
   L->z.resize((size_t)n * d);
-  std::vector<int> key(D);
+  // per point: scale, elevate, enclosing simplex and weights (independent points)
+#pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double* z = &L->z[i * d];
     for (int j = 0; j < d; ++j) z[j] = (double)X[i * d + j] / (double)ls[j];
     double* y = &L->y[i * D];
     elevate(z, d, f, y);
     enclosing_simplex(y, d, &L->rem0[i * D], &L->rank[i * D], &L->w[i * D]);
+  }
+  // vertex insertion in (point, vertex) order: ids by first occurrence
+  std::vector<int> key(D);
+  for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < D; ++k) {
       vertex_key(&L->rem0[i * D], &L->rank[i * D], d, k, key.data());
       auto ins = L->table.emplace(key_bytes(key.data(), D), (int)L->m);
@@ -454,8 +531,11 @@ int orc_mvm(void* h, const double* V, int k, int mode, double alpha, double beta
 // Conjugate gradients on (outputscale K~ + noise I) X = B, every column independent
 // (Sec. 2: the solver touches the matrix only through MVMs).  A column stops when
 // ||r|| / ||b|| <= tol, after max_iter iterations, or when <p, A p> <= 0.
-int orc_cg(void* h, const double* B, int k, double outputscale, double noise, double tol,
-           int max_iter, int mode, double* X, int* iters, double* relres) {
+// history (may be null): [max_iter][k]; entry (j, c) receives ||r|| / ||b|| of column c
+// after its iteration j + 1 (entries of iterations a column did not run are untouched).
+int orc_cg_history(void* h, const double* B, int k, double outputscale, double noise,
+                   double tol, int max_iter, int mode, double* X, int* iters, double* relres,
+                   double* history) {
   const Lattice* L = static_cast<Lattice*>(h);
   if (k < 1 || max_iter < 0) return ORC_ERR_INVALID_ARG;
   const int64_t n = L->n;
@@ -478,6 +558,8 @@ int orc_cg(void* h, const double* B, int k, double outputscale, double noise, do
     for (int c = 0; c < k; ++c) any = any || active[c];
     if (!any) break;
     apply(*L, p.data(), k, mode, outputscale, noise, q.data());
+    // columns are independent; each column's sums run over i in order on one thread
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1)
     for (int c = 0; c < k; ++c) {
       if (!active[c]) continue;
       double pq = 0.0;
@@ -495,6 +577,7 @@ int orc_cg(void* h, const double* B, int k, double outputscale, double noise, do
       }
       it[c] += 1;
       rel[c] = std::sqrt(rr) / bnorm[c];
+      if (history) history[(int64_t)iter * k + c] = rel[c];
       if (rel[c] <= tol) {
         active[c] = 0;
         continue;
@@ -511,9 +594,16 @@ int orc_cg(void* h, const double* B, int k, double outputscale, double noise, do
   return ORC_OK;
 }
 
+int orc_cg(void* h, const double* B, int k, double outputscale, double noise, double tol,
+           int max_iter, int mode, double* X, int* iters, double* relres) {
+  return orc_cg_history(h, B, k, outputscale, noise, tol, max_iter, mode, X, iters, relres,
+                        nullptr);
+}
+
 // Exact RBF MVM: out_i = sum_j exp(-||(x_i - x_j) / l||^2 / 2) V_j (Sec. 3.1).
 void orc_dense_rbf(const float* X, const float* ls, int64_t n, int d, const double* V, int k,
                    double* out) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     for (int c = 0; c < k; ++c) out[i * k + c] = 0.0;
     for (int64_t j = 0; j < n; ++j) {
