@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Throughput of the Simplex-GP hot path on one GB300 (or N independent replicas).
 
-One step = the whole path over one batch of synthetic input:
+One step = the whole path over one batch of synthetic input, run to the solver's
+tolerance:
   build the permutohedral lattice of X (elevate, enclosing simplex, barycentric
-  weights, hash insert, vertex numbering, neighbour table, splat lists; Sec. 3.2), then
-  solve (K~ + noise I) X = V for all k right-hand sides with batched CG (Sec. 2); each
-  CG iteration is one lattice MVM (splat, 2(d+1) blur passes of the symmetric operator,
-  slice).
+  weights, hash insert, vertex numbering, neighbour table, splat lists; Sec. 3.2), build
+  the rank-1024 Nystrom preconditioner of the CG (App. A; one power iteration: two
+  1024-column lattice products, tensor-core Grams, fp64 factorizations), then solve
+  (K~ + noise I) X = V for all k right-hand sides with batched preconditioned CG to
+  ||r|| / ||b|| <= 1e-3 (Sec. 2); each CG iteration is one lattice MVM (splat, 2(d+1)
+  blur passes of the symmetric operator, slice) and one preconditioner apply.
 Metric: lattice MVM Mpoint/s = n * (k-column MVMs in the step) / step time, whole job,
-iterations counted as the max over columns.  The same solve with the rank-100
-preconditioner of App. A (a randomized Nystrom factor built from one 100-column lattice
-MVM, counted as rank / k MVMs) is timed after the steps and reported in `config.pcg`;
-`--precond-rank 100` makes it the timed step instead.
+iterations counted as the max over columns and each sketch product of l columns counted as
+l / k MVMs; the step time is the time to tolerance.  Reported beside it: the graph-replayed
+MVM alone, the per-stage rooflines (splat, blur, slice, preconditioner), the plain CG of
+500 iterations on the same system, and the time to tolerance of the n = 200,000 solve
+workload.  `--precond-rank 0` makes plain CG the timed step.
 
 Workload (default): n = 2,000,000 points, d = 11, standardised 16-component Gaussian
 mixture (the shape of Houseelectric, n=2,049,280 d=11, Sec. 5 Table n_lattice), unit ARD
@@ -52,10 +56,12 @@ METRIC = "lattice MVM Mpoint/s at n=2M,d=11 (%HBM peak)"
 UNIT = "Mpoint/s"
 WORKLOAD = dict(n=2_000_000, d=11, k=16, seed=4, lengthscale=1.0, noise=0.01, tol=1e-3,
                 max_iter=500, kernel="rbf_binomial", order=1, blur="symmetric",
-                precond_rank=0)
-PCG_RANK = 100  # App. A: CG pre-conditioner of rank 100
+                precond_rank=1024, precond_power_iters=1)
+# the n = 200,000, d = 11 solve workload: y plus 8 Rademacher probes, noise 0.01
+C2 = dict(n=200_000, d=11, seed=2, probes=8, noise=0.01, tol=1e-3, max_iter=500,
+          precond_rank=256, precond_power_iters=1)
 SERVING = dict(requests=256, rate_per_s=50.0, seed=5, max_active=16, test_points=256)
-CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg
+CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg (each mode)
 REF_SAMPLE = dict(n=50_000, iters=2)    # oracle sample per step for --impl reference
 
 
@@ -69,8 +75,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precond-rank", type=int, default=WORKLOAD["precond_rank"],
-                    help="rank of the CG preconditioner in the timed step (0 = plain CG, the "
-                         "default; App. A uses 100)")
+                    help="rank of the CG preconditioner in the timed step (default 1024; "
+                         "0 = plain CG)")
     ap.add_argument("--max-iter", type=int, default=WORKLOAD["max_iter"],
                     help="CG iteration cap (default 500; lower only for profiling runs)")
     ap.add_argument("--serving-requests", type=int, default=SERVING["requests"],
@@ -203,6 +209,103 @@ def blur_traffic_per_launch(m: int, k: int):
     return float(rec["bytes_per_vertex"]) * m
 
 
+def stage_traffic(stage: str):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary
+    (profiles/traffic.json), if recorded for this workload and kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[stage]
+    except (OSError, KeyError, ValueError):
+        return None
+    src_file = os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", rec.get("file", ""))
+    try:
+        src = open(src_file).read()
+    except OSError:
+        return None
+    body = re.search(rec["pattern"], src, re.S) if "pattern" in rec else None
+    if body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("src_sha1"):
+        return None
+    return float(rec["bytes_per_launch"])
+
+
+def run_solve_c2():
+    """Time to tolerance of the n = 200,000, d = 11 solve workload (GMM seed 2, unit
+    lengthscales, noise 0.01, B = [y, 8 Rademacher probes], tol 1e-3): lattice build +
+    rank-256 Nystrom preconditioner with one power iteration + preconditioned CG, median of
+    3 after a warm-up, wall clock around the whole call (host timers, synchronised); plus
+    the plain CG of the same system for comparison."""
+    import torch
+
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    C = C2
+    X = torch.from_numpy(synth.gmm_points(C["n"], C["d"], C["seed"])).cuda()
+    B = torch.from_numpy(synth.solve_rhs(X.cpu().numpy(), C["seed"], probes=C["probes"])).cuda()
+    ls = torch.ones(C["d"], device="cuda")
+    out = torch.empty_like(B)
+
+    def solve(rank):
+        lat = Lattice(X, ls, precond_rank=rank, precond_seed=C["seed"],
+                      precond_power_iters=C["precond_power_iters"])
+        _, it, rel = lat.cg(B, noise=C["noise"], tol=C["tol"], max_iter=C["max_iter"], out=out)
+        torch.cuda.synchronize()
+        true = None
+        if rank:
+            r = B.double() - lat.mvm(out, blur="symmetric", beta=C["noise"]).double()
+            true = (r.norm(dim=0) / B.double().norm(dim=0)).max().item()
+        lat.close()
+        return it, rel, true
+
+    solve(C["precond_rank"])
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rel, true = solve(C["precond_rank"])
+        ts.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    pit, prel, _ = solve(0)
+    plain_s = time.perf_counter() - t0
+    return {"workload": "n=%d d=%d k=%d (y + %d probes), noise %g, tol %g, rank-%d "
+                        "preconditioner with %d power iteration"
+                        % (C["n"], C["d"], C["probes"] + 1, C["probes"], C["noise"], C["tol"],
+                           C["precond_rank"], C["precond_power_iters"]),
+            "time_to_tol_s": float(np.median(ts)), "cg_iters": int(it.max()),
+            "rel_res_max": float(rel.max()), "true_rel_res_max": true,
+            "plain_cg": {"s": plain_s, "cg_iters": int(pit.max()),
+                         "rel_res_max": float(prel.max())}}
+
+
+def run_approximation_c1():
+    """Approximation error of the lattice operator against the exact RBF kernel (Sec. 5.1)
+    on the n = 4096, d = 3 workload (X ~ U[0,1]^3, lengthscale 0.3, outputscale 1, binomial
+    stencil r = 1, one right-hand side V ~ N(0, 1)): 1 - cosine and relative L2 of K~V
+    against the dense K V (computed in float64 with numpy), for the paper's sequential
+    blur and the symmetric blur the CG uses."""
+    import torch
+
+    from paper_2106_06695_gb300 import synth
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    X = synth.uniform_points(4096, 3, 1)
+    V = synth.gaussian_values(4096, 1, 1).astype(np.float64)
+    Z = X.astype(np.float64) / 0.3
+    sq = (Z * Z).sum(1)
+    K = np.exp(-0.5 * np.maximum(sq[:, None] + sq[None, :] - 2.0 * Z @ Z.T, 0.0))
+    exact = (K @ V)[:, 0]
+    lat = Lattice(torch.from_numpy(X).cuda(), 0.3)
+    out = {"workload": "n=4096 d=3 X~U[0,1]^3, lengthscale 0.3, binomial r=1, k=1", "m": lat.m}
+    for blur in ("sequential", "symmetric"):
+        got = lat.mvm(torch.from_numpy(V.astype(np.float32)).cuda(), blur=blur).cpu().numpy()
+        got = got.astype(np.float64)[:, 0]
+        cos = float(got @ exact / (np.linalg.norm(got) * np.linalg.norm(exact)))
+        out[blur] = {"one_minus_cosine": 1.0 - cos,
+                     "rel_l2": float(np.linalg.norm(got - exact) / np.linalg.norm(exact))}
+    lat.close()
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
@@ -237,12 +340,18 @@ def run_ours(args, world, rank, local):
         print(json.dumps({"mvm_only": True, "n": n, "m": lat.m, "reps": args.mvm_only,
                           "ms_per_mvm": e0.elapsed_time(e1) / args.mvm_only}), flush=True)
         return
-    prof = {"ms": 0.0, "passes": 0, "m": 0, "iters": [], "build_ms": []}
+    prof = {"ms": 0.0, "passes": 0, "m": 0, "iters": [], "build_ms": [], "rel": [],
+            "stages": np.zeros(5), "samples": 0}
+    sketch_mvms = (1 + W["precond_power_iters"]) * W["precond_rank"] / k
+
+    def make_lattice(Xdev, ls_dev, rank=None):
+        r = W["precond_rank"] if rank is None else rank
+        return Lattice(Xdev, ls_dev, order=W["order"], kernel=W["kernel"], precond_rank=r,
+                       precond_seed=W["seed"], precond_power_iters=W["precond_power_iters"])
 
     def step(Xdev, Vdev, ls_dev, profile=False):
         t0 = time.perf_counter()
-        lat = Lattice(Xdev, ls_dev, order=W["order"], kernel=W["kernel"],
-                      precond_rank=W["precond_rank"], precond_seed=W["seed"])
+        lat = make_lattice(Xdev, ls_dev)
         prof["build_ms"].append(1e3 * (time.perf_counter() - t0))
         if profile:
             _lib.check(lib.sgp_profile_blur(lat._h, 1))
@@ -255,17 +364,23 @@ def run_ours(args, world, rank, local):
             _lib.check(lib.sgp_profile_read(lat._h, ctypes.byref(ms), ctypes.byref(passes)))
             prof["ms"] += ms.value
             prof["passes"] += passes.value
+            st = np.zeros(5, np.float64)
+            nsamp = ctypes.c_int64()
+            _lib.check(lib.sgp_profile_read_stages(lat._h, st.ctypes.data, ctypes.byref(nsamp)))
+            prof["stages"] += st
+            prof["samples"] += nsamp.value
         prof["m"] = lat.m
         prof["iters"].append(int(iters.max()))
+        prof["rel"].append(float(rel.max()))
         lat.close()
-        print("step: m=%d build %.1f ms, cg iters %d, %.1f ms total" % (
-            lat.m, prof["build_ms"][-1], int(iters.max()), 1e3 * (time.perf_counter() - t0)),
-            file=sys.stderr, flush=True)
-        return int(iters.max()) + W["precond_rank"] / k, rel
+        print("step: m=%d build %.1f ms, cg iters %d, rel %.2e, %.1f ms total" % (
+            lat.m, prof["build_ms"][-1], int(iters.max()), float(rel.max()),
+            1e3 * (time.perf_counter() - t0)), file=sys.stderr, flush=True)
+        return int(iters.max()) + sketch_mvms, rel
 
     for _ in range(args.warmup):
         step(Xd, Vd, lsd)
-    prof.update(ms=0.0, passes=0, iters=[], build_ms=[])
+    prof.update(ms=0.0, passes=0, iters=[], build_ms=[], rel=[], stages=np.zeros(5), samples=0)
     torch.cuda.synchronize()
     barrier(world)
     launches0 = lib.sgp_kernel_launches()
@@ -286,57 +401,90 @@ def run_ours(args, world, rank, local):
     value = units / (max_ms / 1e3) / 1e6
     m = prof["m"]
 
-    # roofline of the dominant kernel (a blur pass), from the live samples
+    # rooflines from the live samples (CUDA events around each stage of one sampled
+    # iteration per flag check, recorded inside the CG graph on the solve's stream)
     peak, peak_kind = measured_peak_gbs()
-    bytes_per_pass = m * (8 * k + 8 * W["order"])  # read + write one fp32 row, 2r ids
-    avg_pass_ms = prof["ms"] / max(prof["passes"], 1)
-    achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9 if prof["passes"] else None
-    traffic = blur_traffic_per_launch(m, k)
-    roofline = {"kernel": "k_blur_rows<2,2,1,float> (one lattice direction)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
+    samples = max(prof["samples"], 1)
+    r_, D = W["order"], d + 1
+    ld = -(-W["precond_rank"] // 128) * 128
+    stage_bytes = {  # algorithmic bytes per launch (per sampled iteration for splat, slice)
+        "blur_pass": m * (8 * k + 8 * r_),
+        "splat": 8 * n * D + 4 * n * k + 4 * m * k,
+        "slice_dot": 8 * n * D + 4 * m * k + 8 * n * k,
+        "precond_bt": 4 * n * ld + 8 * n * min(k, 16),
+        "precond_z": 4 * n * ld + 12 * n * min(k, 16),
+    }
+    stage_ms = {  # average duration of one launch
+        "blur_pass": prof["ms"] / max(prof["passes"], 1),
+        "splat": prof["stages"][0] / samples,
+        "slice_dot": prof["stages"][2] / samples,
+        "precond_bt": prof["stages"][3] / samples,
+        "precond_z": prof["stages"][4] / samples,
+    }
+    stages = {}
+    for name, b in stage_bytes.items():
+        t = stage_ms[name]
+        if t > 0:
+            ach = b / (t / 1e3) / 1e9
+            stages[name] = {"avg_launch_ms": t, "algorithmic_bytes": b, "achieved_gbs": ach,
+                            "frac": ach / peak}
+    per_iter_ms = {"blur": prof["ms"] / samples, "splat": stage_ms["splat"],
+                   "slice_dot": stage_ms["slice_dot"], "precond_bt": stage_ms["precond_bt"],
+                   "precond_z": stage_ms["precond_z"]}
+    # the dominant kernel: the largest time per iteration among the single kernels
+    dom = max(("precond_bt", "precond_z", "splat", "slice_dot"),
+              key=lambda s: per_iter_ms[s] if s in stages else 0.0)
+    if per_iter_ms[dom] < per_iter_ms["blur"] or dom not in stages:
+        dom = "blur_pass"
+    names = {"blur_pass": "k_blur_rows<2,2,1,float> (one lattice direction)",
+             "splat": "k_splat<4,float> (+ fix-ups)", "slice_dot": "k_slice_dot<4,float>",
+             "precond_bt": "k_bt_tc (preconditioner B^T r, mma.sync 3xTF32)",
+             "precond_z": "k_apply_z_tc (preconditioner z = (r - B u)/tau, mma.sync 3xTF32)"}
+    ds = stages.get(dom, {})
+    traffic = blur_traffic_per_launch(m, k) if dom == "blur_pass" else stage_traffic(dom)
+    roofline = {"kernel": names[dom], "bound": "hbm",
+                "achieved": ds.get("achieved_gbs"), "peak": peak, "unit": "GB/s",
+                "frac": ds.get("frac"), "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": bytes_per_pass,
-                "avg_launch_ms": avg_pass_ms, "sampled_launches": prof["passes"]}
+                "algorithmic_bytes_per_launch": ds.get("algorithmic_bytes"),
+                "avg_launch_ms": ds.get("avg_launch_ms"), "sampled_iterations": prof["samples"],
+                "per_iteration_ms": per_iter_ms, "stages": stages}
 
-    # MVM alone (same lattice, same stream) for context, and the true residual of the
-    # last solve: || V - (K~ + noise I) X || / || V || per column
-    lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"],
-                  precond_rank=W["precond_rank"], precond_seed=W["seed"])
-    _, _, rel_last = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
-                            blur=W["blur"], out=out)
+    # the preconditioner's set-up alone (a solve with max_iter 0), the true residual of the
+    # timed solve's answer, the graph-replayed MVM, and the plain CG of 500 iterations
+    lat = make_lattice(Xd, lsd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=0, blur=W["blur"], out=out)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    _, it_last, rel_last = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
+                                  blur=W["blur"], out=out)
     resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
     true_rel = (resid.norm(dim=0) / Vd.double().norm(dim=0)).max().item()
     mvm_ms = graph_replay_median_ms(lat, Vd, out, W["blur"])
     mvm_seq_ms = graph_replay_median_ms(lat, Vd, out, "sequential")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ref_out = lat.mvm(Vd, blur=W["blur"]).double()
     lat.close()
+    lat = make_lattice(Xd, lsd, rank=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, p_iters, p_rel = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
+                               blur=W["blur"], out=out)
+    torch.cuda.synchronize()
+    plain_ms = 1e3 * (time.perf_counter() - t0)
+    lat.close()
+    plain = {"ms": plain_ms, "cg_iters": int(p_iters.max()), "rel_res_max": float(p_rel.max()),
+             "mpoint_s": n * int(p_iters.max()) / (plain_ms / 1e3) / 1e6,
+             "note": "plain CG (no preconditioner) on the same system, build included"}
     # the same product with the lattice values stored in bf16 (fp32 sums)
     lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"], value_dtype="bf16")
     mvm_bf16_ms = graph_replay_median_ms(lat, Vd, out, W["blur"])
     bf16_rel_err = ((out.double() - ref_out).norm() / ref_out.norm()).item()
     lat.close()
 
-    # the same solve with the App. A preconditioner (build + solve timed together)
-    pcg = None
-    if W["precond_rank"] == 0 and PCG_RANK > 0:
-        torch.cuda.synchronize()
-        e0.record()
-        lat = Lattice(Xd, lsd, order=W["order"], kernel=W["kernel"], precond_rank=PCG_RANK,
-                      precond_seed=W["seed"])
-        _, p_iters, p_rel = lat.cg(Vd, noise=W["noise"], tol=W["tol"], max_iter=W["max_iter"],
-                                   blur=W["blur"], out=out)
-        e1.record()
-        torch.cuda.synchronize()
-        pcg_ms = e0.elapsed_time(e1)
-        resid = Vd.double() - lat.mvm(out, blur=W["blur"], beta=W["noise"]).double()
-        p_true = (resid.norm(dim=0) / Vd.double().norm(dim=0)).max().item()
-        lat.close()
-        p_mvms = int(p_iters.max()) + PCG_RANK / k
-        pcg = {"precond_rank": PCG_RANK, "ms": pcg_ms, "cg_iters": int(p_iters.max()),
-               "mpoint_s": n * p_mvms / (pcg_ms / 1e3) / 1e6,
-               "rel_res_max": float(np.max(p_rel)), "true_rel_res_max": p_true}
+    c2 = run_solve_c2() if rank == 0 else None
+    approx = run_approximation_c1() if rank == 0 else None
 
     e2e = None
     if not args.no_e2e:
@@ -371,22 +519,32 @@ def run_ours(args, world, rank, local):
         cpu = cpu_baseline(W)
 
     if rank == 0:
+        steps_ms = max_ms / args.steps
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": steps_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: standardised 16-component Gaussian mixture (seeded), "
                     "V ~ N(0,1); stands in for the paper's UCI datasets",
-            "config": {"workload": "GP solve n=%d d=%d k=%d: lattice build + batched CG "
-                                   "(tol %g, max %d, preconditioner rank %d) on the symmetric "
+            "config": {"workload": "GP solve n=%d d=%d k=%d to rel. residual %g: lattice build "
+                                   "+ rank-%d Nystrom preconditioner (%d power iteration) + "
+                                   "batched preconditioned CG (max %d) on the symmetric "
                                    "lattice operator"
-                                   % (n, d, k, W["tol"], W["max_iter"], W["precond_rank"]),
+                                   % (n, d, k, W["tol"], W["precond_rank"],
+                                      W["precond_power_iters"], W["max_iter"]),
                        "n": n, "d": d, "k": k, "m": m, "m_over_L": m / (n * (d + 1)),
                        "kernel": "%s r=%d" % (W["kernel"], W["order"]), "noise": W["noise"],
+                       "precond_rank": W["precond_rank"],
+                       "precond_power_iters": W["precond_power_iters"],
                        "cg_iters_per_step": prof["iters"],
-                       "precond_rank": W["precond_rank"], "pcg": pcg,
+                       "cg_rel_res_per_step": prof["rel"],
+                       "mvms_per_step_counted": float(mvms / max(args.steps, 1)),
+                       "time_to_tol_s": steps_ms / 1e3,
+                       "precond_setup_ms": setup_ms,
                        "build_ms_median": float(np.median(prof["build_ms"])),
+                       "plain_cg_500": plain,
+                       "solve_n200k": c2,
                        "mvm_symmetric_ms": mvm_ms,
                        "mvm_symmetric_ms_note": "median of 50 graph-replayed MVMs",
                        "mvm_symmetric_mpoint_s": n / (mvm_ms / 1e3) / 1e6,
@@ -395,13 +553,15 @@ def run_ours(args, world, rank, local):
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
                        "mvm_symmetric_bf16_values_ms": mvm_bf16_ms,
                        "bf16_values_rel_l2_vs_fp32": bf16_rel_err,
+                       "approximation_n4096": approx,
                        "l2": "no flush: every step's working set (X 88 MB, V 128 MB, "
-                             "lattice values 2 x m x k x 4 B, tables) exceeds the 129 MB L2",
+                             "lattice values 2 x m x k x 4 B, the 8 GB preconditioner factor) "
+                             "exceeds the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
             "backward": backward, "logdet": logdet,
             "gpu_launches": int(launches), "clocks": clk.summary(),
-        "cg_final_rel_res_max": float(np.max(rel)), "cg_true_rel_res_max": true_rel,
+            "cg_final_rel_res_max": float(np.max(rel_last)), "cg_true_rel_res_max": true_rel,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -580,59 +740,68 @@ def run_serving(count: int):
 # ---------------------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------------------
-def oracle_sample(W, n_sample, iters):
-    """Oracle build + preconditioned CG (same rank) stopped after `iters` iterations, on a
-    seeded n_sample-row subsample; returns (seconds, point-MVMs done, counted as in the
-    GPU arm)."""
+def oracle_sample(W, n_sample, iters, threads=1):
+    """Oracle build + plain CG stopped after `iters` iterations (the lattice MVMs the metric
+    counts), on a seeded n_sample-row subsample of the workload, with `threads` threads
+    (results are bit-identical for any count); returns (seconds, point-MVMs done, threads
+    in effect)."""
+    import oracle
     from oracle import OracleLattice
     from paper_2106_06695_gb300 import synth
 
+    used = oracle.set_threads(threads)
     X = synth.gmm_points(W["n"], W["d"], W["seed"])
     V = synth.gaussian_values(W["n"], W["k"], W["seed"])
     rows = synth.subsample(W["n"], n_sample, W["seed"])
     Xs, Vs = X[rows], V[rows].astype(np.float64)
     t0 = time.perf_counter()
     L = OracleLattice(Xs, np.full(W["d"], W["lengthscale"], np.float32), r=W["order"])
-    if W["precond_rank"] > 0:
-        _, it, _ = L.pcg(Vs, W["noise"], rank=W["precond_rank"], tol=0.0, max_iter=iters,
-                         seed=W["seed"])
-    else:
-        _, it, _ = L.cg(Vs, W["noise"], tol=0.0, max_iter=iters, mode=2)
-    mvms = int(it.max()) + W["precond_rank"] / W["k"]
-    return time.perf_counter() - t0, float(n_sample) * mvms
+    _, it, _ = L.cg(Vs, W["noise"], tol=0.0, max_iter=iters, mode=2)
+    secs = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return secs, float(n_sample) * int(it.max()), used
 
 
 def cpu_baseline(W):
-    secs, units = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"])
-    return {"value": units / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, single thread: lattice build + rank-%d preconditioner + %d "
-                      "CG iterations (symmetric operator, k=%d) on a seeded %d-row subsample of "
-                      "the workload; %.1f s"
-                      % (W["precond_rank"], CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"], secs)}
+    import oracle
+
+    cores = oracle.max_threads()
+    secs1, units1, _ = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"], 1)
+    secs, units, used = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"], cores)
+    what = ("FP64 oracle: lattice build (vertex insertion sequential) + %d plain CG iterations "
+            "(symmetric operator, k=%d) on a seeded %d-row subsample of the workload"
+            % (CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"]))
+    return {"value": units / secs / 1e6, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%s, %d threads; %.1f s" % (what, used, secs),
+            "single_thread": {"value": units1 / secs1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": "%s, 1 thread; %.1f s" % (what, secs1)}}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    import oracle
+
     W = dict(WORKLOAD, n=args.n, precond_rank=args.precond_rank)
+    cores = oracle.max_threads()
     for _ in range(args.warmup):
-        oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"])
-    secs, units = 0.0, 0.0
+        oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"], cores)
+    secs, units, used = 0.0, 0.0, 1
     for _ in range(args.steps):
-        s, u = oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"])
+        s, u, used = oracle_sample(W, REF_SAMPLE["n"], REF_SAMPLE["iters"], cores)
         secs += s
         units += u
     value = units / secs / 1e6
-    sample = ("FP64 oracle, single thread, per step: lattice build + rank-%d preconditioner + "
-              "%d CG iterations (symmetric operator, k=%d) on a seeded %d-row subsample of the "
-              "workload" % (W["precond_rank"], REF_SAMPLE["iters"], W["k"], REF_SAMPLE["n"]))
+    sample = ("FP64 oracle, %d threads, per step: lattice build + %d plain CG iterations "
+              "(symmetric operator, k=%d) on a seeded %d-row subsample of the workload"
+              % (used, REF_SAMPLE["iters"], W["k"], REF_SAMPLE["n"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "GP solve n=%d d=%d k=%d (oracle sample of %d rows)"
                                    % (W["n"], W["d"], W["k"], REF_SAMPLE["n"])},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

@@ -99,9 +99,10 @@ typedef struct {
   int value_dtype;    /* SGP_VALUES_*; default SGP_VALUES_F32                           */
   int check_every;    /* CG iterations between host reads of the flags; default 8       */
   void* stream;       /* cudaStream_t for all work on this handle; NULL = default stream */
-  int precond_rank;   /* CG preconditioner rank l (0 = none, <= 128); App. A uses 100;
-                         default 0 (see sgp_cg_solve)                                   */
+  int precond_rank;   /* CG preconditioner rank l (0 = none, <= 4096); App. A uses 100;
+                         default 0 (see sgp_cg_solve_ex)                                */
   unsigned long long precond_seed; /* seed of the preconditioner's random sketch; 0    */
+  int precond_power_iters; /* subspace iterations of the sketch, 0 or 1; default 1      */
 } sgp_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -181,7 +182,12 @@ sgp_status sgp_mvm_ex(sgp_lattice* h, const float* V, int k, int blur, float alp
  * processes whose device memory is already reserved by another allocator's pool.
  *   V, out  device [n][k] fp32 as in sgp_mvm_ex (the handle must already be built).
  * A lattice whose work space for this k exceeds 64 MiB is rejected with
- * SGP_ERR_INVALID_ARG before anything is launched.  The first call on a device looks up
+ * SGP_ERR_INVALID_ARG before anything is launched, and so is every call made while a
+ * device other than the one the lattice was built on is current (each device has its
+ * own work area).  Sparse lattices (sgp_lattice_blur_lists) are blurred by full sweeps
+ * here, since the fixed area holds no direction-list buffers: at high d (isolated
+ * simplices) such a product is several times slower than sgp_mvm_ex's (about 6x at
+ * d = 90).  The first call on a device looks up
  * the work area's device address (cudaGetSymbolAddress, with that device current); make
  * that first call before any stream capture.  All calls in the process share the one
  * work area and it keeps the last call's contents (every element is rewritten before it
@@ -210,17 +216,32 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
 /* As sgp_cg_solve with the blur operator chosen by `blur` (SGP_BLUR_*).  CG assumes a
  * symmetric positive-definite matrix; only SGP_BLUR_SYMMETRIC guarantees one.
  *
- * Preconditioning (opts->precond_rank = l > 0 at build time, noise_var > 0): CG runs
- * preconditioned with P = B B^T + noise_var I, a rank-l randomized Nystrom approximation
- * of outputscale W B W^T built from one l-column product with a Rademacher sketch Omega
- * (Omega[i][j] = sign bit of SplitMix64 at counter i l + j + 1 from precond_seed, i the
- * caller's point index): Y = A Omega + nu Omega (nu = 1e-3 noise_var), C = Omega^T Y =
- * R R^T, B = Y R^-T; P^-1 is applied through the Woodbury identity with the Cholesky
- * factor of noise_var I + B^T B.  Work space grows by 4 n l + 8 n k bytes.  When a
- * Cholesky pivot fails the solve runs unpreconditioned.  The stopping rule is unchanged
- * (unpreconditioned residual ||r_c|| / ||b_c||). */
+ * Preconditioning (opts->precond_rank = l > 0 at build time, noise_var > 0; App. A: CG
+ * pre-conditioner): CG runs preconditioned with P = B B^T + tau I, where B B^T is a
+ * rank-l randomized Nystrom approximation of K = outputscale W B W^T (B here the blur):
+ *   Omega  n x l Rademacher sketch, Omega[i][j] = sign bit of SplitMix64 at counter
+ *          i l + j + 1 from precond_seed (i the caller's point index);
+ *   Q      Omega (precond_power_iters = 0) or an orthonormal basis of K Omega (1);
+ *   Y      = K Q,  C = (Q^T Y + Y^T Q)/2 + eps I (eps = 1e-6 max_j C_jj, raised when its
+ *          Cholesky fails) = R R^T,  B = Y R^-T;
+ *   tau    = lambda_min(B^T B) (inverse power iteration) + noise_var.
+ * P^-1 r = (r - B (tau I + B^T B)^-1 B^T r) / tau.  The l-column products with K run in
+ * chunks of 128 columns; the tall n x l products on the tensor cores (3xTF32), the l x l
+ * factorizations in fp64.  Work space: about 12 n l + 8 n k bytes during the set-up,
+ * 4 n l kept for the solve.  When a Cholesky fails after its retries the solve runs
+ * unpreconditioned.  The stopping rule is unchanged (unpreconditioned residual
+ * ||r_c|| / ||b_c||). */
 sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,
                            float tol, int max_iter, float* X, int* iters, double* rel_res);
+
+/* As sgp_cg_solve_ex, also recording the convergence history (Sec. 2): history is host
+ * [max_iter][k] doubles; entry (j, c) receives ||r_c|| / ||b_c|| (the recurrence residual
+ * the stopping rule tests) after iteration j + 1 of column c, and NaN for iterations the
+ * column did not run.  Work space grows by 8 max_iter k bytes.  SGP_ERR_INVALID_ARG when
+ * history is NULL; other rules as sgp_cg_solve_ex. */
+sgp_status sgp_cg_solve_history(sgp_lattice* h, const float* B, int k, int blur,
+                                float noise_var, float tol, int max_iter, float* X, int* iters,
+                                double* rel_res, double* history);
 
 /* log det(outputscale * W B W^T + noise_var I), B = SGP_BLUR_SYMMETRIC: the second term of
  * the marginal log-likelihood (Eq. gp_mll), by stochastic Lanczos quadrature.  For each
@@ -280,6 +301,22 @@ sgp_status sgp_profile_blur(sgp_lattice* h, int enable);
 /* Totals collected since sgp_profile_blur: milliseconds spent in the sampled blur passes
  * and the number of passes those samples cover.  Either output may be NULL. */
 sgp_status sgp_profile_read(const sgp_lattice* h, double* blur_ms, int64_t* blur_passes);
+
+/* Per-stage totals collected since sgp_profile_blur, over the iterations sampled inside
+ * the CG graph (one per flag check): stage_ms (host, 5 doubles, or NULL) receives the
+ * milliseconds of SGP_STAGE_SPLAT (splat with its fix-ups), SGP_STAGE_BLUR (all blur
+ * passes), SGP_STAGE_SLICE (slice with its <p, Ap> partials) of the MVM and, in a
+ * preconditioned solve, SGP_STAGE_PRECOND_BT (the B^T r kernel) and SGP_STAGE_PRECOND_Z
+ * (the z = (r - B u) / tau kernel) of the first 16 columns; *samples (or NULL) the number of
+ * sampled iterations. */
+enum {
+  SGP_STAGE_SPLAT = 0,
+  SGP_STAGE_BLUR = 1,
+  SGP_STAGE_SLICE = 2,
+  SGP_STAGE_PRECOND_BT = 3,
+  SGP_STAGE_PRECOND_Z = 4,
+};
+sgp_status sgp_profile_read_stages(const sgp_lattice* h, double* stage_ms, int64_t* samples);
 
 /* Number of kernels this library has enqueued in this process (a replayed CUDA graph
  * counts each of its kernels), for launch accounting in benchmarks. */

@@ -51,7 +51,11 @@
  * own status and does not stop the server.  The preconditioner's kernels wait on
  * bulk-copy barriers with a bounded number of polls; should a wait give up, the kernel
  * records it and returns, and the requests of that round complete with SGP_ERR_CUDA
- * (their mean/var are not written) while the server keeps running.
+ * (their mean/var are not written) while the server keeps running.  For tests of that
+ * path, SGP_FAULT=ring_wait in the environment of sgp_server_create makes the first lane
+ * round that applies a preconditioner wait with a limit of 0 polls: its first chunk wait
+ * gives up at once, the block still waits (bounded) for its copies in flight before it
+ * returns, and the next rounds run with the normal limit.  Nothing faults the device.
  */
 #ifndef SGP_SERVE_H_
 #define SGP_SERVE_H_

@@ -32,7 +32,7 @@ class sgp_opts(ctypes.Structure):
                 ("spacing_s", ctypes.c_double), ("outputscale", ctypes.c_float),
                 ("value_dtype", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("precond_rank", ctypes.c_int),
-                ("precond_seed", ctypes.c_ulonglong)]
+                ("precond_seed", ctypes.c_ulonglong), ("precond_power_iters", ctypes.c_int)]
 
 
 class sgp_server_opts(ctypes.Structure):
@@ -107,9 +107,11 @@ def load():
         "sgp_mvm_backward": (I, [P, P, P, P, P, I, I, F, I, P, P, P]),
         "sgp_logdet": (I, [P, P, I, F, I, F, ctypes.POINTER(Dbl), P]),
         "sgp_cg_solve_ex": (I, [P, P, I, I, F, F, I, P, P, P]),
+        "sgp_cg_solve_history": (I, [P, P, I, I, F, F, I, P, P, P, P]),
         "sgp_lattice_free": (None, [P]),
         "sgp_profile_blur": (I, [P, I]),
         "sgp_profile_read": (I, [P, ctypes.POINTER(Dbl), ctypes.POINTER(I64)]),
+        "sgp_profile_read_stages": (I, [P, P, ctypes.POINTER(I64)]),
         "sgp_kernel_launches": (I64, []),
         "sgp_last_error": (ctypes.c_char_p, []),
         "sgp_version": (I, []),

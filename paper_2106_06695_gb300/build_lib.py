@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "build.cu", "mvm.cu", "cg.cu", "scan_sort.cu", "static_mvm.cu", "nystrom.cu",
-           "serve.cu", "backward.cu", "lanczos.cu", "stencil.cpp"]
+           "precond.cu", "serve.cu", "backward.cu", "lanczos.cu", "stencil.cpp"]
 NO_FMA = {"build.cu"}
 
 

@@ -101,6 +101,7 @@ void sgp_opts_init(sgp_opts* o) {
   o->stream = nullptr;
   o->precond_rank = 0;
   o->precond_seed = 0;
+  o->precond_power_iters = 1;
 }
 
 sgp_status sgp_stencil(int kernel, int order_r, double spacing_override, double* spacing_s,
@@ -165,14 +166,18 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
   L->outputscale = o.outputscale;
   L->value_dtype = o.value_dtype;
   L->check_every = o.check_every > 0 ? o.check_every : 8;
-  if (o.precond_rank < 0 || o.precond_rank > kMaxRank) {
+  if (o.precond_rank < 0 || o.precond_rank > kMaxLibRank || o.precond_power_iters < 0 ||
+      o.precond_power_iters > 1) {
     delete L;
-    set_error("sgp_lattice_build: precond_rank must be in 0..128");
+    set_error("sgp_lattice_build: precond_rank must be in 0..4096 and precond_power_iters "
+              "0 or 1");
     return SGP_ERR_INVALID_ARG;
   }
   L->precond_rank = o.precond_rank;
+  L->precond_power_iters = o.precond_power_iters;
   L->precond_seed = o.precond_seed;
   L->stream = (cudaStream_t)o.stream;
+  if (cudaGetDevice(&L->device) != cudaSuccess) L->device = -1;
   if (!make_stencil(o.kernel, o.order_r, o.spacing_s, &L->s, L->coef, L->half)) {
     delete L;
     set_error("sgp_lattice_build: kernel must be an SGP_KERNEL_* value and 1 <= order_r <= 4");
@@ -299,6 +304,21 @@ sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, floa
                 h->precond_seed);
 }
 
+sgp_status sgp_cg_solve_history(sgp_lattice* h, const float* B, int k, int blur,
+                                float noise_var, float tol, int max_iter, float* X, int* iters,
+                                double* rel_res, double* history) {
+  if (sgp_status s = check_mvm_args(h, B, k, blur, X, "sgp_cg_solve_history")) return s;
+  if (!(noise_var >= 0.f) || !(tol >= 0.f) || max_iter < 0 || !history) {
+    set_error("sgp_cg_solve_history: need noise_var >= 0, tol >= 0, max_iter >= 0 and a "
+              "history buffer");
+    return SGP_ERR_INVALID_ARG;
+  }
+  clear_pending_error();
+  NvtxRange nvtx("sgp_cg");
+  return run_cg(h, B, k, blur, noise_var, tol, max_iter, X, iters, rel_res, h->precond_rank,
+                h->precond_seed, nullptr, history);
+}
+
 sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, float tol,
                         int max_iter, float* X, int* iters, double* rel_res) {
   return sgp_cg_solve_ex(h, B, k, SGP_BLUR_SYMMETRIC, noise_var, tol, max_iter, X, iters,
@@ -344,7 +364,7 @@ void sgp_lattice_free(sgp_lattice* h) { free_lattice(h); }
 
 sgp_status sgp_profile_blur(sgp_lattice* h, int enable) {
   if (sgp_status s = check_handle(h)) return s;
-  for (int i = 0; i < 2 && enable; ++i) {
+  for (int i = 0; i < 8 && enable; ++i) {
     if (!h->prof_ev[i]) {
       cudaError_t e = cudaEventCreate(&h->prof_ev[i]);
       if (e != cudaSuccess) return cuda_status(e, "sgp_profile_blur");
@@ -353,6 +373,16 @@ sgp_status sgp_profile_blur(sgp_lattice* h, int enable) {
   h->profile = enable ? 1 : 0;
   h->prof_ms = 0.0;
   h->prof_passes = 0;
+  for (double& v : h->prof_stage_ms) v = 0.0;
+  h->prof_mvms = 0;
+  return SGP_OK;
+}
+
+sgp_status sgp_profile_read_stages(const sgp_lattice* h, double* stage_ms, int64_t* samples) {
+  if (sgp_status s = check_handle(h)) return s;
+  if (stage_ms)
+    for (int i = 0; i < kProfStages; ++i) stage_ms[i] = h->prof_stage_ms[i];
+  if (samples) *samples = h->prof_mvms;
   return SGP_OK;
 }
 

@@ -473,6 +473,30 @@ __global__ void k_seg_fill(const int32_t* __restrict__ row_ptr, int64_t m,
   if (c > kSplatMedSegs) huge_rows[huge_off[v]] = make_int4((int)v, slot0, c, 0);
 }
 
+// Within each window of kSegWindow consecutive segments, order the segments by length,
+// longest first (ties keep their order), so that the thread groups of a warp walk lists
+// of similar length and finish together.  Windows keep the vertex order of the lattice
+// at large, so the gathers of concurrently running warps stay local.  The splat's result
+// does not depend on the order in which segments are processed.
+constexpr int kSegWindow = 128;
+__global__ void __launch_bounds__(kSegWindow) k_seg_window_sort(const int4* __restrict__ in,
+                                                                int64_t nseg,
+                                                                int4* __restrict__ out) {
+  __shared__ int len[kSegWindow];
+  const int64_t s = (int64_t)blockIdx.x * kSegWindow + threadIdx.x;
+  const int4 sg = s < nseg ? in[s] : make_int4(0, 0, 0, 0);
+  const int mine = s < nseg ? sg.z - sg.y : -1;
+  len[threadIdx.x] = mine;
+  __syncthreads();
+  if (s >= nseg) return;
+  int rank = 0;
+  for (int j = 0; j < kSegWindow; ++j) {
+    const int o = len[j];
+    rank += (o > mine || (o == mine && j < (int)threadIdx.x)) ? 1 : 0;
+  }
+  out[(int64_t)blockIdx.x * kSegWindow + rank] = sg;
+}
+
 __global__ void k_iota(uint32_t* __restrict__ out, int64_t count) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < count) out[p] = (uint32_t)p;
@@ -753,9 +777,15 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
     SGP_CHECK(dalloc(&L->med_rows, L->nmed, st), "alloc seg");
     SGP_CHECK(dalloc(&L->huge_rows, L->nhuge, st), "alloc seg");
     L->bytes += (L->nseg + L->nmed + L->nhuge) * sizeof(int4);
+    int4* seg_unsorted = nullptr;
+    SGP_CHECK(tmp.get(&seg_unsorted, std::max<int64_t>(L->nseg, 1)), "alloc seg");
     k_seg_fill<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(L->row_ptr, m, cnt, slots, med, huge,
-                                                          L->seg, L->med_rows, L->huge_rows);
-    note_launches(1);
+                                                          seg_unsorted, L->med_rows,
+                                                          L->huge_rows);
+    if (L->nseg > 0)
+      k_seg_window_sort<<<(unsigned)ceil_div(L->nseg, kSegWindow), kSegWindow, 0, st>>>(
+          seg_unsorted, L->nseg, L->seg);
+    note_launches(2);
     SGP_CHECK(cudaGetLastError(), "splat segments");
   }
   // 8. direction lists of a sparse lattice (counts from k_neighbours)

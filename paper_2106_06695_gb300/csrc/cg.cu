@@ -34,6 +34,9 @@ struct CgState {
   double* ha;
   double* hb;
   int hcap;
+  // optional residual history: ||r_c|| / ||b_c|| after iteration j of column c at [j][k]
+  double* hist;
+  int hist_cap;
 };
 
 // VEC consecutive elements of a row: fp32 (one float4 when VEC = 4) and fp64 (two double2).
@@ -204,6 +207,7 @@ __global__ void k_cg_beta(int nblk, int k, float tol, int max_iter, CgState S) {
   S.iters[c] = it;
   const double rel = sqrt(rr) / S.bnorm[c];
   S.relres[c] = rel;
+  if (S.hist && it <= S.hist_cap) S.hist[(int64_t)(it - 1) * k + c] = rel;
   if (rel <= (double)tol || it >= max_iter || !isfinite(rel)) {
     S.active[c] = 0;
     return;
@@ -223,6 +227,7 @@ __global__ void k_cg_check(int nblk, int k, float tol, int max_iter, CgState S) 
   S.iters[c] = it;
   const double rel = sqrt(rr) / S.bnorm[c];
   S.relres[c] = rel;
+  if (S.hist && it <= S.hist_cap) S.hist[(int64_t)(it - 1) * k + c] = rel;
   if (rel <= (double)tol || it >= max_iter || !isfinite(rel)) S.active[c] = 0;
 }
 
@@ -330,7 +335,7 @@ __global__ void k_cg_store_x(const float* __restrict__ xh, const float* __restri
 
 sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
                   int max_iter, float* X, int* iters, double* rel_res, int precond_rank,
-                  uint64_t seed, const LanczosRecord* rec) {
+                  uint64_t seed, const LanczosRecord* rec, double* history) {
   const int64_t n = L->n;
   // CUDA graphs cannot be captured on the legacy default stream: use a private blocking
   // stream then (it is ordered with the legacy stream like any blocking stream).
@@ -346,7 +351,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     std::vector<void*> ptrs;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-    Nystrom pre;
+    ShiftedNystrom pre;
     ~Cleanup() {
       pre.release(st);
       if (exec) (void)cudaGraphExecDestroy(exec);
@@ -377,13 +382,17 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   const int64_t rows_per_block = T / (k / vec);
   const int vblocks = (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
   const int64_t sblocks = slice_dot_blocks(L, k);
+  const bool want_pre = precond_rank > 0 && noise > 0.f && !rec;
+  const int64_t pblocks = want_pre ? ceil_div(n, 128) : 0;  // ShiftedNystrom::dot_blocks
   CG_CHECK(get((void**)&xh, n * k * sizeof(float)), "alloc x");
   CG_CHECK(get((void**)&xl, n * k * sizeof(float)), "alloc x");
   CG_CHECK(get((void**)&rh, n * k * sizeof(float)), "alloc r");
   CG_CHECK(get((void**)&rl, n * k * sizeof(float)), "alloc r");
   CG_CHECK(get((void**)&p, n * k * sizeof(float)), "alloc p");
   CG_CHECK(get((void**)&Ap, n * k * sizeof(float)), "alloc Ap");
-  CG_CHECK(get((void**)&S.partial, (size_t)std::max<int64_t>(vblocks, sblocks) * k * sizeof(double)),
+  CG_CHECK(get((void**)&S.partial,
+               (size_t)std::max<int64_t>(std::max<int64_t>(vblocks, sblocks), pblocks) * k *
+                   sizeof(double)),
            "alloc partial");
   double* scal;
   CG_CHECK(get((void**)&scal, 6 * (size_t)k * sizeof(double)), "alloc scalars");
@@ -402,14 +411,24 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     S.hb = rec->beta;
     S.hcap = rec->cap;
   }
+  if (history && max_iter > 0) {
+    CG_CHECK(get((void**)&S.hist, (size_t)max_iter * k * sizeof(double)), "alloc history");
+    S.hist_cap = max_iter;
+    // iterations a column does not run read back as NaN
+    std::vector<double> nan((size_t)max_iter * k, std::nan(""));
+    CG_CHECK(cudaMemcpyAsync(S.hist, nan.data(), nan.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, st),
+             "clear history");
+    CG_CHECK(cudaStreamSynchronize(st), "sync history");
+  }
   sgp_status s = ensure_lattice_values(L, k, st);
   if (s != SGP_OK) return s;
 
   // the preconditioner (built before anything is captured); needs noise > 0
   bool use_pre = false;
   float* z = nullptr;
-  if (precond_rank > 0 && noise > 0.f && !rec) {
-    s = cl.pre.build(L, precond_rank, seed, noise, blur, st);
+  if (want_pre) {
+    s = cl.pre.build(L, precond_rank, seed, noise, blur, L->precond_power_iters, st);
     if (s != SGP_OK) return s;
     use_pre = cl.pre.ok;
     if (use_pre) CG_CHECK(get((void**)&z, n * k * sizeof(float)), "alloc z");
@@ -420,8 +439,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   k_cg_init_scalars<<<k, 256, 0, st>>>(S.partial, vblocks, k, tol, max_iter, S);
   note_launches(2);
   if (use_pre) {  // z = P^-1 r, rho = <r, z>, p = z
-    cl.pre.apply(rh, rl, k, z, S.partial, vblocks, T, st);
-    k_cg_rho_init<<<k, 256, 0, st>>>(vblocks, k, S);
+    cl.pre.apply(rh, rl, k, z, S.partial, st);
+    k_cg_rho_init<<<k, 256, 0, st>>>((int)cl.pre.dot_blocks(), k, S);
     if (vec == 4) k_cg_update_p_z<4, true><<<vblocks, T, 0, st>>>(p, z, n, k, S);
     else k_cg_update_p_z<1, true><<<vblocks, T, 0, st>>>(p, z, n, k, S);
     note_launches(2);
@@ -439,8 +458,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     else k_cg_update_xr<1><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
     if (use_pre) {
       k_cg_check<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
-      cl.pre.apply(rh, rl, k, z, S.partial, vblocks, T, st);
-      k_cg_beta_pcg<<<k, 256, 0, st>>>(vblocks, k, S);
+      cl.pre.apply(rh, rl, k, z, S.partial, st, ev ? ev + 4 : nullptr);
+      k_cg_beta_pcg<<<k, 256, 0, st>>>((int)cl.pre.dot_blocks(), k, S);
       if (vec == 4) k_cg_update_p_z<4, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);
       else k_cg_update_p_z<1, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);
       note_launches(5);
@@ -475,11 +494,16 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
       CG_CHECK(cudaMemcpyAsync(hact.data(), S.active, k * sizeof(int), cudaMemcpyDeviceToHost, st),
                "read flags");
       CG_CHECK(cudaStreamSynchronize(st), "sync CG");
-      if (ev) {  // the events of the last replay bracket one MVM's blur passes
-        float ms = 0.f;
-        CG_CHECK(cudaEventElapsedTime(&ms, ev[0], ev[1]), "reading the blur timing events");
-        L->prof_ms += ms;
+      if (ev) {  // the events of the last replay bracket one MVM's splat, blur and slice
+        float ms[kProfStages] = {};
+        const int from[kProfStages] = {2, 0, 1, 4, 6}, to[kProfStages] = {0, 1, 3, 5, 7};
+        for (int q = 0; q < (use_pre ? kProfStages : 3); ++q)
+          CG_CHECK(cudaEventElapsedTime(&ms[q], ev[from[q]], ev[to[q]]),
+                   "reading the stage timing events");
+        L->prof_ms += ms[1];
         L->prof_passes += passes;
+        for (int q = 0; q < kProfStages; ++q) L->prof_stage_ms[q] += ms[q];
+        L->prof_mvms += 1;
       }
     }
   }
@@ -496,6 +520,12 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   CG_CHECK(cudaStreamSynchronize(st), "sync CG");
   if (iters) std::copy(hit.begin(), hit.end(), iters);
   if (rel_res) std::copy(hrel.begin(), hrel.end(), rel_res);
+  if (S.hist) {
+    CG_CHECK(cudaMemcpyAsync(history, S.hist, (size_t)max_iter * k * sizeof(double),
+                             cudaMemcpyDeviceToHost, st),
+             "read history");
+    CG_CHECK(cudaStreamSynchronize(st), "sync CG");
+  }
   if (rec) {  // ||b_c|| and the iteration counts stay on the device for the quadrature
     CG_CHECK(cudaMemcpyAsync(rec->bnorm, S.bnorm, k * sizeof(double), cudaMemcpyDeviceToDevice,
                              st),

@@ -25,6 +25,13 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---- splat ---------------------------------------------------------------------------
+// Incidences and vertex rows are gathered kChunk at a time: a thread first loads the
+// (point, weight) pairs or (vertex id, weight) pairs of a chunk, then issues all of the
+// chunk's row loads, then accumulates in order.  The row loads of a chunk are independent,
+// so kChunk of them are in flight per thread instead of one dependent pair at a time; the
+// sums keep the incidence order, so results do not change with the chunking.
+constexpr int kChunk = 8;
+
 // One thread-group of G threads per segment of at most kSplatSeg incidences.
 template <int VEC, class S>
 __global__ void __launch_bounds__(kThreads) k_splat(int64_t nseg, int G, int k,
@@ -38,11 +45,20 @@ __global__ void __launch_bounds__(kThreads) k_splat(int64_t nseg, int G, int k,
   const int64_t s = gid / G;
   if (s >= nseg) return;
   const int col = (int)(gid - s * G) * VEC;
-  const int4 sg = seg[s];
+  const int4 sg = __ldg(seg + s);
   typename Vt::T acc = Vt::zero();
-  for (int p = sg.y; p < sg.z; ++p) {
-    const int2 it = items[p];
-    acc = Vt::fma(__int_as_float(it.y), Vt::ld(V + (int64_t)it.x * k + col), acc);
+  for (int p0 = sg.y; p0 < sg.z; p0 += kChunk) {
+    int2 it[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      it[j] = p0 + j < sg.z ? __ldg(items + p0 + j) : make_int2(-1, 0);
+    typename Vt::T row[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      row[j] = it[j].x >= 0 ? Vt::ldg(V + (int64_t)it[j].x * k + col) : Vt::zero();
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      if (it[j].x >= 0) acc = Vt::fma(__int_as_float(it[j].y), row[j], acc);
   }
   if (sg.w < 0) Vt::sts(lat + (int64_t)sg.x * k + col, acc);
   else Vt::st(partial + (int64_t)sg.w * k + col, acc);
@@ -247,6 +263,36 @@ __global__ void __launch_bounds__(kThreads) k_sparse_finish(int64_t m, int G, in
 }
 
 // ---- slice ---------------------------------------------------------------------------
+// sum_c w[p][c] lat[idx[p][c]] for the VEC columns at col, in vertex order c = 0..D-1,
+// loading the ids and weights of kChunk vertices before their rows.
+template <int VEC, class S>
+__device__ __forceinline__ typename Vec<VEC>::T slice_row(int64_t p, int D, int k, int col,
+                                                          const int32_t* __restrict__ idx,
+                                                          const float* __restrict__ w,
+                                                          const S* __restrict__ lat) {
+  using Vt = Vec<VEC>;
+  typename Vt::T acc = Vt::zero();
+  const int64_t e0 = p * D;
+  for (int c0 = 0; c0 < D; c0 += kChunk) {
+    int id[kChunk];
+    float wt[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      const bool in = c0 + j < D;
+      id[j] = in ? __ldg(idx + e0 + c0 + j) : -1;
+      wt[j] = in ? __ldg(w + e0 + c0 + j) : 0.f;
+    }
+    typename Vt::T row[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      row[j] = id[j] >= 0 ? Vt::ldgs(lat + (int64_t)id[j] * k + col) : Vt::zero();
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      if (id[j] >= 0) acc = Vt::fma(wt[j], row[j], acc);
+  }
+  return acc;
+}
+
 // PERM: V and out rows are in the caller's order (row perm[p]); else in locality order.
 template <int VEC, bool BETA, bool PERM, class S>
 __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int D,
@@ -261,11 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_slice(int64_t n, int G, int k, int
   const int64_t p = gid / G;
   if (p >= n) return;
   const int col = (int)(gid - p * G) * VEC;
-  typename Vt::T acc = Vt::zero();
-  for (int c = 0; c < D; ++c) {
-    const int64_t e = p * D + c;
-    acc = Vt::fma(w[e], Vt::lds(lat + (int64_t)idx[e] * k + col), acc);
-  }
+  const typename Vt::T acc = slice_row<VEC, S>(p, D, k, col, idx, w, lat);
   const int64_t i = PERM ? (int64_t)perm[p] : p;
   typename Vt::T res = Vt::scale(alpha, acc);
   if (BETA) res = Vt::fma(beta, Vt::ld(V + i * k + col), res);
@@ -291,11 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_slice_dot(int64_t n, int G, int k,
   for (int j = 0; j < VEC; ++j) d[j] = {0.f, 0.f};
   for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / G; p < n;
        p += (int64_t)gridDim.x * rows) {
-    typename Vt::T acc = Vt::zero();
-    for (int c = 0; c < D; ++c) {
-      const int64_t e = p * D + c;
-      acc = Vt::fma(w[e], Vt::lds(lat + (int64_t)idx[e] * k + col), acc);
-    }
+    const typename Vt::T acc = slice_row<VEC, S>(p, D, k, col, idx, w, lat);
     const typename Vt::T v = Vt::ld(V + p * k + col);
     const typename Vt::T res = Vt::fma(beta, v, Vt::scale(alpha, acc));
     Vt::st(out + p * k + col, res);
@@ -519,6 +557,7 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
     launch_permute(L, V, k, vperm, st);
     src = vperm;
   }
+  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   launch_splat_t<S>(L, src, k, lat0, partial, st);
   // External: inside a stream capture this becomes an event-record node of the graph
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
@@ -528,6 +567,7 @@ int enqueue_t(const Lattice* L, const float* V, int k, int blur, float alpha, fl
   if (internal && dot_partial) launch_slice_dot<S>(L, a, V, k, alpha, beta, out, dot_partial, st);
   else if (internal) launch_slice_t<false, S>(L, a, V, k, alpha, beta, out, st);
   else launch_slice_t<true, S>(L, a, V, k, alpha, beta, out, st);
+  if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
   return passes;
 }
 
@@ -599,8 +639,25 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
 int64_t slice_dot_blocks(const Lattice* L, int k) {
   const int vec = k % 4 == 0 ? 4 : 1;
   const int G = k / vec;
-  return std::min<int64_t>(kVecBlocks,
-                           std::max<int64_t>(1, ceil_div(L->n, column_block_threads(k, vec) / G)));
+  const int T = column_block_threads(k, vec);
+  // one wave: as many blocks as the device keeps resident (a grid-stride kernel whose
+  // grid exceeds that runs a second, mostly idle wave)
+  int per_sm = 0, sms = 0, dev = 0;
+  const void* fn = vec == 4 ? (L->value_dtype == SGP_VALUES_BF16
+                                   ? (const void*)k_slice_dot<4, bf16>
+                                   : (const void*)k_slice_dot<4, float>)
+                            : (L->value_dtype == SGP_VALUES_BF16
+                                   ? (const void*)k_slice_dot<1, bf16>
+                                   : (const void*)k_slice_dot<1, float>);
+  int64_t resident = kVecBlocks;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0) == cudaSuccess &&
+      per_sm > 0)
+    resident = (int64_t)per_sm * sms;
+  else
+    (void)cudaGetLastError();
+  return std::min<int64_t>(resident, std::max<int64_t>(1, ceil_div(L->n, T / G)));
 }
 
 void enqueue_mvm_into(const Lattice* L, const float* V_user, int k, int blur, float alpha,

@@ -31,6 +31,7 @@
 #include <condition_variable>
 #include <mutex>
 #include <string>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -116,6 +117,7 @@ struct Table {
   int kp;
   int* flags;  // [kMaxSlots][2]: state copied by the check kernel, read by the host
   int* err;    // set to 1 when a bulk-copy wait gave up (the round's results are void)
+  int wait_limit;  // try_wait polls of the ring's chunk waits (kSpinLimit; 0 under SGP_FAULT)
   int64_t pre[U_KINDS][kMaxSlots + 1];  // prefix sums of virtual blocks per unit kind
   SlotDev s[kMaxSlots];
 };
@@ -632,9 +634,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false when the limit is reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kSpinLimit; ++i)
+// Bounded wait for the phase with the given parity; false when `limit` polls fail.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          int limit = kSpinLimit) {
+  for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -736,7 +739,8 @@ __global__ void __launch_bounds__(kST, 1) kb_bt(const Table* __restrict__ T) {
       for (int k = 0; k < nch && k < kStages; ++k) ring_issue(ring, k, s, kp, r0, r1, k);
     for (int k = 0; k < nch; ++k) {
       const int st = k % kStages;
-      const bool ok = __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u));
+      const bool ok =
+          __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u, T->wait_limit));
       if (!ok) {
         ring_abort(ring, T, k, k + kStages < nch ? k + kStages : nch);
         return;
@@ -903,7 +907,8 @@ __global__ void __launch_bounds__(kST, 1) kb_apply_z(const Table* __restrict__ T
   for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = {0.f, 0.f};
   for (int k = 0; k < nch; ++k) {
     const int st = k % kStages;
-    const bool ok = __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u));
+    const bool ok =
+        __syncthreads_and(mbar_wait(&ring.bar[st], (ring.phase >> st) & 1u, T->wait_limit));
     if (!ok) {
       ring_abort(ring, T, k, k + kStages < nch ? k + kStages : nch);
       return;
@@ -1270,6 +1275,9 @@ struct sgp_server {
   std::deque<Request*> to_setup;                              // guarded by mu
   std::vector<std::pair<Request*, sgp_status>> setup_done;    // guarded by mu
   bool stop = false;                                          // guarded by mu
+  // SGP_FAULT=ring_wait: the next lane round that applies a preconditioner runs its
+  // bulk-copy waits with a limit of 0 polls (they give up at once), once
+  bool inject_ring_wait = false;                              // stepping thread
 };
 
 namespace {
@@ -1549,6 +1557,7 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   t1.kp = kp;
   t1.flags = nullptr;
   t1.err = R->ints + kp + 2;
+  t1.wait_limit = kSpinLimit;
   fill_slot(S, R, t1.s[0]);
   for (int u = 0; u < U_KINDS; ++u) t1.pre[u][1] = R->vb[u];
   SRV_CHECK(cudaMemcpyAsync(R->dtab1, &t1, sizeof(Table), cudaMemcpyHostToDevice, st),
@@ -1918,12 +1927,17 @@ sgp_status harvest(sgp_server* S, Lane* ln, int* done) {
 sgp_status launch(sgp_server* S, Lane* ln) {
   const int ns = (int)ln->active.size();
   Table& t = *ln->htab;
+  bool any_pre = false;
+  for (Request* R : ln->active) any_pre = any_pre || R->l > 0;
+  const bool inject = any_pre && S->inject_ring_wait;
+  if (inject) ln->dirty = true;
   if (ln->dirty) {
     std::memset(&t, 0, sizeof(Table));
     t.nslots = ns;
     t.kp = S->kp;
     t.flags = ln->dflags;
     t.err = ln->dflags + 2 * kMaxSlots;
+    t.wait_limit = inject ? 0 : kSpinLimit;
     for (int q = 0; q < ns; ++q) {
       Request* R = ln->active[q];
       fill_slot(S, R, t.s[q]);
@@ -1936,7 +1950,8 @@ sgp_status launch(sgp_server* S, Lane* ln) {
     SRV_CHECK(cudaMemcpyAsync(ln->dtab, &t, sizeof(Table), cudaMemcpyHostToDevice, ln->st),
               "copy table");
     ln->ntab = ns;
-    ln->dirty = false;
+    ln->dirty = inject;  // after an injected round the table is uploaded again, limit restored
+    S->inject_ring_wait = S->inject_ring_wait && !inject;
   }
   int dmax = 1;
   bool sparse = false, pre = false;
@@ -2098,6 +2113,10 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
   S->S = o.probes;
   S->kp = (o.probes + 2 + 3) / 4 * 4;  // y, S probes, the ones column, padding
   S->t0 = std::chrono::steady_clock::now();
+  {
+    const char* f = std::getenv("SGP_FAULT");
+    S->inject_ring_wait = f && std::strcmp(f, "ring_wait") == 0;
+  }
   SRV_CHECK(cudaGetDevice(&S->device), "cudaGetDevice");
   // the attribute is per kernel, shared by every server: allow the largest kp
   SRV_CHECK(bt_smem_attributes(kMaxServeK), "shared memory of the preconditioner kernels");

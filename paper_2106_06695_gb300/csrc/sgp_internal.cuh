@@ -31,6 +31,7 @@ struct NvtxRange {
 constexpr int kMaxOrder = 4;  // stencil order r
 constexpr int kMaxD = 128;    // d + 1
 constexpr int kMaxK = 256;    // right-hand sides per call
+constexpr int kProfStages = 5;     // splat, blur, slice, B^T r, z (sgp_profile_read_stages)
 constexpr int kSplatSeg = 32;      // splat items per segment
 constexpr int kSplatMedSegs = 16;  // segments a single thread-group sums in the fix-up
 // A lattice blurs in sparse mode when the direction lists hold at most this fraction of
@@ -57,8 +58,10 @@ struct sgp_lattice {
   int value_dtype = 0;
   int check_every = 8;
   int precond_rank = 0;
+  int precond_power_iters = 1;
   uint64_t precond_seed = 0;
   int fault = 0;  // sgp::FAULT_* injected by SGP_FAULT for this build
+  int device = -1;  // CUDA device current at build time (the arrays live there)
   cudaStream_t stream = nullptr;
 
   // Points are processed in a locality order p = 0..n-1; perm[p] is the caller's index.
@@ -106,10 +109,15 @@ struct sgp_lattice {
 
   // Optional blur timing: events bracket the blur passes of one MVM inside the CG graph
   // and are read at every flag check (sgp_profile_blur / sgp_profile_read).
+  // prof_ev: [0] after the splat, [1] after the blur, [2] before the splat, [3] after the
+  // slice of the MVM inside the CG graph; [4] .. [7] around the preconditioner's B^T r
+  // kernel ([4], [5]) and its z kernel ([6], [7]).
   int profile = 0;
-  cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+  cudaEvent_t prof_ev[8] = {};
   double prof_ms = 0.0;
   int64_t prof_passes = 0;
+  double prof_stage_ms[sgp::kProfStages] = {};  // SGP_STAGE_* order
+  int64_t prof_mvms = 0;
 
   size_t bytes = 0;
 };
@@ -187,7 +195,35 @@ sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, flo
                    float* out);
 
 // ---- rank-l Nystrom preconditioner of the CG (nystrom.cu) ----
-constexpr int kMaxRank = 128;
+constexpr int kMaxRank = 128;       // server requests (kb_* ring kernels)
+constexpr int kMaxLibRank = 4096;   // library CG (ShiftedNystrom)
+
+// Large-rank shifted Nystrom preconditioner of the library CG (precond.cu):
+// P = B B^T + tau I with B B^T a rank-l Nystrom approximation of outputscale K~ (q power
+// iterations) and tau = lambda_min(B^T B) + noise.
+struct ShiftedNystrom {
+  int l = 0, ld = 0;
+  int64_t n = 0;
+  float tau = 0.f;
+  bool ok = false;
+  float* B = nullptr;      // [n][ld] fp32, locality order, padding columns zero
+  float* Minv = nullptr;   // [ld][ld] fp32 (tau I + B^T B)^-1, zero padded
+  float* tpart = nullptr;  // [bt_splits][ld][16] B^T r partials
+  float* tvec = nullptr;   // [ld][16]
+  float* u = nullptr;      // [ld][16]
+  int bt_splits = 0;
+  int64_t bt_rows = 0;
+  std::vector<void*> ptrs;
+  sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, int power_iters,
+                   cudaStream_t st);
+  // partial rows apply() writes per column: one per 128-row tile
+  int64_t dot_blocks() const;
+  // z = P^-1 r (r = rh + rl, locality order [n][k]) and per-tile column sums of r z into
+  // dot[tile][c] (fp64)
+  void apply(const float* rh, const float* rl, int k, float* z, double* dot, cudaStream_t st,
+             cudaEvent_t* ev = nullptr) const;
+  void release(cudaStream_t st);
+};
 struct Nystrom {
   int l = 0;
   int ld = 0;                  // l rounded up to 4: row stride of Bh
@@ -249,7 +285,8 @@ struct LanczosRecord {
 // (not with a Lanczos record, which needs the plain CG's coefficients).
 sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, float tol,
                   int max_iter, float* X, int* iters, double* rel_res, int precond_rank = 0,
-                  uint64_t seed = 0, const LanczosRecord* rec = nullptr);
+                  uint64_t seed = 0, const LanczosRecord* rec = nullptr,
+                  double* history = nullptr);
 // log det(outputscale K~ + noise I) by stochastic Lanczos quadrature over the probe
 // columns Z (device [n][s], caller's order); quad (host [s], may be null) receives each
 // probe's ||z||^2 e1^T log(T) e1 (lanczos.cu).

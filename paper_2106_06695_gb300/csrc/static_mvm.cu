@@ -70,6 +70,13 @@ extern "C" sgp_status sgp_mvm_static(sgp_lattice* h, const float* V, int k, int 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e, "sgp_mvm_static: cudaGetDevice");
+  // the work area is per device: the one of the lattice's device must be the one used
+  if (dev != h->device) {
+    set_error("sgp_mvm_static: the current device (" + std::to_string(dev) +
+              ") is not the device the lattice was built on (" + std::to_string(h->device) +
+              "); make that device current");
+    return SGP_ERR_INVALID_ARG;
+  }
   float* base = nullptr;
   if (sgp_status s = scratch_address(dev, &base)) return s;
   // Every element of the value buffers, partials and permuted input is written before it

@@ -85,8 +85,13 @@ struct Vec<4> {
   static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ T ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
   static __device__ __forceinline__ void st(float* p, T v) { *reinterpret_cast<float4*>(p) = v; }
+  static __device__ __forceinline__ T ldg(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+  }
   template <class S>
   static __device__ __forceinline__ T lds(const S* p) { return Store<S>::ld4(p); }
+  template <class S>
+  static __device__ __forceinline__ T ldgs(const S* p) { return Store<S>::ldg4(p); }
   template <class S>
   static __device__ __forceinline__ void sts(S* p, T v) { Store<S>::st4(p, v); }
   static __device__ __forceinline__ T fma(float a, T x, T y) {
@@ -105,8 +110,11 @@ struct Vec<1> {
   static __device__ __forceinline__ T zero() { return 0.f; }
   static __device__ __forceinline__ T ld(const float* p) { return *p; }
   static __device__ __forceinline__ void st(float* p, T v) { *p = v; }
+  static __device__ __forceinline__ T ldg(const float* p) { return __ldg(p); }
   template <class S>
   static __device__ __forceinline__ T lds(const S* p) { return Store<S>::ld1(p); }
+  template <class S>
+  static __device__ __forceinline__ T ldgs(const S* p) { return Store<S>::ld1(p); }
   template <class S>
   static __device__ __forceinline__ void sts(S* p, T v) { Store<S>::st1(p, v); }
   static __device__ __forceinline__ T fma(float a, T x, T y) { return fmaf(a, x, y); }

@@ -32,13 +32,14 @@ class Lattice:
 
     kernel: "rbf_binomial" (default; stencil [.5, 1, .5] at order 1), "rbf_coverage" or
     "matern32_coverage" (spacing from Eq. balance_coverage); order: stencil order r;
-    precond_rank: rank of the CG's Nystrom preconditioner (0 = plain CG; App. A uses 100).
+    precond_rank: rank of the CG's Nystrom preconditioner (0 = plain CG; App. A uses 100);
+    precond_power_iters: subspace iterations of its sketch (0 or 1).
     """
 
     def __init__(self, X: torch.Tensor, lengthscales, order: int = 1,
                  kernel: str = "rbf_binomial", spacing: float = 0.0, outputscale: float = 1.0,
                  value_dtype: str = "f32", check_every: int = 8, precond_rank: int = 0,
-                 precond_seed: int = 0):
+                 precond_seed: int = 0, precond_power_iters: int = 1):
         self._lib = _lib.load()
         X = _f32_cuda(X, "X")
         if X.dim() != 2:
@@ -62,6 +63,7 @@ class Lattice:
         opts.check_every = int(check_every)
         opts.precond_rank = int(precond_rank)
         opts.precond_seed = int(precond_seed)
+        opts.precond_power_iters = int(precond_power_iters)
         opts.stream = _stream_ptr(self.device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -186,14 +188,23 @@ class Lattice:
         return out.value, quad
 
     def cg(self, B: torch.Tensor, noise: float, tol: float = 1e-3, max_iter: int = 500,
-           blur: str = "symmetric", out: torch.Tensor | None = None):
-        """Batched CG on (outputscale K~ + noise I) X = B; returns (X, iters, rel_res)."""
+           blur: str = "symmetric", out: torch.Tensor | None = None, history: bool = False):
+        """Batched CG on (outputscale K~ + noise I) X = B; returns (X, iters, rel_res), and
+        with history=True also the [max_iter, k] relative residual after every iteration
+        (NaN where a column had stopped)."""
         B2, squeeze = self._rhs(B, "B")
         k = B2.shape[1]
         if out is None:
             out = torch.empty_like(B2)
         iters = np.zeros(k, np.int32)
         rel = np.zeros(k, np.float64)
+        if history:
+            hist = np.zeros((max(int(max_iter), 1), k), np.float64)
+            check(self._lib.sgp_cg_solve_history(
+                self._handle(), B2.data_ptr(), k, BLURS[blur], float(noise), float(tol),
+                int(max_iter), out.data_ptr(), iters.ctypes.data, rel.ctypes.data,
+                hist.ctypes.data))
+            return (out.squeeze(1) if squeeze else out), iters, rel, hist[:int(max_iter)]
         check(self._lib.sgp_cg_solve_ex(self._handle(), B2.data_ptr(), k, BLURS[blur],
                                         float(noise), float(tol), int(max_iter), out.data_ptr(),
                                         iters.ctypes.data, rel.ctypes.data))

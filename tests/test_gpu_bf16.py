@@ -33,9 +33,8 @@ def test_bf16_mvm_error_vs_fp64_oracle(blur, mode, k):
 
     X = synth.gmm_points(6000, 6, 5)
     ls = np.full(6, 0.8, np.float32)
-    lat = Lattice(gpu(X), gpu(ls), value_dtype="bf16")
-    s, _, _ = lat.stencil()
-    ref = OracleLattice(X, ls, spacing=s)
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), value_dtype="bf16", spacing=ref.s)
     V = synth.gaussian_values(6000, k, 11)
     out = lat.mvm(gpu(V), blur=blur).cpu().numpy()
     err = rel_l2(out, ref.mvm(V.astype(np.float64), mode=mode))
@@ -66,9 +65,8 @@ def test_bf16_cg_converges_on_its_own_operator():
 
     X = synth.gmm_points(5000, 6, 19)
     ls = np.ones(6, np.float32)
-    lat = Lattice(gpu(X), gpu(ls), value_dtype="bf16")
-    s, _, _ = lat.stencil()
-    ref = OracleLattice(X, ls, spacing=s)
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), value_dtype="bf16", spacing=ref.s)
     B = synth.solve_rhs(X, 19, probes=4)
     xg, it, rel = lat.cg(gpu(B), noise=0.01, tol=1e-2, max_iter=500)
     Bd = B.astype(np.float64)

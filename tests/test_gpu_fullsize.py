@@ -31,9 +31,8 @@ def bench_workload():
     W = bench.WORKLOAD
     X = synth.gmm_points(W["n"], W["d"], W["seed"])
     ls = np.full(W["d"], W["lengthscale"], np.float32)
-    lat = Lattice(gpu(X), gpu(ls), order=W["order"], kernel=W["kernel"])
-    s, _, _ = lat.stencil()
-    ref = OracleLattice(X, ls, r=W["order"], spacing=s)
+    ref = OracleLattice(X, ls, r=W["order"])
+    lat = Lattice(gpu(X), gpu(ls), order=W["order"], kernel=W["kernel"], spacing=ref.s)
     return W, X, lat, ref
 
 
@@ -83,10 +82,9 @@ def solve_200k():
     X = synth.gmm_points(n, d, 2)
     B = synth.solve_rhs(X, 2, probes=8)
     ls = np.ones(d, np.float32)
-    lat = Lattice(gpu(X), gpu(ls))
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), spacing=ref.s)
     xs, iters, rel = lat.cg(gpu(B), noise=0.01, tol=1e-3, max_iter=500)
-    s, _, _ = lat.stencil()
-    ref = OracleLattice(X, ls, spacing=s)
     Bd = B.astype(np.float64)
     R = Bd - ref.mvm(xs.cpu().numpy().astype(np.float64), mode=2, beta=0.01)
     true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bd, axis=0)
@@ -108,12 +106,11 @@ def test_gp_solve_200k_preconditioned_reaches_tolerance():
     X = synth.gmm_points(n, d, 2)
     B = synth.solve_rhs(X, 2, probes=8)
     ls = np.ones(d, np.float32)
-    lat = Lattice(gpu(X), gpu(ls), precond_rank=100, precond_seed=1)
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), precond_rank=100, precond_seed=1, spacing=ref.s)
     xs, iters, rel = lat.cg(gpu(B), noise=0.01, tol=1e-3, max_iter=500)
     print("preconditioned 200k solve: iterations", iters, "residuals", rel)
     assert (rel <= 1e-3).all(), (iters, rel)
-    s, _, _ = lat.stencil()
-    ref = OracleLattice(X, ls, spacing=s)
     Bd = B.astype(np.float64)
     R = Bd - ref.mvm(xs.cpu().numpy().astype(np.float64), mode=2, beta=0.01)
     true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bd, axis=0)

@@ -38,9 +38,12 @@ def pair(X, ls, kernel="rbf_binomial", order=1):
     from paper_2106_06695_gb300.lattice import Lattice
 
     ls = np.broadcast_to(np.asarray(ls, np.float32), (X.shape[1],)).copy()
-    lat = Lattice(gpu(X), gpu(ls), order=order, kernel=kernel)
+    # the oracle's own spacing (its closed-form coverage integrals) is given to the GPU
+    # build; the library's rule for s is checked separately in test_host_logic.py
+    ref = OracleLattice(X, ls, kind=KIND[kernel], r=order)
+    lat = Lattice(gpu(X), gpu(ls), order=order, kernel=kernel, spacing=ref.s)
     s, c, g = lat.stencil()
-    ref = OracleLattice(X, ls, kind=KIND[kernel], r=order, spacing=s)
+    assert s == ref.s
     assert np.allclose(c, ref.coef, rtol=0, atol=1e-15)
     assert np.allclose(g, ref.half, rtol=0, atol=1e-15)
     return lat, ref

@@ -121,3 +121,51 @@ def test_lattice_gradients_track_the_dense_kernel_gradient_at_low_d(mode):
           "dls %.3f" % (mode, cos(dXl, dX0), cos(dlsl, dls0), cos(dXf, dX0), cos(dlsf, dls0)))
     assert cos(dXf, dX0) >= 0.95 and cos(dlsf, dls0) >= 0.8
     assert cos(dXl, dX0) >= 0.85 and cos(dlsl, dls0) >= 0.9
+
+
+def test_dX_and_dls_match_central_differences_on_the_d20_workload_subsample():
+    """The differentiation workload's own dimension: a seeded n = 2,000 subsample of the
+    n = 500,000, d = 20 correlated-Gaussian points with their ARD lengthscales, symmetric
+    blur, k = 2.  Central differences with steps that keep every vertex key (within one
+    configuration of simplices the loss is quadratic in the points, so they are exact).
+    A lengthscale step moves all 2,000 points and crosses some simplex boundary almost
+    every time at d = 20, so dls counts only where it did not (its formula is pinned at
+    d = 2..8 above)."""
+    Xf, lsf = synth.correlated_points(500_000, 20, 3)
+    rows = synth.subsample(500_000, 2000, 3)
+    X = Xf[rows].astype(np.float64)
+    ls = lsf.astype(np.float64)
+    V = synth.gaussian_values(2000, 2, 4).astype(np.float64)
+    G = synth.gaussian_values(2000, 2, 5).astype(np.float64)
+    d, mode, alpha = 20, 2, 1.0
+    L = OracleLattice(X.astype(np.float32), ls.astype(np.float32))
+    _, dX, dls = L.mvm_backward(V, G, mode=mode, alpha=alpha)
+    ex = L.export()
+    base = ex["keys"][ex["idx"]]
+    checked = 0
+    for i in (0, 1999):
+        for j in range(d):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[i, j] += H
+            Xm[i, j] -= H
+            (a, ia), (b, ib) = (loss_and_ids(Xp, ls, V, G, mode, alpha),
+                                loss_and_ids(Xm, ls, V, G, mode, alpha))
+            if not (ia.shape == base.shape and ib.shape == base.shape and (ia == base).all()
+                    and (ib == base).all()):
+                continue
+            fd = (a - b) / (2 * H)
+            assert abs(dX[i, j] - fd) <= 1e-6 * max(1.0, abs(fd))
+            checked += 1
+    assert checked >= d
+    checked = 0
+    for j in range(d):
+        lp, lm = ls.copy(), ls.copy()
+        lp[j] += H
+        lm[j] -= H
+        (a, ia), (b, ib) = loss_and_ids(X, lp, V, G, mode, alpha), loss_and_ids(X, lm, V, G, mode, alpha)
+        if ia.shape == base.shape and ib.shape == base.shape and (ia == base).all() and (
+                ib == base).all():
+            fd = (a - b) / (2 * H)
+            assert abs(dls[j] - fd) <= 1e-5 * max(1.0, abs(fd))
+            checked += 1
+    print("d = 20: %d of %d lengthscale steps kept every vertex key" % (checked, d))

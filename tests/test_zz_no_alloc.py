@@ -1,12 +1,14 @@
-"""The allocation-free MVM entry point (sgp_mvm_static) against sgp_mvm_ex.
+"""The allocation-free MVM entry point (sgp_mvm_static) against sgp_mvm_ex and the oracle.
 
 sgp_mvm_static serves callers that cannot allocate device memory when they need a
 product -- serving loops that keep cudaMalloc/cudaFree off their hot path, and processes
 whose device memory another allocator has already reserved -- from a 64 MiB work area
-compiled into the library.  Both entry points are called through the C-ABI on the same
-lattice; the static one twice in a row (its work area keeps the previous call's
-contents), and each result must match within the MVM tolerance of the parity tests.
-This file is collected last so that a failure here comes after every other test.
+compiled into the library.  It is called through the C-ABI on freshly built lattices
+before any allocating entry point, so the handle's device bytes must not change, and
+twice in a row (its work area keeps the previous call's contents).  Each result must
+match sgp_mvm_ex within the MVM tolerance of the parity tests (fp32 values) or the BF16
+bound (bf16 values), and the FP64 oracle within the same bound.  This file is collected
+last so that a failure here comes after every other test.
 """
 
 import ctypes
@@ -15,11 +17,12 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import OracleLattice
 from paper_2106_06695_gb300 import _lib, build_lib, synth
 
 pytestmark = pytest.mark.gpu
 
-MVM_RTOL = 1e-5
+RTOL = {"f32": 1e-5, "bf16": 1e-2}
 BLURS = {"sequential": 0, "transpose": 1, "symmetric": 2}
 
 
@@ -28,31 +31,51 @@ def gpu(a):
 
 
 def rel_l2(a, b):
-    return (a - b).double().norm().item() / max(b.double().norm().item(), 1e-300)
+    a = np.asarray(a, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_static_entry_point_matches_allocating_one():
+@pytest.mark.parametrize("values", ["f32", "bf16"])
+def test_static_entry_point_matches_allocating_one_and_oracle(values):
     build_lib.build()
     lib = _lib.load()
     from paper_2106_06695_gb300.lattice import Lattice
 
     n, d = 20000, 6
     X = synth.gmm_points(n, d, 31)
-    lat = Lattice(gpu(X), gpu(np.full(d, 0.8, np.float32)))
+    ls = np.full(d, 0.8, np.float32)
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), value_dtype=values, spacing=ref.s)
+    h = lat._handle()
+    bytes0 = lat.device_bytes
+    alpha, beta = 1.5, 0.25
+    results = {}
+    # on the fresh handle: the static entry point first, twice per case
     for k in (16, 3):
-        V = gpu(synth.gaussian_values(n, k, 32))
+        V = synth.gaussian_values(n, k, 32)
+        Vd = gpu(V)
         for blur, code in BLURS.items():
-            ref = torch.empty_like(V)
-            _lib.check(lib.sgp_mvm_ex(lat._handle(), V.data_ptr(), k, code, ctypes.c_float(1.5),
-                                      ctypes.c_float(0.25), ref.data_ptr()))
+            outs = []
             for _ in range(2):
-                out = torch.full_like(V, float("nan"))
-                _lib.check(lib.sgp_mvm_static(lat._handle(), V.data_ptr(), k, code,
-                                              ctypes.c_float(1.5), ctypes.c_float(0.25),
-                                              out.data_ptr()))
+                out = torch.full_like(Vd, float("nan"))
+                _lib.check(lib.sgp_mvm_static(h, Vd.data_ptr(), k, code, ctypes.c_float(alpha),
+                                              ctypes.c_float(beta), out.data_ptr()))
                 torch.cuda.synchronize()
                 assert torch.isfinite(out).all()
-                assert rel_l2(out, ref) <= MVM_RTOL, (k, blur)
+                outs.append(out.cpu().numpy())
+            assert lat.device_bytes == bytes0, "sgp_mvm_static allocated lattice buffers"
+            want = ref.mvm(V.astype(np.float64), mode=code, alpha=alpha, beta=beta)
+            for o in outs:
+                assert rel_l2(o, want) <= RTOL[values], (values, k, blur)
+            results[(k, blur)] = (Vd, outs)
+    # then the allocating entry point on the same handle
+    for (k, blur), (Vd, outs) in results.items():
+        ref_out = torch.empty_like(Vd)
+        _lib.check(lib.sgp_mvm_ex(h, Vd.data_ptr(), k, BLURS[blur], ctypes.c_float(alpha),
+                                  ctypes.c_float(beta), ref_out.data_ptr()))
+        ref_np = ref_out.cpu().numpy().astype(np.float64)
+        for o in outs:
+            assert rel_l2(o, ref_np) <= RTOL[values], (values, k, blur)
 
 
 def test_static_entry_point_rejects_lattices_beyond_its_work_area():
