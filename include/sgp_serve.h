@@ -76,7 +76,13 @@ typedef struct {
   int order_r;        /* stencil order (as sgp_opts); default 1                           */
   int kernel;         /* SGP_KERNEL_*; default SGP_KERNEL_RBF_BINOMIAL                    */
   double spacing_s;   /* > 0 overrides the kernel rule's spacing; default 0               */
-  int value_dtype;    /* SGP_VALUES_F32 / SGP_VALUES_BF16 lattice value storage           */
+  int value_dtype;    /* SGP_VALUES_F32 / SGP_VALUES_BF16 lattice value storage.  With
+                         BF16 a request keeps bf16 values only when its condition estimate
+                         kappa is at most 100: the ~2^-8 relative error of bf16 products
+                         grows with the conditioning of the solve, so a worse-conditioned
+                         request is rebuilt with fp32 values (same lattice) before its
+                         right-hand sides and solve, and serves at the fp32 accuracy.
+                         Admission reserves the fp32 bound in either mode.               */
   double tol;         /* CG tolerance on ||r|| / ||b||; default 1e-3                      */
   int max_iter;       /* CG iteration cap; default 500                                    */
   int check_every;    /* CG iterations per sgp_server_step between flag reads; default 8 */
@@ -123,7 +129,9 @@ typedef struct {
                                 sides) on a set-up thread                                 */
   int lattice_reused;        /* 1 when it ran on a resident lattice (lattice_key)         */
   int precond_rank;          /* rank of its preconditioner (0: plain CG)                  */
-  double kappa_est;          /* its condition estimate (0 when precond_rank option is 0)  */
+  double kappa_est;          /* its condition estimate (0 when precond_rank option is 0
+                                and the server stores fp32 values)                        */
+  int value_dtype;           /* SGP_VALUES_* its solve used (see value_dtype below)       */
 } sgp_request_stats;
 
 /* Fill *opts with the defaults listed above (hbm_budget from the current device, or 0

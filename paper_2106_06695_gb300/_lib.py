@@ -60,7 +60,8 @@ class sgp_request_stats(ctypes.Structure):
                 ("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
                 ("m", ctypes.c_longlong), ("bytes", ctypes.c_ulonglong),
                 ("setup_us", ctypes.c_double), ("lattice_reused", ctypes.c_int),
-                ("precond_rank", ctypes.c_int), ("kappa_est", ctypes.c_double)]
+                ("precond_rank", ctypes.c_int), ("kappa_est", ctypes.c_double),
+                ("value_dtype", ctypes.c_int)]
 
 
 class SGPError(RuntimeError):

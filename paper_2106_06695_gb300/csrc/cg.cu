@@ -66,8 +66,10 @@ __device__ __forceinline__ void stf(float* p, const float (&v)[VEC]) {
 // The solver's vectors live in the lattice's locality order: row p holds the caller's
 // row perm[p], so the MVM's splat gathers and slice writes stay local.  B and X are the
 // caller's buffers (any alignment): read and written element by element.
+// The caller's B has kb <= k columns; columns kb .. k - 1 of the solver's vectors are zero
+// right-hand sides (inactive from the start).
 template <int VEC>
-__global__ void k_cg_init(const float* __restrict__ B, const int32_t* __restrict__ perm,
+__global__ void k_cg_init(const float* __restrict__ B, int kb, const int32_t* __restrict__ perm,
                           float* __restrict__ xh, float* __restrict__ xl,
                           float* __restrict__ rh, float* __restrict__ rl, float* __restrict__ p,
                           int64_t n, int k, double* __restrict__ partial) {
@@ -75,11 +77,11 @@ __global__ void k_cg_init(const float* __restrict__ B, const int32_t* __restrict
 #pragma unroll
   for (int j = 0; j < VEC; ++j) acc[j] = {0.f, 0.f};
   SGP_ROWS_LOOP(row) {
-    const float* b = B + (int64_t)perm[row] * k + c0;
+    const float* b = B + (int64_t)perm[row] * kb + c0;
     float bv[VEC], zero[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
-      bv[j] = b[j];
+      bv[j] = c0 + j < kb ? b[j] : 0.f;
       zero[j] = 0.f;
       acc[j] = df_add(acc[j], df_two_prod(bv[j], bv[j]));
     }
@@ -319,15 +321,16 @@ __global__ void k_cg_update_p(float* __restrict__ p, const float* __restrict__ r
 
 template <int VEC>
 __global__ void k_cg_store_x(const float* __restrict__ xh, const float* __restrict__ xl,
-                             const int32_t* __restrict__ perm, float* __restrict__ X, int64_t n,
-                             int k) {
+                             const int32_t* __restrict__ perm, float* __restrict__ X, int kb,
+                             int64_t n, int k) {
   SGP_ROWS_LOOP(row) {
     float hv[VEC], lv[VEC];
     ldf<VEC>(xh + row * k + c0, hv);
     ldf<VEC>(xl + row * k + c0, lv);
-    float* dst = X + (int64_t)perm[row] * k + c0;
+    float* dst = X + (int64_t)perm[row] * kb + c0;
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) dst[j] = __fadd_rn(hv[j], lv[j]);
+    for (int j = 0; j < VEC; ++j)
+      if (c0 + j < kb) dst[j] = __fadd_rn(hv[j], lv[j]);
   }
 }
 
@@ -337,6 +340,12 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
                   int max_iter, float* X, int* iters, double* rel_res, int precond_rank,
                   uint64_t seed, const LanczosRecord* rec, double* history) {
   const int64_t n = L->n;
+  // The solver works on k rounded up to a multiple of 4 (zero right-hand sides in the
+  // extra columns, inactive from the start), so that its vectors and the lattice values
+  // are rows of float4 and the MVM takes its vectorised kernels.  The Lanczos record of
+  // sgp_logdet is laid out for the caller's k: no padding then.
+  const int kb = k;
+  if (!rec) k = (k + 3) / 4 * 4;
   // CUDA graphs cannot be captured on the legacy default stream: use a private blocking
   // stream then (it is ordered with the legacy stream like any blocking stream).
   cudaStream_t st = L->stream;
@@ -434,8 +443,10 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     if (use_pre) CG_CHECK(get((void**)&z, n * k * sizeof(float)), "alloc z");
   }
 
-  if (vec == 4) k_cg_init<4><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
-  else k_cg_init<1><<<vblocks, T, 0, st>>>(B, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
+  if (vec == 4)
+    k_cg_init<4><<<vblocks, T, 0, st>>>(B, kb, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
+  else
+    k_cg_init<1><<<vblocks, T, 0, st>>>(B, kb, L->perm, xh, xl, rh, rl, p, n, k, S.partial);
   k_cg_init_scalars<<<k, 256, 0, st>>>(S.partial, vblocks, k, tol, max_iter, S);
   note_launches(2);
   if (use_pre) {  // z = P^-1 r, rho = <r, z>, p = z
@@ -507,8 +518,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
       }
     }
   }
-  if (vec == 4) k_cg_store_x<4><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, n, k);
-  else k_cg_store_x<1><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, n, k);
+  if (vec == 4) k_cg_store_x<4><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, kb, n, k);
+  else k_cg_store_x<1><<<vblocks, T, 0, st>>>(xh, xl, L->perm, X, kb, n, k);
   note_launches(1);
   CG_CHECK(cudaGetLastError(), "CG result");
   std::vector<double> hrel(k);
@@ -518,13 +529,17 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   CG_CHECK(cudaMemcpyAsync(hit.data(), S.iters, k * sizeof(int), cudaMemcpyDeviceToHost, st),
            "read iterations");
   CG_CHECK(cudaStreamSynchronize(st), "sync CG");
-  if (iters) std::copy(hit.begin(), hit.end(), iters);
-  if (rel_res) std::copy(hrel.begin(), hrel.end(), rel_res);
-  if (S.hist) {
-    CG_CHECK(cudaMemcpyAsync(history, S.hist, (size_t)max_iter * k * sizeof(double),
+  if (iters) std::copy(hit.begin(), hit.begin() + kb, iters);
+  if (rel_res) std::copy(hrel.begin(), hrel.begin() + kb, rel_res);
+  if (S.hist) {  // [max_iter][k] on the device, the caller's [max_iter][kb] on the host
+    std::vector<double> h((size_t)max_iter * k);
+    CG_CHECK(cudaMemcpyAsync(h.data(), S.hist, h.size() * sizeof(double),
                              cudaMemcpyDeviceToHost, st),
              "read history");
     CG_CHECK(cudaStreamSynchronize(st), "sync CG");
+    for (int j = 0; j < max_iter; ++j)
+      std::copy(h.begin() + (size_t)j * k, h.begin() + (size_t)j * k + kb,
+                history + (size_t)j * kb);
   }
   if (rec) {  // ||b_c|| and the iteration counts stay on the device for the quadrature
     CG_CHECK(cudaMemcpyAsync(rec->bnorm, S.bnorm, k * sizeof(double), cudaMemcpyDeviceToDevice,

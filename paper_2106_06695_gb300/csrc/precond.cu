@@ -8,7 +8,8 @@
 //           (Cholesky QR, twice; the approximation depends only on the subspace);
 //   Y       = K Q;   C = (Q^T Y + Y^T Q) / 2 + eps I,  eps = 1e-6 max_j C_jj (raised when
 //           the Cholesky of C fails);
-//   B       = Y R^-T with C = R R^T, so that B B^T = Y C^-1 Y^T ~ K;
+//   B       = Y R^-T with C = R R^T, so that B B^T = Y C^-1 Y^T ~ K, rounded to bf16 and
+//           stored so (P is defined by the stored values: B^T B is formed from them);
 //   tau     = lambda_min(B^T B) + noise (the smallest retained eigenvalue plus the noise,
 //           estimated by inverse power iteration);
 //   P       = B B^T + tau I,   P^-1 r = (r - B Minv B^T r) / tau,  Minv = (tau I + B^T B)^-1.
@@ -18,16 +19,23 @@
 // accurate in fp32 (with tau = noise, fp32 cancellation in the top eigen-directions breaks
 // positive definiteness at large ranks).
 //
-// The tall n x l products (Grams Q^T Y, B^T B, Y^T Y; panel times l x l matrix; the
-// per-iteration B^T r and B u) run on the tensor cores as m16n8k8 TF32 MMAs with a 3xTF32
-// split (hi hi + hi lo + lo hi, about fp32 accuracy), fp32 sums inside a block and fp64
-// sums across blocks in a fixed order.  The l x l factorizations (Cholesky, triangular
-// inverse, products) run in fp64 on the CUDA cores in 32 x 32 blocks.  Panels are fp32
-// [n][ld] in the lattice's locality order, ld = l rounded up to 128, padding columns zero.
+// The set-up's tall n x l products (Grams Q^T Y, B^T B, Y^T Y; panel times l x l matrix)
+// run on the tensor cores as m16n8k8 TF32 MMAs with a 3xTF32 split (hi hi + hi lo + lo hi,
+// about fp32 accuracy), fp32 sums inside a block and fp64 sums across blocks in a fixed
+// order.  The l x l factorizations (Cholesky, triangular inverse, products) run in fp64 on
+// the CUDA cores in 32 x 32 blocks.  Panels are fp32 [n][ld] in the lattice's locality
+// order, ld = l rounded up to 128, padding columns zero.
+// Per iteration the apply reads the bf16 factor twice (B^T r, then B u): 2 n ld bytes each,
+// half of an fp32 factor.  With tau well above the noise the bf16 rounding of B (a
+// perturbation of order 2^-9 ||B||^2 / sqrt(l) of B B^T, small against tau) leaves the
+// iteration counts unchanged (measured at n = 2M, ranks 1024 and 2048).  The MMAs there are
+// m16n8k16 bf16 with B exact and r, u split in three bf16 parts (about 24 bits).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "sgp_internal.cuh"
 
@@ -43,15 +51,19 @@ constexpr int kSketchCols = 128;  // sketch columns per lattice product
 constexpr int kNB = 32;        // block size of the fp64 factorizations
 
 // ---- TF32 MMA pieces --------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// Round an fp32 bit pattern to TF32 (10 explicit mantissa bits), nearest with ties away
+// from zero, by integer arithmetic on the magnitude bits: adding half a TF32 unit carries
+// into the kept bits (and into the exponent when the mantissa overflows), then the 13 low
+// bits are cleared.  Two integer operations instead of a conversion instruction (whose
+// issue rate limits the per-iteration kernels); same result as cvt.rna for finite x.
+__device__ __forceinline__ uint32_t tf32_round_bits(uint32_t b) {
+  return (b + 0x1000u) & 0xFFFFE000u;
 }
-// x = hi + lo with hi, lo TF32 (hi hi + hi lo + lo hi keeps about fp32 accuracy)
+// x = hi + lo with hi, lo TF32 (hi hi + hi lo + lo hi keeps about fp32 accuracy); x - hi is
+// exact in fp32.
 __device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
+  hi = tf32_round_bits(__float_as_uint(x));
+  lo = tf32_round_bits(__float_as_uint(x - __uint_as_float(hi)));
 }
 // D (16 x 8) += A (16 x 8, row-major) B (8 x 8, column-major); lane = 4 g + t holds
 // A[g][t], A[g + 8][t], A[g][t + 4], A[g + 8][t + 4]; B[t][g], B[t + 4][g];
@@ -308,16 +320,70 @@ __global__ void __launch_bounds__(256, 2) k_panel_tc(const float* __restrict__ Y
     }
 }
 
+// 4-byte cp.async (r rows of any width k are not 16-byte aligned).
+__device__ __forceinline__ void cp4(float* smem, const float* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp16b(void* smem, const void* gmem, bool valid) {
+  cp16(reinterpret_cast<float*>(smem), reinterpret_cast<const float*>(gmem), valid);
+}
+
+// ---- per-iteration apply with the bf16 factor ---------------------------------------------
+// B holds bf16 values exactly, so the products B^T r and B u are formed on the tensor cores
+// as m16n8k16 bf16 MMAs with B as the exact operand and r, u split in three bf16 parts
+// x = x1 + x2 + x3 (about 24 bits): products are exact in fp32, sums fp32 within a block.
+// A fragments of B come from shared memory by ldmatrix (transposed for B^T).
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row_addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((unsigned)__cvta_generic_to_shared(row_addr)));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* row_addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((unsigned)__cvta_generic_to_shared(row_addr)));
+}
+// x = x1 + x2 + x3 in bf16 (each part the nearest bf16 of what is left; the differences are
+// exact in fp32)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
+                                       __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+constexpr int kApplyStages = 4;   // chunks in flight per block in the per-iteration kernels
+constexpr int kBtRowB = 136;      // bf16 per smem row of a [32 r][128 i] tile (272 B)
+constexpr int kBtStageBytes = kKc * kBtRowB * 2 + 2 * kKc * kSR * 4;
+constexpr int kZRowB = 40;        // bf16 per smem row of a [128 r][32 i] tile (80 B)
+constexpr int kZURow = 40;        // bf16 per smem row of a [3][16 c][32 i] u tile
+constexpr int kZStageBytes = kTile * kZRowB * 2 + 3 * 16 * kZURow * 2;
+
 // Per-iteration B^T r for 16 columns [c_off, c_off + kc) of r = rh + rl:
 // tpart[s][i][c] = sum over the rows of split s of B[row][i] r[row][c_off + c], for the
 // 128 rows i of tile blockIdx.x (split blockIdx.y).  Warp w owns i rows 16 w .. 16 w + 15.
-__global__ void __launch_bounds__(256) k_bt_tc(const float* __restrict__ B, int ld,
-                                               const float* __restrict__ rh,
-                                               const float* __restrict__ rl, int k, int c_off,
-                                               int kc, int64_t n, int64_t rows_per_split,
-                                               float* __restrict__ tpart) {
-  __shared__ __align__(16) float bs[2][kKc * kSMN];
-  __shared__ __align__(16) float rs[2][kKc * kSR];
+// Chunks of 32 rows (B: 128 columns, r: both fp32 parts) stream through kApplyStages
+// shared-memory stages by cp.async.
+__global__ void __launch_bounds__(256) k_bt_bf16(const __nv_bfloat16* __restrict__ B, int ld,
+                                                 const float* __restrict__ rh,
+                                                 const float* __restrict__ rl, int k, int c_off,
+                                                 int kc, int64_t n, int64_t rows_per_split,
+                                                 float* __restrict__ tpart) {
+  extern __shared__ __align__(16) uint8_t smb[];  // [kApplyStages][kBtStageBytes]
   const int i0 = blockIdx.x * kTile;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
@@ -327,74 +393,72 @@ __global__ void __launch_bounds__(256) k_bt_tc(const float* __restrict__ B, int 
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  // r values of a chunk: thread t holds rows (t / 16) and (t / 16) + 16, column t % 16
-  const int rr_r = threadIdx.x >> 4, rc = threadIdx.x & 15;
-  auto load_b = [&](int buf, int64_t r0) {
+  auto load = [&](int slot, int64_t r0) {
+    uint8_t* st = smb + slot * kBtStageBytes;
+    __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(st);
+    float* hs = reinterpret_cast<float*>(st + kKc * kBtRowB * 2);
+    float* ls = hs + kKc * kSR;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int rr = e >> 5, c4 = (e & 31) * 4;
+    for (int q = 0; q < 2; ++q) {
+      const int e = threadIdx.x + 256 * q;  // 32 rows x 16 pieces of 16 bytes
+      const int rr = e >> 4, c8 = (e & 15) * 8;
       const int64_t r = r0 + rr;
       const bool ok = r < r_end;
-      cp16(&bs[buf][rr * kSMN + c4], ok ? B + r * ld + i0 + c4 : B, ok);
+      cp16b(bs + rr * kBtRowB + c8, ok ? B + r * ld + i0 + c8 : B, ok);
     }
-    cp_commit();
-  };
-  auto load_r = [&](int64_t r0, float (&v)[2]) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t r = r0 + rr_r + 16 * h;
-      float x = 0.f;
-      if (r < r_end && rc < kc) {
-        const int64_t e = r * k + c_off + rc;
-        x = __fadd_rn(rh[e], rl[e]);
-      }
-      v[h] = x;
+    for (int q = 0; q < 2; ++q) {  // 32 rows x 16 columns of rh and of rl
+      const int e = threadIdx.x + 256 * q;
+      const int rr = e >> 4, c = e & 15;
+      const int64_t r = r0 + rr;
+      const bool ok = r < r_end && c < kc;
+      const int64_t off = ok ? r * k + c_off + c : 0;
+      cp4(hs + rr * kSR + c, rh + off, ok);
+      cp4(ls + rr * kSR + c, rl + off, ok);
     }
   };
   const int64_t nchunks = r_end > r_begin ? ceil_div(r_end - r_begin, kKc) : 0;
-  float rv[2];
-  if (nchunks > 0) {
-    load_b(0, r_begin);
-    load_r(r_begin, rv);
-    rs[0][rr_r * kSR + rc] = rv[0];
-    rs[0][(rr_r + 16) * kSR + rc] = rv[1];
-  }
-  for (int64_t c = 0; c < nchunks; ++c) {
-    const int buf = (int)(c & 1);
-    const bool more = c + 1 < nchunks;
-    if (more) {
-      load_b(buf ^ 1, r_begin + (c + 1) * kKc);
-      load_r(r_begin + (c + 1) * kKc, rv);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const float* Bs = bs[buf];
-    const float* Rs = rs[buf];
 #pragma unroll
-    for (int kk = 0; kk < kKc; kk += 8) {
-      const int ib = warp * 16 + g;
-      uint32_t ah[4], al[4];
-      split(Bs[(kk + tq) * kSMN + ib], ah[0], al[0]);
-      split(Bs[(kk + tq) * kSMN + ib + 8], ah[1], al[1]);
-      split(Bs[(kk + tq + 4) * kSMN + ib], ah[2], al[2]);
-      split(Bs[(kk + tq + 4) * kSMN + ib + 8], ah[3], al[3]);
+  for (int s0 = 0; s0 < kApplyStages - 1; ++s0) {
+    if (s0 < nchunks) load(s0, r_begin + (int64_t)s0 * kKc);
+    cp_commit();
+  }
+  // ldmatrix.trans row addresses: matrix q = lane / 8 covers k rows 8 (q >> 1) .. + 7 and
+  // i columns 8 (q & 1) .. + 7 of the warp's 16 x 16 A tile (A[i][r] = B[r][i])
+  const int q = lane >> 3, j = lane & 7;
+  const int lrow = 8 * (q >> 1) + j, lcol = warp * 16 + 8 * (q & 1);
+  for (int64_t c = 0; c < nchunks; ++c) {
+    cp_wait<kApplyStages - 2>();
+    __syncthreads();  // chunk c has landed; every warp is done with chunk c - 1's stage
+    if (c + kApplyStages - 1 < nchunks)
+      load((int)((c + kApplyStages - 1) % kApplyStages), r_begin + (c + kApplyStages - 1) * kKc);
+    cp_commit();
+    const uint8_t* st = smb + (int)(c % kApplyStages) * kBtStageBytes;
+    const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(st);
+    const float* Hs = reinterpret_cast<const float*>(st + kKc * kBtRowB * 2);
+    const float* Ls = Hs + kKc * kSR;
+#pragma unroll
+    for (int kk = 0; kk < kKc; kk += 16) {
+      uint32_t a[4];
+      ldsm_x4_trans(a, Bs + (kk + lrow) * kBtRowB + lcol);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
-        uint32_t bh0, bl0, bh1, bl1;
-        split(Rs[(kk + tq) * kSR + nt * 8 + g], bh0, bl0);
-        split(Rs[(kk + tq + 4) * kSR + nt * 8 + g], bh1, bl1);
-        mma3(acc[nt], ah, al, bh0, bh1, bl0, bl1);
+        // B operand B'[k][n] = r[kk + k][nt 8 + n]: b0 = rows 2 tq, 2 tq + 1 and b1 = rows
+        // 2 tq + 8, 2 tq + 9 of column g
+        __nv_bfloat16 p[4][3];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+          const int kr = kk + 2 * tq + (e2 & 1) + 8 * (e2 >> 1);
+          const int o = kr * kSR + nt * 8 + g;
+          split3(__fadd_rn(Hs[o], Ls[o]), p[e2][0], p[e2][1], p[e2][2]);
+        }
+#pragma unroll
+        for (int part = 2; part >= 0; --part)
+          mma_bf16(acc[nt], a, pack2(p[0][part], p[1][part]), pack2(p[2][part], p[3][part]));
       }
     }
-    if (more) {  // the other r buffer was last read before the previous barrier
-      rs[buf ^ 1][rr_r * kSR + rc] = rv[0];
-      rs[buf ^ 1][(rr_r + 16) * kSR + rc] = rv[1];
-    }
-    __syncthreads();
   }
+  cp_wait<0>();
   float* out = tpart + (size_t)blockIdx.y * gridDim.x * kTile * 16;
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt) {
@@ -415,30 +479,36 @@ __global__ void k_sum_t(const float* __restrict__ tpart, int splits, int ld,
   t[e] = (float)s;
 }
 
-// u[i][c] = sum_j Minv[i][j] t[j][c] (fp32), i < ld, c < 16; one thread per output.
+// u[i][c] = sum_j Minv[i][j] t[j][c] (fp32), i < ld, c < 16; one thread per output.  Stored
+// split in three bf16 parts, transposed: u3[part][c][i].
 __global__ void k_minv_u(const float* __restrict__ Minv, int ld, const float* __restrict__ t,
-                         float* __restrict__ u) {
+                         __nv_bfloat16* __restrict__ u3) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ld * 16) return;
   const int i = e >> 4, c = e & 15;
   const float* row = Minv + (size_t)i * ld;
   float s = 0.f;
   for (int j = 0; j < ld; ++j) s = fmaf(row[j], t[j * 16 + c], s);
-  u[e] = s;
+  __nv_bfloat16 a, b, d;
+  split3(s, a, b, d);
+  u3[(size_t)(0 * 16 + c) * ld + i] = a;
+  u3[(size_t)(1 * 16 + c) * ld + i] = b;
+  u3[(size_t)(2 * 16 + c) * ld + i] = d;
 }
 
 // z[r][c_off + c] = (r - B u)[r][c] * inv_tau for the 128 rows of tile blockIdx.x, and the
 // tile's column sums of r z (double-float per lane, fixed butterfly over the lanes of a
 // column, warps in order) into dot[blockIdx.x][c_off + c].  Warp w owns rows 16 w .. + 15.
-__global__ void __launch_bounds__(256) k_apply_z_tc(const float* __restrict__ B, int ld,
-                                                    const float* __restrict__ u,
-                                                    const float* __restrict__ rh,
-                                                    const float* __restrict__ rl, int k,
-                                                    int c_off, int kc, int64_t n, float inv_tau,
-                                                    float* __restrict__ z,
-                                                    double* __restrict__ dot) {
-  __shared__ __align__(16) float bsm[2][kTile * kSK];
-  __shared__ __align__(16) float usm[2][kKc * kSR];
+// Chunks of 32 columns of B (and the matching 32 entries of each u part) stream through
+// kApplyStages shared-memory stages by cp.async.
+__global__ void __launch_bounds__(256) k_apply_z_bf16(const __nv_bfloat16* __restrict__ B,
+                                                      int ld, const __nv_bfloat16* __restrict__ u3,
+                                                      const float* __restrict__ rh,
+                                                      const float* __restrict__ rl, int k,
+                                                      int c_off, int kc, int64_t n,
+                                                      float inv_tau, float* __restrict__ z,
+                                                      double* __restrict__ dot) {
+  extern __shared__ __align__(16) uint8_t smb[];  // [kApplyStages][kZStageBytes]
   __shared__ double red[8][16];
   const int64_t r0 = (int64_t)blockIdx.x * kTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
@@ -447,52 +517,59 @@ __global__ void __launch_bounds__(256) k_apply_z_tc(const float* __restrict__ B,
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  auto load = [&](int buf, int k0) {
+  auto load = [&](int slot, int k0) {
+    uint8_t* st = smb + slot * kZStageBytes;
+    __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(st);
+    __nv_bfloat16* us = reinterpret_cast<__nv_bfloat16*>(st + kTile * kZRowB * 2);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;  // 128 rows x 8 float4
-      const int rr = e >> 3, c4 = (e & 7) * 4;
+    for (int q = 0; q < 2; ++q) {
+      const int e = threadIdx.x + 256 * q;  // 128 rows x 4 pieces of 16 bytes
+      const int rr = e >> 2, c8 = (e & 3) * 8;
       const int64_t r = r0 + rr;
       const bool ok = r < n;
-      cp16(&bsm[buf][rr * kSK + c4], ok ? B + r * ld + k0 + c4 : B, ok);
+      cp16b(bs + rr * kZRowB + c8, ok ? B + r * ld + k0 + c8 : B, ok);
     }
-    if (threadIdx.x < kKc * 4) {  // u rows k0 .. k0 + 31, 16 columns: 128 float4
-      const int rr = threadIdx.x >> 2, c4 = (threadIdx.x & 3) * 4;
-      cp16(&usm[buf][rr * kSR + c4], u + (size_t)(k0 + rr) * 16 + c4, true);
+    if (threadIdx.x < 3 * 16 * 4) {  // u parts: 48 rows (part, c) x 4 pieces of 16 bytes
+      const int row = threadIdx.x >> 2, c8 = (threadIdx.x & 3) * 8;
+      cp16b(us + row * kZURow + c8, u3 + (size_t)row * ld + k0 + c8, true);
     }
-    cp_commit();
   };
   const int nchunks = ld / kKc;
-  load(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    const int buf = c & 1;
-    if (c + 1 < nchunks) {
-      load(buf ^ 1, (c + 1) * kKc);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const float* Bs = bsm[buf];
-    const float* Us = usm[buf];
 #pragma unroll
-    for (int kk = 0; kk < kKc; kk += 8) {
-      const int rb = warp * 16 + g;
-      uint32_t ah[4], al[4];
-      split(Bs[rb * kSK + kk + tq], ah[0], al[0]);
-      split(Bs[(rb + 8) * kSK + kk + tq], ah[1], al[1]);
-      split(Bs[rb * kSK + kk + tq + 4], ah[2], al[2]);
-      split(Bs[(rb + 8) * kSK + kk + tq + 4], ah[3], al[3]);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        uint32_t bh0, bl0, bh1, bl1;
-        split(Us[(kk + tq) * kSR + nt * 8 + g], bh0, bl0);
-        split(Us[(kk + tq + 4) * kSR + nt * 8 + g], bh1, bl1);
-        mma3(acc[nt], ah, al, bh0, bh1, bl0, bl1);
-      }
-    }
-    __syncthreads();
+  for (int s0 = 0; s0 < kApplyStages - 1; ++s0) {
+    if (s0 < nchunks) load(s0, s0 * kKc);
+    cp_commit();
   }
+  // ldmatrix row addresses: matrix q = lane / 8 covers rows 8 (q & 1) .. + 7 of the warp's
+  // 16 rows and columns 8 (q >> 1) .. + 7 of the 16-column k step
+  const int q = lane >> 3, j = lane & 7;
+  const int lrow = warp * 16 + 8 * (q & 1) + j, lcol = 8 * (q >> 1);
+  for (int c = 0; c < nchunks; ++c) {
+    cp_wait<kApplyStages - 2>();
+    __syncthreads();  // chunk c has landed; every warp is done with chunk c - 1's stage
+    if (c + kApplyStages - 1 < nchunks)
+      load((c + kApplyStages - 1) % kApplyStages, (c + kApplyStages - 1) * kKc);
+    cp_commit();
+    const uint8_t* st = smb + (c % kApplyStages) * kZStageBytes;
+    const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(st);
+    const __nv_bfloat16* Us = reinterpret_cast<const __nv_bfloat16*>(st + kTile * kZRowB * 2);
+#pragma unroll
+    for (int kk = 0; kk < kKc; kk += 16) {
+      uint32_t a[4];
+      ldsm_x4(a, Bs + lrow * kZRowB + kk + lcol);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int part = 2; part >= 0; --part) {
+          // B operand B'[k][n] = u[kk + k][nt 8 + n]: consecutive k of column n are adjacent
+          const __nv_bfloat16* ub = Us + (part * 16 + nt * 8 + g) * kZURow + kk + 2 * tq;
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(ub);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(ub + 8);
+          mma_bf16(acc[nt], a, b0, b1);
+        }
+    }
+  }
+  cp_wait<0>();
   // epilogue: this lane holds rows g, g + 8 of the warp's 16 and columns nt 8 + 2 tq (+1)
   dfloat d[2][2];
 #pragma unroll
@@ -503,14 +580,14 @@ __global__ void __launch_bounds__(256) k_apply_z_tc(const float* __restrict__ B,
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int c = nt * 8 + 2 * tq + q;
+      for (int q2 = 0; q2 < 2; ++q2) {
+        const int c = nt * 8 + 2 * tq + q2;
         if (r < n && c < kc) {
           const int64_t e = r * k + c_off + c;
           const float rv = __fadd_rn(rh[e], rl[e]);
-          const float zz = (rv - acc[nt][2 * h + q]) * inv_tau;
+          const float zz = (rv - acc[nt][2 * h + q2]) * inv_tau;
           z[e] = zz;
-          d[nt][q] = df_add(d[nt][q], df_two_prod(rv, zz));
+          d[nt][q2] = df_add(d[nt][q2], df_two_prod(rv, zz));
         }
       }
   }
@@ -518,12 +595,12 @@ __global__ void __launch_bounds__(256) k_apply_z_tc(const float* __restrict__ B,
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      double v = df_to_double(d[nt][q]);
+    for (int q2 = 0; q2 < 2; ++q2) {
+      double v = df_to_double(d[nt][q2]);
       v += __shfl_xor_sync(0xffffffffu, v, 4);
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (g == 0) red[warp][nt * 8 + 2 * tq + q] = v;
+      if (g == 0) red[warp][nt * 8 + 2 * tq + q2] = v;
     }
   __syncthreads();
   if (threadIdx.x < 16 && (int)threadIdx.x < kc) {
@@ -817,8 +894,17 @@ __global__ void k_init_unit(double* __restrict__ v, int l) {
   if (j < l) v[j] = 1.0 / sqrt((double)l) * (1.0 + 0.25 * sin(0.7 * j));
 }
 
-// out[i][j] = (float)A[i][j] for i, j < l, 0 elsewhere in [ld][ld]; optionally + d on the
-// diagonal of the fp64 copy first (A stays unchanged).
+// Round a panel to bf16 in place (the fp32 copy then holds the bf16 values exactly) and
+// write the bf16 copy.
+__global__ void k_round_bf16(float* __restrict__ P, int64_t count, __nv_bfloat16* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const __nv_bfloat16 b = __float2bfloat16_rn(P[e]);
+  out[e] = b;
+  P[e] = __bfloat162float(b);
+}
+
+// out[i][j] = (float)A[i][j] for i, j < l, 0 elsewhere in [ld][ld].
 __global__ void k_to_f32_pad(const double* __restrict__ A, int lda, int l, int ld,
                              float* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -931,6 +1017,12 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
       PC_CHECK(cudaFuncSetAttribute(k_panel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     4 * kTile * kSK * (int)sizeof(float)),
                "k_panel_tc smem");
+      PC_CHECK(cudaFuncSetAttribute(k_bt_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kApplyStages * kBtStageBytes),
+               "k_bt_bf16 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_apply_z_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kApplyStages * kZStageBytes),
+               "k_apply_z_bf16 smem");
       attrs[dev].store(true);
     }
   }
@@ -940,7 +1032,8 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   double *G = nullptr, *G0 = nullptr, *Xi = nullptr, *M = nullptr, *pv = nullptr, *py = nullptr,
          *prq = nullptr;
   int* status = nullptr;
-  PC_CHECK(keep((void**)&B, panel), "alloc preconditioner B");
+  PC_CHECK(keep((void**)&B, (size_t)n * ld * sizeof(__nv_bfloat16)),
+           "alloc preconditioner B");
   PC_CHECK(temp((void**)&P1, panel), "alloc preconditioner panel");
   PC_CHECK(temp((void**)&P2, panel), "alloc preconditioner panel");
   PC_CHECK(temp((void**)&Vc, (size_t)n * kSketchCols * sizeof(float)), "alloc sketch chunk");
@@ -964,13 +1057,20 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   PC_CHECK(temp((void**)&prq, sizeof(double)), "alloc power vectors");
   PC_CHECK(temp((void**)&status, sizeof(int)), "alloc status");
   // per-iteration buffers
-  bt_splits = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * 152, ntile),
-                                                          ceil_div(n, kKc)));
+  // B^T r: one wave of the blocks the device keeps resident (i tiles x row splits)
+  int bt_per_sm = 0, sms = 0, dev_now = 0;
+  PC_CHECK(cudaGetDevice(&dev_now), "cudaGetDevice");
+  PC_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_now), "SM count");
+  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &bt_per_sm, k_bt_bf16, 256, kApplyStages * kBtStageBytes),
+           "occupancy");
+  bt_splits = (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::max(1, bt_per_sm) * (int64_t)sms / ntile, ceil_div(n, kKc)));
   bt_rows = ceil_div(ceil_div(n, bt_splits), kKc) * kKc;
   bt_splits = (int)ceil_div(n, bt_rows);
   PC_CHECK(keep((void**)&tpart, (size_t)bt_splits * ld * 16 * sizeof(float)), "alloc B^T r");
   PC_CHECK(keep((void**)&tvec, (size_t)ld * 16 * sizeof(float)), "alloc t");
-  PC_CHECK(keep((void**)&u, (size_t)ld * 16 * sizeof(float)), "alloc u");
+  PC_CHECK(keep((void**)&u, (size_t)3 * 16 * ld * sizeof(__nv_bfloat16)), "alloc u");
   PC_CHECK(keep((void**)&Minv, ll * sizeof(float)), "alloc Minv");
   sgp_status s = ensure_lattice_values(L, kSketchCols, st);
   if (s != SGP_OK) return s;
@@ -1051,12 +1151,16 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     if ((s = robust_chol(G0, G, 1e-6, good)) != SGP_OK) return s;
     if (!good) return SGP_OK;
     PC_CHECK(dn.trtri(G, Xi), "triangular inverse");
-    panel_times(Y, Xi, B);
+    // the factor in fp32 in Q's panel (Q is no longer needed), then rounded to bf16: the
+    // stored values define P, and B^T B below is formed from them
+    panel_times(Y, Xi, Q);
+    k_round_bf16<<<g_panel, 256, 0, st>>>(Q, (int64_t)n * ld, static_cast<__nv_bfloat16*>(B));
+    note_launches(1);
   }
   // 3. G = B^T B; lambda_min(G) by power iteration on G^-1; tau = lambda_min + noise
   double lam_min = 0.0;
   {
-    gram(B, B, G0);
+    gram(Q, Q, G0);
     bool good = false;
     if ((s = robust_chol(G0, G, 1e-9, good)) != SGP_OK) return s;
     if (!good) return SGP_OK;
@@ -1107,14 +1211,16 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
     // B^T r and z kernels are bracketed for the stage timings
     const bool mark = ev && c_off == 0;
     if (mark) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-    k_bt_tc<<<dim3(ntile, bt_splits), 256, 0, st>>>(B, ld, rh, rl, k, c_off, kc, n, bt_rows,
-                                                    tpart);
+    k_bt_bf16<<<dim3(ntile, bt_splits), 256, kApplyStages * kBtStageBytes, st>>>(
+        static_cast<const __nv_bfloat16*>(B), ld, rh, rl, k, c_off, kc, n, bt_rows, tpart);
     if (mark) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     k_sum_t<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(tpart, bt_splits, ld, tvec);
-    k_minv_u<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(Minv, ld, tvec, u);
+    k_minv_u<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(
+        Minv, ld, tvec, static_cast<__nv_bfloat16*>(u));
     if (mark) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    k_apply_z_tc<<<(unsigned)ceil_div(n, kTile), 256, 0, st>>>(B, ld, u, rh, rl, k, c_off, kc, n,
-                                                              1.f / tau, z, dot);
+    k_apply_z_bf16<<<(unsigned)ceil_div(n, kTile), 256, kApplyStages * kZStageBytes, st>>>(
+        static_cast<const __nv_bfloat16*>(B), ld, static_cast<const __nv_bfloat16*>(u), rh, rl,
+        k, c_off, kc, n, 1.f / tau, z, dot);
     if (mark) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     note_launches(4);
   }

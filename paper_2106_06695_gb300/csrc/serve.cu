@@ -61,6 +61,7 @@ constexpr int kRingBytes = 192 * 1024;  // shared memory of the chunk ring
 constexpr int kRingRowsMax = 96;    // rows of one chunk at most
 constexpr int kRingGrid = 152;      // persistent grid of the ring kernels (one block per SM)
 constexpr int kSpinLimit = 1 << 20; // bounded mbarrier waits (about a second at most)
+constexpr double kBf16MaxKappa = 100.0;  // BF16 server: larger condition estimates use fp32
 constexpr uint64_t kPrecondSeedXor = 0x6A09E667F3BCC909ull;  // sketch seed = seed ^ this
 
 enum { U_SPLAT = 0, U_MED, U_HUGE, U_BLUR, U_VEC, U_VERT, U_BT, U_BTS, U_BTT, U_MINV, U_Z,
@@ -1225,6 +1226,7 @@ struct Request {
 
 struct Lane {
   int key = 0;
+  int value_dtype = 0;  // SGP_VALUES_* of every request in the lane
   cudaStream_t st = nullptr;
   Table* dtab = nullptr;
   int* dflags = nullptr;
@@ -1370,15 +1372,16 @@ void unit_counts(const sgp_server* S, const Request* R, int64_t (&vb)[U_KINDS]) 
   vb[U_Z] = R->l ? ceil_div(L->n, kZVbRows) : 0;
 }
 
-// Lane of a built request: dimension class (D <= 4, 8, ..., 128) and work class (blur,
-// slice and preconditioner volume per iteration, classes a factor 8 apart).
+// Lane of a built request: dimension class (D <= 4, 8, ..., 128), work class (blur,
+// slice and preconditioner volume per iteration, classes a factor 8 apart) and the value
+// type of its lattice (a BF16 server keeps fp32 values for ill-conditioned requests).
 int lane_key(const sgp_server* S, const Request* R) {
   const Lattice* L = R->L;
   int dclass = 0;
   while ((4 << dclass) < L->D) ++dclass;
   const double work = ((double)L->m + (double)L->n) * L->D * S->kp + 2.0 * L->n * R->ld;
   const int wclass = std::max(0, (int)std::floor(std::log(std::max(work, 1.0)) / std::log(8.0)));
-  return dclass * 64 + std::min(wclass, 63);
+  return (L->value_dtype == SGP_VALUES_BF16 ? 1 << 16 : 0) + dclass * 64 + std::min(wclass, 63);
 }
 
 void release(sgp_server* S, Request* R, cudaStream_t st) {
@@ -1495,10 +1498,11 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   k_rhs<<<g, 256, 0, st>>>(L->perm, yd, KZ, n_all, in.n, kp, S->S, R->xh, R->xl, R->rh, R->rl,
                            R->p);
   note_launches(1);
-  // App. A preconditioner, for requests whose condition estimate (Gershgorin: largest
-  // training-row sum of outputscale K~ over noise) reaches precond_min_kappa
+  // Condition estimate (Gershgorin: largest training-row sum of outputscale K~ over
+  // noise), for the App. A preconditioner and for the BF16 value gate
   size_t pre_bytes = 0;
-  if (S->o.precond_rank > 0) {
+  const bool bf16 = L->value_dtype == SGP_VALUES_BF16;
+  if (S->o.precond_rank > 0 || bf16) {
     int* rowmax_d = nullptr;
     SRV_CHECK(tmp.get((void**)&rowmax_d, sizeof(int)), "alloc row sum");
     SRV_CHECK(cudaMemsetAsync(rowmax_d, 0, sizeof(int), st), "clear row sum");
@@ -1511,6 +1515,23 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
     float rowmax = 0.f;
     std::memcpy(&rowmax, &rowmax_bits, sizeof(float));
     R->kappa = ((double)rowmax + (double)in.noise) / (double)in.noise;
+  }
+  if (bf16 && R->kappa > kBf16MaxKappa) {
+    // the bf16 operator error (~2^-8 per product) amplified by this conditioning would
+    // exceed the solver's tolerance: fp32 values on the same lattice, and the probe
+    // product and right-hand sides again
+    L->value_dtype = SGP_VALUES_F32;
+    L->lat_elems = 0;      // reallocate the value buffers at the fp32 size,
+    L->act_tmp_elems = 0;  // and a sparse lattice's pass buffer
+    s = ensure_lattice_values(L, kp, st);
+    if (s != SGP_OK) return s;
+    enqueue_mvm(L, Vz, kp, SGP_BLUR_SYMMETRIC, L->outputscale, 0.f, KZ, st);
+    k_rhs<<<g, 256, 0, st>>>(L->perm, yd, KZ, n_all, in.n, kp, S->S, R->xh, R->xl, R->rh,
+                             R->rl, R->p);
+    note_launches(1);
+  }
+  R->st.value_dtype = L->value_dtype;
+  if (S->o.precond_rank > 0) {
     if (R->kappa >= S->o.precond_min_kappa) {
       const int l = (int)std::min<long long>(S->o.precond_rank, in.n);
       const int ld = (l + 3) / 4 * 4;
@@ -1728,7 +1749,7 @@ sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, bool 
     return SGP_OK;
   }
   SRV_CHECK(cudaStreamBeginCapture(ln->st, cudaStreamCaptureModeThreadLocal), "begin capture");
-  const int kernels = S->o.value_dtype == SGP_VALUES_BF16
+  const int kernels = ln->value_dtype == SGP_VALUES_BF16
                           ? enqueue_iteration_s<bf16>(S, ln, dmax, sparse, pre)
                           : enqueue_iteration_s<float>(S, ln, dmax, sparse, pre);
   cudaGraph_t g = nullptr;
@@ -1744,7 +1765,7 @@ sgp_status graph_for(const sgp_server* S, Lane* ln, int dmax, bool sparse, bool 
   return SGP_OK;
 }
 
-sgp_status lane_for(sgp_server* S, int key, Lane** out) {
+sgp_status lane_for(sgp_server* S, int key, int value_dtype, Lane** out) {
   auto it = S->lanes.find(key);
   if (it != S->lanes.end()) {
     *out = it->second.get();
@@ -1752,6 +1773,7 @@ sgp_status lane_for(sgp_server* S, int key, Lane** out) {
   }
   auto ln = std::make_unique<Lane>();
   ln->key = key;
+  ln->value_dtype = value_dtype;
   ln->htab = std::make_unique<Table>();
   SRV_CHECK(cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking), "lane stream");
   SRV_CHECK(cudaMalloc((void**)&ln->dtab, sizeof(Table)), "alloc lane table");
@@ -1820,7 +1842,7 @@ sgp_status collect_setups(sgp_server* S, int* done) {
     sgp_status s = rs.second;
     S->in_use -= R->bound;  // the reservation made at admission
     Lane* ln = nullptr;
-    if (s == SGP_OK) s = lane_for(S, lane_key(S, R), &ln);
+    if (s == SGP_OK) s = lane_for(S, lane_key(S, R), R->L->value_dtype, &ln);
     if (s != SGP_OK) {
       if (!R->setup_error.empty()) set_error("request set-up: " + R->setup_error);
       R->st.status = s;
@@ -2143,8 +2165,10 @@ sgp_status sgp_server_submit(sgp_server* S, const sgp_request* req, long long* i
               "(n + ns)(d + 1) < 2^31");
     return SGP_ERR_INVALID_ARG;
   }
+  // a BF16 server may switch a request to fp32 values after its condition estimate:
+  // reserve the fp32 bound
   const unsigned long long bound =
-      sgp_request_bytes_bound(r.n + r.ns, r.d, S->o.order_r, S->kp, S->o.value_dtype,
+      sgp_request_bytes_bound(r.n + r.ns, r.d, S->o.order_r, S->kp, SGP_VALUES_F32,
                               S->o.precond_rank);
   if (bound > S->o.hbm_budget) {
     set_error("sgp_server_submit: the request's memory bound exceeds the server's budget");

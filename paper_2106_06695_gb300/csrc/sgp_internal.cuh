@@ -206,11 +206,13 @@ struct ShiftedNystrom {
   int64_t n = 0;
   float tau = 0.f;
   bool ok = false;
-  float* B = nullptr;      // [n][ld] fp32, locality order, padding columns zero
-  float* Minv = nullptr;   // [ld][ld] fp32 (tau I + B^T B)^-1, zero padded
+  // [n][ld] bf16 (the factor rounded to bf16; P is defined by these values), locality
+  // order, padding columns zero
+  void* B = nullptr;
+  float* Minv = nullptr;   // [ld][ld] fp32 (tau I + B^T B)^-1 of the stored B, zero padded
   float* tpart = nullptr;  // [bt_splits][ld][16] B^T r partials
   float* tvec = nullptr;   // [ld][16]
-  float* u = nullptr;      // [ld][16]
+  void* u = nullptr;       // [3][16][ld] bf16: Minv B^T r split in three bf16 parts
   int bt_splits = 0;
   int64_t bt_rows = 0;
   std::vector<void*> ptrs;

@@ -178,24 +178,35 @@ def test_admission_respects_the_memory_budget():
             assert np.array_equal(m0, m1) and np.array_equal(v0, v1)
 
 
-def test_bf16_values_error_against_fp32():
-    """BF16 lattice values (fp32 sums) in every product of the solve: the error is stated,
-    not small -- CG amplifies the ~3e-3 per-product storage error by the system's
-    conditioning (noise 0.01): about 2e-3..7e-3 on these requests, 0.16 on an
-    ill-conditioned d = 3 one."""
-    reqs = small_requests(3, seed=31)
-    outs = {}
+def test_bf16_values_are_gated_on_the_condition_estimate():
+    """A BF16 server keeps bf16 lattice values (fp32 sums) only for requests whose
+    condition estimate is at most 100: CG amplifies the ~3e-3 per-product storage error by
+    the system's conditioning, so worse-conditioned requests (low d, many points per
+    vertex) are solved with fp32 values on the same lattice and give the fp32 server's
+    results bitwise; the well-conditioned ones (high d, isolated points) stay bf16 with a
+    stated error of a few 1e-3."""
+    reqs = small_requests(6, seed=31, dims=(3, 50, 90))
+    outs, dts, kap = {}, None, None
     for dt in ("f32", "bf16"):
-        with Server(max_active=3, value_dtype=dt) as srv:
+        with Server(max_active=6, value_dtype=dt) as srv:
             ids = submit_all(srv, reqs)
             srv.run_until_idle()
             outs[dt] = results(srv, ids)
-    for (m32, v32, _), (m16, v16, _) in zip(outs["f32"], outs["bf16"]):
-        err = np.linalg.norm(m16 - m32) / np.linalg.norm(m32)
-        print("bf16 lattice values: mean rel L2 %.2e, var max abs %.2e"
-              % (err, np.abs(v16 - v32).max()))
+            if dt == "bf16":
+                dts = [srv.stats(i)["value_dtype"] for i in ids]
+                kap = [srv.stats(i)["kappa_est"] for i in ids]
+    assert 0 in dts and 1 in dts, (dts, kap)
+    for (m32, v32, _), (m16, v16, _), dt, k in zip(outs["f32"], outs["bf16"], dts, kap):
+        # isolated test points (high d) can have a zero posterior mean
+        err = np.linalg.norm(m16 - m32) / max(np.linalg.norm(m32), 1e-6)
+        print("kappa %.3g, %s values: mean rel L2 %.2e, var max abs %.2e"
+              % (k, "bf16" if dt else "fp32", err, np.abs(v16 - v32).max()))
+        assert dt == (1 if k <= 100.0 else 0)
         assert np.isfinite(m16).all() and np.isfinite(v16).all()
-        assert err <= 0.3
+        if dt == 0:
+            assert np.array_equal(m16, m32) and np.array_equal(v16, v32)
+        else:
+            assert err <= 2e-2
 
 
 def test_every_request_stops_at_tol_or_max_iter_in_fresh_lanes():
