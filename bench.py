@@ -61,8 +61,9 @@ WORKLOAD = dict(n=2_000_000, d=11, k=16, seed=4, lengthscale=1.0, noise=0.01, to
 C2 = dict(n=200_000, d=11, seed=2, probes=8, noise=0.01, tol=1e-3, max_iter=500,
           precond_rank=256, precond_power_iters=1)
 SERVING = dict(requests=256, rate_per_s=50.0, seed=5, max_active=16, test_points=256)
-CPU_SAMPLE = dict(n=100_000, iters=4)   # oracle sample for the cpu_baseline leg (each mode)
-REF_SAMPLE = dict(n=50_000, iters=2)    # oracle sample per step for --impl reference
+CPU_SAMPLE = dict(n=200_000, iters=100)  # oracle sample of the cpu_baseline leg, all cores
+CPU_SAMPLE_1T = dict(n=100_000, iters=4)  # the same on one thread (a smaller sample)
+REF_SAMPLE = dict(n=100_000, iters=20)   # oracle sample per step for --impl reference
 
 
 def parse_args(argv=None):
@@ -411,8 +412,8 @@ def run_ours(args, world, rank, local):
         "blur_pass": m * (8 * k + 8 * r_),
         "splat": 8 * n * D + 4 * n * k + 4 * m * k,
         "slice_dot": 8 * n * D + 4 * m * k + 8 * n * k,
-        "precond_bt": 4 * n * ld + 8 * n * min(k, 16),
-        "precond_z": 4 * n * ld + 12 * n * min(k, 16),
+        "precond_bt": 2 * n * ld + 8 * n * min(k, 16),   # bf16 B once, r = rh + rl once
+        "precond_z": 2 * n * ld + 12 * n * min(k, 16),   # bf16 B once, r read, z written
     }
     stage_ms = {  # average duration of one launch
         "blur_pass": prof["ms"] / max(prof["passes"], 1),
@@ -438,8 +439,8 @@ def run_ours(args, world, rank, local):
         dom = "blur_pass"
     names = {"blur_pass": "k_blur_rows<2,2,1,float> (one lattice direction)",
              "splat": "k_splat<4,float> (+ fix-ups)", "slice_dot": "k_slice_dot<4,float>",
-             "precond_bt": "k_bt_tc (preconditioner B^T r, mma.sync 3xTF32)",
-             "precond_z": "k_apply_z_tc (preconditioner z = (r - B u)/tau, mma.sync 3xTF32)"}
+             "precond_bt": "k_split_r + k_bt_tc (preconditioner B^T r, tcgen05 bf16, TMA)",
+             "precond_z": "k_z_tc (preconditioner z = (r - B u)/tau, tcgen05 bf16, TMA)"}
     ds = stages.get(dom, {})
     traffic = blur_traffic_per_launch(m, k) if dom == "blur_pass" else stage_traffic(dom)
     roofline = {"kernel": names[dom], "bound": "hbm",
@@ -807,15 +808,17 @@ def cpu_baseline(W):
     import oracle
 
     cores = oracle.max_threads()
-    secs1, units1, _ = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"], 1)
+    secs1, units1, _ = oracle_sample(W, CPU_SAMPLE_1T["n"], CPU_SAMPLE_1T["iters"], 1)
     secs, units, used = oracle_sample(W, CPU_SAMPLE["n"], CPU_SAMPLE["iters"], cores)
-    what = ("FP64 oracle: lattice build (vertex insertion sequential) + %d plain CG iterations "
-            "(symmetric operator, k=%d) on a seeded %d-row subsample of the workload"
-            % (CPU_SAMPLE["iters"], W["k"], CPU_SAMPLE["n"]))
+
+    def what(smp):
+        return ("FP64 oracle: lattice build (vertex insertion sequential) + %d plain CG "
+                "iterations (symmetric operator, k=%d) on a seeded %d-row subsample of the "
+                "workload" % (smp["iters"], W["k"], smp["n"]))
     return {"value": units / secs / 1e6, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": "%s, %d threads; %.1f s" % (what, used, secs),
+            "sample": "%s, %d threads; %.1f s" % (what(CPU_SAMPLE), used, secs),
             "single_thread": {"value": units1 / secs1 / 1e6, "unit": UNIT, "cores": 1,
-                              "sample": "%s, 1 thread; %.1f s" % (what, secs1)}}
+                              "sample": "%s, 1 thread; %.1f s" % (what(CPU_SAMPLE_1T), secs1)}}
 
 
 def run_reference(args, world, rank):

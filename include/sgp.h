@@ -227,9 +227,10 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
  *   tau    = lambda_min(B^T B) (inverse power iteration) + noise_var.
  * B is stored rounded to bf16 (P is defined by the stored values) and
  * P^-1 r = (r - B (tau I + B^T B)^-1 B^T r) / tau.  The l-column products with K run in
- * chunks of 128 columns; the tall n x l products on the tensor cores (3xTF32 in the set-up,
- * bf16 B with three-part bf16 r and u per iteration), the l x l factorizations in fp64.
- * Work space: about 10 n l + 8 n k bytes during the set-up, 2 n l kept for the solve.  When a Cholesky fails after its retries the solve runs
+ * chunks of 128 columns; the tall n x l products on the tensor cores (bf16 operands: the
+ * set-up's panels held as three bf16 parts, B exact with three-part r and u per
+ * iteration), the l x l factorizations in fp64.  Work space: about 14 n l + 1100 n bytes
+ * during the set-up, 2 n l + 96 n kept for the solve.  When a Cholesky fails after its retries the solve runs
  * unpreconditioned.  The stopping rule is unchanged (unpreconditioned residual
  * ||r_c|| / ||b_c||). */
 sgp_status sgp_cg_solve_ex(sgp_lattice* h, const float* B, int k, int blur, float noise_var,

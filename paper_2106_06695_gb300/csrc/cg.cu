@@ -529,6 +529,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   CG_CHECK(cudaMemcpyAsync(hit.data(), S.iters, k * sizeof(int), cudaMemcpyDeviceToHost, st),
            "read iterations");
   CG_CHECK(cudaStreamSynchronize(st), "sync CG");
+  if (use_pre && (s = cl.pre.check(st)) != SGP_OK) return s;
   if (iters) std::copy(hit.begin(), hit.begin() + kb, iters);
   if (rel_res) std::copy(hrel.begin(), hrel.begin() + kb, rel_res);
   if (S.hist) {  // [max_iter][k] on the device, the caller's [max_iter][kb] on the host

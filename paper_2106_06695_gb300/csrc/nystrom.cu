@@ -1,21 +1,24 @@
-// Rank-l preconditioner for the CG solve (App. A: CG pre-conditioner of rank 100).
+// Rank-l Nystrom factor of the training block of a GP request's operator (App. A: CG
+// pre-conditioner of rank 100), for the server's preconditioned CG.
 //
 // The lattice operator A = outputscale W M^T M W^T has no cheap entries or diagonal, so
 // the low-rank part is a randomized Nystrom approximation built from products with A
 // only:
-//   Omega  n x l Rademacher sketch, entry (i, j) = sign bit of SplitMix64(seed, i l + j)
-//          for the caller's point i (counter-based: anyone can regenerate it);
-//   Y      = A Omega + nu Omega                 (one l-column lattice MVM, small shift nu);
+//   Omega  n x l Rademacher sketch over the training rows, entry (i, j) = sign bit of
+//          SplitMix64(seed, i l + j) for the caller's point i (counter-based: anyone can
+//          regenerate it);
+//   Y      = A Omega + nu Omega                 (l-column lattice MVMs, small shift nu);
 //   C      = Omega^T Y = R R^T                  (Cholesky, l x l, fp64);
 //   B      = Y R^-T                             (so that B B^T = Y C^-1 Y^T);
 //   P      = B B^T + noise I,
-//   P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise       (Woodbury).
+//   P^-1 r = (r - B (noise I + B^T B)^-1 B^T r) / noise       (Woodbury; applied by the
+//          server's table-driven kernels).
 // P is symmetric positive definite for any computed B, so CG stays a CG whatever the
 // rounding in B; the Cholesky factors of the l x l matrices are computed in fp64 by one
 // block, the tall n x l products in fp32 with fixed-order partial sums (deterministic).
 // B is stored in fp32 with rows padded to a multiple of 4 columns (zeros) and B^T B is
 // formed from the stored values.  All row-indexed arrays are in the lattice's locality
-// order.
+// order.  (The library CG's large-rank preconditioner is precond.cu.)
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -30,7 +33,6 @@ namespace {
 
 constexpr int kRowsPerStage = 32;  // rows staged in shared memory per step
 constexpr int kTallBlocks = 2 * 152;
-constexpr int kApplyBlocks = 8 * 152;  // blocks of the per-iteration B^T r reduction
 
 // SplitMix64 (Steele, Lea & Flood 2014) at counter c: one +-1 per (point, column).
 __device__ __forceinline__ float rademacher(uint64_t seed, int64_t i, int j, int l) {
@@ -39,23 +41,6 @@ __device__ __forceinline__ float rademacher(uint64_t seed, int64_t i, int j, int
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
   z ^= z >> 31;
   return (z >> 63) ? -1.f : 1.f;
-}
-
-__global__ void k_fill_sketch(const int32_t* __restrict__ perm, int64_t n, int l, uint64_t seed,
-                              float* __restrict__ om) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * l) return;
-  const int64_t p = e / l;
-  om[e] = rademacher(seed, perm[p], (int)(e - p * l), l);
-}
-
-// Y += nu Omega (Omega regenerated).
-__global__ void k_shift(const int32_t* __restrict__ perm, int64_t n, int l, uint64_t seed,
-                        float nu, float* __restrict__ Y) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * l) return;
-  const int64_t p = e / l;
-  Y[e] = fmaf(nu, rademacher(seed, perm[p], (int)(e - p * l), l), Y[e]);
 }
 
 __device__ __forceinline__ float to_f(float x) { return x; }
@@ -177,93 +162,6 @@ __global__ void k_tri_inv_t(const double* __restrict__ R, int l, double* __restr
   for (int i = 0; i < l; ++i) T[c * l + i] = (float)x[i];  // T[c][i] = (R^-1)[i][c]
 }
 
-// Row by row: Bh[row] = Y[row] T (T in shared memory), columns l..ld-1 zero.
-__global__ void k_rows_times(const float* __restrict__ Y, const float* __restrict__ T, int64_t n,
-                             int l, int ld, float* __restrict__ Bh) {
-  extern __shared__ float sh[];
-  float* ts = sh;              // [l][l]
-  float* ys = sh + l * l;      // [rows_per_block][l]
-  const int rows = blockDim.x / l;  // blockDim.x = rows * l
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) ts[e] = T[e];
-  const int rr = threadIdx.x / l, c = threadIdx.x - rr * l;
-  for (int64_t base = (int64_t)blockIdx.x * rows; base < n; base += (int64_t)gridDim.x * rows) {
-    __syncthreads();
-    const int64_t row = base + rr;
-    if (rr < rows && row < n) ys[rr * l + c] = Y[row * l + c];
-    __syncthreads();
-    if (rr < rows && row < n) {
-      float a = 0.f;
-      for (int j = 0; j < l; ++j) a = fmaf(ys[rr * l + j], ts[j * l + c], a);
-      Bh[row * ld + c] = a;
-      if (c < ld - l) Bh[row * ld + l + c] = 0.f;
-    }
-  }
-}
-
-// Per-block partial of B^T r for the columns [c_off, c_off + 16) of r = rh + rl (ld x 16
-// outputs, padded rows of B are zero).  Each warp takes a contiguous range of rows; lane
-// `lane` owns the B columns lane, lane + 32, lane + 64, lane + 96 against all 16 r columns
-// (64 accumulators), reading its row of B coalesced; lane c < 16 loads r[row][c_off + c]
-// and shuffles it to the others.  The block's warps are combined in shared memory in a
-// fixed order.
-constexpr int kBtWarps = 8;
-constexpr int kBtRows = 2;
-__global__ void __launch_bounds__(kBtWarps * 32, 2) k_bt_r(const float* __restrict__ Bh, int ld,
-                                                        const float* __restrict__ rh,
-                                                        const float* __restrict__ rl, int64_t n,
-                                                        int k, int c_off,
-                                                        double* __restrict__ partial) {
-  extern __shared__ float red[];  // [kBtWarps][ld][16]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kc = min(16, k - c_off);
-  float acc[4][16];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
-  const int64_t per_warp = ceil_div(n, (int64_t)gridDim.x * kBtWarps);
-  const int64_t r0 = ((int64_t)blockIdx.x * kBtWarps + warp) * per_warp;
-  const int64_t r1 = std::min<int64_t>(n, r0 + per_warp);
-  // kBtRows rows per step: their loads are issued before any of their FMAs
-  for (int64_t row0 = r0; row0 < r1; row0 += kBtRows) {
-    float b[kBtRows][4], rv[kBtRows];
-#pragma unroll
-    for (int q = 0; q < kBtRows; ++q) {
-      const int64_t row = row0 + q;
-      const bool in = row < r1;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int j = lane + 32 * a;
-        b[q][a] = (in && j < ld) ? Bh[row * ld + j] : 0.f;
-      }
-      const int64_t e = row * k + c_off + lane;
-      rv[q] = (in && lane < kc) ? __fadd_rn(rh[e], rl[e]) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < kBtRows; ++q)
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const float rc = __shfl_sync(0xffffffffu, rv[q], c);  // r[row][c_off + c]
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][c] = fmaf(b[q][a], rc, acc[a][c]);
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int j = lane + 32 * a;
-    if (j < ld)
-#pragma unroll
-      for (int c = 0; c < 16; ++c) red[(warp * ld + j) * 16 + c] = acc[a][c];
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < ld * kc; o += blockDim.x) {
-    const int j = o / kc, c = o - j * kc;
-    double sum = 0.0;
-    for (int w = 0; w < kBtWarps; ++w) sum += (double)red[(w * ld + j) * 16 + c];
-    partial[(int64_t)blockIdx.x * ld * k + (int64_t)j * k + c_off + c] = sum;
-  }
-}
-
 // Minv = (Q Q^T)^-1 for lower-triangular Q (fp64): W = Q^-1 by forward substitution per
 // column (thread c), then Minv = W^T W.  `work` holds W ([l][l]).
 __global__ void k_inv_from_cholesky(const double* __restrict__ Q, int l, double* __restrict__ W,
@@ -281,83 +179,6 @@ __global__ void k_inv_from_cholesky(const double* __restrict__ Q, int l, double*
     double s = 0.0;
     for (int i = max(a, b); i < l; ++i) s += W[i * l + a] * W[i * l + b];
     Minv[e] = s;
-  }
-}
-
-// u = Minv t (fp64, one output per thread), written as fp32 [ld][k] (rows >= l stay 0).
-__global__ void k_minv_t(const double* __restrict__ Minv, const double* __restrict__ t, int l,
-                         int k, float* __restrict__ u) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= l * k) return;
-  const int i = o / k, c = o - i * k;
-  double s = 0.0;
-  for (int j = 0; j < l; ++j) s += Minv[i * l + j] * t[j * k + c];
-  u[i * k + c] = (float)s;
-}
-
-// z = (r - B u) / noise for the columns [c_off, c_off + 16) and per-block column sums of
-// r z.  One thread per row: it streams its row of B as float4 and reads u ([ld][16] of the
-// chunk, in shared memory) as broadcasts, 64 FMAs per float4 of B.
-constexpr int kZThreads = 256;
-__global__ void __launch_bounds__(kZThreads) k_apply_z(const float* __restrict__ Bh, int ld,
-                                                       const float* __restrict__ u,
-                                                       const float* __restrict__ rh,
-                                                       const float* __restrict__ rl,
-                                                       float inv_noise, int64_t n, int k,
-                                                       int c_off, float* __restrict__ z,
-                                                       double* __restrict__ partial) {
-  extern __shared__ float sh[];
-  float* us = sh;                                         // [ld][16]
-  double* red = reinterpret_cast<double*>(sh + ld * 16);  // [kZThreads][16]
-  const int kc = min(16, k - c_off);
-  for (int e = threadIdx.x; e < ld * 16; e += blockDim.x) {
-    const int q = e / 16, c = e % 16;
-    us[e] = c < kc ? u[q * k + c_off + c] : 0.f;
-  }
-  __syncthreads();
-  dfloat acc[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = {0.f, 0.f};
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    float s[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) s[c] = 0.f;
-    const float4* b4 = reinterpret_cast<const float4*>(Bh + row * ld);
-    for (int q4 = 0; q4 < ld / 4; ++q4) {
-      const float4 b = b4[q4];
-      const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float4* u4 = reinterpret_cast<const float4*>(us + (q4 * 4 + a) * 16);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const float4 uu = u4[g];
-          s[4 * g + 0] = fmaf(bv[a], uu.x, s[4 * g + 0]);
-          s[4 * g + 1] = fmaf(bv[a], uu.y, s[4 * g + 1]);
-          s[4 * g + 2] = fmaf(bv[a], uu.z, s[4 * g + 2]);
-          s[4 * g + 3] = fmaf(bv[a], uu.w, s[4 * g + 3]);
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      if (c < kc) {
-        const int64_t e = row * k + c_off + c;
-        const float r = __fadd_rn(rh[e], rl[e]);
-        const float zz = (r - s[c]) * inv_noise;
-        z[e] = zz;
-        acc[c] = df_add(acc[c], df_two_prod(r, zz));
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 16; ++c) red[threadIdx.x * 16 + c] = df_to_double(acc[c]);
-  __syncthreads();
-  for (int c = threadIdx.x; c < kc; c += blockDim.x) {
-    double t = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) t += red[i * 16 + c];
-    partial[(int64_t)blockIdx.x * k + c_off + c] = t;
   }
 }
 
@@ -414,113 +235,6 @@ __global__ void k_rows_times_inplace(float* Y, const float* __restrict__ T, int6
 }
 
 }  // namespace
-
-sgp_status Nystrom::build(Lattice* L, int rank, uint64_t seed, float noise, int blur,
-                          cudaStream_t st) {
-  const int64_t n = L->n;
-  l = rank;
-  ld = (rank + 3) / 4 * 4;
-  this->noise = noise;
-  this->n = n;
-#define NY_CHECK(expr, what)                                  \
-  do {                                                        \
-    cudaError_t e_ = (expr);                                  \
-    if (e_ != cudaSuccess) return cuda_status(e_, what);      \
-  } while (0)
-  auto get = [&](void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
-    if (e == cudaSuccess) ptrs.push_back(*p);
-    return e;
-  };
-  {  // shared-memory sizes beyond the 48 KB default, once per device
-    static std::atomic<bool> attrs[64];  // several host threads may arrive here at once
-    int dev = 0;
-    NY_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
-    if (dev >= 0 && dev < 64 && !attrs[dev].load()) {
-      const int big = 200 * 1024;
-      cudaFuncSetAttribute(k_gram<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      cudaFuncSetAttribute(k_gram<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      cudaFuncSetAttribute(k_rows_times, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      cudaFuncSetAttribute(k_bt_r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      cudaFuncSetAttribute(k_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-      attrs[dev].store(true);
-    }
-  }
-  float* Y = nullptr;
-  float* om = nullptr;
-  NY_CHECK(get((void**)&Bh, (size_t)n * ld * sizeof(float)), "alloc Nystrom B");
-  NY_CHECK(cudaMallocAsync((void**)&Y, (size_t)n * l * sizeof(float), st), "alloc Nystrom Y");
-  NY_CHECK(cudaMallocAsync((void**)&om, (size_t)n * l * sizeof(float), st), "alloc sketch");
-  NY_CHECK(get((void**)&partial,
-               std::max((size_t)kTallBlocks * l * l, (size_t)kApplyBlocks * ld * kMaxK) *
-                   sizeof(double)),
-           "alloc partial");
-  NY_CHECK(get((void**)&C, (size_t)l * l * sizeof(double)), "alloc C");
-  NY_CHECK(get((void**)&Q, (size_t)l * l * sizeof(double)), "alloc Q");
-  NY_CHECK(get((void**)&Minv, (size_t)l * l * sizeof(double)), "alloc Minv");
-  NY_CHECK(get((void**)&T, (size_t)l * l * sizeof(float)), "alloc T");
-  NY_CHECK(get((void**)&work, (size_t)std::max(l, kMaxK) * l * sizeof(double)), "alloc work");
-  NY_CHECK(get((void**)&tvec, (size_t)ld * kMaxK * sizeof(double)), "alloc t");
-  NY_CHECK(get((void**)&u, (size_t)ld * kMaxK * sizeof(float)), "alloc u");
-  NY_CHECK(get((void**)&status, sizeof(int)), "alloc status");
-  NY_CHECK(cudaMemsetAsync(status, 0, sizeof(int), st), "clear status");
-  NY_CHECK(cudaMemsetAsync(u, 0, (size_t)ld * kMaxK * sizeof(float), st), "clear u");
-
-  // Y = A Omega (one l-column product in locality order), then Y += nu Omega
-  sgp_status s = ensure_lattice_values(L, l, st);
-  if (s != SGP_OK) return s;
-  const unsigned g1 = (unsigned)ceil_div(n * l, 256);
-  k_fill_sketch<<<g1, 256, 0, st>>>(L->perm, n, l, seed, om);
-  enqueue_mvm(L, om, l, blur, L->outputscale, 0.f, Y, st, nullptr, /*internal=*/true);
-  NY_CHECK(cudaFreeAsync(om, st), "free sketch");
-  // nu: a small shift keeps C positive definite when A Omega is rank deficient
-  const float nu = 1e-3f * noise;
-  k_shift<<<g1, 256, 0, st>>>(L->perm, n, l, seed, nu, Y);
-  note_launches(2);
-  // C = Omega^T Y, Cholesky C = R R^T
-  const size_t gram_smem = 2 * (size_t)kRowsPerStage * l * sizeof(float);
-  k_gram<true, float><<<kTallBlocks, 256, gram_smem, st>>>(Y, l, L->perm, n, l, seed, partial);
-  k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, C);
-  k_cholesky<<<1, 1024, 0, st>>>(C, l, 0.0, 0.0, status);
-  // B = Y R^-T
-  k_tri_inv_t<<<1, 128, 0, st>>>(C, l, work, T);
-  const int rows = std::max(1, 1024 / l);
-  const size_t rt_smem = ((size_t)l * l + (size_t)rows * l) * sizeof(float);
-  k_rows_times<<<kTallBlocks, rows * l, rt_smem, st>>>(Y, T, n, l, ld, (float*)Bh);
-  NY_CHECK(cudaFreeAsync(Y, st), "free Nystrom Y");
-  // M = noise I + B^T B from the stored B, Cholesky M = Q Q^T
-  k_gram<false, float><<<kTallBlocks, 256, gram_smem, st>>>((const float*)Bh, ld, L->perm, n, l,
-                                                            seed, partial);
-  k_sum_blocks<<<(unsigned)ceil_div(l * l, 256), 256, 0, st>>>(partial, kTallBlocks, l * l, Q);
-  k_cholesky<<<1, 1024, 0, st>>>(Q, l, (double)noise, 0.0, status);
-  k_inv_from_cholesky<<<1, 128, 0, st>>>(Q, l, work, Minv);
-  note_launches(9);
-  NY_CHECK(cudaGetLastError(), "building the Nystrom preconditioner");
-  int hs = 0;
-  NY_CHECK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
-  NY_CHECK(cudaStreamSynchronize(st), "sync Nystrom");
-  ok = hs == 0;
-  return SGP_OK;
-#undef NY_CHECK
-}
-
-void Nystrom::apply(const float* rh, const float* rl, int k, float* z, double* dot_partial,
-                    int64_t dot_blocks, int block_threads, cudaStream_t st) const {
-  (void)block_threads;
-  const size_t bt_smem = (size_t)kBtWarps * ld * 16 * sizeof(float);
-  for (int c_off = 0; c_off < k; c_off += 16)
-    k_bt_r<<<kApplyBlocks, kBtWarps * 32, bt_smem, st>>>((const float*)Bh, ld, rh, rl, n, k, c_off,
-                                                         partial);
-  k_sum_blocks<<<(unsigned)ceil_div((int64_t)ld * k, 256), 256, 0, st>>>(partial, kApplyBlocks,
-                                                                       ld * k, tvec);
-  k_minv_t<<<(unsigned)ceil_div((int64_t)l * k, 128), 128, 0, st>>>(Minv, tvec, l, k, u);
-  const size_t z_smem = (size_t)ld * 16 * sizeof(float) + (size_t)kZThreads * 16 * sizeof(double);
-  for (int c_off = 0; c_off < k; c_off += 16)
-    k_apply_z<<<(unsigned)dot_blocks, kZThreads, z_smem, st>>>((const float*)Bh, ld, u, rh, rl,
-                                                               1.f / noise, n, k, c_off, z,
-                                                               dot_partial);
-  note_launches(2 + 2 * ceil_div(k, 16));
-}
 
 // Blocks of the masked build's tall products: one per 1024 rows, at most kTallBlocks.
 static int masked_tall_blocks(int64_t n) {
@@ -591,11 +305,6 @@ sgp_status nystrom_build_masked(Lattice* L, int64_t n_train, int l, int ld, uint
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "building the masked Nystrom factor");
   return SGP_OK;
-}
-
-void Nystrom::release(cudaStream_t st) {
-  for (void* p : ptrs) (void)cudaFreeAsync(p, st);
-  ptrs.clear();
 }
 
 }  // namespace sgp

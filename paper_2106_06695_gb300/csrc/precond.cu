@@ -19,17 +19,20 @@
 // accurate in fp32 (with tau = noise, fp32 cancellation in the top eigen-directions breaks
 // positive definiteness at large ranks).
 //
-// The set-up's tall n x l products (Grams Q^T Y, B^T B, Y^T Y; panel times l x l matrix)
-// run on the tensor cores as m16n8k8 TF32 MMAs with a 3xTF32 split (hi hi + hi lo + lo hi,
-// about fp32 accuracy), fp32 sums inside a block and fp64 sums across blocks in a fixed
-// order.  The l x l factorizations (Cholesky, triangular inverse, products) run in fp64 on
-// the CUDA cores in 32 x 32 blocks.  Panels are fp32 [n][ld] in the lattice's locality
-// order, ld = l rounded up to 128, padding columns zero.
-// Per iteration the apply reads the bf16 factor twice (B^T r, then B u): 2 n ld bytes each,
-// half of an fp32 factor.  With tau well above the noise the bf16 rounding of B (a
-// perturbation of order 2^-9 ||B||^2 / sqrt(l) of B B^T, small against tau) leaves the
-// iteration counts unchanged (measured at n = 2M, ranks 1024 and 2048).  The MMAs there are
-// m16n8k16 bf16 with B exact and r, u split in three bf16 parts (about 24 bits).
+// All tall n x l products run on the fifth-generation tensor cores (tcgen05.mma, kind::f16,
+// fp32 accumulators in tensor memory, operands staged by TMA; see tc05.cuh):
+//   - set-up: the panels are kept as three bf16 planes (x = x1 + x2 + x3, about 24 bits);
+//     the Grams Q^T Y, Y^T Y and the panel products Y X^T take the six plane products
+//     x_a y_b with a + b <= 2; B^T B of the stored bf16 factor is one exact product;
+//     fp32 sums inside a block, fp64 sums across blocks in a fixed order;
+//   - per iteration: B^T r and B u with the exact bf16 B and r, u split in three bf16
+//     parts.  The apply reads the bf16 factor twice, 2 n ld bytes each (half of an fp32
+//     factor).  With tau well above the noise the bf16 rounding of B (a perturbation of
+//     order 2^-9 ||B||^2 / sqrt(l) of B B^T, small against tau) leaves the iteration counts
+//     unchanged (measured at n = 2M, ranks 1024 and 2048).
+// The l x l factorizations (Cholesky, triangular inverse, products) run in fp64 on the CUDA
+// cores in 32 x 32 blocks.  Panels are [n][ld] in the lattice's locality order, ld = l
+// rounded up to 128, padding columns zero.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -38,62 +41,14 @@
 #include <cuda_bf16.h>
 
 #include "sgp_internal.cuh"
+#include "tc05.cuh"
 
 namespace sgp {
 namespace {
 
-constexpr int kTile = 128;     // M and N tile of the panel products
-constexpr int kKc = 32;        // K chunk staged per step
-constexpr int kSMN = 136;      // smem row stride (floats) of [kKc][128] tiles (MN-major use)
-constexpr int kSK = 36;        // smem row stride of [128][kKc] tiles (K-major use)
-constexpr int kSR = 24;        // smem row stride of [kKc][16] right-hand-side tiles
+constexpr int kTile = 128;     // M and N tile of the tensor-core products
 constexpr int kSketchCols = 128;  // sketch columns per lattice product
 constexpr int kNB = 32;        // block size of the fp64 factorizations
-
-// ---- TF32 MMA pieces --------------------------------------------------------------------
-// Round an fp32 bit pattern to TF32 (10 explicit mantissa bits), nearest with ties away
-// from zero, by integer arithmetic on the magnitude bits: adding half a TF32 unit carries
-// into the kept bits (and into the exponent when the mantissa overflows), then the 13 low
-// bits are cleared.  Two integer operations instead of a conversion instruction (whose
-// issue rate limits the per-iteration kernels); same result as cvt.rna for finite x.
-__device__ __forceinline__ uint32_t tf32_round_bits(uint32_t b) {
-  return (b + 0x1000u) & 0xFFFFE000u;
-}
-// x = hi + lo with hi, lo TF32 (hi hi + hi lo + lo hi keeps about fp32 accuracy); x - hi is
-// exact in fp32.
-__device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_round_bits(__float_as_uint(x));
-  lo = tf32_round_bits(__float_as_uint(x - __uint_as_float(hi)));
-}
-// D (16 x 8) += A (16 x 8, row-major) B (8 x 8, column-major); lane = 4 g + t holds
-// A[g][t], A[g + 8][t], A[g][t + 4], A[g + 8][t + 4]; B[t][g], B[t + 4][g];
-// D[g][2t], D[g][2t + 1], D[g + 8][2t], D[g + 8][2t + 1].
-__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                    uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-  mma(d, al, bh0, bh1);
-  mma(d, ah, bl0, bl1);
-  mma(d, ah, bh0, bh1);
-}
-
-// ---- cp.async ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp16(float* smem, const float* gmem, bool valid) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int bytes = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
 
 // SplitMix64 (Steele, Lea & Flood 2014) at counter i l + j + 1: one +-1 per (point, column).
 __device__ __forceinline__ float sketch_sign(uint64_t seed, int64_t i, int j, int l) {
@@ -102,119 +57,6 @@ __device__ __forceinline__ float sketch_sign(uint64_t seed, int64_t i, int j, in
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
   z ^= z >> 31;
   return (z >> 63) ? -1.f : 1.f;
-}
-
-// P[p][j] = Omega[perm[p]][j] for j < l, 0 for l <= j < ld.
-__global__ void k_fill_sketch_panel(const int32_t* __restrict__ perm, int64_t n, int l, int ld,
-                                    uint64_t seed, float* __restrict__ P) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * ld) return;
-  const int64_t p = e / ld;
-  const int j = (int)(e - p * ld);
-  P[e] = j < l ? sketch_sign(seed, perm[p], j, l) : 0.f;
-}
-
-// dst[p][c] = src[p][c0 + c] for c < kc (to_panel = false); the reverse when to_panel.
-__global__ void k_copy_cols(float* __restrict__ panel, int ld, int c0, float* __restrict__ dense,
-                            int kc, int64_t n, bool to_panel) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * kc) return;
-  const int64_t p = e / kc;
-  const int c = (int)(e - p * kc);
-  if (to_panel) panel[p * ld + c0 + c] = dense[e];
-  else dense[e] = panel[p * ld + c0 + c];
-}
-
-// ---- tall products on the tensor cores ---------------------------------------------------
-// partial[s] = X[rows of split s]^T Y[rows of split s], [ldp][ldp] fp32 per split, for the
-// 128 x 128 output tiles on and below the diagonal (symmetric results: the Grams here are
-// symmetric up to rounding), blockIdx.x = ti (ti + 1) / 2 + tj, tj <= ti.  256 threads:
-// warp (wi, wj) owns the 64 x 32 sub-tile (wi = warp / 4, wj = warp % 4).  Rows are
-// staged 32 at a time.
-__global__ void __launch_bounds__(256, 2) k_gram_tc(const float* __restrict__ X, int ldx,
-                                                    const float* __restrict__ Y, int ldy,
-                                                    int64_t n, int ntile, int64_t rows_per_split,
-                                                    int ldp, float* __restrict__ partial) {
-  extern __shared__ __align__(16) float sm[];
-  float* xs = sm;                    // [2][kKc][kSMN]
-  float* ys = sm + 2 * kKc * kSMN;   // [2][kKc][kSMN]
-  int ti = (int)((sqrtf(8.f * blockIdx.x + 1.f) - 1.f) * 0.5f);
-  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
-  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
-  const int i0 = ti * kTile, j0 = ((int)blockIdx.x - ti * (ti + 1) / 2) * kTile;
-  (void)ntile;
-  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
-  const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  const int wi = warp >> 2, wj = warp & 3;
-  float acc[4][4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  auto load = [&](int buf, int64_t r0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;  // 32 rows x 32 float4
-      const int rr = e >> 5, c4 = (e & 31) * 4;
-      const int64_t r = r0 + rr;
-      const bool ok = r < r_end;
-      cp16(xs + (buf * kKc + rr) * kSMN + c4, ok ? X + r * ldx + i0 + c4 : X, ok);
-      cp16(ys + (buf * kKc + rr) * kSMN + c4, ok ? Y + r * ldy + j0 + c4 : Y, ok);
-    }
-    cp_commit();
-  };
-  const int64_t nchunks = r_end > r_begin ? ceil_div(r_end - r_begin, kKc) : 0;
-  if (nchunks > 0) load(0, r_begin);
-  for (int64_t c = 0; c < nchunks; ++c) {
-    const int buf = (int)(c & 1);
-    if (c + 1 < nchunks) {
-      load(buf ^ 1, r_begin + (c + 1) * kKc);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const float* Xs = xs + buf * kKc * kSMN;
-    const float* Ys = ys + buf * kKc * kSMN;
-#pragma unroll
-    for (int kk = 0; kk < kKc; kk += 8) {
-      uint32_t bh[4][2], bl[4][2];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int jb = wj * 32 + nt * 8 + g;
-        split(Ys[(kk + tq) * kSMN + jb], bh[nt][0], bl[nt][0]);
-        split(Ys[(kk + tq + 4) * kSMN + jb], bh[nt][1], bl[nt][1]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        const int ib = wi * 64 + mt * 16 + g;
-        uint32_t ah[4], al[4];
-        split(Xs[(kk + tq) * kSMN + ib], ah[0], al[0]);
-        split(Xs[(kk + tq) * kSMN + ib + 8], ah[1], al[1]);
-        split(Xs[(kk + tq + 4) * kSMN + ib], ah[2], al[2]);
-        split(Xs[(kk + tq + 4) * kSMN + ib + 8], ah[3], al[3]);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-          mma3(acc[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
-      }
-    }
-    __syncthreads();
-  }
-  float* out = partial + (size_t)blockIdx.y * ldp * ldp;
-#pragma unroll
-  for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int i = i0 + wi * 64 + mt * 16 + g;
-      const int j = j0 + wj * 32 + nt * 8 + 2 * tq;
-      *reinterpret_cast<float2*>(out + (size_t)i * ldp + j) =
-          make_float2(acc[mt][nt][0], acc[mt][nt][1]);
-      *reinterpret_cast<float2*>(out + (size_t)(i + 8) * ldp + j) =
-          make_float2(acc[mt][nt][2], acc[mt][nt][3]);
-    }
 }
 
 // G[i][j] = sum over splits of partial[s][i][j] (fp64, in split order) for the tiles on
@@ -236,123 +78,14 @@ __global__ void k_sum_splits(const float* __restrict__ partial, int splits, int 
   G[e] = t;
 }
 
-// Z[r][j] = sum_i Y[r][i] Tt[j][i] for i < kdim (Tt: [ld][ld] fp32), 128 x 128 output tile
-// (blockIdx.x = row tile, blockIdx.y = column tile); warp (wi, wj) owns 64 x 32.  With
-// Tt lower triangular only i < 128 (column tile + 1) contributes.
-__global__ void __launch_bounds__(256, 2) k_panel_tc(const float* __restrict__ Y, int ldy,
-                                                     const float* __restrict__ Tt, int ldt,
-                                                     int kdim, bool lower, int64_t n,
-                                                     float* __restrict__ Z, int ldz) {
-  extern __shared__ __align__(16) float sm[];
-  float* ysm = sm;                    // [2][kTile][kSK]
-  float* tsm = sm + 2 * kTile * kSK;  // [2][kTile][kSK]
-  const int64_t r0 = (int64_t)blockIdx.x * kTile;
-  const int j0 = blockIdx.y * kTile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  const int wi = warp >> 2, wj = warp & 3;
-  float acc[4][4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  auto load = [&](int buf, int k0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;  // 128 rows x 8 float4
-      const int rr = e >> 3, c4 = (e & 7) * 4;
-      const int64_t r = r0 + rr;
-      const bool ok = r < n;
-      cp16(ysm + (buf * kTile + rr) * kSK + c4, ok ? Y + r * ldy + k0 + c4 : Y, ok);
-      cp16(tsm + (buf * kTile + rr) * kSK + c4, Tt + (size_t)(j0 + rr) * ldt + k0 + c4, true);
-    }
-    cp_commit();
-  };
-  const int nchunks = (lower ? min(kdim, j0 + kTile) : kdim) / kKc;
-  load(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    const int buf = c & 1;
-    if (c + 1 < nchunks) {
-      load(buf ^ 1, (c + 1) * kKc);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const float* Ys = ysm + buf * kTile * kSK;
-    const float* Ts = tsm + buf * kTile * kSK;
-#pragma unroll
-    for (int kk = 0; kk < kKc; kk += 8) {
-      uint32_t bh[4][2], bl[4][2];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int jb = wj * 32 + nt * 8 + g;
-        split(Ts[jb * kSK + kk + tq], bh[nt][0], bl[nt][0]);
-        split(Ts[jb * kSK + kk + tq + 4], bh[nt][1], bl[nt][1]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        const int rb = wi * 64 + mt * 16 + g;
-        uint32_t ah[4], al[4];
-        split(Ys[rb * kSK + kk + tq], ah[0], al[0]);
-        split(Ys[(rb + 8) * kSK + kk + tq], ah[1], al[1]);
-        split(Ys[rb * kSK + kk + tq + 4], ah[2], al[2]);
-        split(Ys[(rb + 8) * kSK + kk + tq + 4], ah[3], al[3]);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-          mma3(acc[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int64_t r = r0 + wi * 64 + mt * 16 + g;
-      const int j = j0 + wj * 32 + nt * 8 + 2 * tq;
-      if (r < n)
-        *reinterpret_cast<float2*>(Z + r * ldz + j) = make_float2(acc[mt][nt][0], acc[mt][nt][1]);
-      if (r + 8 < n)
-        *reinterpret_cast<float2*>(Z + (r + 8) * ldz + j) =
-            make_float2(acc[mt][nt][2], acc[mt][nt][3]);
-    }
-}
-
-// 4-byte cp.async (r rows of any width k are not 16-byte aligned).
-__device__ __forceinline__ void cp4(float* smem, const float* gmem, bool valid) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int bytes = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
-}
-__device__ __forceinline__ void cp16b(void* smem, const void* gmem, bool valid) {
-  cp16(reinterpret_cast<float*>(smem), reinterpret_cast<const float*>(gmem), valid);
-}
-
-// ---- per-iteration apply with the bf16 factor ---------------------------------------------
-// B holds bf16 values exactly, so the products B^T r and B u are formed on the tensor cores
-// as m16n8k16 bf16 MMAs with B as the exact operand and r, u split in three bf16 parts
-// x = x1 + x2 + x3 (about 24 bits): products are exact in fp32, sums fp32 within a block.
-// A fragments of B come from shared memory by ldmatrix (transposed for B^T).
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row_addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"((unsigned)__cvta_generic_to_shared(row_addr)));
-}
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* row_addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"((unsigned)__cvta_generic_to_shared(row_addr)));
-}
+// ---- per-iteration apply on the fifth-generation tensor cores ----------------------------
+// B holds bf16 values exactly, so B^T r and B u are tcgen05 MMAs (kind::f16, bf16 operands,
+// fp32 accumulators in tensor memory) with B as the exact operand and r, u split in three
+// bf16 parts x = x1 + x2 + x3 (about 24 bits), stacked along N: the 16 columns of each part
+// make N = 48, and the epilogue adds the three 16-column blocks (x3 + x2 first, then x1).
+// Operand tiles arrive by TMA (128-byte swizzle) in a ring of kTcStages stages; one thread
+// issues the loads and the MMAs, four warps run the epilogue from tensor memory.
+//
 // x = x1 + x2 + x3 in bf16 (each part the nearest bf16 of what is left; the differences are
 // exact in fp32)
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
@@ -366,106 +99,33 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-constexpr int kApplyStages = 4;   // chunks in flight per block in the per-iteration kernels
-constexpr int kBtRowB = 136;      // bf16 per smem row of a [32 r][128 i] tile (272 B)
-constexpr int kBtStageBytes = kKc * kBtRowB * 2 + 2 * kKc * kSR * 4;
-constexpr int kZRowB = 40;        // bf16 per smem row of a [128 r][32 i] tile (80 B)
-constexpr int kZURow = 40;        // bf16 per smem row of a [3][16 c][32 i] u tile
-constexpr int kZStageBytes = kTile * kZRowB * 2 + 3 * 16 * kZURow * 2;
+constexpr int kTcStages = 4;
+constexpr int kTcRows = 64;                   // K rows (bt) or K columns (z) per stage
+constexpr int kTcBoxA = 128 * 128;            // bytes of a 128 x 64 bf16 operand tile
+constexpr int kTcBoxR = 48 * 128;             // bytes of the 48 x 64 bf16 split operand
+constexpr int kTcStage = kTcBoxA + kTcBoxR;   // 22 KB: a multiple of the 1 KB swizzle atom
+constexpr long long kTcSpin = 1ll << 20;      // polls per bounded wait
+constexpr int kTcThreads = 160;               // warp 0: issue; warps 1-4: epilogue
 
-// Per-iteration B^T r for 16 columns [c_off, c_off + kc) of r = rh + rl:
-// tpart[s][i][c] = sum over the rows of split s of B[row][i] r[row][c_off + c], for the
-// 128 rows i of tile blockIdx.x (split blockIdx.y).  Warp w owns i rows 16 w .. 16 w + 15.
-// Chunks of 32 rows (B: 128 columns, r: both fp32 parts) stream through kApplyStages
-// shared-memory stages by cp.async.
-__global__ void __launch_bounds__(256) k_bt_bf16(const __nv_bfloat16* __restrict__ B, int ld,
-                                                 const float* __restrict__ rh,
-                                                 const float* __restrict__ rl, int k, int c_off,
-                                                 int kc, int64_t n, int64_t rows_per_split,
-                                                 float* __restrict__ tpart) {
-  extern __shared__ __align__(16) uint8_t smb[];  // [kApplyStages][kBtStageBytes]
-  const int i0 = blockIdx.x * kTile;
-  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
-  const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  float acc[2][4];
+// r3[part * 16 + c][row] = part `part` of (rh + rl)[row][c_off + c] for c < kc (else 0):
+// the split right-hand side, K-major for the B^T r MMAs (row stride ldr >= n).
+__global__ void k_split_r(const float* __restrict__ rh, const float* __restrict__ rl, int k,
+                          int c_off, int kc, int64_t n, int64_t ldr,
+                          __nv_bfloat16* __restrict__ r3) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  auto load = [&](int slot, int64_t r0) {
-    uint8_t* st = smb + slot * kBtStageBytes;
-    __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(st);
-    float* hs = reinterpret_cast<float*>(st + kKc * kBtRowB * 2);
-    float* ls = hs + kKc * kSR;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = threadIdx.x + 256 * q;  // 32 rows x 16 pieces of 16 bytes
-      const int rr = e >> 4, c8 = (e & 15) * 8;
-      const int64_t r = r0 + rr;
-      const bool ok = r < r_end;
-      cp16b(bs + rr * kBtRowB + c8, ok ? B + r * ld + i0 + c8 : B, ok);
+  for (int c = 0; c < 16; ++c) {
+    float x = 0.f;
+    if (c < kc) {
+      const int64_t e = row * k + c_off + c;
+      x = __fadd_rn(rh[e], rl[e]);
     }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {  // 32 rows x 16 columns of rh and of rl
-      const int e = threadIdx.x + 256 * q;
-      const int rr = e >> 4, c = e & 15;
-      const int64_t r = r0 + rr;
-      const bool ok = r < r_end && c < kc;
-      const int64_t off = ok ? r * k + c_off + c : 0;
-      cp4(hs + rr * kSR + c, rh + off, ok);
-      cp4(ls + rr * kSR + c, rl + off, ok);
-    }
-  };
-  const int64_t nchunks = r_end > r_begin ? ceil_div(r_end - r_begin, kKc) : 0;
-#pragma unroll
-  for (int s0 = 0; s0 < kApplyStages - 1; ++s0) {
-    if (s0 < nchunks) load(s0, r_begin + (int64_t)s0 * kKc);
-    cp_commit();
-  }
-  // ldmatrix.trans row addresses: matrix q = lane / 8 covers k rows 8 (q >> 1) .. + 7 and
-  // i columns 8 (q & 1) .. + 7 of the warp's 16 x 16 A tile (A[i][r] = B[r][i])
-  const int q = lane >> 3, j = lane & 7;
-  const int lrow = 8 * (q >> 1) + j, lcol = warp * 16 + 8 * (q & 1);
-  for (int64_t c = 0; c < nchunks; ++c) {
-    cp_wait<kApplyStages - 2>();
-    __syncthreads();  // chunk c has landed; every warp is done with chunk c - 1's stage
-    if (c + kApplyStages - 1 < nchunks)
-      load((int)((c + kApplyStages - 1) % kApplyStages), r_begin + (c + kApplyStages - 1) * kKc);
-    cp_commit();
-    const uint8_t* st = smb + (int)(c % kApplyStages) * kBtStageBytes;
-    const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(st);
-    const float* Hs = reinterpret_cast<const float*>(st + kKc * kBtRowB * 2);
-    const float* Ls = Hs + kKc * kSR;
-#pragma unroll
-    for (int kk = 0; kk < kKc; kk += 16) {
-      uint32_t a[4];
-      ldsm_x4_trans(a, Bs + (kk + lrow) * kBtRowB + lcol);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        // B operand B'[k][n] = r[kk + k][nt 8 + n]: b0 = rows 2 tq, 2 tq + 1 and b1 = rows
-        // 2 tq + 8, 2 tq + 9 of column g
-        __nv_bfloat16 p[4][3];
-#pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          const int kr = kk + 2 * tq + (e2 & 1) + 8 * (e2 >> 1);
-          const int o = kr * kSR + nt * 8 + g;
-          split3(__fadd_rn(Hs[o], Ls[o]), p[e2][0], p[e2][1], p[e2][2]);
-        }
-#pragma unroll
-        for (int part = 2; part >= 0; --part)
-          mma_bf16(acc[nt], a, pack2(p[0][part], p[1][part]), pack2(p[2][part], p[3][part]));
-      }
-    }
-  }
-  cp_wait<0>();
-  float* out = tpart + (size_t)blockIdx.y * gridDim.x * kTile * 16;
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    const int i = i0 + warp * 16 + g;
-    const int c = nt * 8 + 2 * tq;
-    *reinterpret_cast<float2*>(out + (size_t)i * 16 + c) = make_float2(acc[nt][0], acc[nt][1]);
-    *reinterpret_cast<float2*>(out + (size_t)(i + 8) * 16 + c) = make_float2(acc[nt][2], acc[nt][3]);
+    __nv_bfloat16 a, b, d;
+    split3(x, a, b, d);
+    r3[(int64_t)(0 * 16 + c) * ldr + row] = a;
+    r3[(int64_t)(1 * 16 + c) * ldr + row] = b;
+    r3[(int64_t)(2 * 16 + c) * ldr + row] = d;
   }
 }
 
@@ -480,7 +140,7 @@ __global__ void k_sum_t(const float* __restrict__ tpart, int splits, int ld,
 }
 
 // u[i][c] = sum_j Minv[i][j] t[j][c] (fp32), i < ld, c < 16; one thread per output.  Stored
-// split in three bf16 parts, transposed: u3[part][c][i].
+// split in three bf16 parts, transposed: u3[part][c][i] (the K-major [48][ld] operand).
 __global__ void k_minv_u(const float* __restrict__ Minv, int ld, const float* __restrict__ t,
                          __nv_bfloat16* __restrict__ u3) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -496,118 +156,695 @@ __global__ void k_minv_u(const float* __restrict__ Minv, int ld, const float* __
   u3[(size_t)(2 * 16 + c) * ld + i] = d;
 }
 
-// z[r][c_off + c] = (r - B u)[r][c] * inv_tau for the 128 rows of tile blockIdx.x, and the
-// tile's column sums of r z (double-float per lane, fixed butterfly over the lanes of a
-// column, warps in order) into dot[blockIdx.x][c_off + c].  Warp w owns rows 16 w .. + 15.
-// Chunks of 32 columns of B (and the matching 32 entries of each u part) stream through
-// kApplyStages shared-memory stages by cp.async.
-__global__ void __launch_bounds__(256) k_apply_z_bf16(const __nv_bfloat16* __restrict__ B,
-                                                      int ld, const __nv_bfloat16* __restrict__ u3,
-                                                      const float* __restrict__ rh,
-                                                      const float* __restrict__ rl, int k,
-                                                      int c_off, int kc, int64_t n,
-                                                      float inv_tau, float* __restrict__ z,
-                                                      double* __restrict__ dot) {
-  extern __shared__ __align__(16) uint8_t smb[];  // [kApplyStages][kZStageBytes]
-  __shared__ double red[8][16];
-  const int64_t r0 = (int64_t)blockIdx.x * kTile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  float acc[2][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  auto load = [&](int slot, int k0) {
-    uint8_t* st = smb + slot * kZStageBytes;
-    __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(st);
-    __nv_bfloat16* us = reinterpret_cast<__nv_bfloat16*>(st + kTile * kZRowB * 2);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = threadIdx.x + 256 * q;  // 128 rows x 4 pieces of 16 bytes
-      const int rr = e >> 2, c8 = (e & 3) * 8;
-      const int64_t r = r0 + rr;
-      const bool ok = r < n;
-      cp16b(bs + rr * kZRowB + c8, ok ? B + r * ld + k0 + c8 : B, ok);
+// Block-wide pieces shared by the two kernels: barrier set-up, tensor-memory allocation and
+// the AND over the four epilogue warps (named barrier 1).
+__device__ __forceinline__ bool epilogue_and(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)v)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void epilogue_sync() {
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+// A ring of S shared-memory stages of SB bytes (1 KB aligned) with its mbarriers, the
+// tensor-memory slot and the block's abort word.
+template <int S, int SB>
+struct TcRing {
+  static constexpr int kStages = S;
+  static constexpr int kStageBytes = SB;
+  static constexpr int kSmem = S * SB + 1024 /* alignment */ + 256 /* barriers */;
+  uint8_t* stage;   // S x SB bytes
+  uint64_t* full;   // [S] TMA -> MMA
+  uint64_t* empty;  // [S] MMA -> TMA
+  uint64_t* accf;   // [2] MMAs of an accumulator done -> epilogue
+  uint64_t* acce;   // [2] epilogue done with an accumulator -> MMA (128 arrivals)
+  uint32_t* tslot;
+  int* abort;
+  __device__ uint8_t* at(int64_t g) const { return stage + (int)(g % S) * SB; }
+  __device__ uint64_t* full_of(int64_t g) const { return &full[g % S]; }
+  __device__ uint64_t* empty_of(int64_t g) const { return &empty[g % S]; }
+  __device__ static uint32_t parity(int64_t g) { return (uint32_t)(g / S) & 1u; }
+};
+template <class Ring>
+__device__ __forceinline__ Ring tc_ring(uint8_t* raw) {
+  Ring R;
+  R.stage = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                       ~static_cast<uintptr_t>(1023));
+  R.full = reinterpret_cast<uint64_t*>(R.stage + Ring::kStages * Ring::kStageBytes);
+  R.empty = R.full + Ring::kStages;
+  R.accf = R.empty + Ring::kStages;
+  R.acce = R.accf + 2;
+  R.tslot = reinterpret_cast<uint32_t*>(R.acce + 2);
+  R.abort = reinterpret_cast<int*>(R.tslot + 1);
+  return R;
+}
+template <class Ring>
+__device__ __forceinline__ void tc_setup(const Ring& R, uint32_t tmem_cols) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Ring::kStages; ++s) {
+      tc05::mbar_init(&R.full[s], 1);
+      tc05::mbar_init(&R.empty[s], 1);
     }
-    if (threadIdx.x < 3 * 16 * 4) {  // u parts: 48 rows (part, c) x 4 pieces of 16 bytes
-      const int row = threadIdx.x >> 2, c8 = (threadIdx.x & 3) * 8;
-      cp16b(us + row * kZURow + c8, u3 + (size_t)row * ld + k0 + c8, true);
+    for (int b = 0; b < 2; ++b) {
+      tc05::mbar_init(&R.accf[b], 1);
+      tc05::mbar_init(&R.acce[b], 128);
     }
-  };
-  const int nchunks = ld / kKc;
-#pragma unroll
-  for (int s0 = 0; s0 < kApplyStages - 1; ++s0) {
-    if (s0 < nchunks) load(s0, s0 * kKc);
-    cp_commit();
+    *R.abort = 0;
+    tc05::mbar_fence_init();
   }
-  // ldmatrix row addresses: matrix q = lane / 8 covers rows 8 (q & 1) .. + 7 of the warp's
-  // 16 rows and columns 8 (q >> 1) .. + 7 of the 16-column k step
-  const int q = lane >> 3, j = lane & 7;
-  const int lrow = warp * 16 + 8 * (q & 1) + j, lcol = 8 * (q >> 1);
-  for (int c = 0; c < nchunks; ++c) {
-    cp_wait<kApplyStages - 2>();
-    __syncthreads();  // chunk c has landed; every warp is done with chunk c - 1's stage
-    if (c + kApplyStages - 1 < nchunks)
-      load((c + kApplyStages - 1) % kApplyStages, (c + kApplyStages - 1) * kKc);
-    cp_commit();
-    const uint8_t* st = smb + (c % kApplyStages) * kZStageBytes;
-    const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(st);
-    const __nv_bfloat16* Us = reinterpret_cast<const __nv_bfloat16*>(st + kTile * kZRowB * 2);
-#pragma unroll
-    for (int kk = 0; kk < kKc; kk += 16) {
-      uint32_t a[4];
-      ldsm_x4(a, Bs + lrow * kZRowB + kk + lcol);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int part = 2; part >= 0; --part) {
-          // B operand B'[k][n] = u[kk + k][nt 8 + n]: consecutive k of column n are adjacent
-          const __nv_bfloat16* ub = Us + (part * 16 + nt * 8 + g) * kZURow + kk + 2 * tq;
-          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(ub);
-          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(ub + 8);
-          mma_bf16(acc[nt], a, b0, b1);
+  if (threadIdx.x < 32) tc05::tmem_alloc(R.tslot, tmem_cols);
+  tc05::fence_before_sync();
+  __syncthreads();
+  tc05::fence_after_sync();
+}
+// The issuing thread after a wait gave up (or the epilogue aborted): wait, bounded and
+// without the abort check, for the loads still in flight and for the last committed MMAs,
+// so that nothing lands in shared or tensor memory after the block exits.
+template <class Ring>
+__device__ __forceinline__ void tc_drain(const Ring& R, int64_t landed, int64_t issued,
+                                         int64_t committed) {
+  for (int64_t g = landed; g < issued; ++g)
+    (void)tc05::mbar_wait(R.full_of(g), Ring::parity(g), kTcSpin);
+  if (committed >= 0)
+    (void)tc05::mbar_wait(R.empty_of(committed), Ring::parity(committed), kTcSpin);
+}
+using ApplyRing = TcRing<kTcStages, kTcStage>;
+
+// Per-iteration B^T r for 16 columns of r (split in r3): tpart[s][i][c] = sum over the rows
+// of split s (blockIdx.y) of B[row][i] r[row][c], i in the 128-column tile blockIdx.x.
+// A = B^T is MN-major: the TMA boxes of B are 64 rows (K) x 64 columns (M), two per stage
+// (columns i0 .. + 63, i0 + 64 .. + 127: leading offset 8 KB); r3 boxes are 48 x 64 K-major.
+// rows_per_split is a multiple of 64; rows >= n read as zero.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_bt_tc(const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ CUtensorMap mapR,
+            int64_t n, int64_t rows_per_split, float* __restrict__ tpart, int* __restrict__ err) {
+  extern __shared__ uint8_t tc_raw[];
+  const ApplyRing R = tc_ring<ApplyRing>(tc_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 128;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
+  const int64_t total = r_end > r_begin ? ceil_div(r_end - r_begin, kTcRows) : 0;
+  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 48, /*a_mn=*/true, /*b_mn=*/false);
+  if (*reinterpret_cast<volatile int*>(err)) return;  // an earlier launch gave up: skip
+  if (threadIdx.x == 0) {
+    tc05::prefetch_map(&mapBt);
+    tc05::prefetch_map(&mapR);
+  }
+  tc_setup(R, 64);
+  const uint32_t tmem = *R.tslot;
+  volatile int* abort = R.abort;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t issued = 0, landed = 0, committed = -1;
+      auto issue = [&](int64_t g) {
+        uint8_t* st = R.stage + (g % kTcStages) * kTcStage;
+        const int row0 = (int)(r_begin + g * kTcRows);
+        tc05::mbar_expect_tx(&R.full[g % kTcStages], kTcStage);
+        tc05::tma_load_2d(st, &mapBt, i0, row0, &R.full[g % kTcStages]);
+        tc05::tma_load_2d(st + kTcBoxA / 2, &mapBt, i0 + 64, row0, &R.full[g % kTcStages]);
+        tc05::tma_load_2d(st + kTcBoxA, &mapR, row0, 0, &R.full[g % kTcStages]);
+        issued = g + 1;
+      };
+      for (int64_t g = 0; g < total && g < kTcStages; ++g) issue(g);
+      bool ok = true;
+      for (int64_t g = 0; g < total; ++g) {
+        const int s = (int)(g % kTcStages);
+        if (!tc05::mbar_wait(&R.full[s], (uint32_t)(g / kTcStages) & 1u, kTcSpin, abort)) {
+          ok = false;
+          break;
         }
-    }
-  }
-  cp_wait<0>();
-  // epilogue: this lane holds rows g, g + 8 of the warp's 16 and columns nt 8 + 2 tq (+1)
-  dfloat d[2][2];
+        landed = g + 1;
+        tc05::fence_after_sync();
+        const uint32_t a0 = tc05::smem_u32(R.stage + s * kTcStage), b0 = a0 + kTcBoxA;
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) d[nt][0] = d[nt][1] = {0.f, 0.f};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int64_t r = r0 + warp * 16 + g + 8 * h;
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int q2 = 0; q2 < 2; ++q2) {
-        const int c = nt * 8 + 2 * tq + q2;
-        if (r < n && c < kc) {
-          const int64_t e = r * k + c_off + c;
-          const float rv = __fadd_rn(rh[e], rl[e]);
-          const float zz = (rv - acc[nt][2 * h + q2]) * inv_tau;
-          z[e] = zz;
-          d[nt][q2] = df_add(d[nt][q2], df_two_prod(rv, zz));
+        for (int kk = 0; kk < kTcRows / 16; ++kk)
+          tc05::mma_bf16(tmem, tc05::desc_sw128(a0 + kk * 2048, kTcBoxA / 2, 1024),
+                         tc05::desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                         (g | kk) ? 1u : 0u);
+        tc05::mma_commit(&R.empty[s]);
+        committed = g;
+        // refill the previous chunk's stage once its MMAs are done
+        if (g >= 1 && g - 1 + kTcStages < total) {
+          const int64_t p = g - 1;
+          if (!tc05::mbar_wait(&R.empty[p % kTcStages], (uint32_t)(p / kTcStages) & 1u, kTcSpin,
+                               abort)) {
+            ok = false;
+            break;
+          }
+          issue(p + kTcStages);
         }
       }
-  }
-  // lanes with the same tq hold the same columns: combine over g (xor 4, 8, 16)
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int q2 = 0; q2 < 2; ++q2) {
-      double v = df_to_double(d[nt][q2]);
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (g == 0) red[warp][nt * 8 + 2 * tq + q2] = v;
+      if (ok) {
+        tc05::mma_commit(&R.accf[0]);
+      } else {
+        *abort = 1;
+        atomicExch(err, 1);
+        tc_drain(R, landed, issued, committed);
+      }
     }
-  __syncthreads();
-  if (threadIdx.x < 16 && (int)threadIdx.x < kc) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-    dot[(int64_t)blockIdx.x * k + c_off + threadIdx.x] = s;
+  } else {
+    const int q = warp & 3;  // tensor-memory lanes 32 q .. + 31 = rows i0 + 32 q + lane
+    bool ok = true;
+    if (total > 0) {
+      ok = tc05::mbar_wait(&R.accf[0], 0u, kTcSpin, abort);
+      ok = epilogue_and(ok);
+    }
+    if (!ok) {
+      if (threadIdx.x == 32) {
+        *abort = 1;
+        atomicExch(err, 1);
+      }
+    } else {
+      float t[16];
+      if (total > 0) {
+        tc05::fence_after_sync();
+        float d1[16], d2[16], d3[16];
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16);
+        tc05::tmem_ld16(ta, d1);
+        tc05::tmem_ld16(ta + 16, d2);
+        tc05::tmem_ld16(ta + 32, d3);
+        tc05::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) t[c] = d1[c] + (d2[c] + d3[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) t[c] = 0.f;
+      }
+      float4* out = reinterpret_cast<float4*>(
+          tpart + ((size_t)blockIdx.y * gridDim.x * 128 + i0 + 32 * q + lane) * 16);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        out[c] = make_float4(t[4 * c], t[4 * c + 1], t[4 * c + 2], t[4 * c + 3]);
+    }
   }
+  tc05::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, 64);
+}
+
+// z[r][c_off + c] = (r - B u)[r][c] * inv_tau over 128-row tiles (tile t: rows 128 t ..),
+// and each tile's column sums of r z (fp64; the products are exact in fp64) into
+// dot[t][c_off + c].  Persistent: block b takes tiles b, b + gridDim.x, ..., with two
+// accumulators in tensor memory so that the MMAs of one tile overlap the epilogue of the
+// previous.  A = B is K-major (boxes 128 rows x 64 columns); u3 ([48][ld], the three parts
+// of u = Minv B^T r) is K-major (boxes 48 x 64).
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_z_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapU,
+           const float* __restrict__ rh, const float* __restrict__ rl, int k, int c_off, int kc,
+           int64_t n, int ld, float inv_tau, float* __restrict__ z, double* __restrict__ dot,
+           int* __restrict__ err) {
+  extern __shared__ uint8_t tc_raw[];
+  __shared__ double red[2][4][16];
+  const ApplyRing R = tc_ring<ApplyRing>(tc_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = ceil_div(n, 128);
+  const int nk = ld / kTcRows;
+  const int64_t my_tiles =
+      (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * nk;
+  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 48, /*a_mn=*/false, /*b_mn=*/false);
+  if (*reinterpret_cast<volatile int*>(err)) return;  // an earlier launch gave up: skip
+  if (threadIdx.x == 0) {
+    tc05::prefetch_map(&mapB);
+    tc05::prefetch_map(&mapU);
+  }
+  tc_setup(R, 128);
+  const uint32_t tmem = *R.tslot;
+  volatile int* abort = R.abort;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t issued = 0, landed = 0, committed = -1;
+      auto issue = [&](int64_t g) {
+        uint8_t* st = R.stage + (g % kTcStages) * kTcStage;
+        const int64_t tile = blockIdx.x + (g / nk) * (int64_t)gridDim.x;
+        const int kq = (int)(g % nk);
+        tc05::mbar_expect_tx(&R.full[g % kTcStages], kTcStage);
+        tc05::tma_load_2d(st, &mapB, kq * kTcRows, (int)(tile * 128), &R.full[g % kTcStages]);
+        tc05::tma_load_2d(st + kTcBoxA, &mapU, kq * kTcRows, 0, &R.full[g % kTcStages]);
+        issued = g + 1;
+      };
+      for (int64_t g = 0; g < total && g < kTcStages; ++g) issue(g);
+      bool ok = true;
+      for (int64_t j = 0; j < my_tiles && ok; ++j) {
+        const int b = (int)(j & 1);
+        if (j >= 2 && !tc05::mbar_wait(&R.acce[b], (uint32_t)((j - 2) >> 1) & 1u, kTcSpin,
+                                       abort)) {
+          ok = false;
+          break;
+        }
+        tc05::fence_after_sync();
+        for (int kq = 0; kq < nk; ++kq) {
+          const int64_t g = j * nk + kq;
+          const int s = (int)(g % kTcStages);
+          if (!tc05::mbar_wait(&R.full[s], (uint32_t)(g / kTcStages) & 1u, kTcSpin, abort)) {
+            ok = false;
+            break;
+          }
+          landed = g + 1;
+          tc05::fence_after_sync();
+          const uint32_t a0 = tc05::smem_u32(R.stage + s * kTcStage), b0 = a0 + kTcBoxA;
+#pragma unroll
+          for (int kk = 0; kk < kTcRows / 16; ++kk)
+            tc05::mma_bf16(tmem + 64 * b, tc05::desc_sw128(a0 + kk * 32, 16, 1024),
+                           tc05::desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                           (kq | kk) ? 1u : 0u);
+          tc05::mma_commit(&R.empty[s]);
+          committed = g;
+          if (kq == nk - 1) tc05::mma_commit(&R.accf[b]);
+          if (g >= 1 && g - 1 + kTcStages < total) {
+            const int64_t p = g - 1;
+            if (!tc05::mbar_wait(&R.empty[p % kTcStages], (uint32_t)(p / kTcStages) & 1u,
+                                 kTcSpin, abort)) {
+              ok = false;
+              break;
+            }
+            issue(p + kTcStages);
+          }
+        }
+      }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(err, 1);
+        tc_drain(R, landed, issued, committed);
+      }
+    }
+  } else {
+    const int q = warp & 3;  // tensor-memory lanes 32 q .. + 31
+    const bool vec = (k & 3) == 0 && (c_off & 3) == 0;
+    for (int64_t j = 0; j < my_tiles; ++j) {
+      const int b = (int)(j & 1);
+      const int64_t tile = blockIdx.x + j * (int64_t)gridDim.x;
+      bool ok = tc05::mbar_wait(&R.accf[b], (uint32_t)(j >> 1) & 1u, kTcSpin, abort);
+      ok = epilogue_and(ok);
+      if (!ok) {
+        if (threadIdx.x == 32) {
+          *abort = 1;
+          atomicExch(err, 1);
+        }
+        break;
+      }
+      tc05::fence_after_sync();
+      float d1[16], d2[16], d3[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + 64u * b;
+      tc05::tmem_ld16(ta, d1);
+      tc05::tmem_ld16(ta + 16, d2);
+      tc05::tmem_ld16(ta + 32, d3);
+      tc05::tmem_wait_ld();
+      tc05::fence_before_sync();
+      tc05::mbar_arrive(&R.acce[b]);
+      const int64_t row = tile * 128 + 32 * q + lane;
+      double pr[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) pr[c] = 0.0;
+      if (row < n) {
+        float rv[16];
+        const int64_t e0 = row * k + c_off;
+        if (vec) {
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            if (4 * c4 < kc) {
+              const float4 h = *reinterpret_cast<const float4*>(rh + e0 + 4 * c4);
+              const float4 l = *reinterpret_cast<const float4*>(rl + e0 + 4 * c4);
+              rv[4 * c4] = __fadd_rn(h.x, l.x);
+              rv[4 * c4 + 1] = __fadd_rn(h.y, l.y);
+              rv[4 * c4 + 2] = __fadd_rn(h.z, l.z);
+              rv[4 * c4 + 3] = __fadd_rn(h.w, l.w);
+            }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c < kc) rv[c] = __fadd_rn(rh[e0 + c], rl[e0 + c]);
+        }
+        float zz[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          zz[c] = 0.f;
+          if (c < kc) {
+            zz[c] = (rv[c] - (d1[c] + (d2[c] + d3[c]))) * inv_tau;
+            pr[c] = (double)rv[c] * (double)zz[c];
+          }
+        }
+        if (vec) {
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            if (4 * c4 < kc)
+              *reinterpret_cast<float4*>(z + e0 + 4 * c4) =
+                  make_float4(zz[4 * c4], zz[4 * c4 + 1], zz[4 * c4 + 2], zz[4 * c4 + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c < kc) z[e0 + c] = zz[c];
+        }
+      }
+      // column sums over the tile's rows: butterfly within each warp, then the four
+      // quarters in row order
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        double v = pr[c];
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (lane == 0) red[b][q][c] = v;
+      }
+      epilogue_sync();
+      if (warp == 1 && lane < kc)
+        dot[tile * k + c_off + lane] =
+            ((red[b][0][lane] + red[b][1][lane]) + red[b][2][lane]) + red[b][3][lane];
+    }
+  }
+  tc05::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, 128);
+}
+
+// ---- set-up panels on the fifth-generation tensor cores ----------------------------------
+// The set-up's n x ld panels are kept as three bf16 planes [3][n][ld] holding the parts of
+// an fp32 value x = x1 + x2 + x3 (split3: about 24 significant bits, as fp32).  The Grams
+// X^T Y and the panel products Y T^T then run as tcgen05 MMAs over plane pairs: the six
+// products x_a y_b with a + b <= 2 (the dropped ones are below 2^-24 relative), smallest
+// first, all accumulated in one fp32 tensor-memory accumulator.  Operand tiles arrive by
+// 3D TMA loads (one box per operand tile covers all planes).
+
+// P3[.][p][j]: plane 0 = Omega[perm[p]][j] for j < l, 0 for l <= j < ld; planes 1, 2 = 0.
+__global__ void k_fill_sketch3(const int32_t* __restrict__ perm, int64_t n, int l, int ld,
+                               uint64_t seed, __nv_bfloat16* __restrict__ P3) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t plane = n * ld;
+  if (e >= plane) return;
+  const int64_t p = e / ld;
+  const int j = (int)(e - p * ld);
+  P3[e] = __float2bfloat16_rn(j < l ? sketch_sign(seed, perm[p], j, l) : 0.f);
+  P3[plane + e] = __float2bfloat16_rn(0.f);
+  P3[2 * plane + e] = __float2bfloat16_rn(0.f);
+}
+
+// dense[p][c] = (x3 + x2) + x1 of panel column c0 + c (to_panel = false), or the split of
+// dense[p][c] into the panel's planes (to_panel = true); c < kc.
+__global__ void k_cols3(__nv_bfloat16* __restrict__ P3, int ld, int c0, float* __restrict__ dense,
+                        int kc, int64_t n, bool to_panel) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * kc) return;
+  const int64_t p = e / kc;
+  const int c = (int)(e - p * kc);
+  const int64_t plane = n * ld, q = p * ld + c0 + c;
+  if (to_panel) {
+    __nv_bfloat16 a, b, d;
+    split3(dense[e], a, b, d);
+    P3[q] = a;
+    P3[plane + q] = b;
+    P3[2 * plane + q] = d;
+  } else {
+    dense[e] = (__bfloat162float(P3[2 * plane + q]) + __bfloat162float(P3[plane + q])) +
+               __bfloat162float(P3[q]);
+  }
+}
+
+// T3 = the three planes of (float)A for the l x l block of A (fp64, leading dimension lda),
+// zero elsewhere in [ld][ld].
+__global__ void k_split3_pad(const double* __restrict__ A, int lda, int l, int ld,
+                             __nv_bfloat16* __restrict__ T3) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)ld * ld;
+  if (e >= plane) return;
+  const int i = (int)(e / ld), j = (int)(e % ld);
+  __nv_bfloat16 a, b, d;
+  split3((i < l && j < l) ? (float)A[(size_t)i * lda + j] : 0.f, a, b, d);
+  T3[e] = a;
+  T3[plane + e] = b;
+  T3[2 * plane + e] = d;
+}
+
+// The plane pairs (a, b) of the products, smallest first: (2,0) (0,2) (1,1) (1,0) (0,1)
+// (0,0).
+__host__ __device__ constexpr int pair_a(int q) { return q == 0 ? 2 : (q == 2 || q == 3) ? 1 : 0; }
+__host__ __device__ constexpr int pair_b(int q) { return q == 1 ? 2 : (q == 2 || q == 4) ? 1 : 0; }
+
+// Gram partials: partial[s][i][j] = sum over the rows of split s (blockIdx.y) of X[r][i]
+// Y[r][j] for the 128 x 128 tile blockIdx.x = ti (ti + 1) / 2 + tj, tj <= ti (the results
+// are symmetric up to rounding; k_sum_splits mirrors them).  X and Y are P-plane panels
+// (P = 3: six plane products; P = 1: bf16 values, one exact product); both are MN-major
+// operands: per stage, 32 rows of each 64-column half as one box over the P planes
+// (leading offset = one half's bytes).  rows_per_split is a multiple of 32.
+template <int P>
+struct GramCfg {
+  static constexpr int kBox = 32 * 128;        // one plane of a half: 32 rows x 64 bf16
+  static constexpr int kHalf = P * kBox;
+  static constexpr int kStage = 4 * kHalf;     // X halves 0, 1, then Y halves 0, 1
+  using Ring = TcRing<P == 3 ? 4 : 8, kStage>;
+};
+template <int P>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gram5(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+            int64_t n, int64_t rows_per_split, int ldp, float* __restrict__ partial,
+            int* __restrict__ err) {
+  using Cfg = GramCfg<P>;
+  using Ring = typename Cfg::Ring;
+  extern __shared__ uint8_t tc_raw[];
+  const Ring R = tc_ring<Ring>(tc_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ti = (int)((sqrtf(8.f * blockIdx.x + 1.f) - 1.f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+  const int i0 = ti * 128, j0 = ((int)blockIdx.x - ti * (ti + 1) / 2) * 128;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
+  const int64_t total = r_end > r_begin ? ceil_div(r_end - r_begin, 32) : 0;
+  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 128, /*a_mn=*/true, /*b_mn=*/true);
+  if (*reinterpret_cast<volatile int*>(err)) return;
+  if (threadIdx.x == 0) {
+    tc05::prefetch_map(&mapX);
+    tc05::prefetch_map(&mapY);
+  }
+  tc_setup(R, 128);
+  const uint32_t tmem = *R.tslot;
+  volatile int* abort = R.abort;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t issued = 0, landed = 0, committed = -1;
+      auto issue = [&](int64_t g) {
+        uint8_t* st = R.at(g);
+        const int row0 = (int)(r_begin + g * 32);
+        tc05::mbar_expect_tx(R.full_of(g), Cfg::kStage);
+        tc05::tma_load_3d(st, &mapX, i0, row0, 0, R.full_of(g));
+        tc05::tma_load_3d(st + Cfg::kHalf, &mapX, i0 + 64, row0, 0, R.full_of(g));
+        tc05::tma_load_3d(st + 2 * Cfg::kHalf, &mapY, j0, row0, 0, R.full_of(g));
+        tc05::tma_load_3d(st + 3 * Cfg::kHalf, &mapY, j0 + 64, row0, 0, R.full_of(g));
+        issued = g + 1;
+      };
+      for (int64_t g = 0; g < total && g < Ring::kStages; ++g) issue(g);
+      bool ok = true;
+      for (int64_t g = 0; g < total; ++g) {
+        if (!tc05::mbar_wait(R.full_of(g), Ring::parity(g), kTcSpin, abort)) {
+          ok = false;
+          break;
+        }
+        landed = g + 1;
+        tc05::fence_after_sync();
+        const uint32_t xa = tc05::smem_u32(R.at(g)), ya = xa + 2 * Cfg::kHalf;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+          for (int q = 0; q < (P == 3 ? 6 : 1); ++q) {
+            const int pa = P == 3 ? pair_a(q) : 0, pb = P == 3 ? pair_b(q) : 0;
+            tc05::mma_bf16(tmem,
+                           tc05::desc_sw128(xa + pa * Cfg::kBox + kk * 2048, Cfg::kHalf, 1024),
+                           tc05::desc_sw128(ya + pb * Cfg::kBox + kk * 2048, Cfg::kHalf, 1024),
+                           kIdesc, (g | kk | q) ? 1u : 0u);
+          }
+        tc05::mma_commit(R.empty_of(g));
+        committed = g;
+        if (g >= 1 && g - 1 + Ring::kStages < total) {
+          if (!tc05::mbar_wait(R.empty_of(g - 1), Ring::parity(g - 1), kTcSpin, abort)) {
+            ok = false;
+            break;
+          }
+          issue(g - 1 + Ring::kStages);
+        }
+      }
+      if (ok) {
+        tc05::mma_commit(&R.accf[0]);
+      } else {
+        *abort = 1;
+        atomicExch(err, 1);
+        tc_drain(R, landed, issued, committed);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    bool ok = true;
+    if (total > 0) ok = epilogue_and(tc05::mbar_wait(&R.accf[0], 0u, kTcSpin, abort));
+    if (!ok) {
+      if (threadIdx.x == 32) {
+        *abort = 1;
+        atomicExch(err, 1);
+      }
+    } else {
+      float4* out = reinterpret_cast<float4*>(
+          partial + ((size_t)blockIdx.y * ldp + i0 + 32 * q + lane) * ldp + j0);
+      if (total > 0) tc05::fence_after_sync();
+#pragma unroll 1
+      for (int cb = 0; cb < 8; ++cb) {
+        float v[16];
+        if (total > 0) {
+          tc05::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 16u * cb, v);
+          tc05::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          out[4 * cb + c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+      }
+    }
+  }
+  tc05::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, 128);
+}
+
+// Panel product Z[r][j] = sum_i Y[r][i] T[j][i] for i < kdim (with `lower`, T is lower
+// triangular and only i < j0 + 128 contributes), on the 128 x 128 tile (row tile
+// blockIdx.x, column tile blockIdx.y).  Y ([3][n][ld]) and T ([3][ld][ld]) are 3-plane,
+// both K-major (boxes 128 rows x 64 columns over the 3 planes).  ROUND = false: Z is
+// stored as 3 planes [3][n][ld]; ROUND = true: Z is stored rounded to bf16 [n][ld].
+struct PanelCfg {
+  static constexpr int kBox = 128 * 128;   // one plane: 128 rows x 64 bf16
+  static constexpr int kStage = 6 * kBox;  // Y planes, then T planes
+  using Ring = TcRing<2, kStage>;
+};
+template <bool ROUND>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_panel5(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapT,
+             int64_t n, int ld, int kdim, bool lower, __nv_bfloat16* __restrict__ Z,
+             int* __restrict__ err) {
+  using Ring = PanelCfg::Ring;
+  extern __shared__ uint8_t tc_raw[];
+  const Ring R = tc_ring<Ring>(tc_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * 128;
+  const int j0 = blockIdx.y * 128;
+  const int64_t total = (lower ? min(kdim, j0 + 128) : kdim) / 64;
+  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 128, /*a_mn=*/false, /*b_mn=*/false);
+  if (*reinterpret_cast<volatile int*>(err)) return;
+  if (threadIdx.x == 0) {
+    tc05::prefetch_map(&mapY);
+    tc05::prefetch_map(&mapT);
+  }
+  tc_setup(R, 128);
+  const uint32_t tmem = *R.tslot;
+  volatile int* abort = R.abort;
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t issued = 0, landed = 0, committed = -1;
+      auto issue = [&](int64_t g) {
+        uint8_t* st = R.at(g);
+        tc05::mbar_expect_tx(R.full_of(g), PanelCfg::kStage);
+        tc05::tma_load_3d(st, &mapY, (int)(g * 64), (int)r0, 0, R.full_of(g));
+        tc05::tma_load_3d(st + 3 * PanelCfg::kBox, &mapT, (int)(g * 64), j0, 0, R.full_of(g));
+        issued = g + 1;
+      };
+      for (int64_t g = 0; g < total && g < Ring::kStages; ++g) issue(g);
+      bool ok = true;
+      for (int64_t g = 0; g < total; ++g) {
+        if (!tc05::mbar_wait(R.full_of(g), Ring::parity(g), kTcSpin, abort)) {
+          ok = false;
+          break;
+        }
+        landed = g + 1;
+        tc05::fence_after_sync();
+        const uint32_t ya = tc05::smem_u32(R.at(g)), ta = ya + 3 * PanelCfg::kBox;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            tc05::mma_bf16(tmem, tc05::desc_sw128(ya + pair_a(q) * PanelCfg::kBox + kk * 32, 16, 1024),
+                           tc05::desc_sw128(ta + pair_b(q) * PanelCfg::kBox + kk * 32, 16, 1024),
+                           kIdesc, (g | kk | q) ? 1u : 0u);
+        tc05::mma_commit(R.empty_of(g));
+        committed = g;
+        if (g >= 1 && g - 1 + Ring::kStages < total) {
+          if (!tc05::mbar_wait(R.empty_of(g - 1), Ring::parity(g - 1), kTcSpin, abort)) {
+            ok = false;
+            break;
+          }
+          issue(g - 1 + Ring::kStages);
+        }
+      }
+      if (ok) {
+        tc05::mma_commit(&R.accf[0]);
+      } else {
+        *abort = 1;
+        atomicExch(err, 1);
+        tc_drain(R, landed, issued, committed);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    bool ok = true;
+    if (total > 0) ok = epilogue_and(tc05::mbar_wait(&R.accf[0], 0u, kTcSpin, abort));
+    if (!ok) {
+      if (threadIdx.x == 32) {
+        *abort = 1;
+        atomicExch(err, 1);
+      }
+    } else {
+      const int64_t r = r0 + 32 * q + lane;
+      const int64_t plane = n * ld;
+      if (total > 0) tc05::fence_after_sync();
+#pragma unroll 1
+      for (int cb = 0; cb < 8; ++cb) {
+        float v[16];
+        if (total > 0) {
+          tc05::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 16u * cb, v);
+          tc05::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = 0.f;
+        }
+        if (r < n) {
+          const int64_t e = r * ld + j0 + 16 * cb;
+          if (ROUND) {
+            uint32_t w[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              w[c] = pack2(__float2bfloat16_rn(v[2 * c]), __float2bfloat16_rn(v[2 * c + 1]));
+            uint4* o = reinterpret_cast<uint4*>(Z + e);
+            o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+            uint32_t w[3][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              __nv_bfloat16 a0, b0, d0, a1, b1, d1;
+              split3(v[2 * c], a0, b0, d0);
+              split3(v[2 * c + 1], a1, b1, d1);
+              w[0][c] = pack2(a0, a1);
+              w[1][c] = pack2(b0, b1);
+              w[2][c] = pack2(d0, d1);
+            }
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+              uint4* o = reinterpret_cast<uint4*>(Z + pl * plane + e);
+              o[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+              o[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc05::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, 128);
 }
 
 // ---- l x l fp64 factorizations (row-major, leading dimension lda, size l) ---------------
@@ -894,16 +1131,6 @@ __global__ void k_init_unit(double* __restrict__ v, int l) {
   if (j < l) v[j] = 1.0 / sqrt((double)l) * (1.0 + 0.25 * sin(0.7 * j));
 }
 
-// Round a panel to bf16 in place (the fp32 copy then holds the bf16 values exactly) and
-// write the bf16 copy.
-__global__ void k_round_bf16(float* __restrict__ P, int64_t count, __nv_bfloat16* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= count) return;
-  const __nv_bfloat16 b = __float2bfloat16_rn(P[e]);
-  out[e] = b;
-  P[e] = __bfloat162float(b);
-}
-
 // out[i][j] = (float)A[i][j] for i, j < l, 0 elsewhere in [ld][ld].
 __global__ void k_to_f32_pad(const double* __restrict__ A, int lda, int l, int ld,
                              float* __restrict__ out) {
@@ -988,6 +1215,13 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     cudaError_t e_ = (expr);                                  \
     if (e_ != cudaSuccess) return cuda_status(e_, what);      \
   } while (0)
+#define PC_MAP(expr)                                                   \
+  do {                                                                 \
+    if (!(expr)) {                                                     \
+      set_error("encoding a preconditioner tensor map failed");        \
+      return SGP_ERR_CUDA;                                             \
+    }                                                                  \
+  } while (0)
   std::vector<void*> temps;
   struct Free {
     std::vector<void*>& t;
@@ -1011,43 +1245,68 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     int dev = 0;
     PC_CHECK(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev >= 0 && dev < 64 && !attrs[dev].load()) {
-      PC_CHECK(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    4 * kKc * kSMN * (int)sizeof(float)),
-               "k_gram_tc smem");
-      PC_CHECK(cudaFuncSetAttribute(k_panel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    4 * kTile * kSK * (int)sizeof(float)),
-               "k_panel_tc smem");
-      PC_CHECK(cudaFuncSetAttribute(k_bt_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kApplyStages * kBtStageBytes),
-               "k_bt_bf16 smem");
-      PC_CHECK(cudaFuncSetAttribute(k_apply_z_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kApplyStages * kZStageBytes),
-               "k_apply_z_bf16 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_gram5<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GramCfg<3>::Ring::kSmem),
+               "k_gram5 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_gram5<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GramCfg<1>::Ring::kSmem),
+               "k_gram5 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_panel5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    PanelCfg::Ring::kSmem),
+               "k_panel5 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_panel5<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    PanelCfg::Ring::kSmem),
+               "k_panel5 smem");
+      PC_CHECK(cudaFuncSetAttribute(k_bt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ApplyRing::kSmem),
+               "k_bt_tc smem");
+      PC_CHECK(cudaFuncSetAttribute(k_z_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ApplyRing::kSmem),
+               "k_z_tc smem");
       attrs[dev].store(true);
     }
   }
-  const size_t panel = (size_t)n * ld * sizeof(float);
-  float *P1 = nullptr, *P2 = nullptr, *Vc = nullptr, *KVc = nullptr, *gpart = nullptr,
-        *Tt = nullptr;
+  int sms = 0, dev_now = 0;
+  PC_CHECK(cudaGetDevice(&dev_now), "cudaGetDevice");
+  PC_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_now), "SM count");
+  const size_t panel3 = (size_t)3 * n * ld * sizeof(__nv_bfloat16);
+  __nv_bfloat16 *P1 = nullptr, *P2 = nullptr, *T3 = nullptr;
+  float *Vc = nullptr, *KVc = nullptr, *gpart = nullptr;
   double *G = nullptr, *G0 = nullptr, *Xi = nullptr, *M = nullptr, *pv = nullptr, *py = nullptr,
          *prq = nullptr;
   int* status = nullptr;
   PC_CHECK(keep((void**)&B, (size_t)n * ld * sizeof(__nv_bfloat16)),
            "alloc preconditioner B");
-  PC_CHECK(temp((void**)&P1, panel), "alloc preconditioner panel");
-  PC_CHECK(temp((void**)&P2, panel), "alloc preconditioner panel");
+  PC_CHECK(keep((void**)&err, sizeof(int)), "alloc error flag");
+  PC_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st), "clear error flag");
+  PC_CHECK(temp((void**)&P1, panel3), "alloc preconditioner panel");
+  PC_CHECK(temp((void**)&P2, panel3), "alloc preconditioner panel");
   PC_CHECK(temp((void**)&Vc, (size_t)n * kSketchCols * sizeof(float)), "alloc sketch chunk");
   PC_CHECK(temp((void**)&KVc, (size_t)n * kSketchCols * sizeof(float)), "alloc sketch chunk");
   const int ntile = ld / kTile;
-  // row splits of the Grams: at most 64 k rows per split, at least 2 waves of blocks
-  int splits = (int)std::max<int64_t>(ceil_div(n, 65536),
-                                      ceil_div(2 * 2 * 152, ntile * (ntile + 1) / 2));
-  splits = (int)std::min<int64_t>(splits, std::max<int64_t>(1, ceil_div(n, kKc)));
-  const int64_t rows_per_split = ceil_div(ceil_div(n, splits), kKc) * kKc;
+  // row splits of the Grams (multiples of 32 rows): the count whose blocks fill the last
+  // of their waves best, between 1 and 8 waves (one block per SM), at least 2048 rows each
+  const int tiles = ntile * (ntile + 1) / 2;
+  int splits = 1;
+  {
+    const int64_t lo = std::max<int64_t>(1, ceil_div(sms, tiles));
+    const int64_t hi = std::max<int64_t>(lo, std::min<int64_t>(ceil_div(8 * (int64_t)sms, tiles),
+                                                               ceil_div(n, 2048)));
+    double best = -1.0;
+    for (int64_t sp = lo; sp <= hi; ++sp) {
+      const int64_t blocks = sp * tiles, waves = ceil_div(blocks, sms);
+      const double eff = (double)blocks / (double)(waves * sms);
+      if (eff > best + 1e-9) {
+        best = eff;
+        splits = (int)sp;
+      }
+    }
+  }
+  const int64_t rows_per_split = ceil_div(ceil_div(n, splits), 32) * 32;
   splits = (int)ceil_div(n, rows_per_split);
   const size_t ll = (size_t)ld * ld;
   PC_CHECK(temp((void**)&gpart, (size_t)splits * ll * sizeof(float)), "alloc Gram partials");
-  PC_CHECK(temp((void**)&Tt, ll * sizeof(float)), "alloc l x l");
+  PC_CHECK(temp((void**)&T3, 3 * ll * sizeof(__nv_bfloat16)), "alloc l x l");
   PC_CHECK(temp((void**)&G, ll * sizeof(double)), "alloc l x l");
   PC_CHECK(temp((void**)&G0, ll * sizeof(double)), "alloc l x l");
   PC_CHECK(temp((void**)&Xi, ll * sizeof(double)), "alloc l x l");
@@ -1056,54 +1315,89 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   PC_CHECK(temp((void**)&py, ld * sizeof(double)), "alloc power vectors");
   PC_CHECK(temp((void**)&prq, sizeof(double)), "alloc power vectors");
   PC_CHECK(temp((void**)&status, sizeof(int)), "alloc status");
-  // per-iteration buffers
-  // B^T r: one wave of the blocks the device keeps resident (i tiles x row splits)
-  int bt_per_sm = 0, sms = 0, dev_now = 0;
-  PC_CHECK(cudaGetDevice(&dev_now), "cudaGetDevice");
-  PC_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_now), "SM count");
-  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-               &bt_per_sm, k_bt_bf16, 256, kApplyStages * kBtStageBytes),
+  // per-iteration buffers.  B^T r: one wave of the blocks the device keeps resident (i
+  // tiles x row splits of a multiple of 64 rows); z: one persistent block per resident slot
+  int tc_per_sm = 0;
+  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tc_per_sm, k_bt_tc, kTcThreads,
+                                                         ApplyRing::kSmem),
            "occupancy");
+  tc_per_sm = std::max(1, tc_per_sm);
   bt_splits = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::max(1, bt_per_sm) * (int64_t)sms / ntile, ceil_div(n, kKc)));
-  bt_rows = ceil_div(ceil_div(n, bt_splits), kKc) * kKc;
+      1, std::min<int64_t>(tc_per_sm * (int64_t)sms / ntile, ceil_div(n, kTcRows)));
+  bt_rows = ceil_div(ceil_div(n, bt_splits), kTcRows) * kTcRows;
   bt_splits = (int)ceil_div(n, bt_rows);
+  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tc_per_sm, k_z_tc, kTcThreads,
+                                                         ApplyRing::kSmem),
+           "occupancy");
+  z_blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::max(1, tc_per_sm) * (int64_t)sms, ceil_div(n, kTile)));
+  ldr = ceil_div(n, kTcRows) * kTcRows;
   PC_CHECK(keep((void**)&tpart, (size_t)bt_splits * ld * 16 * sizeof(float)), "alloc B^T r");
   PC_CHECK(keep((void**)&tvec, (size_t)ld * 16 * sizeof(float)), "alloc t");
   PC_CHECK(keep((void**)&u, (size_t)3 * 16 * ld * sizeof(__nv_bfloat16)), "alloc u");
+  PC_CHECK(keep((void**)&r3, (size_t)3 * 16 * ldr * sizeof(__nv_bfloat16)), "alloc split r");
   PC_CHECK(keep((void**)&Minv, ll * sizeof(float)), "alloc Minv");
+  {  // TMA maps of the factor (as the K-major A of B u and the MN-major A of B^T r), of u
+     // and of the split r
+    const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    PC_MAP(tc05::make_map_2d(&map_b_k, bf, B, (uint64_t)n, (uint64_t)ld, (uint64_t)ld * 2, 128,
+                             kTcRows));
+    PC_MAP(tc05::make_map_2d(&map_b_mn, bf, B, (uint64_t)n, (uint64_t)ld, (uint64_t)ld * 2,
+                             kTcRows, kTcRows));
+    PC_MAP(tc05::make_map_2d(&map_u, bf, u, 48, (uint64_t)ld, (uint64_t)ld * 2, 48, kTcRows));
+    PC_MAP(tc05::make_map_2d(&map_r, bf, r3, 48, (uint64_t)n, (uint64_t)ldr * 2, 48, kTcRows));
+  }
   sgp_status s = ensure_lattice_values(L, kSketchCols, st);
   if (s != SGP_OK) return s;
 
   Dense dn{l, ld, st, status};
-  const unsigned g_panel = (unsigned)ceil_div((int64_t)n * ld, 256);
+  const unsigned g_plane = (unsigned)ceil_div((int64_t)n * ld, 256);
   const unsigned g_chunk = (unsigned)ceil_div((int64_t)n * kSketchCols, 256);
-  // dst = outputscale K src, column chunk by chunk (padding columns of dst: zero)
-  auto product = [&](const float* src, float* dst) -> sgp_status {
+  // dst = outputscale K src, column chunk by chunk (3-plane panels; padding columns of dst:
+  // zero)
+  auto product = [&](__nv_bfloat16* src, __nv_bfloat16* dst) -> sgp_status {
     for (int c0 = 0; c0 < ld; c0 += kSketchCols) {
-      k_copy_cols<<<g_chunk, 256, 0, st>>>(const_cast<float*>(src), ld, c0, Vc, kSketchCols, n,
-                                           false);
+      k_cols3<<<g_chunk, 256, 0, st>>>(src, ld, c0, Vc, kSketchCols, n, false);
       enqueue_mvm(L, Vc, kSketchCols, blur, L->outputscale, 0.f, KVc, st, nullptr,
                   /*internal=*/true);
-      k_copy_cols<<<g_chunk, 256, 0, st>>>(dst, ld, c0, KVc, kSketchCols, n, true);
+      k_cols3<<<g_chunk, 256, 0, st>>>(dst, ld, c0, KVc, kSketchCols, n, true);
       note_launches(2);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SGP_OK : cuda_status(e, "sketch products");
   };
-  // G = X^T Y (fp64 [ld][ld])
-  auto gram = [&](const float* X, const float* Y, double* out) {
-    k_gram_tc<<<dim3(ntile * (ntile + 1) / 2, splits), 256, 4 * kKc * kSMN * sizeof(float),
-                st>>>(X, ld, Y, ld, n, ntile, rows_per_split, ld, gpart);
+  // G = X^T Y (fp64 [ld][ld]) of two 3-plane panels, or (planes = 1) of bf16 panels
+  auto gram = [&](const void* X, const void* Y, int planes, double* out) -> sgp_status {
+    CUtensorMap mx, my;
+    PC_MAP(tc05::make_map_planes(&mx, X, planes, n, ld, ld, planes, 32));
+    PC_MAP(tc05::make_map_planes(&my, Y, planes, n, ld, ld, planes, 32));
+    if (planes == 3)
+      k_gram5<3><<<dim3(tiles, splits), kTcThreads, GramCfg<3>::Ring::kSmem, st>>>(
+          mx, my, n, rows_per_split, ld, gpart, err);
+    else
+      k_gram5<1><<<dim3(tiles, splits), kTcThreads, GramCfg<1>::Ring::kSmem, st>>>(
+          mx, my, n, rows_per_split, ld, gpart, err);
     k_sum_splits<<<(unsigned)ceil_div((int64_t)ll, 256), 256, 0, st>>>(gpart, splits, ld, out);
     note_launches(2);
+    return SGP_OK;
   };
-  // Z = Y X^T for the fp64 lower-triangular X (Z[r][j] = sum_i Y[r][i] X[j][i])
-  auto panel_times = [&](const float* Y, const double* X, float* Z) {
-    k_to_f32_pad<<<(unsigned)ceil_div((int64_t)ll, 256), 256, 0, st>>>(X, ld, l, ld, Tt);
-    k_panel_tc<<<dim3((unsigned)ceil_div(n, kTile), ntile), 256, 4 * kTile * kSK * sizeof(float),
-                 st>>>(Y, ld, Tt, ld, ld, /*lower=*/true, n, Z, ld);
+  // Z = Y X^T for the fp64 lower-triangular X (Z[r][j] = sum_i Y[r][i] X[j][i]): Y 3-plane,
+  // Z 3-plane, or rounded to bf16 when `round`
+  auto panel_times = [&](const __nv_bfloat16* Y, const double* X, void* Z, bool round)
+      -> sgp_status {
+    k_split3_pad<<<(unsigned)ceil_div((int64_t)ll, 256), 256, 0, st>>>(X, ld, l, ld, T3);
+    CUtensorMap my, mt;
+    PC_MAP(tc05::make_map_planes(&my, Y, 3, n, ld, ld, 3, 128));
+    PC_MAP(tc05::make_map_planes(&mt, T3, 3, ld, ld, ld, 3, 128));
+    const dim3 grid((unsigned)ceil_div(n, kTile), ntile);
+    if (round)
+      k_panel5<true><<<grid, kTcThreads, PanelCfg::Ring::kSmem, st>>>(
+          my, mt, n, ld, ld, /*lower=*/true, static_cast<__nv_bfloat16*>(Z), err);
+    else
+      k_panel5<false><<<grid, kTcThreads, PanelCfg::Ring::kSmem, st>>>(
+          my, mt, n, ld, ld, /*lower=*/true, static_cast<__nv_bfloat16*>(Z), err);
     note_launches(2);
+    return SGP_OK;
   };
   // Cholesky of the symmetrised out-of-place copy of src with a relative diagonal shift,
   // raised 100-fold (at most 4 times) while a pivot fails; the factor lands in dst.
@@ -1114,53 +1408,48 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
                "copy l x l");
       k_prepare_spd<<<1, 1024, 0, st>>>(dst, l, ld, 0.0, rel);
       note_launches(1);
-      cudaError_t err = cudaSuccess;
-      if (!dn.chol(dst, good, err)) return cuda_status(err, "Cholesky");
+      cudaError_t err_ = cudaSuccess;
+      if (!dn.chol(dst, good, err_)) return cuda_status(err_, "Cholesky");
     }
     return SGP_OK;
   };
 
   // 1. Q: the sketch, or an orthonormal basis of K Omega (Cholesky QR twice)
-  k_fill_sketch_panel<<<g_panel, 256, 0, st>>>(L->perm, n, l, ld, seed, P1);
+  k_fill_sketch3<<<g_plane, 256, 0, st>>>(L->perm, n, l, ld, seed, P1);
   note_launches(1);
-  float* Q = P1;
-  float* Y = P2;
+  __nv_bfloat16* Q = P1;
+  __nv_bfloat16* Y = P2;
+  if ((s = product(P1, P2)) != SGP_OK) return s;  // P2 = K Omega
   if (power_iters > 0) {
-    if ((s = product(P1, P2)) != SGP_OK) return s;  // P2 = K Omega
-    float* src = P2;
-    float* dst = P1;
+    __nv_bfloat16* src = P2;
+    __nv_bfloat16* dst = P1;
     for (int pass = 0; pass < 2; ++pass) {
       bool good = false;
-      gram(src, src, G0);
+      if ((s = gram(src, src, 3, G0)) != SGP_OK) return s;
       if ((s = robust_chol(G0, G, 1e-7, good)) != SGP_OK) return s;
       if (!good) return SGP_OK;  // ok stays false: the solve runs unpreconditioned
       PC_CHECK(dn.trtri(G, Xi), "triangular inverse");
-      panel_times(src, Xi, dst);  // dst = src R^-T
+      if ((s = panel_times(src, Xi, dst, false)) != SGP_OK) return s;  // dst = src R^-T
       std::swap(src, dst);
     }
-    Q = src;   // orthonormal basis (P2 after two passes)
+    Q = src;  // orthonormal basis (P2 after two passes)
     Y = dst;
     if ((s = product(Q, Y)) != SGP_OK) return s;
-  } else {
-    if ((s = product(P1, P2)) != SGP_OK) return s;
   }
-  // 2. C = Q^T Y, C = R R^T, B = Y R^-T
+  // 2. C = Q^T Y, C = R R^T, B = Y R^-T rounded to bf16 (the stored values define P)
   {
     bool good = false;
-    gram(Q, Y, G0);
+    if ((s = gram(Q, Y, 3, G0)) != SGP_OK) return s;
     if ((s = robust_chol(G0, G, 1e-6, good)) != SGP_OK) return s;
     if (!good) return SGP_OK;
     PC_CHECK(dn.trtri(G, Xi), "triangular inverse");
-    // the factor in fp32 in Q's panel (Q is no longer needed), then rounded to bf16: the
-    // stored values define P, and B^T B below is formed from them
-    panel_times(Y, Xi, Q);
-    k_round_bf16<<<g_panel, 256, 0, st>>>(Q, (int64_t)n * ld, static_cast<__nv_bfloat16*>(B));
-    note_launches(1);
+    if ((s = panel_times(Y, Xi, B, true)) != SGP_OK) return s;
   }
-  // 3. G = B^T B; lambda_min(G) by power iteration on G^-1; tau = lambda_min + noise
+  // 3. G = B^T B (exact products of the bf16 values); lambda_min(G) by power iteration on
+  // G^-1; tau = lambda_min + noise
   double lam_min = 0.0;
   {
-    gram(Q, Q, G0);
+    if ((s = gram(B, B, 1, G0)) != SGP_OK) return s;
     bool good = false;
     if ((s = robust_chol(G0, G, 1e-9, good)) != SGP_OK) return s;
     if (!good) return SGP_OK;
@@ -1195,9 +1484,11 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   }
   PC_CHECK(cudaGetLastError(), "building the preconditioner");
   PC_CHECK(cudaStreamSynchronize(st), "sync preconditioner");
+  if ((s = check(st)) != SGP_OK) return s;
   ok = true;
   return SGP_OK;
 #undef PC_CHECK
+#undef PC_MAP
 }
 
 int64_t ShiftedNystrom::dot_blocks() const { return ceil_div(n, kTile); }
@@ -1211,19 +1502,33 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
     // B^T r and z kernels are bracketed for the stage timings
     const bool mark = ev && c_off == 0;
     if (mark) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-    k_bt_bf16<<<dim3(ntile, bt_splits), 256, kApplyStages * kBtStageBytes, st>>>(
-        static_cast<const __nv_bfloat16*>(B), ld, rh, rl, k, c_off, kc, n, bt_rows, tpart);
+    k_split_r<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(rh, rl, k, c_off, kc, n, ldr,
+                                                         static_cast<__nv_bfloat16*>(r3));
+    k_bt_tc<<<dim3(ntile, bt_splits), kTcThreads, ApplyRing::kSmem, st>>>(map_b_mn, map_r, n, bt_rows,
+                                                                  tpart, err);
     if (mark) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     k_sum_t<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(tpart, bt_splits, ld, tvec);
     k_minv_u<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(
         Minv, ld, tvec, static_cast<__nv_bfloat16*>(u));
     if (mark) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    k_apply_z_bf16<<<(unsigned)ceil_div(n, kTile), 256, kApplyStages * kZStageBytes, st>>>(
-        static_cast<const __nv_bfloat16*>(B), ld, static_cast<const __nv_bfloat16*>(u), rh, rl,
-        k, c_off, kc, n, 1.f / tau, z, dot);
+    k_z_tc<<<z_blocks, kTcThreads, ApplyRing::kSmem, st>>>(map_b_k, map_u, rh, rl, k, c_off, kc, n, ld,
+                                                  1.f / tau, z, dot, err);
     if (mark) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
-    note_launches(4);
+    note_launches(5);
   }
+}
+
+sgp_status ShiftedNystrom::check(cudaStream_t st) const {
+  if (!err) return SGP_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "reading the preconditioner's error flag");
+  if (h) {
+    set_error("a preconditioner kernel gave up waiting for its tensor-memory copies");
+    return SGP_ERR_CUDA;
+  }
+  return SGP_OK;
 }
 
 void ShiftedNystrom::release(cudaStream_t st) {

@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a Simplex-GP library (not part of the C-ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -194,7 +195,7 @@ size_t lattice_value_bytes(const Lattice* L, int k);
 sgp_status run_mvm(Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                    float* out);
 
-// ---- rank-l Nystrom preconditioner of the CG (nystrom.cu) ----
+// ---- Nystrom preconditioners of the CG (server: nystrom.cu + serve.cu; library: precond.cu) ----
 constexpr int kMaxRank = 128;       // server requests (kb_* ring kernels)
 constexpr int kMaxLibRank = 4096;   // library CG (ShiftedNystrom)
 
@@ -213,8 +214,15 @@ struct ShiftedNystrom {
   float* tpart = nullptr;  // [bt_splits][ld][16] B^T r partials
   float* tvec = nullptr;   // [ld][16]
   void* u = nullptr;       // [3][16][ld] bf16: Minv B^T r split in three bf16 parts
+  void* r3 = nullptr;      // [3][16][ldr] bf16: r split in three bf16 parts, transposed
+  int* err = nullptr;      // set when a per-iteration kernel's bounded wait gave up
+  int64_t ldr = 0;         // n rounded up to 64
   int bt_splits = 0;
   int64_t bt_rows = 0;
+  int z_blocks = 0;
+  // TMA maps: B as [n][ld] in 128 x 64 boxes (A of B u) and 64 x 64 boxes (A of B^T r),
+  // u as [48][ld] and r3 as [48][n] in 48 x 64 boxes
+  CUtensorMap map_b_k, map_b_mn, map_u, map_r;
   std::vector<void*> ptrs;
   sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, int power_iters,
                    cudaStream_t st);
@@ -224,32 +232,8 @@ struct ShiftedNystrom {
   // dot[tile][c] (fp64)
   void apply(const float* rh, const float* rl, int k, float* z, double* dot, cudaStream_t st,
              cudaEvent_t* ev = nullptr) const;
-  void release(cudaStream_t st);
-};
-struct Nystrom {
-  int l = 0;
-  int ld = 0;                  // l rounded up to 4: row stride of Bh
-  int64_t n = 0;
-  float noise = 0.f;
-  bool ok = false;             // false when a Cholesky pivot failed (then not used)
-  void* Bh = nullptr;          // fp32 [n][ld] B = (A Omega + nu Omega) R^-T, locality order
-  double* partial = nullptr;   // per-block partial sums of the tall products
-  double* C = nullptr;         // [l][l] Omega^T Y, then its Cholesky factor R
-  double* Q = nullptr;         // [l][l] Cholesky factor of noise I + B^T B
-  double* Minv = nullptr;      // [l][l] (noise I + B^T B)^-1
-  float* T = nullptr;          // [l][l] R^-T
-  double* work = nullptr;
-  double* tvec = nullptr;      // [ld][k] B^T r
-  float* u = nullptr;          // [ld][k] (noise I + B^T B)^-1 B^T r, rows >= l zero
-  int* status = nullptr;
-  std::vector<void*> ptrs;
-  // Sketch, factor and keep B, Q for the handle's operator `blur` (enqueued on st, one
-  // synchronisation to read the factorisation status).
-  sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, cudaStream_t st);
-  // z = P^-1 r for r = rh + rl ([n][k], locality order), and the per-block column sums of
-  // r z into dot_partial ([dot_blocks][k]) with the CG's column-owning block shape.
-  void apply(const float* rh, const float* rl, int k, float* z, double* dot_partial,
-             int64_t dot_blocks, int block_threads, cudaStream_t st) const;
+  // SGP_ERR_CUDA when a per-iteration kernel gave up waiting (synchronizes st)
+  sgp_status check(cudaStream_t st) const;
   void release(cudaStream_t st);
 };
 
