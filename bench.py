@@ -741,6 +741,19 @@ def run_serving(count: int):
                            "mean_rel_l2_vs_fp32_max": float(np.max(errs)),
                            "mean_rel_l2_vs_fp32_max_bf16_requests":
                                float(max([e for e, k_ in zip(errs, kept) if k_] or [0.0]))}
+    # the same stream through one lane for all requests (lane_classes off): every round then
+    # runs the blur passes of the largest active d for every request
+    with Server(max_active=SERVING["max_active"], lane_classes=False) as srv:
+        res = run_stream(srv, reqs)
+        one = [tuple(a.copy() for a in srv.result(i)) for i in res.ids]
+        iters_one = [srv.stats(i)["iters"] for i in res.ids]
+    out["batched_one_lane"] = {
+        "solves_per_s": res.solves_per_s, "p50_s": res.percentile(50),
+        "p99_s": res.percentile(99), "makespan_s": res.makespan_s,
+        "cg_iters_mean": float(np.mean(iters_one)),
+        "identical_results_vs_lanes": bool(all(
+            np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+            for a, b in zip(results["batched"], one)))}
     # a stream the GPU keeps up with: 64 requests arriving at 5/s, so that p50/p99 measure
     # a request's own latency rather than queueing
     light = synth.serving_stream(64, SERVING["seed"] + 2, rate_per_s=5.0,
@@ -771,7 +784,7 @@ def run_serving(count: int):
                 "stream": "n log-uniform [5e3, 5e5], d uniform over {3, 8, 20, 50, 90}, "
                           "standardised 16-component GMM, y = sum sin(2 x) + N(0, 0.01), "
                           "%d test points, unit lengthscales, noise 0.01, k = 1 + 8 probes, "
-                          "tol 1e-3, max 500 iterations, rank-100 Nystrom preconditioner "
+                          "tol 1e-3, max 1000 iterations, rank-100 Nystrom preconditioner "
                           "(App. A) where the condition estimate is >= 1e3; generated in %.1f s"
                           % (SERVING["test_points"], gen_s),
                 "solves_per_s_ratio": out["batched"]["solves_per_s"] / out["plain"]["solves_per_s"],

@@ -84,12 +84,15 @@ typedef struct {
                          right-hand sides and solve, and serves at the fp32 accuracy.
                          Admission reserves the fp32 bound in either mode.               */
   double tol;         /* CG tolerance on ||r|| / ||b||; default 1e-3                      */
-  int max_iter;       /* CG iteration cap; default 500                                    */
+  int max_iter;       /* CG iteration cap; default 1000                                   */
   int check_every;    /* CG iterations per sgp_server_step between flag reads; default 8 */
   int precond_rank;   /* rank l of the Nystrom preconditioner, 0..128 (0 = none); default
                          100 (App. A)                                                     */
   double precond_min_kappa; /* precondition requests whose condition estimate kappa is at
                          least this; default 1e3 (0 = every request)                      */
+  int lane_classes;   /* 1 (default): lanes by dimension class, work class and value type;
+                         0: one lane per value type for all requests (every iteration round
+                         then runs the blur passes of the largest active d for all)       */
 } sgp_server_opts;
 
 typedef struct {

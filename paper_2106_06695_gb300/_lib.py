@@ -41,7 +41,7 @@ class sgp_server_opts(ctypes.Structure):
                 ("spacing_s", ctypes.c_double), ("value_dtype", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("precond_rank", ctypes.c_int),
-                ("precond_min_kappa", ctypes.c_double)]
+                ("precond_min_kappa", ctypes.c_double), ("lane_classes", ctypes.c_int)]
 
 
 class sgp_request(ctypes.Structure):

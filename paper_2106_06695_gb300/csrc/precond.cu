@@ -534,36 +534,72 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // 3D TMA loads (one box per operand tile covers all planes).
 
 // P3[.][p][j]: plane 0 = Omega[perm[p]][j] for j < l, 0 for l <= j < ld; planes 1, 2 = 0.
+// Eight columns per thread (16-byte stores).
 __global__ void k_fill_sketch3(const int32_t* __restrict__ perm, int64_t n, int l, int ld,
                                uint64_t seed, __nv_bfloat16* __restrict__ P3) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
   const int64_t plane = n * ld;
   if (e >= plane) return;
   const int64_t p = e / ld;
-  const int j = (int)(e - p * ld);
-  P3[e] = __float2bfloat16_rn(j < l ? sketch_sign(seed, perm[p], j, l) : 0.f);
-  P3[plane + e] = __float2bfloat16_rn(0.f);
-  P3[2 * plane + e] = __float2bfloat16_rn(0.f);
+  const int j0 = (int)(e - p * ld);
+  const int64_t ip = perm[p];
+  uint32_t w[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = j0 + 2 * c;
+    w[c] = pack2(__float2bfloat16_rn(j < l ? sketch_sign(seed, ip, j, l) : 0.f),
+                 __float2bfloat16_rn(j + 1 < l ? sketch_sign(seed, ip, j + 1, l) : 0.f));
+  }
+  *reinterpret_cast<uint4*>(P3 + e) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(P3 + plane + e) = make_uint4(0u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(P3 + 2 * plane + e) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // dense[p][c] = (x3 + x2) + x1 of panel column c0 + c (to_panel = false), or the split of
-// dense[p][c] into the panel's planes (to_panel = true); c < kc.
+// dense[p][c] into the panel's planes (to_panel = true); c < kc (a multiple of 8).  Eight
+// columns per thread (16-byte plane accesses, two float4 of dense).
 __global__ void k_cols3(__nv_bfloat16* __restrict__ P3, int ld, int c0, float* __restrict__ dense,
                         int kc, int64_t n, bool to_panel) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
   if (e >= n * kc) return;
   const int64_t p = e / kc;
   const int c = (int)(e - p * kc);
   const int64_t plane = n * ld, q = p * ld + c0 + c;
+  float4* d4 = reinterpret_cast<float4*>(dense + e);
   if (to_panel) {
-    __nv_bfloat16 a, b, d;
-    split3(dense[e], a, b, d);
-    P3[q] = a;
-    P3[plane + q] = b;
-    P3[2 * plane + q] = d;
+    const float4 x0 = d4[0], x1 = d4[1];
+    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    uint32_t w[3][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      __nv_bfloat16 a0, b0, g0, a1, b1, g1;
+      split3(x[2 * t], a0, b0, g0);
+      split3(x[2 * t + 1], a1, b1, g1);
+      w[0][t] = pack2(a0, a1);
+      w[1][t] = pack2(b0, b1);
+      w[2][t] = pack2(g0, g1);
+    }
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl)
+      *reinterpret_cast<uint4*>(P3 + pl * plane + q) =
+          make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
   } else {
-    dense[e] = (__bfloat162float(P3[2 * plane + q]) + __bfloat162float(P3[plane + q])) +
-               __bfloat162float(P3[q]);
+    const uint4 u0 = *reinterpret_cast<const uint4*>(P3 + q);
+    const uint4 u1 = *reinterpret_cast<const uint4*>(P3 + plane + q);
+    const uint4 u2 = *reinterpret_cast<const uint4*>(P3 + 2 * plane + q);
+    const uint32_t a[4] = {u0.x, u0.y, u0.z, u0.w}, b[4] = {u1.x, u1.y, u1.z, u1.w},
+                   g[4] = {u2.x, u2.y, u2.z, u2.w};
+    float x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int sh = (t & 1) * 16;
+      const float x1 = __uint_as_float(((a[t >> 1] >> sh) & 0xFFFFu) << 16);
+      const float x2 = __uint_as_float(((b[t >> 1] >> sh) & 0xFFFFu) << 16);
+      const float x3 = __uint_as_float(((g[t >> 1] >> sh) & 0xFFFFu) << 16);
+      x[t] = (x3 + x2) + x1;
+    }
+    d4[0] = make_float4(x[0], x[1], x[2], x[3]);
+    d4[1] = make_float4(x[4], x[5], x[6], x[7]);
   }
 }
 
@@ -712,8 +748,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Panel product Z[r][j] = sum_i Y[r][i] T[j][i] for i < kdim (with `lower`, T is lower
-// triangular and only i < j0 + 128 contributes), on the 128 x 128 tile (row tile
-// blockIdx.x, column tile blockIdx.y).  Y ([3][n][ld]) and T ([3][ld][ld]) are 3-plane,
+// triangular and only i < j0 + 128 contributes), on the 128 x 128 tile (column tile
+// blockIdx.x, row tile blockIdx.y; the two swapped when the row tiles exceed a grid's y
+// extent).  Y ([3][n][ld]) and T ([3][ld][ld]) are 3-plane,
 // both K-major (boxes 128 rows x 64 columns over the 3 planes).  ROUND = false: Z is
 // stored as 3 planes [3][n][ld]; ROUND = true: Z is stored rounded to bf16 [n][ld].
 struct PanelCfg {
@@ -724,14 +761,14 @@ struct PanelCfg {
 template <bool ROUND>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_panel5(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapT,
-             int64_t n, int ld, int kdim, bool lower, __nv_bfloat16* __restrict__ Z,
-             int* __restrict__ err) {
+             int64_t n, int ld, int kdim, bool lower, bool rows_in_y,
+             __nv_bfloat16* __restrict__ Z, int* __restrict__ err) {
   using Ring = PanelCfg::Ring;
   extern __shared__ uint8_t tc_raw[];
   const Ring R = tc_ring<Ring>(tc_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r0 = (int64_t)blockIdx.x * 128;
-  const int j0 = blockIdx.y * 128;
+  const int64_t r0 = (int64_t)(rows_in_y ? blockIdx.y : blockIdx.x) * 128;
+  const int j0 = (int)(rows_in_y ? blockIdx.x : blockIdx.y) * 128;
   const int64_t total = (lower ? min(kdim, j0 + 128) : kdim) / 64;
   constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 128, /*a_mn=*/false, /*b_mn=*/false);
   if (*reinterpret_cast<volatile int*>(err)) return;
@@ -847,29 +884,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) tc05::tmem_dealloc(tmem, 128);
 }
 
-// ---- l x l fp64 factorizations (row-major, leading dimension lda, size l) ---------------
-// (A + A^T) / 2 into the lower triangle, plus `shift` + rel * max_j A[j][j] on the
-// diagonal; the strict upper triangle is zeroed.  One block.
-__global__ void k_prepare_spd(double* __restrict__ A, int l, int lda, double shift,
-                              double rel) {
-  __shared__ double dmax;
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int j = 0; j < l; ++j) m = fmax(m, A[(size_t)j * lda + j]);
-    dmax = m;
-  }
+// dst = the lower triangle of (src + src^T) / 2 plus `shift` + rel * max_j src[j][j] on
+// the diagonal, strict upper triangle zero (l x l, leading dimension lda), and zero in the
+// rest of the lda x lda array; out of place, any grid (each block reads the diagonal for
+// the maximum).
+__global__ void __launch_bounds__(256) k_prepare_spd(const double* __restrict__ src,
+                                                     double* __restrict__ dst, int l, int lda,
+                                                     double shift, double rel) {
+  __shared__ double red[256];
+  double m = 0.0;
+  for (int j = threadIdx.x; j < l; j += blockDim.x) m = fmax(m, src[(size_t)j * lda + j]);
+  red[threadIdx.x] = m;
   __syncthreads();
-  const double sh = shift + rel * dmax;
-  for (int64_t e = threadIdx.x; e < (int64_t)l * l; e += blockDim.x) {
-    const int i = (int)(e / l), j = (int)(e % l);
-    if (i > j) A[(size_t)i * lda + j] = 0.5 * (A[(size_t)i * lda + j] + A[(size_t)j * lda + i]);
-    else if (i == j) A[(size_t)i * lda + j] += sh;
+  for (int h = blockDim.x / 2; h >= 1; h /= 2) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)l * l; e += blockDim.x) {
-    const int i = (int)(e / l), j = (int)(e % l);
-    if (j > i) A[(size_t)i * lda + j] = 0.0;
+  const double sh = shift + rel * red[0];
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)lda * lda) return;
+  const int i = (int)(e / lda), j = (int)(e % lda);
+  if (i >= l || j >= l) {
+    dst[e] = 0.0;
+    return;
   }
+  dst[e] = i > j ? 0.5 * (src[e] + src[(size_t)j * lda + i]) : (i == j ? src[e] + sh : 0.0);
 }
 
 // Cholesky of the diagonal block [kb, kb + nb): unblocked, in shared memory; *status = 1
@@ -1152,6 +1191,33 @@ __global__ void k_copy_shift(const double* __restrict__ src, double* __restrict_
 }  // namespace
 
 // ---- host side ----------------------------------------------------------------------------
+// Blocks of `func` (threads per block, dynamic shared bytes) that one SM holds at once,
+// from its registers, its static and dynamic shared memory (plus the per-block reserve)
+// and the SM's limits; at least 1.  (The runtime's occupancy query may assume a smaller
+// shared-memory carve-out than the one a launch gets.)
+static cudaError_t resident_blocks(const void* func, int threads, int dyn_smem, int dev,
+                                   int* out) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  int smem_sm = 0, reserve = 0, regs_sm = 0, threads_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (e != cudaSuccess) return e;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocation unit: 256
+  const int by_regs = regs_sm / std::max(1, regs_warp * warps);
+  const int by_smem = smem_sm / std::max(1, (int)fa.sharedSizeBytes + dyn_smem + reserve);
+  const int by_threads = threads_sm / std::max(1, threads);
+  *out = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_threads, 32)));
+  return cudaSuccess;
+}
+
 namespace {
 
 struct Dense {
@@ -1263,6 +1329,13 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
       PC_CHECK(cudaFuncSetAttribute(k_z_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     ApplyRing::kSmem),
                "k_z_tc smem");
+      // the largest shared-memory carve-out, so that two apply blocks share an SM
+      PC_CHECK(cudaFuncSetAttribute(k_bt_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cudaSharedmemCarveoutMaxShared),
+               "k_bt_tc carve-out");
+      PC_CHECK(cudaFuncSetAttribute(k_z_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cudaSharedmemCarveoutMaxShared),
+               "k_z_tc carve-out");
       attrs[dev].store(true);
     }
   }
@@ -1318,19 +1391,18 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   // per-iteration buffers.  B^T r: one wave of the blocks the device keeps resident (i
   // tiles x row splits of a multiple of 64 rows); z: one persistent block per resident slot
   int tc_per_sm = 0;
-  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tc_per_sm, k_bt_tc, kTcThreads,
-                                                         ApplyRing::kSmem),
+  PC_CHECK(resident_blocks(reinterpret_cast<const void*>(k_bt_tc), kTcThreads, ApplyRing::kSmem,
+                           dev_now, &tc_per_sm),
            "occupancy");
-  tc_per_sm = std::max(1, tc_per_sm);
   bt_splits = (int)std::max<int64_t>(
       1, std::min<int64_t>(tc_per_sm * (int64_t)sms / ntile, ceil_div(n, kTcRows)));
   bt_rows = ceil_div(ceil_div(n, bt_splits), kTcRows) * kTcRows;
   bt_splits = (int)ceil_div(n, bt_rows);
-  PC_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tc_per_sm, k_z_tc, kTcThreads,
-                                                         ApplyRing::kSmem),
+  PC_CHECK(resident_blocks(reinterpret_cast<const void*>(k_z_tc), kTcThreads, ApplyRing::kSmem,
+                           dev_now, &tc_per_sm),
            "occupancy");
-  z_blocks = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::max(1, tc_per_sm) * (int64_t)sms, ceil_div(n, kTile)));
+  z_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tc_per_sm * (int64_t)sms,
+                                                         ceil_div(n, kTile)));
   ldr = ceil_div(n, kTcRows) * kTcRows;
   PC_CHECK(keep((void**)&tpart, (size_t)bt_splits * ld * 16 * sizeof(float)), "alloc B^T r");
   PC_CHECK(keep((void**)&tvec, (size_t)ld * 16 * sizeof(float)), "alloc t");
@@ -1351,8 +1423,8 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   if (s != SGP_OK) return s;
 
   Dense dn{l, ld, st, status};
-  const unsigned g_plane = (unsigned)ceil_div((int64_t)n * ld, 256);
-  const unsigned g_chunk = (unsigned)ceil_div((int64_t)n * kSketchCols, 256);
+  const unsigned g_plane = (unsigned)ceil_div((int64_t)n * ld / 8, 256);
+  const unsigned g_chunk = (unsigned)ceil_div((int64_t)n * kSketchCols / 8, 256);
   // dst = outputscale K src, column chunk by chunk (3-plane panels; padding columns of dst:
   // zero)
   auto product = [&](__nv_bfloat16* src, __nv_bfloat16* dst) -> sgp_status {
@@ -1389,13 +1461,18 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     CUtensorMap my, mt;
     PC_MAP(tc05::make_map_planes(&my, Y, 3, n, ld, ld, 3, 128));
     PC_MAP(tc05::make_map_planes(&mt, T3, 3, ld, ld, ld, 3, 128));
-    const dim3 grid((unsigned)ceil_div(n, kTile), ntile);
+    // column tiles fastest: the tiles of one row block run together and read its rows
+    // of Y from L2 after the first
+    const int64_t row_tiles = ceil_div(n, kTile);
+    const dim3 grid = row_tiles <= 65535 ? dim3(ntile, (unsigned)row_tiles)
+                                         : dim3((unsigned)row_tiles, ntile);
+    const bool rows_in_y = row_tiles <= 65535;
     if (round)
       k_panel5<true><<<grid, kTcThreads, PanelCfg::Ring::kSmem, st>>>(
-          my, mt, n, ld, ld, /*lower=*/true, static_cast<__nv_bfloat16*>(Z), err);
+          my, mt, n, ld, ld, /*lower=*/true, rows_in_y, static_cast<__nv_bfloat16*>(Z), err);
     else
       k_panel5<false><<<grid, kTcThreads, PanelCfg::Ring::kSmem, st>>>(
-          my, mt, n, ld, ld, /*lower=*/true, static_cast<__nv_bfloat16*>(Z), err);
+          my, mt, n, ld, ld, /*lower=*/true, rows_in_y, static_cast<__nv_bfloat16*>(Z), err);
     note_launches(2);
     return SGP_OK;
   };
@@ -1404,9 +1481,8 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   auto robust_chol = [&](const double* src, double* dst, double rel, bool& good) -> sgp_status {
     good = false;
     for (int attempt = 0; attempt < 4 && !good; ++attempt, rel *= 100.0) {
-      PC_CHECK(cudaMemcpyAsync(dst, src, ll * sizeof(double), cudaMemcpyDeviceToDevice, st),
-               "copy l x l");
-      k_prepare_spd<<<1, 1024, 0, st>>>(dst, l, ld, 0.0, rel);
+      k_prepare_spd<<<(unsigned)ceil_div((int64_t)ll, 256), 256, 0, st>>>(src, dst, l, ld, 0.0,
+                                                                          rel);
       note_launches(1);
       cudaError_t err_ = cudaSuccess;
       if (!dn.chol(dst, good, err_)) return cuda_status(err_, "Cholesky");

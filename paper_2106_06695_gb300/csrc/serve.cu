@@ -1377,6 +1377,7 @@ void unit_counts(const sgp_server* S, const Request* R, int64_t (&vb)[U_KINDS]) 
 // type of its lattice (a BF16 server keeps fp32 values for ill-conditioned requests).
 int lane_key(const sgp_server* S, const Request* R) {
   const Lattice* L = R->L;
+  if (!S->o.lane_classes) return L->value_dtype == SGP_VALUES_BF16 ? 1 << 16 : 0;
   int dclass = 0;
   while ((4 << dclass) < L->D) ++dclass;
   const double work = ((double)L->m + (double)L->n) * L->D * S->kp + 2.0 * L->n * R->ld;
@@ -2060,10 +2061,11 @@ void sgp_server_opts_init(sgp_server_opts* o) {
   o->spacing_s = 0.0;
   o->value_dtype = SGP_VALUES_F32;
   o->tol = 1e-3;
-  o->max_iter = 500;
+  o->max_iter = 1000;
   o->check_every = 8;
   o->precond_rank = 100;
   o->precond_min_kappa = 1e3;
+  o->lane_classes = 1;
 }
 
 unsigned long long sgp_request_bytes_bound(long long n_points, int d, int order_r, int k,
@@ -2114,10 +2116,11 @@ sgp_status sgp_server_create(const sgp_server_opts* opts, sgp_server** out) {
       o.probes + 2 > kMaxServeK || o.order_r < 1 || o.order_r > kMaxOrder || o.max_iter < 0 ||
       !(o.tol >= 0.0) || o.check_every < 1 ||
       (o.value_dtype != SGP_VALUES_F32 && o.value_dtype != SGP_VALUES_BF16) ||
-      o.precond_rank < 0 || o.precond_rank > kMaxRank || !(o.precond_min_kappa >= 0.0)) {
+      o.precond_rank < 0 || o.precond_rank > kMaxRank || !(o.precond_min_kappa >= 0.0) ||
+      (o.lane_classes != 0 && o.lane_classes != 1)) {
     set_error("sgp_server_create: need 1 <= max_active <= 64, 0 <= probes <= 30, "
               "1 <= order_r <= 4, max_iter >= 0, tol >= 0, check_every >= 1, "
-              "0 <= precond_rank <= 128, precond_min_kappa >= 0");
+              "0 <= precond_rank <= 128, precond_min_kappa >= 0, lane_classes 0 or 1");
     return SGP_ERR_INVALID_ARG;
   }
   double sp, c[kMaxOrder + 1], g[kMaxOrder + 1];

@@ -36,8 +36,9 @@ class Server:
 
     def __init__(self, max_active: int = 16, probes: int = 8, hbm_budget: int | None = None,
                  order: int = 1, kernel: str = "rbf_binomial", value_dtype: str = "f32",
-                 tol: float = 1e-3, max_iter: int = 500, check_every: int = 8,
-                 precond_rank: int = 100, precond_min_kappa: float = 1e3):
+                 tol: float = 1e-3, max_iter: int = 1000, check_every: int = 8,
+                 precond_rank: int = 100, precond_min_kappa: float = 1e3,
+                 lane_classes: bool = True):
         self._lib = _lib.load()
         o = _lib.sgp_server_opts()
         self._lib.sgp_server_opts_init(ctypes.byref(o))
@@ -53,6 +54,7 @@ class Server:
         o.check_every = int(check_every)
         o.precond_rank = int(precond_rank)
         o.precond_min_kappa = float(precond_min_kappa)
+        o.lane_classes = 1 if lane_classes else 0
         self.opts = o
         h = ctypes.c_void_p()
         check(self._lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)))

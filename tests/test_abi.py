@@ -100,8 +100,8 @@ def test_request_bytes_bound_is_host_only_and_monotone(lib):
 def test_server_without_gpu_fails_loudly(lib):
     o = _lib.sgp_server_opts()
     lib.sgp_server_opts_init(ctypes.byref(o))
-    assert (o.max_active, o.probes, o.max_iter, o.check_every, o.hbm_budget) == (16, 8, 500, 8, 0)
-    assert (o.precond_rank, o.precond_min_kappa) == (100, 1e3)
+    assert (o.max_active, o.probes, o.max_iter, o.check_every, o.hbm_budget) == (16, 8, 1000, 8, 0)
+    assert (o.precond_rank, o.precond_min_kappa, o.lane_classes) == (100, 1e3, 1)
     h = ctypes.c_void_p()
     assert lib.sgp_server_create(ctypes.byref(o), ctypes.byref(h)) == 6
     assert not h.value

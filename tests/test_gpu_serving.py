@@ -138,6 +138,21 @@ def test_alone_equals_in_the_mix_bitwise(min_kappa):
         assert np.array_equal(m, m1) and np.array_equal(v, v1)
 
 
+def test_one_lane_for_all_dimensions_gives_identical_results():
+    """lane_classes off: requests of d = 3 .. 50 share one lane (one graph per round with
+    the largest active d's blur passes); each request's arithmetic is partitioned by its
+    own sizes, so its results are bitwise those of the lane-per-class server."""
+    reqs = small_requests(6, seed=31) + small_requests(2, seed=32, dims=(20, 50))
+    out = {}
+    for classes in (True, False):
+        with Server(max_active=8, lane_classes=classes) as srv:
+            ids = submit_all(srv, reqs)
+            srv.run_until_idle()
+            out[classes] = results(srv, ids)
+    for (m0, v0, i0), (m1, v1, i1) in zip(out[True], out[False]):
+        assert np.array_equal(m0, m1) and np.array_equal(v0, v1) and i0 == i1
+
+
 def test_stream_plain_and_batched_give_identical_results():
     reqs = small_requests(8, seed=12)
     out = {}
