@@ -130,30 +130,63 @@ __global__ void k_split_r(const float* __restrict__ rh, const float* __restrict_
 }
 
 // t[i][c] = sum over splits of tpart[s][i][c] (fp64 in split order, stored fp32), i < ld.
+// The loads of eight splits are issued together (they are independent) before their sums.
 __global__ void k_sum_t(const float* __restrict__ tpart, int splits, int ld,
                         float* __restrict__ t) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ld * 16) return;
+  const size_t stride = (size_t)ld * 16;
   double s = 0.0;
-  for (int q = 0; q < splits; ++q) s += (double)tpart[(size_t)q * ld * 16 + e];
+  for (int q0 = 0; q0 < splits; q0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = q0 + j < splits ? tpart[(q0 + j) * stride + e] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += (double)v[j];
+  }
   t[e] = (float)s;
 }
 
-// u[i][c] = sum_j Minv[i][j] t[j][c] (fp32), i < ld, c < 16; one thread per output.  Stored
-// split in three bf16 parts, transposed: u3[part][c][i] (the K-major [48][ld] operand).
-__global__ void k_minv_u(const float* __restrict__ Minv, int ld, const float* __restrict__ t,
-                         __nv_bfloat16* __restrict__ u3) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ld * 16) return;
-  const int i = e >> 4, c = e & 15;
+// u[i][c] = sum_j Minv[i][j] t[j][c] (fp32), i < ld, c < 16: one warp per row i, lane q
+// takes j = 32 q' + q (coalesced reads of the row), then a fixed butterfly over the lanes.
+// Stored split in three bf16 parts, transposed: u3[part][c][i] (the K-major [48][ld]
+// operand).
+__global__ void __launch_bounds__(256) k_minv_u(const float* __restrict__ Minv, int ld,
+                                                const float* __restrict__ t,
+                                                __nv_bfloat16* __restrict__ u3) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= ld) return;
   const float* row = Minv + (size_t)i * ld;
-  float s = 0.f;
-  for (int j = 0; j < ld; ++j) s = fmaf(row[j], t[j * 16 + c], s);
-  __nv_bfloat16 a, b, d;
-  split3(s, a, b, d);
-  u3[(size_t)(0 * 16 + c) * ld + i] = a;
-  u3[(size_t)(1 * 16 + c) * ld + i] = b;
-  u3[(size_t)(2 * 16 + c) * ld + i] = d;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int j = lane; j < ld; j += 32) {
+    const float m = row[j];
+    const float4* tj = reinterpret_cast<const float4*>(t + (size_t)j * 16);
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      const float4 v = tj[c4];
+      acc[4 * c4] = fmaf(m, v.x, acc[4 * c4]);
+      acc[4 * c4 + 1] = fmaf(m, v.y, acc[4 * c4 + 1]);
+      acc[4 * c4 + 2] = fmaf(m, v.z, acc[4 * c4 + 2]);
+      acc[4 * c4 + 3] = fmaf(m, v.w, acc[4 * c4 + 3]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  if (lane < 16) {
+    float sum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c == lane) sum = acc[c];
+    __nv_bfloat16 a, b, d;
+    split3(sum, a, b, d);
+    u3[(size_t)(0 * 16 + lane) * ld + i] = a;
+    u3[(size_t)(1 * 16 + lane) * ld + i] = b;
+    u3[(size_t)(2 * 16 + lane) * ld + i] = d;
+  }
 }
 
 // Block-wide pieces shared by the two kernels: barrier set-up, tensor-memory allocation and
@@ -1584,8 +1617,8 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
                                                                   tpart, err);
     if (mark) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     k_sum_t<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(tpart, bt_splits, ld, tvec);
-    k_minv_u<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(
-        Minv, ld, tvec, static_cast<__nv_bfloat16*>(u));
+    k_minv_u<<<(unsigned)ceil_div(ld, 8), 256, 0, st>>>(Minv, ld, tvec,
+                                                         static_cast<__nv_bfloat16*>(u));
     if (mark) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
     k_z_tc<<<z_blocks, kTcThreads, ApplyRing::kSmem, st>>>(map_b_k, map_u, rh, rl, k, c_off, kc, n, ld,
                                                   1.f / tau, z, dot, err);
