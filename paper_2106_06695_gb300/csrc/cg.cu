@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "sgp_internal.cuh"
+#include "values.cuh"
 
 namespace sgp {
 namespace {
@@ -37,6 +38,9 @@ struct CgState {
   // optional residual history: ||r_c|| / ||b_c|| after iteration j of column c at [j][k]
   double* hist;
   int hist_cap;
+  // optional: the preconditioner's split residual [n][64] (bf16; part p of column c < 16
+  // at 16 p + c), written by the x, r update
+  bf16* r3;
 };
 
 // VEC consecutive elements of a row: fp32 (one float4 when VEC = 4) and fp64 (two double2).
@@ -152,6 +156,8 @@ __global__ void k_cg_alpha(int nblk, int k, CgState S) {
 }
 
 // x += alpha p, r -= alpha A p on active columns (double-float); block partials of <r, r>.
+// With S.r3 (VEC = 4), also the three bf16 parts of r = rh + rl for columns 0..15, the
+// operand of the preconditioner's B^T r (as its split kernel would write them).
 template <int VEC>
 __global__ void k_cg_update_xr(float* __restrict__ xh, float* __restrict__ xl,
                                float* __restrict__ rh, float* __restrict__ rl,
@@ -193,6 +199,22 @@ __global__ void k_cg_update_xr(float* __restrict__ xh, float* __restrict__ xl,
     stf<VEC>(xl + e, xlv);
     stf<VEC>(rh + e, rhv);
     stf<VEC>(rl + e, rlv);
+    if constexpr (VEC == 4) {
+      if (S.r3 && c0 < 16) {
+        bf16 q[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split3(__fadd_rn(rhv[j], rlv[j]), q[j][0], q[j][1], q[j][2]);
+#pragma unroll
+        for (int part = 0; part < 3; ++part) {
+          uint2 w;
+          w.x = (uint32_t)__bfloat16_as_ushort(q[0][part]) |
+                ((uint32_t)__bfloat16_as_ushort(q[1][part]) << 16);
+          w.y = (uint32_t)__bfloat16_as_ushort(q[2][part]) |
+                ((uint32_t)__bfloat16_as_ushort(q[3][part]) << 16);
+          *reinterpret_cast<uint2*>(S.r3 + row * 64 + part * 16 + c0) = w;
+        }
+      }
+    }
   }
   double dd[VEC];
 #pragma unroll
@@ -441,6 +463,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     if (s != SGP_OK) return s;
     use_pre = cl.pre.ok;
     if (use_pre) CG_CHECK(get((void**)&z, n * k * sizeof(float)), "alloc z");
+    // the x, r update writes the split residual the preconditioner's B^T r reads
+    if (use_pre && vec == 4) S.r3 = static_cast<bf16*>(cl.pre.r3);
   }
 
   if (vec == 4)
@@ -469,7 +493,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     else k_cg_update_xr<1><<<vblocks, T, 0, st>>>(xh, xl, rh, rl, p, Ap, n, k, S);
     if (use_pre) {
       k_cg_check<<<k, 256, 0, st>>>(vblocks, k, tol, max_iter, S);
-      cl.pre.apply(rh, rl, k, z, S.partial, st, ev ? ev + 4 : nullptr);
+      cl.pre.apply(rh, rl, k, z, S.partial, st, ev ? ev + 4 : nullptr, S.r3 != nullptr);
       k_cg_beta_pcg<<<k, 256, 0, st>>>((int)cl.pre.dot_blocks(), k, S);
       if (vec == 4) k_cg_update_p_z<4, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);
       else k_cg_update_p_z<1, false><<<vblocks, T, 0, st>>>(p, z, n, k, S);

@@ -42,6 +42,7 @@
 
 #include "sgp_internal.cuh"
 #include "tc05.cuh"
+#include "values.cuh"
 
 namespace sgp {
 namespace {
@@ -86,15 +87,6 @@ __global__ void k_sum_splits(const float* __restrict__ partial, int splits, int 
 // Operand tiles arrive by TMA (128-byte swizzle) in a ring of kTcStages stages; one thread
 // issues the loads and the MMAs, four warps run the epilogue from tensor memory.
 //
-// x = x1 + x2 + x3 in bf16 (each part the nearest bf16 of what is left; the differences are
-// exact in fp32)
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
-                                       __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-}
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
@@ -102,30 +94,43 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
 constexpr int kTcStages = 4;
 constexpr int kTcRows = 64;                   // K rows (bt) or K columns (z) per stage
 constexpr int kTcBoxA = 128 * 128;            // bytes of a 128 x 64 bf16 operand tile
-constexpr int kTcBoxR = 48 * 128;             // bytes of the 48 x 64 bf16 split operand
-constexpr int kTcStage = kTcBoxA + kTcBoxR;   // 22 KB: a multiple of the 1 KB swizzle atom
+constexpr int kTcBoxU = 48 * 128;             // bytes of the 48 x 64 bf16 parts of u
+constexpr int kTcBoxR = 64 * 128;             // bytes of 64 rows of the split r ([n][64])
+constexpr int kTcStage = kTcBoxA + kTcBoxU;   // z: 22 KB (a multiple of the 1 KB atom)
+constexpr int kBtStage = kTcBoxA + kTcBoxR;   // B^T r: 24 KB
 constexpr long long kTcSpin = 1ll << 20;      // polls per bounded wait
 constexpr int kTcThreads = 160;               // warp 0: issue; warps 1-4: epilogue
 
-// r3[part * 16 + c][row] = part `part` of (rh + rl)[row][c_off + c] for c < kc (else 0):
-// the split right-hand side, K-major for the B^T r MMAs (row stride ldr >= n).
+// r3[row][part * 16 + c] = part `part` of (rh + rl)[row][c_off + c] for c < kc (else 0):
+// the split right-hand side as rows of 64 bf16 (columns 48..63 stay zero), MN-major for
+// the B^T r MMAs.  One row per thread, 16-byte stores.  (The CG's x, r update writes the
+// first 16 columns' split itself; this kernel serves the CG start and further chunks.)
 __global__ void k_split_r(const float* __restrict__ rh, const float* __restrict__ rl, int k,
-                          int c_off, int kc, int64_t n, int64_t ldr,
-                          __nv_bfloat16* __restrict__ r3) {
+                          int c_off, int kc, int64_t n, __nv_bfloat16* __restrict__ r3) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
+  uint32_t w[3][8];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    float x = 0.f;
-    if (c < kc) {
-      const int64_t e = row * k + c_off + c;
-      x = __fadd_rn(rh[e], rl[e]);
+  for (int c2 = 0; c2 < 8; ++c2) {
+    __nv_bfloat16 p[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = 2 * c2 + h;
+      float x = 0.f;
+      if (c < kc) {
+        const int64_t e = row * k + c_off + c;
+        x = __fadd_rn(rh[e], rl[e]);
+      }
+      split3(x, p[h][0], p[h][1], p[h][2]);
     }
-    __nv_bfloat16 a, b, d;
-    split3(x, a, b, d);
-    r3[(int64_t)(0 * 16 + c) * ldr + row] = a;
-    r3[(int64_t)(1 * 16 + c) * ldr + row] = b;
-    r3[(int64_t)(2 * 16 + c) * ldr + row] = d;
+#pragma unroll
+    for (int part = 0; part < 3; ++part) w[part][c2] = pack2(p[0][part], p[1][part]);
+  }
+  uint4* o = reinterpret_cast<uint4*>(r3 + row * 64);
+#pragma unroll
+  for (int part = 0; part < 3; ++part) {
+    o[2 * part] = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
+    o[2 * part + 1] = make_uint4(w[part][4], w[part][5], w[part][6], w[part][7]);
   }
 }
 
@@ -266,24 +271,26 @@ __device__ __forceinline__ void tc_drain(const Ring& R, int64_t landed, int64_t 
   if (committed >= 0)
     (void)tc05::mbar_wait(R.empty_of(committed), Ring::parity(committed), kTcSpin);
 }
-using ApplyRing = TcRing<kTcStages, kTcStage>;
+using ApplyRing = TcRing<kTcStages, kTcStage>;  // z
+using BtRing = TcRing<kTcStages, kBtStage>;       // B^T r
 
 // Per-iteration B^T r for 16 columns of r (split in r3): tpart[s][i][c] = sum over the rows
 // of split s (blockIdx.y) of B[row][i] r[row][c], i in the 128-column tile blockIdx.x.
-// A = B^T is MN-major: the TMA boxes of B are 64 rows (K) x 64 columns (M), two per stage
-// (columns i0 .. + 63, i0 + 64 .. + 127: leading offset 8 KB); r3 boxes are 48 x 64 K-major.
+// Both operands are MN-major: the TMA boxes of B are 64 rows (K) x 64 columns (M), two per
+// stage (columns i0 .. + 63, i0 + 64 .. + 127: leading offset 8 KB); the box of r3 is 64
+// rows x its 64 columns (N = 64: the three 16-column parts and 16 zero columns).
 // rows_per_split is a multiple of 64; rows >= n read as zero.
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_bt_tc(const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ CUtensorMap mapR,
             int64_t n, int64_t rows_per_split, float* __restrict__ tpart, int* __restrict__ err) {
   extern __shared__ uint8_t tc_raw[];
-  const ApplyRing R = tc_ring<ApplyRing>(tc_raw);
+  const BtRing R = tc_ring<BtRing>(tc_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.x * 128;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
   const int64_t r_end = std::min<int64_t>(n, r_begin + rows_per_split);
   const int64_t total = r_end > r_begin ? ceil_div(r_end - r_begin, kTcRows) : 0;
-  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 48, /*a_mn=*/true, /*b_mn=*/false);
+  constexpr uint32_t kIdesc = tc05::idesc_bf16(128, 64, /*a_mn=*/true, /*b_mn=*/true);
   if (*reinterpret_cast<volatile int*>(err)) return;  // an earlier launch gave up: skip
   if (threadIdx.x == 0) {
     tc05::prefetch_map(&mapBt);
@@ -296,37 +303,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int64_t issued = 0, landed = 0, committed = -1;
       auto issue = [&](int64_t g) {
-        uint8_t* st = R.stage + (g % kTcStages) * kTcStage;
+        uint8_t* st = R.at(g);
         const int row0 = (int)(r_begin + g * kTcRows);
-        tc05::mbar_expect_tx(&R.full[g % kTcStages], kTcStage);
-        tc05::tma_load_2d(st, &mapBt, i0, row0, &R.full[g % kTcStages]);
-        tc05::tma_load_2d(st + kTcBoxA / 2, &mapBt, i0 + 64, row0, &R.full[g % kTcStages]);
-        tc05::tma_load_2d(st + kTcBoxA, &mapR, row0, 0, &R.full[g % kTcStages]);
+        tc05::mbar_expect_tx(R.full_of(g), kBtStage);
+        tc05::tma_load_2d(st, &mapBt, i0, row0, R.full_of(g));
+        tc05::tma_load_2d(st + kTcBoxA / 2, &mapBt, i0 + 64, row0, R.full_of(g));
+        tc05::tma_load_2d(st + kTcBoxA, &mapR, 0, row0, R.full_of(g));
         issued = g + 1;
       };
       for (int64_t g = 0; g < total && g < kTcStages; ++g) issue(g);
       bool ok = true;
       for (int64_t g = 0; g < total; ++g) {
-        const int s = (int)(g % kTcStages);
-        if (!tc05::mbar_wait(&R.full[s], (uint32_t)(g / kTcStages) & 1u, kTcSpin, abort)) {
+        if (!tc05::mbar_wait(R.full_of(g), BtRing::parity(g), kTcSpin, abort)) {
           ok = false;
           break;
         }
         landed = g + 1;
         tc05::fence_after_sync();
-        const uint32_t a0 = tc05::smem_u32(R.stage + s * kTcStage), b0 = a0 + kTcBoxA;
+        const uint32_t a0 = tc05::smem_u32(R.at(g)), b0 = a0 + kTcBoxA;
 #pragma unroll
         for (int kk = 0; kk < kTcRows / 16; ++kk)
           tc05::mma_bf16(tmem, tc05::desc_sw128(a0 + kk * 2048, kTcBoxA / 2, 1024),
-                         tc05::desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                         tc05::desc_sw128(b0 + kk * 2048, kTcBoxR, 1024), kIdesc,
                          (g | kk) ? 1u : 0u);
-        tc05::mma_commit(&R.empty[s]);
+        tc05::mma_commit(R.empty_of(g));
         committed = g;
         // refill the previous chunk's stage once its MMAs are done
         if (g >= 1 && g - 1 + kTcStages < total) {
           const int64_t p = g - 1;
-          if (!tc05::mbar_wait(&R.empty[p % kTcStages], (uint32_t)(p / kTcStages) & 1u, kTcSpin,
-                               abort)) {
+          if (!tc05::mbar_wait(R.empty_of(p), BtRing::parity(p), kTcSpin, abort)) {
             ok = false;
             break;
           }
@@ -1357,7 +1362,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
                                     PanelCfg::Ring::kSmem),
                "k_panel5 smem");
       PC_CHECK(cudaFuncSetAttribute(k_bt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    ApplyRing::kSmem),
+                                    BtRing::kSmem),
                "k_bt_tc smem");
       PC_CHECK(cudaFuncSetAttribute(k_z_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     ApplyRing::kSmem),
@@ -1424,7 +1429,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   // per-iteration buffers.  B^T r: one wave of the blocks the device keeps resident (i
   // tiles x row splits of a multiple of 64 rows); z: one persistent block per resident slot
   int tc_per_sm = 0;
-  PC_CHECK(resident_blocks(reinterpret_cast<const void*>(k_bt_tc), kTcThreads, ApplyRing::kSmem,
+  PC_CHECK(resident_blocks(reinterpret_cast<const void*>(k_bt_tc), kTcThreads, BtRing::kSmem,
                            dev_now, &tc_per_sm),
            "occupancy");
   bt_splits = (int)std::max<int64_t>(
@@ -1440,7 +1445,8 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   PC_CHECK(keep((void**)&tpart, (size_t)bt_splits * ld * 16 * sizeof(float)), "alloc B^T r");
   PC_CHECK(keep((void**)&tvec, (size_t)ld * 16 * sizeof(float)), "alloc t");
   PC_CHECK(keep((void**)&u, (size_t)3 * 16 * ld * sizeof(__nv_bfloat16)), "alloc u");
-  PC_CHECK(keep((void**)&r3, (size_t)3 * 16 * ldr * sizeof(__nv_bfloat16)), "alloc split r");
+  PC_CHECK(keep((void**)&r3, (size_t)ldr * 64 * sizeof(__nv_bfloat16)), "alloc split r");
+  PC_CHECK(cudaMemsetAsync(r3, 0, (size_t)ldr * 64 * sizeof(__nv_bfloat16), st), "clear split r");
   PC_CHECK(keep((void**)&Minv, ll * sizeof(float)), "alloc Minv");
   {  // TMA maps of the factor (as the K-major A of B u and the MN-major A of B^T r), of u
      // and of the split r
@@ -1450,7 +1456,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     PC_MAP(tc05::make_map_2d(&map_b_mn, bf, B, (uint64_t)n, (uint64_t)ld, (uint64_t)ld * 2,
                              kTcRows, kTcRows));
     PC_MAP(tc05::make_map_2d(&map_u, bf, u, 48, (uint64_t)ld, (uint64_t)ld * 2, 48, kTcRows));
-    PC_MAP(tc05::make_map_2d(&map_r, bf, r3, 48, (uint64_t)n, (uint64_t)ldr * 2, 48, kTcRows));
+    PC_MAP(tc05::make_map_2d(&map_r, bf, r3, (uint64_t)n, 64, 128, kTcRows, 64));
   }
   sgp_status s = ensure_lattice_values(L, kSketchCols, st);
   if (s != SGP_OK) return s;
@@ -1603,7 +1609,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
 int64_t ShiftedNystrom::dot_blocks() const { return ceil_div(n, kTile); }
 
 void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, double* dot,
-                           cudaStream_t st, cudaEvent_t* ev) const {
+                           cudaStream_t st, cudaEvent_t* ev, bool split_ready) const {
   const int ntile = ld / kTile;
   for (int c_off = 0; c_off < k; c_off += 16) {
     const int kc = std::min(16, k - c_off);
@@ -1611,9 +1617,12 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
     // B^T r and z kernels are bracketed for the stage timings
     const bool mark = ev && c_off == 0;
     if (mark) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-    k_split_r<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(rh, rl, k, c_off, kc, n, ldr,
-                                                         static_cast<__nv_bfloat16*>(r3));
-    k_bt_tc<<<dim3(ntile, bt_splits), kTcThreads, ApplyRing::kSmem, st>>>(map_b_mn, map_r, n, bt_rows,
+    if (!(split_ready && c_off == 0)) {
+      k_split_r<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(rh, rl, k, c_off, kc, n,
+                                                           static_cast<__nv_bfloat16*>(r3));
+      note_launches(1);
+    }
+    k_bt_tc<<<dim3(ntile, bt_splits), kTcThreads, BtRing::kSmem, st>>>(map_b_mn, map_r, n, bt_rows,
                                                                   tpart, err);
     if (mark) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     k_sum_t<<<(unsigned)ceil_div(ld * 16, 256), 256, 0, st>>>(tpart, bt_splits, ld, tvec);
@@ -1623,7 +1632,7 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
     k_z_tc<<<z_blocks, kTcThreads, ApplyRing::kSmem, st>>>(map_b_k, map_u, rh, rl, k, c_off, kc, n, ld,
                                                   1.f / tau, z, dot, err);
     if (mark) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
-    note_launches(5);
+    note_launches(4);
   }
 }
 

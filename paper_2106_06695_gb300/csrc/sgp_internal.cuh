@@ -214,14 +214,15 @@ struct ShiftedNystrom {
   float* tpart = nullptr;  // [bt_splits][ld][16] B^T r partials
   float* tvec = nullptr;   // [ld][16]
   void* u = nullptr;       // [3][16][ld] bf16: Minv B^T r split in three bf16 parts
-  void* r3 = nullptr;      // [3][16][ldr] bf16: r split in three bf16 parts, transposed
+  void* r3 = nullptr;      // [ldr][64] bf16: r split in three bf16 parts (columns 16 p + c
+                           // hold part p of column c; 48..63 zero)
   int* err = nullptr;      // set when a per-iteration kernel's bounded wait gave up
   int64_t ldr = 0;         // n rounded up to 64
   int bt_splits = 0;
   int64_t bt_rows = 0;
   int z_blocks = 0;
   // TMA maps: B as [n][ld] in 128 x 64 boxes (A of B u) and 64 x 64 boxes (A of B^T r),
-  // u as [48][ld] and r3 as [48][n] in 48 x 64 boxes
+  // u as [48][ld] in 48 x 64 boxes and r3 as [n][64] in 64 x 64 boxes
   CUtensorMap map_b_k, map_b_mn, map_u, map_r;
   std::vector<void*> ptrs;
   sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, int power_iters,
@@ -229,9 +230,10 @@ struct ShiftedNystrom {
   // partial rows apply() writes per column: one per 128-row tile
   int64_t dot_blocks() const;
   // z = P^-1 r (r = rh + rl, locality order [n][k]) and per-tile column sums of r z into
-  // dot[tile][c] (fp64)
+  // dot[tile][c] (fp64).  split_ready: r3 already holds the split of columns 0..15 of r
+  // (written by the CG's x, r update).
   void apply(const float* rh, const float* rl, int k, float* z, double* dot, cudaStream_t st,
-             cudaEvent_t* ev = nullptr) const;
+             cudaEvent_t* ev = nullptr, bool split_ready = false) const;
   // SGP_ERR_CUDA when a per-iteration kernel gave up waiting (synchronizes st)
   sgp_status check(cudaStream_t st) const;
   void release(cudaStream_t st);

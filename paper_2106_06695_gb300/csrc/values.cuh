@@ -76,6 +76,16 @@ struct Store<bf16> {
   static __device__ __forceinline__ void st1(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// x = x1 + x2 + x3 in bf16 (each part the nearest bf16 of what is left; the differences are
+// exact in fp32): about 24 significant bits, the three-part operands of the bf16 tensor-core
+// products.
+__device__ __forceinline__ void split3(float x, bf16& a, bf16& b, bf16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
 // ---- fp32 register vectors of VEC = 4 or 1 columns ----------------------------------
 template <int VEC>
 struct Vec;
