@@ -412,7 +412,7 @@ def run_ours(args, world, rank, local):
         "blur_pass": m * (8 * k + 8 * r_),
         "splat": 8 * n * D + 4 * n * k + 4 * m * k,
         "slice_dot": 8 * n * D + 4 * m * k + 8 * n * k,
-        "precond_bt": 2 * n * ld + 8 * n * min(k, 16),   # bf16 B once, r = rh + rl once
+        "precond_bt": 2 * n * ld + 128 * n,   # bf16 B once, the split r ([n][64] bf16) once
         "precond_z": 2 * n * ld + 12 * n * min(k, 16),   # bf16 B once, r read, z written
     }
     stage_ms = {  # average duration of one launch
@@ -439,7 +439,7 @@ def run_ours(args, world, rank, local):
         dom = "blur_pass"
     names = {"blur_pass": "k_blur_rows<2,2,1,float> (one lattice direction)",
              "splat": "k_splat<4,float> (+ fix-ups)", "slice_dot": "k_slice_dot<4,float>",
-             "precond_bt": "k_split_r + k_bt_tc (preconditioner B^T r, tcgen05 bf16, TMA)",
+             "precond_bt": "k_bt_tc (preconditioner B^T r, tcgen05 bf16, TMA)",
              "precond_z": "k_z_tc (preconditioner z = (r - B u)/tau, tcgen05 bf16, TMA)"}
     ds = stages.get(dom, {})
     traffic = blur_traffic_per_launch(m, k) if dom == "blur_pass" else stage_traffic(dom)

@@ -324,6 +324,14 @@ sgp_status sgp_profile_read_stages(const sgp_lattice* h, double* stage_ms, int64
  * counts each of its kernels), for launch accounting in benchmarks. */
 int64_t sgp_kernel_launches(void);
 
+/* Device memory: the library allocates its work space and handle arrays stream-ordered
+ * from a memory pool of its own per device, which keeps the blocks freed by a finished call
+ * mapped so that the next build, product or solve reuses them (at n = 2M a preconditioner
+ * set-up frees and re-takes about 30 GB; mapping it afresh cost 65 ms per solve).
+ * sgp_trim_memory synchronizes the current device and returns every unused pooled block of
+ * it to the driver.  SGP_ERR_CUDA without a device. */
+sgp_status sgp_trim_memory(void);
+
 /* Release the handle and every device array it owns (stream-ordered on its stream). */
 void sgp_lattice_free(sgp_lattice* h);
 

@@ -9,7 +9,7 @@ from ._lib import SGPError  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Lattice", "lattice_mvm"):
+    if name in ("Lattice", "lattice_mvm", "trim_memory"):
         from . import lattice
 
         return getattr(lattice, name)

@@ -114,6 +114,7 @@ def load():
         "sgp_profile_read": (I, [P, ctypes.POINTER(Dbl), ctypes.POINTER(I64)]),
         "sgp_profile_read_stages": (I, [P, P, ctypes.POINTER(I64)]),
         "sgp_kernel_launches": (I64, []),
+        "sgp_trim_memory": (I, []),
         "sgp_last_error": (ctypes.c_char_p, []),
         "sgp_version": (I, []),
         "sgp_server_opts_init": (None, [ctypes.POINTER(sgp_server_opts)]),

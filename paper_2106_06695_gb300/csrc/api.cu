@@ -1,6 +1,7 @@
 // C-ABI entry points of the lattice library (declared in include/sgp.h): argument
 // validation, handle lifetime and error reporting around the build, MVM and CG paths.
 #include <atomic>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -29,6 +30,37 @@ NvtxRange::~NvtxRange() { nvtxRangePop(); }
 namespace {
 thread_local std::string g_last_error;
 std::atomic<int64_t> g_launches{0};
+
+// The library's stream-ordered memory pool per device: freed blocks stay mapped (release
+// threshold: all of them) so that the next build or solve reuses them instead of mapping
+// fresh pages; sgp_trim_memory returns them.
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kPoolDevices] = {};
+
+cudaError_t pool_of(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      (void)cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pools[dev] = p;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
 
 bool have_device() {
   int count = 0;
@@ -71,6 +103,15 @@ void clear_pending_error() {
 }
 
 void note_launches(int64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) e = pool_of(dev, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
@@ -183,7 +224,7 @@ sgp_status sgp_lattice_build(const float* X, const float* lengthscales, int64_t 
     set_error("sgp_lattice_build: kernel must be an SGP_KERNEL_* value and 1 <= order_r <= 4");
     return SGP_ERR_INVALID_ARG;
   }
-  cudaError_t e = cudaMallocAsync((void**)&L->err, sizeof(unsigned), L->stream);
+  cudaError_t e = dev_malloc((void**)&L->err, sizeof(unsigned), L->stream);
   if (e != cudaSuccess) {
     delete L;
     return cuda_status(e, "sgp_lattice_build: allocating the error word");
@@ -394,6 +435,17 @@ sgp_status sgp_profile_read(const sgp_lattice* h, double* blur_ms, int64_t* blur
 }
 
 int64_t sgp_kernel_launches(void) { return launches_so_far(); }
+
+sgp_status sgp_trim_memory(void) {
+  clear_pending_error();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) e = pool_of(dev, &pool);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  return e == cudaSuccess ? SGP_OK : cuda_status(e, "sgp_trim_memory");
+}
 
 const char* sgp_last_error(void) { return g_last_error.c_str(); }
 

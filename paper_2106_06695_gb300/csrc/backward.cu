@@ -203,7 +203,7 @@ struct Work {
   }
   template <class T>
   cudaError_t get(T** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync((void**)p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc((void**)p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) ptrs.push_back((void*)*p);
     return e;
   }

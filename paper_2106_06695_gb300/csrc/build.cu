@@ -519,7 +519,7 @@ __global__ void k_row_ptr(const uint32_t* __restrict__ sorted_ids, int64_t nD, i
 // ---------------------------------------------------------------------------------
 template <class T>
 cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
-  return cudaMallocAsync((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
+  return dev_malloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), st);
 }
 
 struct Temps {

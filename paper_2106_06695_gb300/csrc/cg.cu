@@ -396,7 +396,7 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
     }
   } cl{st, own, {}};
   auto get = [&](void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) cl.ptrs.push_back(*p);
     return e;
   };

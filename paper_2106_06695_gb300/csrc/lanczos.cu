@@ -118,7 +118,7 @@ sgp_status run_logdet(Lattice* L, const float* Z, int s, float noise, int max_la
     }
   } b{st, {}};
   auto get = [&](void** x, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(x, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc(x, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) b.p.push_back(*x);
     return e;
   };

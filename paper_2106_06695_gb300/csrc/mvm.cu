@@ -597,7 +597,7 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
     if (L->act_tmp) cudaFreeAsync(L->act_tmp, st);
     L->act_tmp = nullptr;
     const size_t bytes = std::max<size_t>((size_t)L->act_max * k * value_size(L), 16);
-    cudaError_t e = cudaMallocAsync(&L->act_tmp, bytes, st);
+    cudaError_t e = dev_malloc(&L->act_tmp, bytes, st);
     if (e != cudaSuccess) return cuda_status(e, "allocating the sparse blur buffer");
     L->act_tmp_elems = (size_t)L->act_max * k;
   }
@@ -617,7 +617,7 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st) {
   const size_t sizes[4] = {vbytes, vbytes, (size_t)L->nslots * k * sizeof(float),
                            (size_t)L->n * k * sizeof(float)};
   for (int b = 0; b < 4; ++b) {
-    cudaError_t e = cudaMallocAsync(bufs[b], std::max<size_t>(sizes[b], 16), st);
+    cudaError_t e = dev_malloc(bufs[b], std::max<size_t>(sizes[b], 16), st);
     if (e != cudaSuccess) return cuda_status(e, "allocating lattice values");
   }
   L->lat_elems = (size_t)L->m * k;

@@ -1335,12 +1335,12 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     }
   } free_temps{temps, st};
   auto keep = [&](void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   };
   auto temp = [&](void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) temps.push_back(*p);
     return e;
   };

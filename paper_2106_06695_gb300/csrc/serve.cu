@@ -1418,7 +1418,7 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
   const int64_t n_all = in.n + in.ns;
   const int d = in.d, kp = S->kp;
   auto get = [&](void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 16), st);
     if (e == cudaSuccess) R->ptrs.push_back(*p);
     return e;
   };
@@ -1429,7 +1429,7 @@ sgp_status setup(sgp_server* S, Request* R, cudaStream_t st, Table& t1) {
       for (void* x : p) (void)cudaFreeAsync(x, st);
     }
     cudaError_t get(void** x, size_t bytes) {
-      cudaError_t e = cudaMallocAsync(x, std::max<size_t>(bytes, 16), st);
+      cudaError_t e = dev_malloc(x, std::max<size_t>(bytes, 16), st);
       if (e == cudaSuccess) p.push_back(*x);
       return e;
     }

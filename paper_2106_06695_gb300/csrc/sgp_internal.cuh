@@ -137,6 +137,9 @@ void clear_pending_error();
 // Count kernels enqueued by this library (graph replays count every kernel node).
 void note_launches(int64_t count);
 int64_t launches_so_far();
+// Stream-ordered device allocation from the library's pool on the current device (freed
+// with cudaFreeAsync; freed blocks stay mapped for reuse until sgp_trim_memory).
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t st);
 
 // ---- stencils (stencil.cpp) ----
 // Spacing s and taps c[0..r] (kernel values k(t s)) and g[0..r] (half-kernel taps).

@@ -247,3 +247,9 @@ def lattice_mvm(X: torch.Tensor, lengthscales: torch.Tensor, V: torch.Tensor, or
         lengthscales = torch.full((X.shape[1],), float(lengthscales), dtype=torch.float32,
                                   device=X.device)
     return _LatticeMVM.apply(X, lengthscales, V, order, kernel, blur, alpha, grad, value_dtype)
+
+
+def trim_memory() -> None:
+    """Return the library's unused pooled device blocks on the current device to the driver
+    (sgp_trim_memory; the pool otherwise keeps freed blocks mapped for the next call)."""
+    check(_lib.load().sgp_trim_memory())

@@ -3,8 +3,9 @@
 The sketch is the same counter-based Rademacher matrix on both sides and the subspace
 iteration reaches the same subspace (the GPU orthonormalises by Cholesky QR, the oracle
 by Householder QR; the approximation depends only on the subspace).  The GPU forms the
-factor in fp32 with tensor-core products and estimates the smallest captured eigenvalue
-by inverse power iteration, the oracle takes it from a dense eigensolver, so the two
+factor from three-part bf16 panels with tensor-core (tcgen05) products, stores it rounded
+to bf16, and estimates the smallest captured eigenvalue by inverse power iteration; the
+oracle keeps it in fp64 and takes the eigenvalue from a dense eigensolver, so the two
 preconditioners differ slightly and the iterates are compared through what does not
 depend on that: each solve reaches its tolerance, the true residual of the GPU's answer
 under the oracle's FP64 operator is within 1.5 x tol, and the iteration counts stay close
@@ -67,3 +68,22 @@ def test_pcg_rank_validation_and_noise_free_fallback():
     # noise 0: the preconditioner needs noise > 0, the solve runs unpreconditioned
     _, it, rel = lat.cg(B, noise=0.0, tol=1e-2, max_iter=50)
     assert (it >= 1).all() and np.isfinite(rel).all()
+
+
+def test_pooled_memory_is_reused_and_trimmed():
+    """The library's pool keeps the blocks a solve frees; a second solve on the same handle
+    gives bitwise the same answer, and so does one after the pool is trimmed."""
+    from paper_2106_06695_gb300.lattice import Lattice, trim_memory
+
+    n, d, k = 30000, 5, 8
+    X = gpu(synth.gmm_points(n, d, 41))
+    B = gpu(synth.gaussian_values(n, k, 41))
+    lat = Lattice(X, gpu(np.ones(d, np.float32)), precond_rank=128, precond_seed=3)
+    x1, it1, _ = lat.cg(B, noise=0.01, tol=1e-4, max_iter=300)
+    x2, it2, _ = lat.cg(B, noise=0.01, tol=1e-4, max_iter=300)
+    trim_memory()
+    x3, it3, _ = lat.cg(B, noise=0.01, tol=1e-4, max_iter=300)
+    assert torch.equal(x1, x2) and torch.equal(x1, x3)
+    assert np.array_equal(it1, it2) and np.array_equal(it1, it3)
+    lat.close()
+    trim_memory()
