@@ -550,8 +550,16 @@ def run_ours(args, world, rank, local):
                        "mvm_symmetric_ms_note": "median of 50 graph-replayed MVMs",
                        "mvm_symmetric_mpoint_s": n / (mvm_ms / 1e3) / 1e6,
                        "mvm_symmetric_mpoint_columns_s": n * k / (mvm_ms / 1e3) / 1e6,
+                       "mvm_symmetric_hbm_frac": mvm_bytes(n, d + 1, k, m, W["order"], 2 * (d + 1))
+                                                 / (mvm_ms / 1e3) / 1e9 / peak,
                        "mvm_sequential_ms": mvm_seq_ms,
                        "mvm_sequential_mpoint_s": n / (mvm_seq_ms / 1e3) / 1e6,
+                       "mvm_sequential_hbm_frac": mvm_bytes(n, d + 1, k, m, W["order"], d + 1)
+                                                  / (mvm_seq_ms / 1e3) / 1e9 / peak,
+                       "mvm_hbm_frac_note": "algorithmic bytes of one MVM, 16 n D + 8 n k + "
+                                            "8 m k + P m (8 r + 8 k) + 4 (m + 1) for P blur "
+                                            "passes, over the graph-replayed time and the "
+                                            "measured HBM peak",
                        "mvm_symmetric_bf16_values_ms": mvm_bf16_ms,
                        "bf16_values_rel_l2_vs_fp32": bf16_rel_err,
                        "approximation_n4096": approx,
@@ -569,6 +577,13 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def mvm_bytes(n, D, k, m, r, passes):
+    """Algorithmic bytes of one lattice MVM: ids and weights read by splat and slice, V
+    read and out written, the splatted and sliced lattice rows, and per blur pass each
+    vertex's row read and written plus its 2r neighbour ids."""
+    return 16 * n * D + 8 * n * k + 8 * m * k + passes * m * (8 * r + 8 * k) + 4 * (m + 1)
 
 
 def graph_replay_median_ms(lat, V, out, blur, replays=50, warmup=5):

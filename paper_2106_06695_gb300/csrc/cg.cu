@@ -414,7 +414,8 @@ sgp_status run_cg(Lattice* L, const float* B, int k, int blur, float noise, floa
   const int vblocks = (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, ceil_div(n, rows_per_block)));
   const int64_t sblocks = slice_dot_blocks(L, k);
   const bool want_pre = precond_rank > 0 && noise > 0.f && !rec;
-  const int64_t pblocks = want_pre ? ceil_div(n, 128) : 0;  // ShiftedNystrom::dot_blocks
+  // bounds ShiftedNystrom::dot_blocks (its z blocks: at most one per 128-row tile)
+  const int64_t pblocks = want_pre ? ceil_div(n, 128) : 0;
   CG_CHECK(get((void**)&xh, n * k * sizeof(float)), "alloc x");
   CG_CHECK(get((void**)&xl, n * k * sizeof(float)), "alloc x");
   CG_CHECK(get((void**)&rh, n * k * sizeof(float)), "alloc r");

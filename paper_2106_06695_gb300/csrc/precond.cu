@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // z[r][c_off + c] = (r - B u)[r][c] * inv_tau over 128-row tiles (tile t: rows 128 t ..),
-// and each tile's column sums of r z (fp64; the products are exact in fp64) into
-// dot[t][c_off + c].  Persistent: block b takes tiles b, b + gridDim.x, ..., with two
+// and the column sums of r z (fp64; the products are exact in fp64) over each block's
+// tiles, in tile order, into dot[blockIdx.x][c_off + c].  Persistent: block b takes tiles b, b + gridDim.x, ..., with two
 // accumulators in tensor memory so that the MMAs of one tile overlap the epilogue of the
 // previous.  A = B is K-major (boxes 128 rows x 64 columns); u3 ([48][ld], the three parts
 // of u = Minv B^T r) is K-major (boxes 48 x 64).
@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     const int q = warp & 3;  // tensor-memory lanes 32 q .. + 31
     const bool vec = (k & 3) == 0 && (c_off & 3) == 0;
+    double blk = 0.0;  // warp 1, lane c: the block's column sum over its tiles, in order
     for (int64_t j = 0; j < my_tiles; ++j) {
       const int b = (int)(j & 1);
       const int64_t tile = blockIdx.x + j * (int64_t)gridDim.x;
@@ -554,9 +555,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       epilogue_sync();
       if (warp == 1 && lane < kc)
-        dot[tile * k + c_off + lane] =
-            ((red[b][0][lane] + red[b][1][lane]) + red[b][2][lane]) + red[b][3][lane];
+        blk += ((red[b][0][lane] + red[b][1][lane]) + red[b][2][lane]) + red[b][3][lane];
     }
+    if (warp == 1 && lane < kc) dot[(int64_t)blockIdx.x * k + c_off + lane] = blk;
   }
   tc05::fence_before_sync();
   __syncthreads();
@@ -1606,7 +1607,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
 #undef PC_MAP
 }
 
-int64_t ShiftedNystrom::dot_blocks() const { return ceil_div(n, kTile); }
+int64_t ShiftedNystrom::dot_blocks() const { return z_blocks; }
 
 void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, double* dot,
                            cudaStream_t st, cudaEvent_t* ev, bool split_ready) const {

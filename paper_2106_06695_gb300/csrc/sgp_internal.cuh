@@ -230,10 +230,10 @@ struct ShiftedNystrom {
   std::vector<void*> ptrs;
   sgp_status build(Lattice* L, int rank, uint64_t seed, float noise, int blur, int power_iters,
                    cudaStream_t st);
-  // partial rows apply() writes per column: one per 128-row tile
+  // partial rows apply() writes per column: one per block of the z kernel
   int64_t dot_blocks() const;
-  // z = P^-1 r (r = rh + rl, locality order [n][k]) and per-tile column sums of r z into
-  // dot[tile][c] (fp64).  split_ready: r3 already holds the split of columns 0..15 of r
+  // z = P^-1 r (r = rh + rl, locality order [n][k]) and per-block column sums of r z into
+  // dot[block][c] (fp64).  split_ready: r3 already holds the split of columns 0..15 of r
   // (written by the CG's x, r update).
   void apply(const float* rh, const float* rl, int k, float* z, double* dot, cudaStream_t st,
              cudaEvent_t* ev = nullptr, bool split_ready = false) const;
