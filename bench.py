@@ -195,16 +195,16 @@ def measured_peak_gbs():
 
 def blur_traffic_per_launch(m: int, k: int):
     """DRAM bytes per blur launch from the committed ncu summary, scaled to this m, if the
-    k_blur_rows source has not changed since it was captured; else None."""
+    blur kernel's source has not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))["blur_pass"]
     except (OSError, KeyError, ValueError):
         return None
     src = open(os.path.join(ROOT, "paper_2106_06695_gb300", "csrc", "mvm.cu")).read()
-    body = re.search(r"template <int CH, int U, int R, class S>\n__global__ void "
-                     r"__launch_bounds__\(kThreads\) k_blur_rows\(.*?\n}\n", src, re.S)
-    if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("k_blur_rows_src_sha1")
+    body = re.search(r"template <class S>\n__global__ void __launch_bounds__\(kThreads\) "
+                     r"k_blur_pipe\(.*?\n}\n", src, re.S)
+    if (body is None or hashlib.sha1(body.group(0).encode()).hexdigest() != rec.get("src_sha1")
             or rec.get("k") != k):
         return None
     return float(rec["bytes_per_vertex"]) * m
@@ -437,7 +437,7 @@ def run_ours(args, world, rank, local):
               key=lambda s: per_iter_ms[s] if s in stages else 0.0)
     if per_iter_ms[dom] < per_iter_ms["blur"] or dom not in stages:
         dom = "blur_pass"
-    names = {"blur_pass": "k_blur_rows<2,2,1,float> (one lattice direction)",
+    names = {"blur_pass": "k_blur_pipe<float> (one lattice direction)",
              "splat": "k_splat<4,float> (+ fix-ups)", "slice_dot": "k_slice_dot<4,float>",
              "precond_bt": "k_bt_tc (preconditioner B^T r, tcgen05 bf16, TMA)",
              "precond_z": "k_z_tc (preconditioner z = (r - B u)/tau, tcgen05 bf16, TMA)"}

@@ -14,6 +14,8 @@
 // half the bytes of the dominant blur traffic); every sum is accumulated in fp32.  A
 // thread owns 4 consecutive columns of a row when k is a multiple of 4 and the buffers are
 // aligned, else one column; the blur gives each thread 8 columns when k allows.
+#include <atomic>
+
 #include <cuda_bf16.h>
 
 #include "sgp_internal.cuh"
@@ -190,6 +192,88 @@ __global__ void __launch_bounds__(kThreads) k_blur_rows(int64_t m, int G, int k,
     if (CH == 2) Store<S>::st8(out + v[u] * k + col, acc[0], acc[CH - 1]);
     else Store<S>::st4(out + v[u] * k + col, acc[0]);
   }
+}
+
+// Stencil order 1 with eight columns per thread, persistent and software-pipelined: each
+// thread group walks rows v, v + stride, ...; while it combines row v, the rows of v +
+// stride (own and both neighbours) and the neighbour ids of v + 2 stride are in flight, so
+// the memory system sees a steady stream instead of one burst per block.  Same arithmetic
+// as k_blur_rows (bitwise equal results).
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_blur_pipe(int64_t m, int G, int k, Taps tp,
+                                                        const int32_t* __restrict__ nbr,
+                                                        const S* __restrict__ in,
+                                                        S* __restrict__ out) {
+  const int rows_per_block = blockDim.x / G;
+  const int col = (int)(threadIdx.x % G) * 8;
+  const int64_t stride = (int64_t)gridDim.x * rows_per_block;
+  int64_t row = (int64_t)blockIdx.x * rows_per_block + threadIdx.x / G;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto ids = [&](int64_t v, int& a, int& c) {  // neighbour ids of v - u_j, v + u_j
+    if (v < m) {
+      a = __ldg(nbr + v);
+      c = __ldg(nbr + m + v);
+    } else {
+      a = c = -1;
+    }
+  };
+  auto load = [&](int64_t v, int a, int c, float4 (&x)[3][2]) {  // own, minus, plus rows
+    x[0][0] = x[0][1] = x[1][0] = x[1][1] = x[2][0] = x[2][1] = zero;
+    if (v < m) Store<S>::ldg8(in + v * k + col, x[0][0], x[0][1]);
+    if (a >= 0) Store<S>::ldg8(in + (int64_t)a * k + col, x[1][0], x[1][1]);
+    if (c >= 0) Store<S>::ldg8(in + (int64_t)c * k + col, x[2][0], x[2][1]);
+  };
+  int a0, c0, a1, c1;
+  ids(row, a0, c0);
+  ids(row + stride, a1, c1);
+  float4 cur[3][2];
+  load(row, a0, c0, cur);
+  while (row < m) {
+    const int64_t nrow = row + stride;
+    int a2, c2;
+    ids(nrow + stride, a2, c2);
+    float4 nxt[3][2];
+    load(nrow, a1, c1, nxt);
+    float4 acc[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      acc[h] = make_float4(tp.t[0] * cur[0][h].x, tp.t[0] * cur[0][h].y, tp.t[0] * cur[0][h].z,
+                           tp.t[0] * cur[0][h].w);
+      acc[h].x = fmaf(tp.t[1], cur[1][h].x + cur[2][h].x, acc[h].x);
+      acc[h].y = fmaf(tp.t[1], cur[1][h].y + cur[2][h].y, acc[h].y);
+      acc[h].z = fmaf(tp.t[1], cur[1][h].z + cur[2][h].z, acc[h].z);
+      acc[h].w = fmaf(tp.t[1], cur[1][h].w + cur[2][h].w, acc[h].w);
+    }
+    Store<S>::st8(out + row * k + col, acc[0], acc[1]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      cur[q][0] = nxt[q][0];
+      cur[q][1] = nxt[q][1];
+    }
+    a1 = a2;
+    c1 = c2;
+    row = nrow;
+  }
+}
+
+// Blocks of k_blur_pipe<S> the device keeps resident (one wave), cached per device.
+template <class S>
+int blur_pipe_blocks() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int b = cache[dev].load();
+  if (b > 0) return b;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blur_pipe<S>, kThreads, 0) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    clear_pending_error();
+    return 152;
+  }
+  b = std::max(1, per_sm) * std::max(1, sms);
+  cache[dev].store(b);
+  return b;
 }
 
 // ---- sparse blur (lattices whose direction lists are short) ------------------------------
@@ -418,7 +502,11 @@ template <class S>
 void launch_blur_t(const Lattice* L, int j, const Taps& taps, const S* in, S* out, int k,
                    cudaStream_t st) {
   const int32_t* nbr = L->nbr + (size_t)j * L->r * 2 * L->m;
-  if (k % 8 == 0 && k / 8 <= kThreads) {  // eight columns of two rows per thread
+  if (k % 8 == 0 && k / 8 <= kThreads && L->r == 1) {  // eight columns, pipelined rows
+    const int G = k / 8, threads = G * (kThreads / G);
+    const int64_t blocks = std::min<int64_t>(blur_pipe_blocks<S>(), ceil_div(L->m, threads / G));
+    k_blur_pipe<S><<<(unsigned)blocks, threads, 0, st>>>(L->m, G, k, taps, nbr, in, out);
+  } else if (k % 8 == 0 && k / 8 <= kThreads) {  // eight columns of two rows per thread
     launch_blur_rows<2, 2, S>(L, nbr, taps, in, out, k, st);
   } else if (k % 4 == 0 && k / 4 <= kThreads) {
     launch_blur_rows<1, 2, S>(L, nbr, taps, in, out, k, st);

@@ -54,6 +54,28 @@ def test_pcg_converges_like_the_oracle(n, d, k, rank, q):
     assert (ig < ic).all()
 
 
+@pytest.mark.parametrize("n,d,k,rank", [(40, 3, 4, 8), (300, 4, 3, 256), (129, 2, 16, 64),
+                                       (70, 5, 5, 128)])
+def test_pcg_on_tiny_and_ragged_systems(n, d, k, rank):
+    """Fewer rows than one 128-row tile or one 64-row chunk, a rank close to n (C may be
+    singular: the shifted Cholesky then either succeeds or the solve falls back to plain
+    CG), and a rank equal to n's tile: every solve stops at its tolerance and its answer
+    has the oracle's residual."""
+    from paper_2106_06695_gb300.lattice import Lattice
+
+    X = synth.gmm_points(n, d, 23)
+    ls = np.ones(d, np.float32)
+    ref = OracleLattice(X, ls)
+    lat = Lattice(gpu(X), gpu(ls), precond_rank=rank, precond_seed=5, spacing=ref.s)
+    B = synth.solve_rhs(X, 23, probes=k - 1)
+    tol = 1e-4
+    xg, ig, rg = lat.cg(gpu(B), noise=0.01, tol=tol, max_iter=500)
+    Bd = B.astype(np.float64)
+    R = Bd - ref.mvm(xg.cpu().numpy().astype(np.float64), mode=2, beta=0.01)
+    true_rel = np.linalg.norm(R, axis=0) / np.linalg.norm(Bd, axis=0)
+    assert (rg <= tol).all() and (true_rel <= 3 * tol).all(), (ig, rg, true_rel)
+
+
 def test_pcg_rank_validation_and_noise_free_fallback():
     from paper_2106_06695_gb300 import SGPError
     from paper_2106_06695_gb300.lattice import Lattice
