@@ -334,11 +334,15 @@ __device__ __forceinline__ bool entry_is_neighbour(uint32_t e, const int16_t* __
   return true;
 }
 
-// One thread per vertex, all directions j: ids of v -+ t u_j, t = 1..r.  The neighbour's
+// One thread per vertex, all directions j: ids of v -+ t u_j, t = 1..r, and hasnb[j / 32]
+// [v] bit j % 32: whether v has a neighbour along j.  The neighbour's
 // hash comes from the vertex's linear hash in O(1) (sum_A = sum_c A_c); most absent
 // neighbours stop at the vertex filter (one bit per hash, sized to stay in L2); the key
-// itself is read only to confirm a tag match.  A neighbour outside the int16 key range
-// does not exist.  counts[j] accumulates the vertices with a neighbour along j.
+// itself is read only to confirm a tag match.  The filter words of kNbrGroup directions
+// (both signs) are loaded together before any of them is tested, so that their latencies
+// overlap.  A neighbour outside the int16 key range does not exist.  counts[j]
+// accumulates the vertices with a neighbour along j.
+constexpr int kNbrGroup = 8;
 __global__ void __launch_bounds__(256) k_neighbours(
     const int16_t* __restrict__ keys, const uint64_t* __restrict__ vhash,
     const int2* __restrict__ vrange, int64_t m, int d, int r, uint64_t sum_A,
@@ -346,76 +350,96 @@ __global__ void __launch_bounds__(256) k_neighbours(
     const int32_t* __restrict__ slot_id, const int32_t* __restrict__ perm,
     const int16_t* __restrict__ rem0, const uint8_t* __restrict__ rank,
     const uint32_t* __restrict__ bloom, uint64_t bloom_mask, int32_t* __restrict__ nbr,
-    unsigned long long* __restrict__ counts) {
+    unsigned long long* __restrict__ counts, uint32_t* __restrict__ hasnb) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int D = d + 1;
   const bool live = v < m;
   const uint64_t hv = live ? vhash[v] : 0;
   const int2 rg = live ? vrange[v] : make_int2(0, 0);
   const int16_t* kv = keys + (live ? v : 0) * D;
-  for (int j = 0; j < D; ++j) {
-    bool any = false;
-    if (live) {
-      const uint64_t dj = (uint64_t)D * coord_mult(j) - sum_A;  // lin(u_j)
-      for (int t = 1; t <= r; ++t) {
+  uint32_t word = 0;  // bits j % 32 of the directions with a neighbour, 32 at a time
+  for (int j0 = 0; j0 < D; j0 += kNbrGroup) {
+    uint32_t any = 0;  // bit q: a neighbour along j0 + q
+    for (int t = 1; t <= r; ++t) {
+      // filter bits of the group's 2 kNbrGroup candidates: bit 2 q + sg
+      uint32_t hits = 0;
+#pragma unroll
+      for (int q = 0; q < kNbrGroup; ++q) {
+        const int j = j0 + q;
+        const uint64_t dj = (uint64_t)D * coord_mult(j < D ? j : 0) - sum_A;  // lin(u_j)
+#pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
           const int step = sg ? t : -t;
-          // every coordinate moves by -step except j, which moves by d step
-          bool in_range = rg.x - t * d >= -32768 && rg.y + t * d <= 32767;
-          if (!in_range) {
-            in_range = true;
-            for (int c = 0; c < D; ++c) {
-              const int x = (int)kv[c] + step * ((c == j ? D : 0) - 1);
-              in_range = in_range && x >= -32768 && x <= 32767;
-            }
+          const uint64_t b = (mix64(hv + (uint64_t)(int64_t)step * dj) >> 20) & bloom_mask;
+          const uint32_t word = (live && j < D) ? __ldg(bloom + (b >> 5)) : 0u;
+          hits |= ((word >> (b & 31)) & 1u) << (2 * q + sg);
+        }
+      }
+      // absent unless a filter hit is confirmed in the table
+      if (live)
+#pragma unroll
+        for (int q = 0; q < kNbrGroup; ++q)
+          if (j0 + q < D) {
+            nbr[(((int64_t)(j0 + q) * r + (t - 1)) * 2 + 0) * m + v] = -1;
+            nbr[(((int64_t)(j0 + q) * r + (t - 1)) * 2 + 1) * m + v] = -1;
           }
-          int32_t found = -1;
-          const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * dj);
-          const uint64_t b = (h >> 20) & bloom_mask;
-          if (in_range && (bloom[b >> 5] >> (b & 31) & 1u)) {
-            const uint32_t tag = (uint32_t)(h >> 33);
-            uint64_t slot = h & mask;
-            for (uint64_t probe = 0; probe <= mask; ++probe) {
-              const unsigned long long cur = table[slot];
-              if (cur == kEmpty) break;
-              if ((uint32_t)(cur >> 32) == tag &&
-                  entry_is_neighbour((uint32_t)cur, kv, j, step, d, perm, rem0, rank)) {
-                found = slot_id[slot];
-                break;
-              }
-              slot = (slot + 1) & mask;
-            }
+      while (hits) {
+        const int bit = __ffs(hits) - 1;
+        hits &= hits - 1;
+        const int q = bit >> 1, sg = bit & 1, j = j0 + q;
+        const int step = sg ? t : -t;
+        // every coordinate moves by -step except j, which moves by d step
+        bool in_range = rg.x - t * d >= -32768 && rg.y + t * d <= 32767;
+        if (!in_range) {
+          in_range = true;
+          for (int c = 0; c < D; ++c) {
+            const int x = (int)kv[c] + step * ((c == j ? D : 0) - 1);
+            in_range = in_range && x >= -32768 && x <= 32767;
           }
-          nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = found;
-          any = any || found >= 0;
+        }
+        if (!in_range) continue;
+        const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * ((uint64_t)D * coord_mult(j) - sum_A));
+        const uint32_t tag = (uint32_t)(h >> 33);
+        uint64_t slot = h & mask;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+          const unsigned long long cur = table[slot];
+          if (cur == kEmpty) break;
+          if ((uint32_t)(cur >> 32) == tag &&
+              entry_is_neighbour((uint32_t)cur, kv, j, step, d, perm, rem0, rank)) {
+            nbr[(((int64_t)j * r + (t - 1)) * 2 + sg) * m + v] = slot_id[slot];
+            any |= 1u << q;
+            break;
+          }
+          slot = (slot + 1) & mask;
         }
       }
     }
     // vertices with a neighbour along j: one atomic per warp
-    const unsigned with = __ballot_sync(0xffffffffu, any);
-    if (with && (int)(threadIdx.x & 31) == __ffs(with) - 1)
-      atomicAdd(&counts[j], (unsigned long long)__popc(with));
+#pragma unroll
+    for (int q = 0; q < kNbrGroup; ++q) {
+      if (j0 + q >= D) break;
+      const unsigned with = __ballot_sync(0xffffffffu, (any >> q) & 1u);
+      if (with && (int)(threadIdx.x & 31) == __ffs(with) - 1)
+        atomicAdd(&counts[j0 + q], (unsigned long long)__popc(with));
+    }
+    word |= any << (j0 & 31);
+    if (((j0 + kNbrGroup) & 31) == 0 || j0 + kNbrGroup >= D) {
+      if (live) hasnb[(int64_t)(j0 >> 5) * m + v] = word;
+      word = 0;
+    }
   }
-}
-
-// Vertices with at least one neighbour along direction j (the sparse blur's lists).
-__device__ __forceinline__ bool has_neighbour(const int32_t* __restrict__ nbr_j, int64_t m,
-                                              int r, int64_t v) {
-  for (int q = 0; q < 2 * r; ++q)
-    if (nbr_j[(int64_t)q * m + v] >= 0) return true;
-  return false;
 }
 
 // Direction lists: thread per (vertex, direction); a warp's vertices (one direction per
 // block row) take consecutive slots with one atomic.  The order of a list is immaterial to
 // the blur, which updates its vertices independently.
-__global__ void k_active_fill(const int32_t* __restrict__ nbr, int64_t m, int D, int r,
+__global__ void k_active_fill(const uint32_t* __restrict__ hasnb, int64_t m, int D,
                               const int64_t* __restrict__ off,
                               unsigned long long* __restrict__ fill, int32_t* __restrict__ act) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // grid y: direction
   const int j = (int)blockIdx.y;
   if (v >= m) return;
-  const bool on = has_neighbour(nbr + (int64_t)j * r * 2 * m, m, r, v);
+  const bool on = (hasnb[(int64_t)(j >> 5) * m + v] >> (j & 31)) & 1u;
   const unsigned with = __ballot_sync(__activemask(), on);
   if (!on) return;  // the remaining lanes are exactly `with`
   const int lane = (int)(threadIdx.x & 31);
@@ -713,13 +737,15 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   unsigned long long* counts = nullptr;
   SGP_CHECK(tmp.get(&counts, 2 * D), "alloc counts");
   SGP_CHECK(cudaMemsetAsync(counts, 0, 2 * D * sizeof(unsigned long long), st), "clear counts");
+  uint32_t* hasnb = nullptr;  // [ceil(D / 32)][m] neighbour bits per direction
+  SGP_CHECK(tmp.get(&hasnb, (int64_t)((D + 31) / 32) * m), "alloc neighbour bits");
   {
     // sum_c A_c over the D coordinates, as the kernels compute A_c
     uint64_t sum_A = 0;
     for (int c = 0; c < D; ++c) sum_A += host_coord_mult(c);
     k_neighbours<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(
         L->keys, vhash, vrange, m, d, r, sum_A, table, mask, slot_id, L->perm, rem0, rank,
-        bloom, bloom_bits - 1, L->nbr, counts);
+        bloom, bloom_bits - 1, L->nbr, counts, hasnb);
     note_launches(1);
   }
   SGP_CHECK(cudaGetLastError(), "k_neighbours");
@@ -813,7 +839,7 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
                                 cudaMemcpyHostToDevice, st),
                 "copy list offsets");
       k_active_fill<<<dim3((unsigned)ceil_div(m, 256), (unsigned)D), 256, 0, st>>>(
-          L->nbr, m, D, r, L->act_off_dev, counts + D, L->act);
+          hasnb, m, D, L->act_off_dev, counts + D, L->act);
       note_launches(1);
       // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
       std::vector<float> pw(2 * D + 1);
