@@ -37,6 +37,18 @@ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
   h ^= h >> 33;
   return h;
 }
+// Vertex-filter bit of a linear hash: the two halves folded and mixed with 32-bit
+// multiplies (the murmur3 finalizer), cheaper than mix64 for the filter test every
+// (vertex, direction) candidate makes; the table's slot and tag still come from mix64.
+__device__ __forceinline__ uint32_t filter_hash(uint64_t h) {
+  uint32_t x = (uint32_t)(h >> 32) ^ (uint32_t)h;
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
+}
 
 uint64_t host_mix64(uint64_t h) {
   h ^= h >> 33;
@@ -146,14 +158,19 @@ __global__ void __launch_bounds__(128) k_elevate(const float* __restrict__ X,
       rem0[c] = 0;
     }
   }
-  // rank: strictly larger residuals, plus equal residuals at a lower index
+  // rank: strictly larger residuals, plus equal residuals at a lower index.  The residuals
+  // are compared through an order-preserving integer image of their fp64 bits (-0 taken as
+  // +0, no NaN here), the same order as the fp64 comparison at integer-compare cost.
+  long long key[MAXD];
   for (int c = 0; c < D; ++c) {
-    const double dc = __dsub_rn(y[c], (double)rem0[c]);
+    const long long bits = __double_as_longlong(__dadd_rn(__dsub_rn(y[c], (double)rem0[c]), 0.0));
+    key[c] = bits ^ ((bits >> 63) & 0x7fffffffffffffffLL);
+  }
+  for (int c = 0; c < D; ++c) {
+    const long long kc = key[c];
     int rk = 0;
-    for (int c2 = 0; c2 < D; ++c2) {
-      const double d2 = __dsub_rn(y[c2], (double)rem0[c2]);
-      rk += (d2 > dc || (d2 == dc && c2 < c)) ? 1 : 0;
-    }
+    for (int c2 = 0; c2 < c; ++c2) rk += key[c2] >= kc ? 1 : 0;
+    for (int c2 = c + 1; c2 < D; ++c2) rk += key[c2] > kc ? 1 : 0;
     rank[c] = rk;
   }
   // move rem0 onto H_d (coordinate sum 0)
@@ -286,16 +303,36 @@ __global__ void k_assign_ids(const uint32_t* __restrict__ scanned,
   const int k = (int)(e % D);
   uint64_t h = 0;
   int lo = 1 << 30, hi = -(1 << 30);
-  for (int c = 0; c < D; ++c) {
+  int16_t* row = keys + (int64_t)id * D;
+  // the row's coordinates, stored two per 4-byte word where the row is 4-byte aligned
+  int c = 0;
+  if ((reinterpret_cast<uintptr_t>(row) & 3u) != 0) {
+    const int x = vertex_coord(rem0 + i * D, rank + i * D, d, k, 0);
+    row[0] = (int16_t)x;
+    h += coord_mult(0) * (uint64_t)(int64_t)x;
+    lo = min(lo, x);
+    hi = max(hi, x);
+    c = 1;
+  }
+  for (; c + 1 < D; c += 2) {
+    const int x0 = vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
+    const int x1 = vertex_coord(rem0 + i * D, rank + i * D, d, k, c + 1);
+    *reinterpret_cast<uint32_t*>(row + c) =
+        (uint32_t)(uint16_t)(int16_t)x0 | ((uint32_t)(uint16_t)(int16_t)x1 << 16);
+    h += coord_mult(c) * (uint64_t)(int64_t)x0 + coord_mult(c + 1) * (uint64_t)(int64_t)x1;
+    lo = min(lo, min(x0, x1));
+    hi = max(hi, max(x0, x1));
+  }
+  if (c < D) {
     const int x = vertex_coord(rem0 + i * D, rank + i * D, d, k, c);
-    keys[(int64_t)id * D + c] = (int16_t)x;
+    row[c] = (int16_t)x;
     h += coord_mult(c) * (uint64_t)(int64_t)x;
     lo = min(lo, x);
     hi = max(hi, x);
   }
   vhash[id] = h;
   vrange[id] = make_int2(lo, hi);
-  const uint64_t b = (mix64(h) >> 20) & bloom_mask;  // the vertex's filter bit
+  const uint64_t b = filter_hash(h) & bloom_mask;  // the vertex's filter bit
   atomicOr(&bloom[b >> 5], 1u << (b & 31));
 }
 
@@ -370,18 +407,19 @@ __global__ void __launch_bounds__(256) k_neighbours(
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
           const int step = sg ? t : -t;
-          const uint64_t b = (mix64(hv + (uint64_t)(int64_t)step * dj) >> 20) & bloom_mask;
+          const uint64_t b = filter_hash(hv + (uint64_t)(int64_t)step * dj) & bloom_mask;
           const uint32_t word = (live && j < D) ? __ldg(bloom + (b >> 5)) : 0u;
           hits |= ((word >> (b & 31)) & 1u) << (2 * q + sg);
         }
       }
-      // absent unless a filter hit is confirmed in the table
+      // absent unless a filter hit is confirmed in the table (streaming stores: the table
+      // is written once, and the vertex filter should keep its place in L2)
       if (live)
 #pragma unroll
         for (int q = 0; q < kNbrGroup; ++q)
           if (j0 + q < D) {
-            nbr[(((int64_t)(j0 + q) * r + (t - 1)) * 2 + 0) * m + v] = -1;
-            nbr[(((int64_t)(j0 + q) * r + (t - 1)) * 2 + 1) * m + v] = -1;
+            __stcs(nbr + (((int64_t)(j0 + q) * r + (t - 1)) * 2 + 0) * m + v, -1);
+            __stcs(nbr + (((int64_t)(j0 + q) * r + (t - 1)) * 2 + 1) * m + v, -1);
           }
       while (hits) {
         const int bit = __ffs(hits) - 1;
@@ -430,24 +468,32 @@ __global__ void __launch_bounds__(256) k_neighbours(
   }
 }
 
-// Direction lists: thread per (vertex, direction); a warp's vertices (one direction per
-// block row) take consecutive slots with one atomic.  The order of a list is immaterial to
-// the blur, which updates its vertices independently.
+// Direction lists: thread per vertex, reading its direction bits (32 directions per word);
+// for each direction the warp's vertices with a neighbour along it take consecutive slots
+// with one atomic.  The order of a list is immaterial to the blur, which updates its
+// vertices independently.
 __global__ void k_active_fill(const uint32_t* __restrict__ hasnb, int64_t m, int D,
                               const int64_t* __restrict__ off,
                               unsigned long long* __restrict__ fill, int32_t* __restrict__ act) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // grid y: direction
-  const int j = (int)blockIdx.y;
-  if (v >= m) return;
-  const bool on = (hasnb[(int64_t)(j >> 5) * m + v] >> (j & 31)) & 1u;
-  const unsigned with = __ballot_sync(__activemask(), on);
-  if (!on) return;  // the remaining lanes are exactly `with`
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = v < m;
   const int lane = (int)(threadIdx.x & 31);
-  const int leader = __ffs(with) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(&fill[j], (unsigned long long)__popc(with));
-  base = __shfl_sync(with, base, leader);
-  act[off[j] + base + __popc(with & ((1u << lane) - 1u))] = (int32_t)v;
+  for (int w = 0; w * 32 < D; ++w) {
+    const uint32_t bits = live ? hasnb[(int64_t)w * m + v] : 0u;
+    uint32_t seen = __reduce_or_sync(0xffffffffu, bits);  // directions any lane has
+    while (seen) {
+      const int b = __ffs(seen) - 1;
+      seen &= seen - 1;
+      const int j = w * 32 + b;
+      const bool on = (bits >> b) & 1u;
+      const unsigned with = __ballot_sync(0xffffffffu, on);
+      const int leader = __ffs(with) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(&fill[j], (unsigned long long)__popc(with));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (on) act[off[j] + base + __popc(with & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -838,7 +884,7 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
       SGP_CHECK(cudaMemcpyAsync(L->act_off_dev, L->act_off.data(), (D + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice, st),
                 "copy list offsets");
-      k_active_fill<<<dim3((unsigned)ceil_div(m, 256), (unsigned)D), 256, 0, st>>>(
+      k_active_fill<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(
           hasnb, m, D, L->act_off_dev, counts + D, L->act);
       note_launches(1);
       // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
