@@ -20,6 +20,7 @@
 //                    each vertex the list of (point, weight) it gathers.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "sgp_internal.cuh"
@@ -37,18 +38,10 @@ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
   h ^= h >> 33;
   return h;
 }
-// Vertex-filter bit of a linear hash: the two halves folded and mixed with 32-bit
-// multiplies (the murmur3 finalizer), cheaper than mix64 for the filter test every
+// Vertex-filter bit of a linear hash: its upper half (the linear hash's high bits mix every
+// coordinate through the odd 64-bit multipliers), cheap for the filter test that every
 // (vertex, direction) candidate makes; the table's slot and tag still come from mix64.
-__device__ __forceinline__ uint32_t filter_hash(uint64_t h) {
-  uint32_t x = (uint32_t)(h >> 32) ^ (uint32_t)h;
-  x ^= x >> 16;
-  x *= 0x85ebca6bu;
-  x ^= x >> 13;
-  x *= 0xc2b2ae35u;
-  x ^= x >> 16;
-  return x;
-}
+__device__ __forceinline__ uint32_t filter_hash(uint64_t h) { return (uint32_t)(h >> 32); }
 
 uint64_t host_mix64(uint64_t h) {
   h ^= h >> 33;
@@ -63,9 +56,10 @@ uint64_t host_coord_mult(int c) { return host_mix64(0x9e3779b97f4a7c15ull * (uin
 // Vertex hash, linear in the integer key: lin(key) = sum_c A_c key_c (mod 2^64) with odd
 // per-coordinate multipliers A_c, then mixed.  A lattice step u_j = (d+1) e_j - 1 moves
 // lin by (d+1) A_j - sum_c A_c, so a neighbour's hash costs O(1) from the vertex's.
-__device__ __forceinline__ uint64_t coord_mult(int c) {
-  return mix64(0x9e3779b97f4a7c15ull * (uint64_t)(c + 1)) | 1ull;
-}
+// The multipliers A_c = mix64(0x9e3779b97f4a7c15 (c + 1)) | 1, one table per device
+// (constant memory: the lattice kernels read them with warp-uniform c).
+__constant__ uint64_t c_coord_mult[kMaxD];
+__device__ __forceinline__ uint64_t coord_mult(int c) { return c_coord_mult[c]; }
 
 __device__ __forceinline__ uint64_t lin_hash(const int* key, int D) {
   uint64_t h = 0;
@@ -388,8 +382,11 @@ __global__ void __launch_bounds__(256) k_neighbours(
     const int16_t* __restrict__ rem0, const uint8_t* __restrict__ rank,
     const uint32_t* __restrict__ bloom, uint64_t bloom_mask, int32_t* __restrict__ nbr,
     unsigned long long* __restrict__ counts, uint32_t* __restrict__ hasnb) {
+  __shared__ unsigned block_count[kMaxD];  // this block's vertices with a neighbour along j
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int D = d + 1;
+  for (int j = threadIdx.x; j < D; j += blockDim.x) block_count[j] = 0;
+  __syncthreads();
   const bool live = v < m;
   const uint64_t hv = live ? vhash[v] : 0;
   const int2 rg = live ? vrange[v] : make_int2(0, 0);
@@ -403,24 +400,27 @@ __global__ void __launch_bounds__(256) k_neighbours(
 #pragma unroll
       for (int q = 0; q < kNbrGroup; ++q) {
         const int j = j0 + q;
-        const uint64_t dj = (uint64_t)D * coord_mult(j < D ? j : 0) - sum_A;  // lin(u_j)
+        // t lin(u_j): the hash moves by -t lin(u_j) (sg = 0) or + t lin(u_j) (sg = 1)
+        const uint64_t tdj = (uint64_t)t * ((uint64_t)D * coord_mult(j < D ? j : 0) - sum_A);
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
-          const int step = sg ? t : -t;
-          const uint64_t b = filter_hash(hv + (uint64_t)(int64_t)step * dj) & bloom_mask;
+          const uint64_t b = filter_hash(sg ? hv + tdj : hv - tdj) & bloom_mask;
           const uint32_t word = (live && j < D) ? __ldg(bloom + (b >> 5)) : 0u;
           hits |= ((word >> (b & 31)) & 1u) << (2 * q + sg);
         }
       }
       // absent unless a filter hit is confirmed in the table (streaming stores: the table
       // is written once, and the vertex filter should keep its place in L2)
-      if (live)
+      if (live) {
+        const int64_t sj = (int64_t)2 * r * m;  // from direction j to j + 1
+        int32_t* p0 = nbr + ((int64_t)j0 * 2 * r + 2 * (t - 1)) * m + v;
 #pragma unroll
         for (int q = 0; q < kNbrGroup; ++q)
           if (j0 + q < D) {
-            __stcs(nbr + (((int64_t)(j0 + q) * r + (t - 1)) * 2 + 0) * m + v, -1);
-            __stcs(nbr + (((int64_t)(j0 + q) * r + (t - 1)) * 2 + 1) * m + v, -1);
+            __stcs(p0 + q * sj, -1);
+            __stcs(p0 + q * sj + m, -1);
           }
+      }
       while (hits) {
         const int bit = __ffs(hits) - 1;
         hits &= hits - 1;
@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(256) k_neighbours(
           }
         }
         if (!in_range) continue;
-        const uint64_t h = mix64(hv + (uint64_t)(int64_t)step * ((uint64_t)D * coord_mult(j) - sum_A));
+        const uint64_t tdj = (uint64_t)t * ((uint64_t)D * coord_mult(j) - sum_A);
+        const uint64_t h = mix64(sg ? hv + tdj : hv - tdj);
         const uint32_t tag = (uint32_t)(h >> 33);
         uint64_t slot = h & mask;
         for (uint64_t probe = 0; probe <= mask; ++probe) {
@@ -452,13 +453,14 @@ __global__ void __launch_bounds__(256) k_neighbours(
         }
       }
     }
-    // vertices with a neighbour along j: one atomic per warp
+    // vertices with a neighbour along j: one shared-memory add per warp, one global add
+    // per block at the end
 #pragma unroll
     for (int q = 0; q < kNbrGroup; ++q) {
       if (j0 + q >= D) break;
       const unsigned with = __ballot_sync(0xffffffffu, (any >> q) & 1u);
       if (with && (int)(threadIdx.x & 31) == __ffs(with) - 1)
-        atomicAdd(&counts[j0 + q], (unsigned long long)__popc(with));
+        atomicAdd(&block_count[j0 + q], (unsigned)__popc(with));
     }
     word |= any << (j0 & 31);
     if (((j0 + kNbrGroup) & 31) == 0 || j0 + kNbrGroup >= D) {
@@ -466,6 +468,9 @@ __global__ void __launch_bounds__(256) k_neighbours(
       word = 0;
     }
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < D; j += blockDim.x)
+    if (block_count[j]) atomicAdd(&counts[j], (unsigned long long)block_count[j]);
 }
 
 // Direction lists: thread per vertex, reading its direction bits (32 directions per word);
@@ -631,8 +636,34 @@ int bits_for(uint64_t v) {  // bits needed to hold values 0..v
 
 }  // namespace
 
+// Upload the hash multipliers to the current device once (blocking, so that every stream
+// of the process sees them before its first build kernel).
+static sgp_status ensure_coord_mults() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    set_error("sgp_lattice_build: device ordinal out of range");
+    return SGP_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return SGP_OK;
+  uint64_t table[kMaxD];
+  for (int c = 0; c < kMaxD; ++c) table[c] = host_coord_mult(c);
+  e = cudaMemcpyToSymbol(c_coord_mult, table, sizeof(table));
+  if (e != cudaSuccess) return cuda_status(e, "uploading the hash multipliers");
+  done[dev] = true;
+  return SGP_OK;
+}
+
 sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
   cudaStream_t st = L->stream;
+  {
+    const sgp_status s0 = ensure_coord_mults();
+    if (s0 != SGP_OK) return s0;
+  }
   const int64_t n = L->n;
   const int d = L->d, D = L->D, r = L->r;
   const int64_t nD = n * D;
