@@ -473,30 +473,55 @@ __global__ void __launch_bounds__(256) k_neighbours(
     if (block_count[j]) atomicAdd(&counts[j], (unsigned long long)block_count[j]);
 }
 
-// Direction lists: thread per vertex, reading its direction bits (32 directions per word);
-// for each direction the warp's vertices with a neighbour along it take consecutive slots
-// with one atomic.  The order of a list is immaterial to the blur, which updates its
-// vertices independently.
-__global__ void k_active_fill(const uint32_t* __restrict__ hasnb, int64_t m, int D,
-                              const int64_t* __restrict__ off,
-                              unsigned long long* __restrict__ fill, int32_t* __restrict__ act) {
+// Direction lists: thread per vertex, reading its direction bits (32 directions per word).
+// A block first counts, per warp and direction, its vertices with a neighbour along the
+// direction, takes one slot range per direction with one atomic, then each warp writes its
+// vertices at its prefix within that range.  The order of a list is immaterial to the
+// blur, which updates its vertices independently.
+constexpr int kFillThreads = 512;
+__global__ void __launch_bounds__(kFillThreads) k_active_fill(
+    const uint32_t* __restrict__ hasnb, int64_t m, int D, const int64_t* __restrict__ off,
+    unsigned long long* __restrict__ fill, int32_t* __restrict__ act) {
+  constexpr int kWarps = kFillThreads / 32;
+  __shared__ unsigned wpos[kWarps][kMaxD];  // counts, then each warp's offset in the list
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = v < m;
-  const int lane = (int)(threadIdx.x & 31);
+  const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5);
+  for (int e = threadIdx.x; e < kWarps * kMaxD; e += blockDim.x) (&wpos[0][0])[e] = 0;
+  __syncthreads();
   for (int w = 0; w * 32 < D; ++w) {
     const uint32_t bits = live ? hasnb[(int64_t)w * m + v] : 0u;
-    uint32_t seen = __reduce_or_sync(0xffffffffu, bits);  // directions any lane has
+    uint32_t seen = __reduce_or_sync(0xffffffffu, bits);
+    while (seen) {
+      const int b = __ffs(seen) - 1;
+      seen &= seen - 1;
+      const unsigned with = __ballot_sync(0xffffffffu, (bits >> b) & 1u);
+      if (lane == 0) wpos[warp][w * 32 + b] = (unsigned)__popc(with);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < D; j += blockDim.x) {
+    unsigned total = 0;
+    for (int q = 0; q < kWarps; ++q) total += wpos[q][j];
+    if (total == 0) continue;
+    unsigned run = (unsigned)atomicAdd(&fill[j], (unsigned long long)total);
+    for (int q = 0; q < kWarps; ++q) {
+      const unsigned c = wpos[q][j];
+      wpos[q][j] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int w = 0; w * 32 < D; ++w) {
+    const uint32_t bits = live ? hasnb[(int64_t)w * m + v] : 0u;
+    uint32_t seen = __reduce_or_sync(0xffffffffu, bits);
     while (seen) {
       const int b = __ffs(seen) - 1;
       seen &= seen - 1;
       const int j = w * 32 + b;
       const bool on = (bits >> b) & 1u;
       const unsigned with = __ballot_sync(0xffffffffu, on);
-      const int leader = __ffs(with) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(&fill[j], (unsigned long long)__popc(with));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (on) act[off[j] + base + __popc(with & ((1u << lane) - 1u))] = (int32_t)v;
+      if (on) act[off[j] + wpos[warp][j] + __popc(with & ((1u << lane) - 1u))] = (int32_t)v;
     }
   }
 }
@@ -915,7 +940,7 @@ sgp_status build_lattice(Lattice* L, const float* X, const float* ls) {
       SGP_CHECK(cudaMemcpyAsync(L->act_off_dev, L->act_off.data(), (D + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice, st),
                 "copy list offsets");
-      k_active_fill<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(
+      k_active_fill<<<(unsigned)ceil_div(m, kFillThreads), kFillThreads, 0, st>>>(
           hasnb, m, D, L->act_off_dev, counts + D, L->act);
       note_launches(1);
       // powers of the symmetric blur's centre tap g_0 (stored rows are rescaled lazily)
