@@ -221,7 +221,9 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
  * rank-l randomized Nystrom approximation of K = outputscale W B W^T (B here the blur):
  *   Omega  n x l Rademacher sketch, Omega[i][j] = sign bit of SplitMix64 at counter
  *          i l + j + 1 from precond_seed (i the caller's point index);
- *   Q      Omega (precond_power_iters = 0) or an orthonormal basis of K Omega (1);
+ *   Q      Omega (precond_power_iters = 0) or a basis of the range of K Omega (1), by
+ *          Cholesky QR (a second pass only when the first needed a raised shift: the
+ *          approximation depends only on the range);
  *   Y      = K Q,  C = (Q^T Y + Y^T Q)/2 + eps I (eps = 1e-6 max_j C_jj, raised when its
  *          Cholesky fails) = R R^T,  B = Y R^-T;
  *   tau    = lambda_min(B^T B) (inverse power iteration) + noise_var.

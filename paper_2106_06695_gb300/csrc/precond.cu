@@ -4,8 +4,9 @@
 // With A = K + noise I (K = outputscale W M^T M W^T, reachable only through products):
 //   Omega   n x l Rademacher sketch, entry (i, j) = sign bit of SplitMix64 at counter
 //           i l + j + 1 from the seed (i = the caller's point index);
-//   Q       Omega, or after q = 1 subspace iteration an orthonormal basis of K Omega
-//           (Cholesky QR, twice; the approximation depends only on the subspace);
+//   Q       Omega, or after q = 1 subspace iteration a basis of the range of K Omega
+//           (Cholesky QR; the approximation depends only on the subspace, so a second
+//           pass runs only when the first Gram's Cholesky needed a raised shift);
 //   Y       = K Q;   C = (Q^T Y + Y^T Q) / 2 + eps I,  eps = 1e-6 max_j C_jj (raised when
 //           the Cholesky of C fails);
 //   B       = Y R^-T with C = R R^T, so that B B^T = Y C^-1 Y^T ~ K, rounded to bf16 and
@@ -31,7 +32,8 @@
 //     order 2^-9 ||B||^2 / sqrt(l) of B B^T, small against tau) leaves the iteration counts
 //     unchanged (measured at n = 2M, ranks 1024 and 2048).
 // The l x l factorizations (Cholesky, triangular inverse, products) run in fp64 on the CUDA
-// cores in 32 x 32 blocks.  Panels are [n][ld] in the lattice's locality order, ld = l
+// cores in 32 x 32 blocks; the triangular inverse joins inverted diagonal blocks pairwise,
+// level by level, so its dependent chain is O(l / 32) tile products instead of O((l / 32)^2).  Panels are [n][ld] in the lattice's locality order, ld = l
 // rounded up to 128, padding columns zero.
 #include <algorithm>
 #include <atomic>
@@ -987,7 +989,8 @@ __global__ void k_potrf_diag(double* __restrict__ A, int lda, int kb, int nb,
 }
 
 // Panel below the diagonal block: rows i >= kb + nb, A[i][kb .. kb + nb) <- solve of
-// x L_kk^T = A[i][kb ..]; one thread per row.
+// x L_kk^T = A[i][kb ..]; one thread per row, one warp per block (an SM's fp64 pipe is
+// narrow: the rows are spread over as many SMs as possible).
 __global__ void k_trsm_panel(double* __restrict__ A, int lda, int l, int kb, int nb) {
   __shared__ double Lk[kNB][kNB + 1];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
@@ -1079,48 +1082,61 @@ __global__ void k_trtri_diag(const double* __restrict__ L, double* __restrict__ 
   }
 }
 
-// Block row I of X = L^-1: X[I][J] = -X[I][I] sum_{K = J}^{I - 1} L[I][K] X[K][J] for every
-// J < I (blockIdx.x = J); rows I of the blocks before it are final.
-__global__ void __launch_bounds__(256) k_trtri_row(const double* __restrict__ L,
-                                                    double* __restrict__ X, int lda, int l,
-                                                    int I) {
-  __shared__ double lt[kNB][kNB + 1], xt[kNB][kNB + 1], sacc[kNB][kNB + 1];
-  const int J = blockIdx.x;
-  const int ib = I * kNB, jb = J * kNB;
+// One level of the recursive triangular inverse.  With the inverses X11, X22 of two
+// consecutive diagonal blocks of size b, at [i0, i0 + b) and [i0 + b, i0 + b + b2),
+// b2 = min(b, l - i0 - b), the inverse of their union is
+//   inv([[L11, 0], [L21, L22]]) = [[X11, 0], [-X22 L21 X11, X22]],
+// computed in two launches per level:
+//   MODE 0: S21 = L21 X11   (X11 lower triangular: column tile c needs row tiles >= c)
+//   MODE 1: X21 = -X22 S21  (X22 lower triangular: row tile r needs column tiles <= r)
+// Every pair of the level at once; one 32 x 32 tile of the b2 x b result per block
+// (blockIdx.x = pair, row tile, column tile), 4 outputs per thread.  Reads beyond l are
+// zero.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_trtri_level(const double* __restrict__ L,
+                                                      double* __restrict__ X,
+                                                      double* __restrict__ S, int lda, int l,
+                                                      int b) {
+  __shared__ double at[kNB][kNB + 1], bt[kNB][kNB + 1];
+  const int tb = b / kNB;
+  const int pair = (int)(blockIdx.x / (unsigned)(tb * tb));
+  const int t = (int)(blockIdx.x % (unsigned)(tb * tb));
+  const int rt = t / tb, ct = t % tb;
+  const int i0 = pair * 2 * b;
+  const int r0 = i0 + b + rt * kNB;  // first row of the tile (in the second block)
+  const int c0 = i0 + ct * kNB;      // first column of the tile (in the first block)
+  if (i0 + b >= l || r0 >= l) return;  // uniform per block
+  const double* A = MODE == 0 ? L : X;
+  const double* Bm = MODE == 0 ? X : S;
+  const int k_base = MODE == 0 ? i0 : i0 + b;
+  const int kt0 = MODE == 0 ? ct : 0, kt1 = MODE == 0 ? tb - 1 : rt;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int K = J; K < I; ++K) {
-    const int kbk = K * kNB;
+  for (int kt = kt0; kt <= kt1; ++kt) {
+    const int kb = k_base + kt * kNB;
     for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
       const int r = e / kNB, c = e % kNB;
-      lt[r][c] = (ib + r < l) ? L[(size_t)(ib + r) * lda + kbk + c] : 0.0;
-      xt[r][c] = X[(size_t)(kbk + r) * lda + jb + c];
+      at[r][c] = (r0 + r < l && kb + c < l) ? A[(size_t)(r0 + r) * lda + kb + c] : 0.0;
+      bt[r][c] = (kb + r < l) ? Bm[(size_t)(kb + r) * lda + c0 + c] : 0.0;
     }
     __syncthreads();
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = threadIdx.x + 256 * q;
       const int r = e / kNB, c = e % kNB;
       double s = 0.0;
-      for (int t = 0; t < kNB; ++t) s += lt[r][t] * xt[t][c];
+#pragma unroll 8
+      for (int k = 0; k < kNB; ++k) s += at[r][k] * bt[k][c];
       acc[q] += s;
     }
     __syncthreads();
   }
-  for (int q = 0; q < 4; ++q) {
-    const int e = threadIdx.x + 256 * q;
-    sacc[e / kNB][e % kNB] = acc[q];
-  }
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int r = e / kNB, c = e % kNB;
-    lt[r][c] = (ib + r < l && ib + c < l) ? X[(size_t)(ib + r) * lda + ib + c] : 0.0;
-  }
-  __syncthreads();
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int e = threadIdx.x + 256 * q;
     const int r = e / kNB, c = e % kNB;
-    if (ib + r < l) {
-      double s = 0.0;
-      for (int t = 0; t < kNB; ++t) s += lt[r][t] * sacc[t][c];
-      X[(size_t)(ib + r) * lda + jb + c] = -s;
+    if (r0 + r < l) {
+      if (MODE == 0) S[(size_t)(r0 + r) * lda + c0 + c] = acc[q];
+      else X[(size_t)(r0 + r) * lda + c0 + c] = -acc[q];
     }
   }
 }
@@ -1263,6 +1279,7 @@ struct Dense {
   int l, lda;
   cudaStream_t st;
   int* status;  // device
+  double* S;    // l x l scratch of the triangular inverse
   // In-place lower Cholesky of A (already symmetrised); returns false on a failed pivot.
   bool chol(double* A, bool& ok_out, cudaError_t& err) {
     err = cudaMemsetAsync(status, 0, sizeof(int), st);
@@ -1273,7 +1290,7 @@ struct Dense {
       note_launches(1);
       const int rest = l - kb - nb;
       if (rest > 0) {
-        k_trsm_panel<<<(unsigned)ceil_div(rest, 128), 128, 0, st>>>(A, lda, l, kb, nb);
+        k_trsm_panel<<<(unsigned)ceil_div(rest, 32), 32, 0, st>>>(A, lda, l, kb, nb);
         const int64_t T = ceil_div(rest, kNB);
         k_syrk_trailing<<<(unsigned)(T * (T + 1) / 2), 256, 0, st>>>(A, lda, l, kb, nb);
         note_launches(2);
@@ -1285,16 +1302,20 @@ struct Dense {
     ok_out = hs == 0;
     return err == cudaSuccess;
   }
-  // X = L^-1 (lower), X zero above the diagonal.
+  // X = L^-1 (lower), X zero above the diagonal: the 32 x 32 diagonal blocks inverted,
+  // then pairs of inverted blocks joined level by level (b = 32, 64, ...); S: l x l scratch.
   cudaError_t trtri(const double* L, double* X) {
     cudaError_t e = cudaMemsetAsync(X, 0, (size_t)lda * lda * sizeof(double), st);
     if (e != cudaSuccess) return e;
     const int nblk = (l + kNB - 1) / kNB;
     k_trtri_diag<<<nblk, kNB, 0, st>>>(L, X, lda, l);
     note_launches(1);
-    for (int I = 1; I < nblk; ++I) {
-      k_trtri_row<<<I, 256, 0, st>>>(L, X, lda, l, I);
-      note_launches(1);
+    for (int b = kNB; b < l; b *= 2) {
+      const int tb = b / kNB;
+      const unsigned grid = (unsigned)(ceil_div(l - b, 2 * b) * tb * tb);
+      k_trtri_level<0><<<grid, 256, 0, st>>>(L, X, S, lda, l, b);
+      k_trtri_level<1><<<grid, 256, 0, st>>>(L, X, S, lda, l, b);
+      note_launches(2);
     }
     return cudaGetLastError();
   }
@@ -1384,8 +1405,8 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   const size_t panel3 = (size_t)3 * n * ld * sizeof(__nv_bfloat16);
   __nv_bfloat16 *P1 = nullptr, *P2 = nullptr, *T3 = nullptr;
   float *Vc = nullptr, *KVc = nullptr, *gpart = nullptr;
-  double *G = nullptr, *G0 = nullptr, *Xi = nullptr, *M = nullptr, *pv = nullptr, *py = nullptr,
-         *prq = nullptr;
+  double *G = nullptr, *G0 = nullptr, *Xi = nullptr, *M = nullptr, *Sx = nullptr, *pv = nullptr,
+         *py = nullptr, *prq = nullptr;
   int* status = nullptr;
   PC_CHECK(keep((void**)&B, (size_t)n * ld * sizeof(__nv_bfloat16)),
            "alloc preconditioner B");
@@ -1423,6 +1444,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   PC_CHECK(temp((void**)&G0, ll * sizeof(double)), "alloc l x l");
   PC_CHECK(temp((void**)&Xi, ll * sizeof(double)), "alloc l x l");
   PC_CHECK(temp((void**)&M, ll * sizeof(double)), "alloc l x l");
+  PC_CHECK(temp((void**)&Sx, ll * sizeof(double)), "alloc l x l");
   PC_CHECK(temp((void**)&pv, ld * sizeof(double)), "alloc power vectors");
   PC_CHECK(temp((void**)&py, ld * sizeof(double)), "alloc power vectors");
   PC_CHECK(temp((void**)&prq, sizeof(double)), "alloc power vectors");
@@ -1462,7 +1484,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   sgp_status s = ensure_lattice_values(L, kSketchCols, st);
   if (s != SGP_OK) return s;
 
-  Dense dn{l, ld, st, status};
+  Dense dn{l, ld, st, status, Sx};
   const unsigned g_plane = (unsigned)ceil_div((int64_t)n * ld / 8, 256);
   const unsigned g_chunk = (unsigned)ceil_div((int64_t)n * kSketchCols / 8, 256);
   // dst = outputscale K src, column chunk by chunk (3-plane panels; padding columns of dst:
@@ -1517,10 +1539,14 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     return SGP_OK;
   };
   // Cholesky of the symmetrised out-of-place copy of src with a relative diagonal shift,
-  // raised 100-fold (at most 4 times) while a pivot fails; the factor lands in dst.
+  // raised 100-fold (at most 4 times) while a pivot fails; the factor lands in dst, and
+  // `raised` tells whether the first shift failed.
+  bool raised = false;
   auto robust_chol = [&](const double* src, double* dst, double rel, bool& good) -> sgp_status {
     good = false;
+    raised = false;
     for (int attempt = 0; attempt < 4 && !good; ++attempt, rel *= 100.0) {
+      raised = attempt > 0;
       k_prepare_spd<<<(unsigned)ceil_div((int64_t)ll, 256), 256, 0, st>>>(src, dst, l, ld, 0.0,
                                                                           rel);
       note_launches(1);
@@ -1530,7 +1556,10 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     return SGP_OK;
   };
 
-  // 1. Q: the sketch, or an orthonormal basis of K Omega (Cholesky QR twice)
+  // 1. Q: the sketch, or a basis of the range of K Omega by Cholesky QR.  The Nystrom
+  // approximation depends only on that range, so one pass suffices while the Gram's first
+  // Cholesky succeeds; a second pass restores the orthogonality when its shift had to be
+  // raised.
   k_fill_sketch3<<<g_plane, 256, 0, st>>>(L->perm, n, l, ld, seed, P1);
   note_launches(1);
   __nv_bfloat16* Q = P1;
@@ -1547,8 +1576,9 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
       PC_CHECK(dn.trtri(G, Xi), "triangular inverse");
       if ((s = panel_times(src, Xi, dst, false)) != SGP_OK) return s;  // dst = src R^-T
       std::swap(src, dst);
+      if (!raised) break;
     }
-    Q = src;  // orthonormal basis (P2 after two passes)
+    Q = src;  // the basis (P1 after one pass, P2 after two)
     Y = dst;
     if ((s = product(Q, Y)) != SGP_OK) return s;
   }

@@ -1,7 +1,7 @@
 """GPU preconditioned CG (shifted rank-l Nystrom preconditioner, App. A) against the oracle.
 
 The sketch is the same counter-based Rademacher matrix on both sides and the subspace
-iteration reaches the same subspace (the GPU orthonormalises by Cholesky QR, the oracle
+iteration reaches the same subspace (the GPU takes its basis by Cholesky QR, the oracle
 by Householder QR; the approximation depends only on the subspace).  The GPU forms the
 factor from three-part bf16 panels with tensor-core (tcgen05) products, stores it rounded
 to bf16, and estimates the smallest captured eigenvalue by inverse power iteration; the
