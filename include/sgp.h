@@ -223,7 +223,8 @@ sgp_status sgp_cg_solve(sgp_lattice* h, const float* B, int k, float noise_var, 
  *          i l + j + 1 from precond_seed (i the caller's point index);
  *   Q      Omega (precond_power_iters = 0) or a basis of the range of K Omega (1), by
  *          Cholesky QR (a second pass only when the first needed a raised shift: the
- *          approximation depends only on the range);
+ *          approximation depends only on the range, so K Omega is formed with bf16
+ *          lattice values and fp32 sums);
  *   Y      = K Q,  C = (Q^T Y + Y^T Q)/2 + eps I (eps = 1e-6 max_j C_jj, raised when its
  *          Cholesky fails) = R R^T,  B = Y R^-T;
  *   tau    = lambda_min(B^T B) (inverse power iteration) + noise_var.

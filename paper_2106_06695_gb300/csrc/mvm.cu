@@ -724,6 +724,12 @@ int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, 
                           L->partial, L->vperm, st, ev, internal, dot_partial);
 }
 
+void enqueue_mvm_bf16_values(const Lattice* L, const float* V, int k, int blur, float alpha,
+                             float* out, cudaStream_t st) {
+  enqueue_t<bf16>(L, V, k, blur, alpha, 0.f, out, (bf16*)L->lat[0], (bf16*)L->lat[1], L->partial,
+                  L->vperm, st, nullptr, /*internal=*/true);
+}
+
 int64_t slice_dot_blocks(const Lattice* L, int k) {
   const int vec = k % 4 == 0 ? 4 : 1;
   const int G = k / vec;

@@ -6,7 +6,8 @@
 //           i l + j + 1 from the seed (i = the caller's point index);
 //   Q       Omega, or after q = 1 subspace iteration a basis of the range of K Omega
 //           (Cholesky QR; the approximation depends only on the subspace, so a second
-//           pass runs only when the first Gram's Cholesky needed a raised shift);
+//           pass runs only when the first Gram's Cholesky needed a raised shift, and the
+//           product K Omega runs on bf16 lattice values);
 //   Y       = K Q;   C = (Q^T Y + Y^T Q) / 2 + eps I,  eps = 1e-6 max_j C_jj (raised when
 //           the Cholesky of C fails);
 //   B       = Y R^-T with C = R R^T, so that B B^T = Y C^-1 Y^T ~ K, rounded to bf16 and
@@ -952,37 +953,39 @@ __global__ void __launch_bounds__(256) k_prepare_spd(const double* __restrict__ 
   dst[e] = i > j ? 0.5 * (src[e] + src[(size_t)j * lda + i]) : (i == j ? src[e] + sh : 0.0);
 }
 
-// Cholesky of the diagonal block [kb, kb + nb): unblocked, in shared memory; *status = 1
-// when a pivot is not positive (the pivot is then taken as 1 so that nothing overflows).
-__global__ void k_potrf_diag(double* __restrict__ A, int lda, int kb, int nb,
-                             int* __restrict__ status) {
+// Cholesky of the diagonal block [kb, kb + nb): unblocked, in shared memory, one warp (a
+// lane per row below the pivot); *status = 1 when a pivot is not positive (the pivot is
+// then taken as 1 so that nothing overflows).  Every lane computes the pivot and its
+// reciprocal itself, so a column step costs one square root and one division in sequence.
+__global__ void __launch_bounds__(32) k_potrf_diag(double* __restrict__ A, int lda, int kb,
+                                                   int nb, int* __restrict__ status) {
   __shared__ double a[kNB][kNB + 1];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e % nb;
-    a[i][j] = j <= i ? A[(size_t)(kb + i) * lda + kb + j] : 0.0;
+  const int t = threadIdx.x;
+  for (int e = t; e < kNB * kNB; e += 32) {
+    const int i = e / kNB, j = e % kNB;
+    a[i][j] = (i < nb && j <= i) ? A[(size_t)(kb + i) * lda + kb + j] : 0.0;
   }
-  __syncthreads();
+  __syncwarp();
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = a[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        *status = 1;
-        a[j][j] = 1.0;
-      } else {
-        a[j][j] = sqrt(d);
-      }
+    double d = a[j][j];
+    const bool bad = !(d > 0.0) || !isfinite(d);
+    const double piv = bad ? 1.0 : sqrt(d);
+    const double rinv = 1.0 / piv;
+    __syncwarp();  // every lane has read a[j][j]
+    if (t == 0) {
+      if (bad) *status = 1;
+      a[j][j] = piv;
     }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= a[j][j];
-    __syncthreads();
-    const int rem = nb - j - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int i = j + 1 + e / rem, c = j + 1 + e % rem;
-      if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+    const int i = j + 1 + t;
+    if (i < nb) a[i][j] *= rinv;
+    __syncwarp();
+    if (i < nb) {
+      const double lij = a[i][j];
+      for (int c = j + 1; c <= i; ++c) a[i][c] -= lij * a[c][j];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+  for (int e = t; e < nb * nb; e += 32) {
     const int i = e / nb, j = e % nb;
     if (j <= i) A[(size_t)(kb + i) * lda + kb + j] = a[i][j];
   }
@@ -990,14 +993,20 @@ __global__ void k_potrf_diag(double* __restrict__ A, int lda, int kb, int nb,
 
 // Panel below the diagonal block: rows i >= kb + nb, A[i][kb .. kb + nb) <- solve of
 // x L_kk^T = A[i][kb ..]; one thread per row, one warp per block (an SM's fp64 pipe is
-// narrow: the rows are spread over as many SMs as possible).
-__global__ void k_trsm_panel(double* __restrict__ A, int lda, int l, int kb, int nb) {
+// narrow: the rows are spread over as many SMs as possible).  Column c is final once the
+// updates of columns t < c have reached it (in increasing t, as a row-by-row substitution
+// orders them); it then updates the columns after it, which are independent of each other.
+__global__ void __launch_bounds__(32) k_trsm_panel(double* __restrict__ A, int lda, int l,
+                                                   int kb, int nb) {
   __shared__ double Lk[kNB][kNB + 1];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, j = e % nb;
-    Lk[i][j] = j <= i ? A[(size_t)(kb + i) * lda + kb + j] : 0.0;
+  __shared__ double rd[kNB];
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int i = e / kNB, j = e % kNB;
+    Lk[i][j] = (i < nb && j <= i) ? A[(size_t)(kb + i) * lda + kb + j] : 0.0;
   }
-  __syncthreads();
+  __syncwarp();
+  if ((int)threadIdx.x < nb) rd[threadIdx.x] = 1.0 / Lk[threadIdx.x][threadIdx.x];
+  __syncwarp();
   const int i = kb + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= l) return;
   double x[kNB];
@@ -1007,11 +1016,9 @@ __global__ void k_trsm_panel(double* __restrict__ A, int lda, int l, int kb, int
 #pragma unroll
   for (int c = 0; c < kNB; ++c) {
     if (c < nb) {
-      double s = x[c];
+      x[c] *= rd[c];
 #pragma unroll
-      for (int t = 0; t < kNB; ++t)
-        if (t < c) s -= x[t] * Lk[c][t];
-      x[c] = s / Lk[c][c];
+      for (int q = c + 1; q < kNB; ++q) x[q] -= x[c] * Lk[q][c];
     }
   }
 #pragma unroll
@@ -1286,7 +1293,7 @@ struct Dense {
     if (err != cudaSuccess) return false;
     for (int kb = 0; kb < l; kb += kNB) {
       const int nb = std::min(kNB, l - kb);
-      k_potrf_diag<<<1, 256, 0, st>>>(A, lda, kb, nb, status);
+      k_potrf_diag<<<1, 32, 0, st>>>(A, lda, kb, nb, status);
       note_launches(1);
       const int rest = l - kb - nb;
       if (rest > 0) {
@@ -1488,12 +1495,16 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   const unsigned g_plane = (unsigned)ceil_div((int64_t)n * ld / 8, 256);
   const unsigned g_chunk = (unsigned)ceil_div((int64_t)n * kSketchCols / 8, 256);
   // dst = outputscale K src, column chunk by chunk (3-plane panels; padding columns of dst:
-  // zero)
-  auto product = [&](__nv_bfloat16* src, __nv_bfloat16* dst) -> sgp_status {
+  // zero).  bf16_values: lattice values held in bf16 (the subspace product, whose result
+  // only fixes the subspace)
+  auto product = [&](__nv_bfloat16* src, __nv_bfloat16* dst, bool bf16_values) -> sgp_status {
     for (int c0 = 0; c0 < ld; c0 += kSketchCols) {
       k_cols3<<<g_chunk, 256, 0, st>>>(src, ld, c0, Vc, kSketchCols, n, false);
-      enqueue_mvm(L, Vc, kSketchCols, blur, L->outputscale, 0.f, KVc, st, nullptr,
-                  /*internal=*/true);
+      if (bf16_values)
+        enqueue_mvm_bf16_values(L, Vc, kSketchCols, blur, L->outputscale, KVc, st);
+      else
+        enqueue_mvm(L, Vc, kSketchCols, blur, L->outputscale, 0.f, KVc, st, nullptr,
+                    /*internal=*/true);
       k_cols3<<<g_chunk, 256, 0, st>>>(dst, ld, c0, KVc, kSketchCols, n, true);
       note_launches(2);
     }
@@ -1564,7 +1575,10 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
   note_launches(1);
   __nv_bfloat16* Q = P1;
   __nv_bfloat16* Y = P2;
-  if ((s = product(P1, P2)) != SGP_OK) return s;  // P2 = K Omega
+  // P2 = K Omega.  With the subspace iteration this product only fixes the subspace (Q's
+  // range): it runs on bf16 lattice values, whose ~2.5e-3 relative error perturbs the
+  // captured directions negligibly, while Y = K Q below, which defines B, stays fp32.
+  if ((s = product(P1, P2, power_iters > 0)) != SGP_OK) return s;
   if (power_iters > 0) {
     __nv_bfloat16* src = P2;
     __nv_bfloat16* dst = P1;
@@ -1580,7 +1594,7 @@ sgp_status ShiftedNystrom::build(Lattice* L, int rank, uint64_t seed, float nois
     }
     Q = src;  // the basis (P1 after one pass, P2 after two)
     Y = dst;
-    if ((s = product(Q, Y)) != SGP_OK) return s;
+    if ((s = product(Q, Y, false)) != SGP_OK) return s;
   }
   // 2. C = Q^T Y, C = R R^T, B = Y R^-T rounded to bf16 (the stored values define P)
   {

@@ -174,6 +174,12 @@ sgp_status ensure_lattice_values(Lattice* L, int k, cudaStream_t st);
 int enqueue_mvm(const Lattice* L, const float* V, int k, int blur, float alpha, float beta,
                 float* out, cudaStream_t st, cudaEvent_t* ev = nullptr, bool internal = false,
                 double* dot_partial = nullptr);
+// out = alpha K V (V and out in locality order) with the lattice values held in bf16 whatever
+// the lattice's value type, in the lattice's own value buffers, which
+// ensure_lattice_values(L, k) must have sized (a bf16 value takes half the room of an fp32
+// one); every sum stays fp32.
+void enqueue_mvm_bf16_values(const Lattice* L, const float* V, int k, int blur, float alpha,
+                             float* out, cudaStream_t st);
 // With internal = true and dot_partial set, the slice also writes per-block column sums of
 // V * out (the CG's <p, A p>) to dot_partial[block][k]; this many blocks (grid-stride).
 int64_t slice_dot_blocks(const Lattice* L, int k);
