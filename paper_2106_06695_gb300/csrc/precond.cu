@@ -953,39 +953,40 @@ __global__ void __launch_bounds__(256) k_prepare_spd(const double* __restrict__ 
   dst[e] = i > j ? 0.5 * (src[e] + src[(size_t)j * lda + i]) : (i == j ? src[e] + sh : 0.0);
 }
 
-// Cholesky of the diagonal block [kb, kb + nb): unblocked, in shared memory, one warp (a
-// lane per row below the pivot); *status = 1 when a pivot is not positive (the pivot is
-// then taken as 1 so that nothing overflows).  Every lane computes the pivot and its
-// reciprocal itself, so a column step costs one square root and one division in sequence.
-__global__ void __launch_bounds__(32) k_potrf_diag(double* __restrict__ A, int lda, int kb,
-                                                   int nb, int* __restrict__ status) {
+// Cholesky of the diagonal block [kb, kb + nb): unblocked, in shared memory; *status = 1
+// when a pivot is not positive (the pivot is then taken as 1 so that nothing overflows).
+// Per column j: thread 0 takes the pivot and its reciprocal, one warp scales the column,
+// then the 32 x 8 threads update the trailing lower triangle (thread (c, t) owns column
+// c, rows c + t, c + t + 8, ...).
+__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int lda, int kb,
+                                                    int nb, int* __restrict__ status) {
   __shared__ double a[kNB][kNB + 1];
-  const int t = threadIdx.x;
-  for (int e = t; e < kNB * kNB; e += 32) {
+  __shared__ double rinv;
+  const int tx = (int)threadIdx.x % kNB, ty = (int)threadIdx.x / kNB;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
     const int i = e / kNB, j = e % kNB;
     a[i][j] = (i < nb && j <= i) ? A[(size_t)(kb + i) * lda + kb + j] : 0.0;
   }
-  __syncwarp();
+  __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    double d = a[j][j];
-    const bool bad = !(d > 0.0) || !isfinite(d);
-    const double piv = bad ? 1.0 : sqrt(d);
-    const double rinv = 1.0 / piv;
-    __syncwarp();  // every lane has read a[j][j]
-    if (t == 0) {
-      if (bad) *status = 1;
+    if (threadIdx.x == 0) {
+      const double d = a[j][j];
+      double piv = 1.0;
+      if (!(d > 0.0) || !isfinite(d)) *status = 1;
+      else piv = sqrt(d);
       a[j][j] = piv;
+      rinv = 1.0 / piv;
     }
-    const int i = j + 1 + t;
-    if (i < nb) a[i][j] *= rinv;
-    __syncwarp();
-    if (i < nb) {
-      const double lij = a[i][j];
-      for (int c = j + 1; c <= i; ++c) a[i][c] -= lij * a[c][j];
+    __syncthreads();
+    if (ty == 0 && j + 1 + tx < nb) a[j + 1 + tx][j] *= rinv;
+    __syncthreads();
+    if (tx > j && tx < nb) {
+      const double lcj = a[tx][j];
+      for (int i = tx + ty; i < nb; i += 8) a[i][tx] -= a[i][j] * lcj;
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int e = t; e < nb * nb; e += 32) {
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e % nb;
     if (j <= i) A[(size_t)(kb + i) * lda + kb + j] = a[i][j];
   }
@@ -1293,7 +1294,7 @@ struct Dense {
     if (err != cudaSuccess) return false;
     for (int kb = 0; kb < l; kb += kNB) {
       const int nb = std::min(kNB, l - kb);
-      k_potrf_diag<<<1, 32, 0, st>>>(A, lda, kb, nb, status);
+      k_potrf_diag<<<1, 256, 0, st>>>(A, lda, kb, nb, status);
       note_launches(1);
       const int rest = l - kb - nb;
       if (rest > 0) {
