@@ -89,6 +89,10 @@ def parse_args(argv=None):
     ap.add_argument("--serve-single", action="store_true",
                     help="profiling aid: serve two ill-conditioned requests (d = 3, n = 240k "
                          "and d = 8, n = 100k) one at a time and print their statistics")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="time the FP64 oracle on the whole workload (build + one symmetric "
+                         "MVM at n = 2M, all host cores and one thread; about 1.5 min of CPU "
+                         "work) and print one JSON line; no GPU work")
     return ap.parse_args(argv)
 
 
@@ -849,6 +853,37 @@ def cpu_baseline(W):
                               "sample": "%s, 1 thread; %.1f s" % (what(CPU_SAMPLE_1T), secs1)}}
 
 
+def run_oracle_full(args):
+    """The FP64 oracle on the whole workload: the lattice build (sequential vertex
+    insertion) and one symmetric-operator MVM with k columns, once with every host core and
+    once with one thread (results are bit-identical for any thread count).  Mpoint/s is
+    n / MVM seconds, the unit of the metric."""
+    import oracle
+    from oracle import OracleLattice
+    from paper_2106_06695_gb300 import synth
+
+    W = dict(WORKLOAD, n=args.n)
+    X = synth.gmm_points(W["n"], W["d"], W["seed"])
+    V = synth.gaussian_values(W["n"], W["k"], W["seed"]).astype(np.float64)
+    ls = np.full(W["d"], W["lengthscale"], np.float32)
+    modes = []
+    for threads in (oracle.max_threads(), 1):
+        used = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        L = OracleLattice(X, ls, r=W["order"])
+        build_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        L.mvm(V, mode=2)
+        mvm_s = time.perf_counter() - t0
+        modes.append({"threads": used, "build_s": build_s, "mvm_s": mvm_s,
+                      "mvm_mpoint_s": W["n"] / mvm_s / 1e6, "m": int(L.m)})
+        del L
+    oracle.set_threads(1)
+    print(json.dumps({"oracle_full": {"workload": "n=%d d=%d k=%d, symmetric operator"
+                                                  % (W["n"], W["d"], W["k"]),
+                                      "modes": modes}}), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -909,6 +944,10 @@ def main(argv=None):
     world, rank, local = dist_env()
     if args.serve_single:
         run_serve_single()
+        return
+    if args.oracle_full:
+        if rank == 0:
+            run_oracle_full(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
