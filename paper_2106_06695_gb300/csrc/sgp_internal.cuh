@@ -61,7 +61,7 @@ struct sgp_lattice {
   int precond_rank = 0;
   int precond_power_iters = 1;
   uint64_t precond_seed = 0;
-  int fault = 0;  // sgp::FAULT_* injected by SGP_FAULT for this build
+  int fault = 0;  // sgp::FAULT_* injected by SGP_FAULT into this lattice's construction
   int device = -1;  // CUDA device current at build time (the arrays live there)
   cudaStream_t stream = nullptr;
 
