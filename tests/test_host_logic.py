@@ -88,3 +88,17 @@ def test_bench_replica_aggregation_two_ranks():
             assert p.exitcode == 0
         for r in range(2):
             assert results[r] == (150.0, 3000.0)
+
+
+def test_mvm_bytes_matches_a_case_worked_by_hand():
+    """The roofline's algorithmic bytes per MVM (16 n D ids and weights, 8 n k for V and
+    out, 8 m k for the splatted and sliced rows, m (8 r + 8 k) per blur pass, 4 (m + 1)
+    offsets), checked against n = 2M, D = 12, k = 16, r = 1, m = 1e6 worked by hand with
+    one pass per direction: 0.384 + 0.256 + 0.128 + 1.632 GB + 4 MB."""
+    import bench
+
+    got = bench.mvm_bytes(2_000_000, 12, 16, 1_000_000, 1, 12)
+    assert got == 384_000_000 + 256_000_000 + 128_000_000 + 1_632_000_000 + 4_000_004
+    # the symmetric operator runs twice the passes; only the blur term doubles
+    sym = bench.mvm_bytes(2_000_000, 12, 16, 1_000_000, 1, 24)
+    assert sym - got == 1_632_000_000
