@@ -417,7 +417,7 @@ def run_ours(args, world, rank, local):
         "splat": 8 * n * D + 4 * n * k + 4 * m * k,
         "slice_dot": 8 * n * D + 4 * m * k + 8 * n * k,
         "precond_bt": 2 * n * ld + 128 * n,   # bf16 B once, the split r ([n][64] bf16) once
-        "precond_z": 2 * n * ld + 12 * n * min(k, 16),   # bf16 B once, r read, z written
+        "precond_z": 2 * n * ld + 8 * n * min(k, 16),   # bf16 B once, r (fp32) read, z written
     }
     stage_ms = {  # average duration of one launch
         "blur_pass": prof["ms"] / max(prof["passes"], 1),

@@ -394,11 +394,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // tiles, in tile order, into dot[blockIdx.x][c_off + c].  Persistent: block b takes tiles b, b + gridDim.x, ..., with two
 // accumulators in tensor memory so that the MMAs of one tile overlap the epilogue of the
 // previous.  A = B is K-major (boxes 128 rows x 64 columns); u3 ([48][ld], the three parts
-// of u = Minv B^T r) is K-major (boxes 48 x 64).
+// of u = Minv B^T r) is K-major (boxes 48 x 64).  r enters rounded to fp32, which is the
+// high word rh of the CG's double-float residual: the CG keeps its pairs normalised (each
+// update ends in a FastTwoSum, so fl(hi + lo) = hi), and the low words are not read.
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_z_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapU,
-           const float* __restrict__ rh, const float* __restrict__ rl, int k, int c_off, int kc,
-           int64_t n, int ld, float inv_tau, float* __restrict__ z, double* __restrict__ dot,
+           const float* __restrict__ rh, int k, int c_off, int kc, int64_t n, int ld,
+           float inv_tau, float* __restrict__ z, double* __restrict__ dot,
            int* __restrict__ err) {
   extern __shared__ uint8_t tc_raw[];
   __shared__ double red[2][4][16];
@@ -512,16 +514,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int c4 = 0; c4 < 4; ++c4)
             if (4 * c4 < kc) {
               const float4 h = *reinterpret_cast<const float4*>(rh + e0 + 4 * c4);
-              const float4 l = *reinterpret_cast<const float4*>(rl + e0 + 4 * c4);
-              rv[4 * c4] = __fadd_rn(h.x, l.x);
-              rv[4 * c4 + 1] = __fadd_rn(h.y, l.y);
-              rv[4 * c4 + 2] = __fadd_rn(h.z, l.z);
-              rv[4 * c4 + 3] = __fadd_rn(h.w, l.w);
+              rv[4 * c4] = h.x;
+              rv[4 * c4 + 1] = h.y;
+              rv[4 * c4 + 2] = h.z;
+              rv[4 * c4 + 3] = h.w;
             }
         } else {
 #pragma unroll
           for (int c = 0; c < 16; ++c)
-            if (c < kc) rv[c] = __fadd_rn(rh[e0 + c], rl[e0 + c]);
+            if (c < kc) rv[c] = rh[e0 + c];
         }
         float zz[16];
 #pragma unroll
@@ -1675,7 +1676,7 @@ void ShiftedNystrom::apply(const float* rh, const float* rl, int k, float* z, do
     k_minv_u<<<(unsigned)ceil_div(ld, 8), 256, 0, st>>>(Minv, ld, tvec,
                                                          static_cast<__nv_bfloat16*>(u));
     if (mark) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    k_z_tc<<<z_blocks, kTcThreads, ApplyRing::kSmem, st>>>(map_b_k, map_u, rh, rl, k, c_off, kc, n, ld,
+    k_z_tc<<<z_blocks, kTcThreads, ApplyRing::kSmem, st>>>(map_b_k, map_u, rh, k, c_off, kc, n, ld,
                                                   1.f / tau, z, dot, err);
     if (mark) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     note_launches(4);
